@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Benchmark: GPop/s of the two-dimensional-stack GP interpreter on GB300.
+
+Workload (default): symbolic regression, 4096 ramped half-and-half trees
+(depth 2-8, <= 256 nodes, functions {+,-,*,protected /}, terminals x and
+constants U[-1,1]), 65536 binary32 fitness cases x ~ U[-1,1], target
+x^4+x^3+x^2+x, fitness = sum |error|.  Synthetic, seeded.
+
+A step is one fitness evaluation of the whole population (encoded programs,
+cases and targets resident in HBM).  GPop = tree nodes x fitness cases
+(Chitty, Sec. 3).  `value` is the 2D-stack interpreter at its tuned K;
+`stack1d` reports the one-case-per-thread interpreter of the same design and
+the BlockGP-style local-memory interpreter on the same inputs; `e2e` measures
+the public API from host buffers (host encoding of the user token format,
+host->device copy of the encoded population, evaluation, device->host copy of
+the fitness vector) per step.
+
+`--impl reference` times the CPU oracle (plain C, test infrastructure) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GPop/s on 1 GB300, 2D-stack vs 1D-stack kernel; serving p50/p99 latency"
+UNIT = "GPop/s"
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--programs", type=int, default=4096)
+    ap.add_argument("--cases", type=int, default=65536)
+    ap.add_argument("--no-compare", action="store_true", help="skip the 1D-stack comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--k", type=int, default=0, help="force K (0 = tune)")
+    ap.add_argument("--block", type=int, default=0, help="force the block size (0 = tune)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power) if power else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1601_00221_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.startswith(("eval_float", "common", "isa")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(f"{kernel}|{workload}")
+    if not e or e.get("source_digest") != kernel_source_digest():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def l2_flusher(torch, device):
+    buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=device)
+
+    def flush():
+        buf.fill_(1)
+    return flush
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1601_00221_gb300 as gp
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(device)
+    n_sm = props.multi_processor_count
+    gp.lib()
+
+    # --- workload: each rank evaluates its own population (weak scaling) ---
+    w = synth.regression_large(seed=2 + 1000 * rank, n_progs=args.programs, n_cases=args.cases)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM,
+                               gp.ORDER_MIN_DEPTH)
+    P, O, L = enc.to_device(device)
+    X = torch.from_numpy(w.cases).to(device)
+    Y = torch.from_numpy(w.targets).to(device)
+    fit = torch.empty(w.pop.n, dtype=torch.float64, device=device)
+    nodes = int(w.pop.nodes.sum())
+    n_cases = int(w.cases.shape[1])
+    gpop_step = nodes * n_cases
+    # function nodes: each is one binary32 operation per case (terminals are
+    # operands, not operations)
+    funcs = int(((w.pop.nodes - 1) // 2).sum())  # binary trees: (nodes - 1) / 2 functions
+    flops_step = funcs * n_cases
+    stream = torch.cuda.current_stream(device)
+    flush = l2_flusher(torch, device)
+
+    def timed(cfg, steps, warmup, flush_l2=True):
+        for _ in range(warmup):
+            gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg)
+        torch.cuda.synchronize(device)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for s, e in evs:
+            if flush_l2:
+                flush()
+            s.record(stream)
+            gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg)
+            e.record(stream)
+        torch.cuda.synchronize(device)
+        return [s.elapsed_time(e) for s, e in evs]
+
+    # --- tune K and block for the 2D stack (short sweep) ---
+    cands = []
+    ks = [args.k] if args.k else [2, 4, 8]
+    blocks = [args.block] if args.block else [64, 128, 256]
+    for k in ks:
+        for b in blocks:
+            cfg = gp.Config(gp.VARIANT_REGISTER, k, b, 0)
+            t = statistics.median(timed(cfg, 3, 1, flush_l2=False))
+            cands.append((t, k, b))
+    cands.sort()
+    _, best_k, best_b = cands[0]
+    cfg = gp.Config(gp.VARIANT_REGISTER, best_k, best_b, 0)
+
+    # --- timed region ---
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(device)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    times = timed(cfg, args.steps, args.warmup)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    torch.cuda.synchronize(device)
+    if world > 1:
+        dist.barrier()
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = gpop_step * world * args.steps / (total_ms / 1e3) / 1e9
+
+    # --- roofline of the interpreter kernel ---
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tops = n_sm * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    achieved = flops_step / (statistics.mean(times) / 1e3) / 1e12
+    kernel_name = f"eval_float_kernel<{best_k},true>"
+    workload = f"regression-{w.pop.n}x{n_cases}"
+    traffic = measured_traffic(kernel_name, workload)
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tops, 3),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tops, 4), "traffic": traffic,
+                "kernel": kernel_name,
+                "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
+                              "(MEASURED_PEAKS sm_max_mhz); one binary32 op per function node per case",
+                "gpop_per_lane_op": round(value / world / (peak_tops * 1e3), 4)}
+
+    # --- 1D-stack comparison on the same inputs ---
+    compare = None
+    if not args.no_compare:
+        compare = {}
+        for name, c in (("stack1d_register_k1", gp.Config(gp.VARIANT_REGISTER, 1, 128, 0)),
+                        ("blockgp_local_memory", gp.Config(gp.VARIANT_LOCAL, 1, 256, 0))):
+            if name.startswith("blockgp"):
+                encr = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths,
+                                            gp.KIND_RPN, gp.ORDER_PAPER)
+                Pr, Or, Lr = encr.to_device(device)
+                saved = (P, O, L)
+                P, O, L = Pr, Or, Lr
+            tt = timed(c, max(3, args.steps // 4), 2)
+            if name.startswith("blockgp"):
+                P, O, L = saved
+            compare[name] = round(gpop_step / (statistics.mean(tt) / 1e3) / 1e9, 2)
+        # RPN 2D at the same K and block
+        encr = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_RPN,
+                                    gp.ORDER_MIN_DEPTH)
+        saved = (P, O, L)
+        P, O, L = encr.to_device(device)
+        tt = timed(cfg, max(3, args.steps // 4), 2)
+        compare[f"stack2d_rpn_k{best_k}"] = round(gpop_step / (statistics.mean(tt) / 1e3) / 1e9, 2)
+        P, O, L = saved
+        compare["stack2d_sform_sweep"] = {f"k{k}_b{b}": round(gpop_step / (t / 1e3) / 1e9, 1)
+                                          for t, k, b in cands}
+        compare["speedup_2d_over_1d"] = round(value / world / compare["stack1d_register_k1"], 3)
+        compare["speedup_2d_over_blockgp"] = round(value / world / compare["blockgp_local_memory"], 3)
+
+    # --- end to end through the public API from host buffers ---
+    e2e = None
+    if True:
+        host_fit = torch.empty(w.pop.n, dtype=torch.float64).pin_memory()
+        e2e_times = []
+        h2d = d2h = 0
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize(device)
+            t1 = time.perf_counter()
+            e = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM,
+                                     gp.ORDER_MIN_DEPTH)
+            hw = torch.from_numpy(e.words.view(np.int32)).pin_memory()
+            ho = torch.from_numpy(e.offsets).pin_memory()
+            hl = torch.from_numpy(e.lengths).pin_memory()
+            dP = hw.to(device, non_blocking=True)
+            dO = ho.to(device, non_blocking=True)
+            dL = hl.to(device, non_blocking=True)
+            gp.eval_population(dP, dO, dL, X, Y, fitness_out=fit, config=cfg)
+            host_fit.copy_(fit, non_blocking=True)
+            torch.cuda.synchronize(device)
+            t2 = time.perf_counter()
+            if i >= args.warmup:
+                e2e_times.append(t2 - t1)
+            h2d = hw.numel() * 4 + ho.numel() * 8 + hl.numel() * 4
+            d2h = host_fit.numel() * 8
+        e2e_s = sum(e2e_times)
+        if world > 1:
+            t = torch.tensor([e2e_s], device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": round(gpop_step * world * args.steps / e2e_s / 1e9, 2), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(e2e_s / args.steps * 1e3, 4),
+               "includes": "host encoding of the user token format, pinned H2D copy, evaluation, D2H of fitness"}
+
+    # --- fitness error against the binary64 oracle on a sample (stated per result) ---
+    cpu_baseline = None
+    err_stats = None
+    if rank == 0 and not args.no_cpu:
+        cpu_baseline, err_stats = cpu_oracle_baseline(w, fit.cpu().numpy(), n_cases)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ramped half-and-half trees, x~U[-1,1], quartic target)",
+        "config": {"workload": f"symbolic regression, {w.pop.n} trees (depth 2-8, <=256 nodes, "
+                               f"{{+,-,*,pdiv}}) x {n_cases} fp32 cases",
+                   "programs": w.pop.n, "cases": n_cases, "tree_nodes": nodes,
+                   "function_nodes": funcs, "kind": "sform", "order": "min_depth",
+                   "k": best_k, "block": best_b, "variant": "register 2D stack",
+                   "l2": "flushed between timed steps (512 MiB write outside the CUDA-event pair)",
+                   "parallelism": f"population sharded over {world} GPU(s), no collective"},
+        "roofline": roofline,
+        "cpu_baseline": cpu_baseline,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "stack1d": compare,
+        "fitness_rel_err_vs_fp64_oracle": err_stats,
+        "wall_s_timed_region": round(wall, 3),
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_oracle_baseline(w, gpu_fit, n_cases, budget_s: float = 12.0):
+    """Times the plain C oracle on a bounded program sample over all cases,
+    threads over programs on every core in the affinity mask."""
+    import numpy as np
+    import oracle
+
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(0)
+    order = rng.permutation(w.pop.n)
+    # calibrate: one program's cost
+    t0 = time.perf_counter()
+    oracle.population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, w.cases, w.targets,
+                              p_range=(int(order[0]), int(order[0]) + 1))
+    one = max(time.perf_counter() - t0, 1e-4)
+    n_sample = int(min(w.pop.n, max(cores, budget_s * cores / one / 1.0)))
+    n_sample = max(cores, min(n_sample, w.pop.n))
+    sample = np.sort(order[:n_sample])
+    res = {}
+
+    def job(p):
+        f = oracle.population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, w.cases,
+                                      w.targets, p_range=(int(p), int(p) + 1))
+        return int(p), f[int(p)]
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        for p, f in ex.map(job, sample):
+            res[p] = f
+    wall = time.perf_counter() - t0
+    gpop = int(w.pop.nodes[sample].sum()) * n_cases
+    ps = np.array(sorted(res))
+    exp = np.array([res[p] for p in ps])
+    got = gpu_fit[ps]
+    m = np.isfinite(exp) & (exp != 0)
+    rel = np.abs(got[m] - exp[m]) / np.abs(exp[m])
+    exact_ok = bool(np.all((got[~m] == exp[~m]) | (np.isnan(got[~m]) & np.isnan(exp[~m]))))
+    err = {"programs_checked": int(ps.size), "max": float(rel.max()) if rel.size else 0.0,
+           "median": float(np.median(rel)) if rel.size else 0.0, "bound": 1e-5,
+           "zero_or_inf_exact": exact_ok}
+    return ({"value": round(gpop / wall / 1e9, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"{ps.size} of {w.pop.n} programs x all {n_cases} cases "
+                       f"({wall:.1f} s wall, threads over programs)"}, err)
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    """The CPU oracle as the reference arm, on the host cores."""
+    import numpy as np
+    import oracle
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    oracle.build()
+    w = synth.regression_large(seed=2, n_progs=args.programs, n_cases=args.cases)
+    cores = len(os.sched_getaffinity(0))
+    n_cases = int(w.cases.shape[1])
+    # each step: a fixed sample of programs over all cases (bounded work)
+    rng = np.random.default_rng(1)
+    sample = np.sort(rng.choice(w.pop.n, min(w.pop.n, 4 * cores), replace=False))
+    gpop_step = int(w.pop.nodes[sample].sum()) * n_cases
+
+    def job(p):
+        oracle.population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, w.cases, w.targets,
+                                  p_range=(int(p), int(p) + 1))
+
+    times = []
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            list(ex.map(job, sample))
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                times.append(dt)
+    total = sum(times)
+    value = gpop_step * args.steps / total / 1e9
+    sample_txt = f"{sample.size} of {w.pop.n} programs x all {n_cases} cases per step"
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ramped half-and-half trees, x~U[-1,1], quartic target)",
+            "config": {"workload": f"symbolic regression, {w.pop.n} trees (depth 2-8, <=256 nodes, "
+                                   f"{{+,-,*,pdiv}}) x {n_cases} fp32 cases",
+                       "programs": w.pop.n, "cases": n_cases},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample_txt},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * gpeval.h -- C ABI of the GB300 (sm_103a) GP population evaluator.
+ *
+ * The library evaluates the fitness of whole populations of genetic-programming
+ * programs on one GPU with the two-dimensional-stack interpreter of
+ * D. M. Chitty, "Faster GPU Based Genetic Programming Using A Two Dimensional
+ * Stack" (arXiv:1601.00221): every interpreter pass of a thread runs each
+ * program step over K fitness cases at once (Sec. 4, Sec. 4.1), the program is
+ * read warp-uniformly so opcode dispatch never diverges, and per-case errors
+ * are reduced on the GPU into one fitness value per program.
+ *
+ * Conventions for every entry point below:
+ *   - Return value: GP_OK (0) or one of the gp_status codes.  Argument errors
+ *     are detected on the host before anything is launched.
+ *   - "device" pointers must point to memory of the current CUDA device;
+ *     "host" pointers to ordinary host memory.  The caller owns every buffer it
+ *     passes; the library never frees or keeps a caller pointer after return.
+ *   - Evaluation calls are asynchronous on `stream` (a cudaStream_t; 0 = the
+ *     legacy default stream): results are valid once the stream has reached
+ *     the call.  The library owns only an internal workspace per (device,
+ *     stream), grown on demand and released by gp_shutdown().  Concurrent
+ *     calls on one stream from several host threads are not supported; calls
+ *     on different streams are independent.
+ *   - A program that is malformed on the device side (an unknown instruction
+ *     code, an input index >= n_inputs, a header that does not fit its length)
+ *     yields fitness NaN (Boolean: hits UINT64_MAX) for that program only and
+ *     sets the status word read by gp_last_error().
+ */
+#ifndef GPEVAL_H
+#define GPEVAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* gp_stream_t; /* same type as cudaStream_t */
+
+typedef enum gp_status {
+  GP_OK = 0,
+  GP_ERR_INVALID_ARG = 1,     /* a null pointer, a negative size, an unknown enum */
+  GP_ERR_PROGRAM = 2,         /* malformed program: bad token, missing operand, too deep */
+  GP_ERR_CUDA = 3,            /* a CUDA runtime call failed (see gp_error_string) */
+  GP_ERR_OOM = 4,             /* workspace or admission memory could not be had */
+  GP_ERR_TIMEOUT = 5,         /* a bounded wait gave up */
+  GP_ERR_NOT_IMPLEMENTED = 6,
+  GP_ERR_BUSY = 7             /* a serving queue is full */
+} gp_status;
+
+/* ------------------------------------------------------------------------
+ * User token format of a prefix tree (host memory), Sec. 3 / Sec. 5:
+ * one uint32 per token, bits 0..7 opcode, bits 8..31 operand (the input index
+ * of GP_OP_VAR).  A GP_OP_CONST token is followed by one word holding the
+ * binary32 bit pattern of the constant.  GP_OP_DIV is protected division:
+ * a denominator equal to zero (+0 or -0) gives 1.0f, otherwise the IEEE
+ * binary32 quotient rounded to nearest even.  SUB(a,b) = a - b and
+ * DIV(a,b) = a / b where a is the first child.  Boolean trees use VAR and the
+ * bitwise functions AND, OR, NAND, NOR and IF(c,a,b) = (c&a)|(~c&b).
+ * ---------------------------------------------------------------------- */
+enum {
+  GP_OP_ADD = 1, GP_OP_SUB = 2, GP_OP_MUL = 3, GP_OP_DIV = 4,
+  GP_OP_VAR = 5, GP_OP_CONST = 6,
+  GP_OP_AND = 7, GP_OP_OR = 8, GP_OP_NAND = 9, GP_OP_NOR = 10, GP_OP_IF = 11
+};
+
+/* Encoded program kinds (the interpreter a program is compiled for). */
+typedef enum gp_kind {
+  GP_KIND_SFORM = 1,  /* prefix linear "S-form" of a float tree (Sec. 5): one
+                         instruction per function, operands input/constant/stack */
+  GP_KIND_RPN = 2,    /* postfix reverse-Polish form of a float tree (Sec. 4, 4.1) */
+  GP_KIND_LINEAR = 3, /* register linear GP r[d] = r[a] op r[b], 8 registers */
+  GP_KIND_BOOL = 4    /* S-form of a bit-packed Boolean tree (Sec. 4.2) */
+} gp_kind;
+
+/* Evaluation order of the children of a tree node when it is encoded. */
+typedef enum gp_order {
+  GP_ORDER_PAPER = 0,     /* children left to right, exactly as the paper's converter */
+  GP_ORDER_MIN_DEPTH = 1  /* deeper-needing child first (Sethi-Ullman), fewest stack levels;
+                             per-case values are bit-identical to GP_ORDER_PAPER */
+} gp_order;
+
+/* Number of stack levels the register interpreters hold (per case) and the
+ * longest program (instructions) one interpreter pass accepts. */
+#define GP_STACK_LEVELS 8
+#define GP_MAX_INSTR 1024
+#define GP_HEADER_WORDS 4
+#define GP_INSTR_WORDS 4
+
+typedef struct gp_prog_info {
+  int32_t n_nodes;      /* tree nodes (functions + terminals): the GPop unit */
+  int32_t n_instr;      /* interpreter instructions */
+  int32_t max_depth;    /* stack levels used */
+  int32_t stack_reads;  /* operands taken from the stack */
+  int32_t max_input;    /* largest input index referenced, -1 if none */
+  int32_t words;        /* encoded size in uint32 words */
+} gp_prog_info;
+
+/* ------------------------------------------------------------------------
+ * Host encoder (Sec. 5: symbolic-stack conversion of an RPN tree to the
+ * prefix linear form; host memory only, no CUDA calls).
+ *
+ * gp_encode_tree: encodes one prefix tree `prefix[0..n_words)` into `out`
+ * (capacity `cap_words`) as kind `kind` (GP_KIND_SFORM, GP_KIND_RPN or
+ * GP_KIND_BOOL) with child order `order`.  `info` (may be NULL) receives the
+ * counts.  Returns GP_ERR_PROGRAM for a malformed tree or one that needs more
+ * than GP_STACK_LEVELS levels or GP_MAX_INSTR instructions, GP_ERR_INVALID_ARG
+ * if `out` is too small (info->words still tells the size needed).
+ *
+ * Encoded layout (uint32 words, every program a multiple of 4 words):
+ *   header {kind | order<<8, n_instr, n_nodes, max_depth | (max_input+1)<<16}
+ *   then n_instr instructions of 4 words {code, payload_a, payload_b, payload_c}.
+ * ---------------------------------------------------------------------- */
+int gp_encode_tree(const uint32_t* prefix, int64_t n_words, int32_t kind, int32_t order,
+                   uint32_t* out, int64_t cap_words, gp_prog_info* info);
+
+/* Encodes programs p = 0..n_progs-1, program p being
+ * words[offsets[p] .. offsets[p] + lengths[p]).  With out == NULL only the
+ * sizes are computed: *total_words receives the encoded size.  Otherwise
+ * out_offsets[p] / out_lengths[p] (host, n_progs entries each) receive the
+ * encoded word offset and length of program p, *total_nodes the sum of nodes.
+ * `info` (may be NULL) receives n_progs entries.  Stops at the first bad
+ * program and reports its index in *bad_prog (may be NULL). */
+int gp_encode_population(const uint32_t* words, const int64_t* offsets, const int32_t* lengths,
+                         int32_t n_progs, int32_t kind, int32_t order, uint32_t* out,
+                         int64_t cap_words, int64_t* out_offsets, int32_t* out_lengths,
+                         int64_t* total_words, int64_t* total_nodes, gp_prog_info* info,
+                         int32_t* bad_prog);
+
+/* Register linear GP programs: instr[(offsets[p] + i)*4 + {0,1,2,3}] =
+ * {dst, op, a, b} (registers 0..7, op GP_OP_ADD..GP_OP_DIV).  Same output
+ * conventions as gp_encode_population; nodes = instructions. */
+int gp_encode_linear_population(const uint8_t* instr, const int64_t* offsets,
+                                const int32_t* lengths, int32_t n_progs, uint32_t* out,
+                                int64_t cap_words, int64_t* out_offsets, int32_t* out_lengths,
+                                int64_t* total_words, int64_t* total_nodes, int32_t* bad_prog);
+
+/* ------------------------------------------------------------------------
+ * Evaluation configuration.  k = fitness cases per thread per interpreter pass
+ * (the second dimension of the 2D stack, Sec. 4; 1 = the one-dimensional
+ * stack); block = threads per block; chunk_cases = cases one block covers
+ * (0 = choose); variant selects the interpreter.
+ * ---------------------------------------------------------------------- */
+typedef enum gp_variant {
+  GP_VARIANT_AUTO = 0,      /* the tuned default for the workload */
+  GP_VARIANT_REGISTER = 1,  /* stack levels in registers, K cases per thread */
+  GP_VARIANT_LOCAL = 2      /* BlockGP-style one-case-per-thread stack in local memory
+                               (Sec. 3 prior art), GP_KIND_RPN programs only */
+} gp_variant;
+
+typedef struct gp_config {
+  int32_t variant;
+  int32_t k;            /* 1, 2, 4 or 8 (0 = tuned) */
+  int32_t block;        /* 32..1024, multiple of 32 (0 = tuned) */
+  int32_t chunk_cases;  /* 0 = choose; else a multiple of k*block */
+} gp_config;
+
+/* ------------------------------------------------------------------------
+ * Float fitness of a population (device pointers).
+ *   programs     encoded words (gp_encode_*), GP_KIND_SFORM, GP_KIND_RPN or
+ *                GP_KIND_LINEAR, any mix; offsets[p] (int64, multiple of 4)
+ *                and lengths[p] (int32) in words.
+ *   cases        binary32 [n_inputs][n_cases], structure of arrays:
+ *                input v of case c at cases[v * n_cases + c].
+ *   targets      binary32 [n_cases].
+ *   fitness_out  binary64 [n_progs]: sum over cases of |o - y| where each
+ *                error is binary32 (Sec. 4.1 GetError; the paper leaves the
+ *                error unstated, this library fixes the absolute error),
+ *                accumulated with compensated binary32 sums per thread and
+ *                summed in binary64 across blocks in a fixed order; +inf if any
+ *                per-case error is not finite, NaN for a malformed program.
+ * The result depends only on (program, cases, config), never on what else
+ * runs on the GPU.  n_cases may be 0 (fitness 0).  Sec. 4.1, Listing 1/2.
+ * ---------------------------------------------------------------------- */
+int gp_eval_population(const uint32_t* programs, const int64_t* offsets, const int32_t* lengths,
+                       int32_t n_progs, const float* cases, int32_t n_inputs, int64_t n_cases,
+                       const float* targets, double* fitness_out, gp_stream_t stream);
+
+/* As gp_eval_population with an explicit configuration (NULL = default).
+ * `fitness_out` may be NULL; `outputs` (may be NULL) receives the per-case
+ * program outputs, binary32 [n_progs][n_cases] (row p, column c). */
+int gp_eval_population_ex(const uint32_t* programs, const int64_t* offsets,
+                          const int32_t* lengths, int32_t n_progs, const float* cases,
+                          int32_t n_inputs, int64_t n_cases, const float* targets,
+                          double* fitness_out, float* outputs, const gp_config* cfg,
+                          gp_stream_t stream);
+
+/* Per-case outputs only (parity testing): outputs[p * n_cases + c]. */
+int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets, const int32_t* lengths,
+                    int32_t n_progs, const float* cases, int32_t n_inputs, int64_t n_cases,
+                    float* outputs, const gp_config* cfg, gp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Bit-packed Boolean fitness (Sec. 4.2: 32 fitness cases per 32-bit word,
+ * sub-machine-code GP).  programs: GP_KIND_BOOL.  case_bits uint32
+ * [n_inputs][ceil(n_cases/32)]: case c of input v is bit (c & 31) of word
+ * case_bits[v * n_words + (c >> 5)].  target_bits uint32 [n_words].
+ * hits_out uint64 [n_progs]: cases c < n_cases whose output bit equals the
+ * target bit (bits beyond n_cases in the last word are ignored).  Exact.
+ * ---------------------------------------------------------------------- */
+int gp_eval_population_bool(const uint32_t* programs, const int64_t* offsets,
+                            const int32_t* lengths, int32_t n_progs, const uint32_t* case_bits,
+                            int32_t n_inputs, int64_t n_cases, const uint32_t* target_bits,
+                            uint64_t* hits_out, gp_stream_t stream);
+
+/* As gp_eval_population_bool with a configuration (NULL = default); hits_out
+ * may be NULL; out_words (may be NULL) receives the output words
+ * [n_progs][n_words] (bits beyond n_cases unspecified). */
+int gp_eval_population_bool_ex(const uint32_t* programs, const int64_t* offsets,
+                               const int32_t* lengths, int32_t n_progs,
+                               const uint32_t* case_bits, int32_t n_inputs, int64_t n_cases,
+                               const uint32_t* target_bits, uint64_t* hits_out,
+                               uint32_t* out_words, const gp_config* cfg, gp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Configuration, status and lifetime.
+ * ---------------------------------------------------------------------- */
+/* Default configuration used when cfg is NULL or a field is 0. */
+int gp_set_config(const gp_config* cfg);
+int gp_get_config(gp_config* cfg);
+
+/* Program-error status of the last evaluations on `stream`: synchronises the
+ * stream, writes the status (0 = none, else a GP_ERR_* code) and clears it. */
+int gp_last_error(gp_stream_t stream, int32_t* status);
+
+/* Text of the last host-side error of the calling thread (never NULL). */
+const char* gp_error_string(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t gp_version(void);
+
+/* Releases every internal workspace of every device (synchronises them). */
+int gp_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPEVAL_H */

@@ -1,0 +1,295 @@
+"""Python binding of libgpeval.so, the GB300 (sm_103a) GP population evaluator.
+
+The binding only marshals arguments: every step of an evaluation runs in the
+library's CUDA kernels (``csrc/``), and the host encoder runs in the library's
+C++ code.  PyTorch supplies device memory and streams.  There is no fallback:
+if the library is missing or fails to load, importing the evaluation entry
+points raises.
+
+Function names follow ``include/gpeval.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "GPError", "lib", "Config", "EncodedPopulation",
+    "encode_tree", "encode_population", "encode_linear_population",
+    "eval_population", "eval_outputs", "eval_population_bool",
+    "set_config", "get_config", "last_error", "shutdown", "version",
+    "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "ORDER_PAPER", "ORDER_MIN_DEPTH",
+    "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL",
+]
+
+KIND_SFORM, KIND_RPN, KIND_LINEAR, KIND_BOOL = 1, 2, 3, 4
+ORDER_PAPER, ORDER_MIN_DEPTH = 0, 1
+VARIANT_AUTO, VARIANT_REGISTER, VARIANT_LOCAL = 0, 1, 2
+STACK_LEVELS = 8
+MAX_INSTR = 1024
+
+_STATUS = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_PROGRAM", 3: "GP_ERR_CUDA",
+           4: "GP_ERR_OOM", 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_NOT_IMPLEMENTED", 7: "GP_ERR_BUSY"}
+
+
+class GPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _ProgInfo(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_instr", ctypes.c_int32),
+                ("max_depth", ctypes.c_int32), ("stack_reads", ctypes.c_int32),
+                ("max_input", ctypes.c_int32), ("words", ctypes.c_int32)]
+
+
+class Config(ctypes.Structure):
+    """gp_config: variant, k (cases per thread per pass), block, chunk_cases (0 = choose)."""
+    _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("chunk_cases", ctypes.c_int32)]
+
+    def __repr__(self):
+        return f"Config(variant={self.variant}, k={self.k}, block={self.block}, chunk_cases={self.chunk_cases})"
+
+
+_lib = None
+
+
+def lib(rebuild: bool = False) -> ctypes.CDLL:
+    """Loads (building first if needed) libgpeval.so.  Raises if it cannot."""
+    global _lib
+    if _lib is not None and not rebuild:
+        return _lib
+    path = _build.LIB
+    if rebuild or not os.path.exists(path):
+        path = _build.build()
+    L = ctypes.CDLL(path)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "gp_encode_tree": [P, i64, i32, i32, P, i64, P],
+        "gp_encode_population": [P, P, P, i32, i32, i32, P, i64, P, P, P, P, P, P],
+        "gp_encode_linear_population": [P, P, P, i32, P, i64, P, P, P, P, P],
+        "gp_eval_population": [P, P, P, i32, P, i32, i64, P, P, P],
+        "gp_eval_population_ex": [P, P, P, i32, P, i32, i64, P, P, P, P, P],
+        "gp_eval_outputs": [P, P, P, i32, P, i32, i64, P, P, P],
+        "gp_eval_population_bool": [P, P, P, i32, P, i32, i64, P, P, P],
+        "gp_eval_population_bool_ex": [P, P, P, i32, P, i32, i64, P, P, P, P, P],
+        "gp_set_config": [P],
+        "gp_get_config": [P],
+        "gp_last_error": [P, P],
+        "gp_shutdown": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.gp_error_string.argtypes = []
+    L.gp_error_string.restype = ctypes.c_char_p
+    L.gp_version.argtypes = []
+    L.gp_version.restype = ctypes.c_int32
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise GPError(rc, lib().gp_error_string().decode(errors="replace"))
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def version() -> int:
+    return int(lib().gp_version())
+
+
+# ---------------------------------------------------------------------------
+# host encoder
+# ---------------------------------------------------------------------------
+@dataclass
+class EncodedPopulation:
+    words: np.ndarray      # uint32, 16-byte aligned programs back to back
+    offsets: np.ndarray    # int64 word offsets
+    lengths: np.ndarray    # int32 word lengths
+    nodes: int             # total tree nodes (GPop unit per case)
+    kind: int
+    order: int
+    info: Optional[np.ndarray] = None  # structured per-program info (tree kinds)
+
+    @property
+    def n(self) -> int:
+        return int(self.lengths.size)
+
+    def to_device(self, device="cuda"):
+        import torch
+        return (torch.from_numpy(self.words.view(np.int32)).to(device),
+                torch.from_numpy(self.offsets).to(device),
+                torch.from_numpy(self.lengths).to(device))
+
+
+def encode_tree(prefix, kind: int = KIND_SFORM, order: int = ORDER_MIN_DEPTH):
+    """One prefix tree -> (encoded uint32 words, info dict)."""
+    p = np.ascontiguousarray(prefix, dtype=np.uint32)
+    info = _ProgInfo()
+    cap = 4 + 4 * max(1, p.size)
+    out = np.zeros(cap, np.uint32)
+    _check(lib().gp_encode_tree(_np_ptr(p), p.size, kind, order, _np_ptr(out), cap,
+                                ctypes.byref(info)))
+    d = {f: getattr(info, f) for f, _ in _ProgInfo._fields_}
+    return out[:info.words].copy(), d
+
+
+def encode_population(words, offsets, lengths, kind: int = KIND_SFORM,
+                      order: int = ORDER_MIN_DEPTH, with_info: bool = False) -> EncodedPopulation:
+    w = np.ascontiguousarray(words, np.uint32)
+    off = np.ascontiguousarray(offsets, np.int64)
+    ln = np.ascontiguousarray(lengths, np.int32)
+    n = int(ln.size)
+    total = ctypes.c_int64(0)
+    nodes = ctypes.c_int64(0)
+    bad = ctypes.c_int32(-1)
+    L = lib()
+    rc = L.gp_encode_population(_np_ptr(w), _np_ptr(off), _np_ptr(ln), n, kind, order, None, 0,
+                                None, None, ctypes.byref(total), ctypes.byref(nodes), None,
+                                ctypes.byref(bad))
+    _check(rc)
+    out = _aligned_empty(max(int(total.value), 4))
+    out_off = np.zeros(n, np.int64)
+    out_len = np.zeros(n, np.int32)
+    info = (_ProgInfo * n)() if with_info else None
+    rc = L.gp_encode_population(_np_ptr(w), _np_ptr(off), _np_ptr(ln), n, kind, order,
+                                _np_ptr(out), out.size, _np_ptr(out_off), _np_ptr(out_len),
+                                ctypes.byref(total), ctypes.byref(nodes),
+                                ctypes.cast(info, ctypes.c_void_p) if info is not None else None,
+                                ctypes.byref(bad))
+    _check(rc)
+    arr = None
+    if info is not None:
+        arr = np.ctypeslib.as_array(info).copy()
+    return EncodedPopulation(out, out_off, out_len, int(nodes.value), kind, order, arr)
+
+
+def encode_linear_population(instr, offsets, lengths) -> EncodedPopulation:
+    ins = np.ascontiguousarray(instr, np.uint8).reshape(-1)
+    off = np.ascontiguousarray(offsets, np.int64)
+    ln = np.ascontiguousarray(lengths, np.int32)
+    n = int(ln.size)
+    total = ctypes.c_int64(0)
+    nodes = ctypes.c_int64(0)
+    bad = ctypes.c_int32(-1)
+    L = lib()
+    _check(L.gp_encode_linear_population(_np_ptr(ins), _np_ptr(off), _np_ptr(ln), n, None, 0,
+                                         None, None, ctypes.byref(total), ctypes.byref(nodes),
+                                         ctypes.byref(bad)))
+    out = _aligned_empty(max(int(total.value), 4))
+    out_off = np.zeros(n, np.int64)
+    out_len = np.zeros(n, np.int32)
+    _check(L.gp_encode_linear_population(_np_ptr(ins), _np_ptr(off), _np_ptr(ln), n,
+                                         _np_ptr(out), out.size, _np_ptr(out_off),
+                                         _np_ptr(out_len), ctypes.byref(total),
+                                         ctypes.byref(nodes), ctypes.byref(bad)))
+    return EncodedPopulation(out, out_off, out_len, int(nodes.value), KIND_LINEAR, 0)
+
+
+def _aligned_empty(n_words: int) -> np.ndarray:
+    buf = np.zeros(n_words + 4, np.uint32)
+    shift = (-(buf.ctypes.data // 4)) % 4
+    return buf[shift:shift + n_words]
+
+
+# ---------------------------------------------------------------------------
+# evaluation (torch tensors on the current CUDA device)
+# ---------------------------------------------------------------------------
+def _tptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _cfg(config):
+    if config is None:
+        return None
+    if isinstance(config, Config):
+        return ctypes.byref(config)
+    c = Config(**config)
+    return ctypes.byref(c)
+
+
+def eval_population(programs, offsets, lengths, cases, targets, fitness_out=None, outputs=None,
+                    config=None, stream=None):
+    """Fitness (float64 [n]) of encoded float programs (GP_KIND_SFORM/RPN/LINEAR).
+
+    programs int32/uint32 words, offsets int64, lengths int32, cases float32
+    [n_inputs, n_cases], targets float32 [n_cases]; all CUDA tensors.
+    Returns fitness_out (allocated when None).  `outputs` (float32
+    [n, n_cases]) optionally receives per-case outputs.
+    """
+    import torch
+    n = int(lengths.numel())
+    n_inputs, n_cases = (int(cases.shape[0]), int(cases.shape[1])) if cases.dim() == 2 else (1, int(cases.numel()))
+    if fitness_out is None:
+        fitness_out = torch.empty(n, dtype=torch.float64, device=cases.device)
+    _check(lib().gp_eval_population_ex(_tptr(programs), _tptr(offsets), _tptr(lengths), n,
+                                       _tptr(cases), n_inputs, n_cases, _tptr(targets),
+                                       _tptr(fitness_out), _tptr(outputs), _cfg(config),
+                                       _stream(stream)))
+    return fitness_out
+
+
+def eval_outputs(programs, offsets, lengths, cases, outputs=None, config=None, stream=None):
+    import torch
+    n = int(lengths.numel())
+    n_inputs, n_cases = (int(cases.shape[0]), int(cases.shape[1])) if cases.dim() == 2 else (1, int(cases.numel()))
+    if outputs is None:
+        outputs = torch.empty((n, n_cases), dtype=torch.float32, device=cases.device)
+    _check(lib().gp_eval_outputs(_tptr(programs), _tptr(offsets), _tptr(lengths), n,
+                                 _tptr(cases), n_inputs, n_cases, _tptr(outputs), _cfg(config),
+                                 _stream(stream)))
+    return outputs
+
+
+def eval_population_bool(programs, offsets, lengths, case_bits, n_cases, target_bits,
+                         hits_out=None, out_words=None, config=None, stream=None):
+    """Hit counts (int64 tensor [n], exact) of encoded Boolean programs."""
+    import torch
+    n = int(lengths.numel())
+    n_inputs = int(case_bits.shape[0]) if case_bits.dim() == 2 else 1
+    if hits_out is None and out_words is None:
+        hits_out = torch.empty(n, dtype=torch.int64, device=case_bits.device)
+    _check(lib().gp_eval_population_bool_ex(_tptr(programs), _tptr(offsets), _tptr(lengths), n,
+                                            _tptr(case_bits), n_inputs, int(n_cases),
+                                            _tptr(target_bits), _tptr(hits_out),
+                                            _tptr(out_words), _cfg(config), _stream(stream)))
+    return hits_out
+
+
+def set_config(variant=VARIANT_REGISTER, k=8, block=128):
+    _check(lib().gp_set_config(ctypes.byref(Config(variant, k, block, 0))))
+
+
+def get_config() -> Config:
+    c = Config()
+    _check(lib().gp_get_config(ctypes.byref(c)))
+    return c
+
+
+def last_error(stream=None) -> int:
+    v = ctypes.c_int32(0)
+    _check(lib().gp_last_error(_stream(stream), ctypes.byref(v)))
+    return int(v.value)
+
+
+def shutdown():
+    _check(lib().gp_shutdown())

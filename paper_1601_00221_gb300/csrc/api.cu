@@ -1,0 +1,351 @@
+// api.cu -- the C ABI of include/gpeval.h: argument checks, the per-stream
+// workspace, launch configuration and the evaluation entry points.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "../../include/gpeval.h"
+#include "eval_bool.cuh"
+#include "launch.h"
+#include "status.h"
+
+using namespace gpdev;
+
+namespace {
+
+std::mutex g_mu;
+gp_config g_default = {GP_VARIANT_REGISTER, 8, 128, 0};
+
+// Internal workspace of one (device, stream): per-block partial sums, the
+// per-program arrival counters of the fused reduction (zero between
+// launches) and the program-error status word.
+struct Workspace {
+  int device;
+  cudaStream_t stream;
+  Partial* partials = nullptr;
+  size_t partial_cap = 0;  // entries
+  unsigned* counters = nullptr;
+  size_t counter_cap = 0;  // entries
+  int* status = nullptr;
+};
+std::vector<Workspace*> g_ws;
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return gp_fail(e == cudaErrorMemoryAllocation ? GP_ERR_OOM : GP_ERR_CUDA, "%s: %s", what,
+                 cudaGetErrorString(e));
+}
+
+int get_workspace(cudaStream_t s, size_t n_partials, size_t n_counters, Workspace** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace* w = nullptr;
+  for (Workspace* x : g_ws)
+    if (x->device == dev && x->stream == s) w = x;
+  if (!w) {
+    w = new Workspace();
+    w->device = dev;
+    w->stream = s;
+    e = cudaMallocAsync((void**)&w->status, sizeof(int), s);
+    if (e != cudaSuccess) { delete w; return cuda_fail(e, "workspace allocation"); }
+    e = cudaMemsetAsync(w->status, 0, sizeof(int), s);
+    if (e != cudaSuccess) { delete w; return cuda_fail(e, "workspace clear"); }
+    g_ws.push_back(w);
+  }
+  if (n_partials > w->partial_cap) {
+    size_t cap = std::max(n_partials, 2 * w->partial_cap);
+    Partial* p = nullptr;
+    e = cudaMallocAsync((void**)&p, cap * sizeof(Partial), s);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+    if (w->partials) cudaFreeAsync(w->partials, s);
+    w->partials = p;
+    w->partial_cap = cap;
+  }
+  if (n_counters > w->counter_cap) {
+    size_t cap = std::max(n_counters, 2 * w->counter_cap);
+    unsigned* c = nullptr;
+    e = cudaMallocAsync((void**)&c, cap * sizeof(unsigned), s);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+    e = cudaMemsetAsync(c, 0, cap * sizeof(unsigned), s);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+    if (w->counters) cudaFreeAsync(w->counters, s);
+    w->counters = c;
+    w->counter_cap = cap;
+  }
+  *out = w;
+  return GP_OK;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      n = v;
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Fills zero fields of `c` from the default configuration and checks it.
+int resolve_config(const gp_config* user, gp_config* c) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    *c = g_default;
+  }
+  if (user) {
+    if (user->variant) c->variant = user->variant;
+    if (user->k) c->k = user->k;
+    if (user->block) c->block = user->block;
+    c->chunk_cases = user->chunk_cases;
+  }
+  if (c->variant != GP_VARIANT_REGISTER && c->variant != GP_VARIANT_LOCAL && c->variant != GP_VARIANT_AUTO)
+    return gp_fail(GP_ERR_INVALID_ARG, "unknown variant %d", c->variant);
+  if (c->variant == GP_VARIANT_AUTO) c->variant = GP_VARIANT_REGISTER;
+  if (c->k != 1 && c->k != 2 && c->k != 4 && c->k != 8)
+    return gp_fail(GP_ERR_INVALID_ARG, "k must be 1, 2, 4 or 8 (got %d)", c->k);
+  if (c->variant == GP_VARIANT_LOCAL) c->k = 1;
+  if (c->block < 32 || c->block > 256 || c->block % 32)
+    return gp_fail(GP_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 256] (got %d)", c->block);
+  if (c->chunk_cases < 0 || (c->chunk_cases % ((int64_t)c->k * c->block)) != 0)
+    return gp_fail(GP_ERR_INVALID_ARG, "chunk_cases must be a multiple of k*block");
+  return GP_OK;
+}
+
+// Cases (or words) per block: enough blocks to fill the GPU several times
+// over, each covering whole passes of the block.
+int64_t choose_chunk(int64_t n_units, int32_t n_progs, int per_pass, int64_t user_chunk) {
+  if (user_chunk > 0) return user_chunk;
+  const int64_t target_blocks = 48LL * sm_count();
+  int64_t want = (target_blocks + n_progs - 1) / std::max<int32_t>(n_progs, 1);
+  want = std::max<int64_t>(want, 1);
+  int64_t chunk = (n_units + want - 1) / want;
+  chunk = ((chunk + per_pass - 1) / per_pass) * per_pass;
+  return std::max<int64_t>(chunk, per_pass);
+}
+
+}  // namespace
+
+extern "C" int gp_set_config(const gp_config* cfg) {
+  gp_clear_error();
+  if (!cfg) return gp_fail(GP_ERR_INVALID_ARG, "null config");
+  gp_config c;
+  gp_config saved;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    saved = g_default;
+  }
+  int rc = resolve_config(cfg, &c);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  (void)saved;
+  g_default = c;
+  g_default.chunk_cases = 0;
+  return GP_OK;
+}
+
+extern "C" int gp_get_config(gp_config* cfg) {
+  gp_clear_error();
+  if (!cfg) return gp_fail(GP_ERR_INVALID_ARG, "null config");
+  std::lock_guard<std::mutex> lk(g_mu);
+  *cfg = g_default;
+  return GP_OK;
+}
+
+extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* offsets,
+                                     const int32_t* lengths, int32_t n_progs, const float* cases,
+                                     int32_t n_inputs, int64_t n_cases, const float* targets,
+                                     double* fitness_out, float* outputs, const gp_config* cfg,
+                                     gp_stream_t stream) {
+  gp_clear_error();
+  if (n_progs < 0 || n_inputs < 0 || n_cases < 0)
+    return gp_fail(GP_ERR_INVALID_ARG, "negative size");
+  if (!fitness_out && !outputs) return gp_fail(GP_ERR_INVALID_ARG, "no output requested");
+  if (n_progs == 0) return GP_OK;
+  if (!programs || !offsets || !lengths) return gp_fail(GP_ERR_INVALID_ARG, "null program arrays");
+  if (!aligned16(programs)) return gp_fail(GP_ERR_INVALID_ARG, "programs must be 16-byte aligned");
+  if (n_cases > 0 && n_inputs > 0 && !cases) return gp_fail(GP_ERR_INVALID_ARG, "null cases");
+  if (fitness_out && n_cases > 0 && !targets) return gp_fail(GP_ERR_INVALID_ARG, "null targets");
+  if (n_cases > ((int64_t)1 << 40)) return gp_fail(GP_ERR_INVALID_ARG, "n_cases too large");
+  gp_config c;
+  int rc = resolve_config(cfg, &c);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  const int per_pass = c.k * c.block;
+  const int64_t chunk = choose_chunk(n_cases, n_progs, per_pass, c.chunk_cases);
+  const int64_t n_chunks64 = std::max<int64_t>(1, (n_cases + chunk - 1) / chunk);
+  if (n_chunks64 * n_progs > 0x7fffffffLL) return gp_fail(GP_ERR_INVALID_ARG, "too many blocks");
+  const int32_t n_chunks = (int32_t)n_chunks64;
+
+  Workspace* w = nullptr;
+  rc = get_workspace(s, n_chunks > 1 ? (size_t)n_chunks * n_progs : 0, n_chunks > 1 ? n_progs : 0, &w);
+  if (rc) return rc;
+
+  FloatArgs a;
+  a.programs = programs;
+  a.offsets = offsets;
+  a.lengths = lengths;
+  a.n_progs = n_progs;
+  a.cases = cases;
+  a.n_inputs = n_inputs;
+  a.n_cases = n_cases;
+  a.targets = fitness_out ? targets : nullptr;
+  a.fitness_out = fitness_out;
+  a.outputs = outputs;
+  a.partials = w->partials;
+  a.counters = w->counters;
+  a.status = w->status;
+  a.chunk_cases = chunk;
+  a.n_chunks = n_chunks;
+  a.x_aligned = aligned16(cases) && (n_inputs <= 1 || n_cases % 4 == 0);
+  a.y_aligned = aligned16(targets);
+  a.o_aligned = aligned16(outputs) && (n_progs == 1 || n_cases % 4 == 0);
+  a.want_fitness = fitness_out != nullptr;
+  const int grid = n_progs * n_chunks;
+  const bool xreg = (n_inputs == 1);
+  cudaError_t e;
+  if (c.variant == GP_VARIANT_LOCAL) e = launch_blockgp(a, c.block, grid, s);
+  else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, s);
+  else if (c.k == 2) e = launch_float_k2(a, xreg, c.block, grid, s);
+  else if (c.k == 4) e = launch_float_k4(a, xreg, c.block, grid, s);
+  else e = launch_float_k8(a, xreg, c.block, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return GP_OK;
+}
+
+extern "C" int gp_eval_population(const uint32_t* programs, const int64_t* offsets,
+                                  const int32_t* lengths, int32_t n_progs, const float* cases,
+                                  int32_t n_inputs, int64_t n_cases, const float* targets,
+                                  double* fitness_out, gp_stream_t stream) {
+  if (!fitness_out) {
+    gp_clear_error();
+    return gp_fail(GP_ERR_INVALID_ARG, "null fitness_out");
+  }
+  return gp_eval_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases,
+                               targets, fitness_out, nullptr, nullptr, stream);
+}
+
+extern "C" int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets,
+                               const int32_t* lengths, int32_t n_progs, const float* cases,
+                               int32_t n_inputs, int64_t n_cases, float* outputs,
+                               const gp_config* cfg, gp_stream_t stream) {
+  if (!outputs) {
+    gp_clear_error();
+    return gp_fail(GP_ERR_INVALID_ARG, "null outputs");
+  }
+  return gp_eval_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases,
+                               nullptr, nullptr, outputs, cfg, stream);
+}
+
+extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_t* offsets,
+                                          const int32_t* lengths, int32_t n_progs,
+                                          const uint32_t* case_bits, int32_t n_inputs,
+                                          int64_t n_cases, const uint32_t* target_bits,
+                                          uint64_t* hits_out, uint32_t* out_words,
+                                          const gp_config* cfg, gp_stream_t stream) {
+  gp_clear_error();
+  if (n_progs < 0 || n_inputs < 0 || n_cases < 0)
+    return gp_fail(GP_ERR_INVALID_ARG, "negative size");
+  if (!hits_out && !out_words) return gp_fail(GP_ERR_INVALID_ARG, "no output requested");
+  if (n_progs == 0) return GP_OK;
+  if (!programs || !offsets || !lengths) return gp_fail(GP_ERR_INVALID_ARG, "null program arrays");
+  if (!aligned16(programs)) return gp_fail(GP_ERR_INVALID_ARG, "programs must be 16-byte aligned");
+  const int64_t n_words = (n_cases + 31) / 32;
+  if (n_words > 0 && n_inputs > 0 && !case_bits) return gp_fail(GP_ERR_INVALID_ARG, "null case_bits");
+  if (hits_out && n_words > 0 && !target_bits) return gp_fail(GP_ERR_INVALID_ARG, "null target_bits");
+  gp_config c;
+  int rc = resolve_config(cfg, &c);
+  if (rc) return rc;
+  if (c.variant != GP_VARIANT_REGISTER) return gp_fail(GP_ERR_INVALID_ARG, "Boolean programs use the register variant");
+  if (!cfg || !cfg->block) {  // small case sets: do not launch idle warps
+    int64_t need = (n_words + c.k - 1) / c.k;
+    c.block = (int)std::min<int64_t>(c.block, std::max<int64_t>(32, ((need + 31) / 32) * 32));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int per_pass = c.k * c.block;
+  const int64_t chunk = choose_chunk(n_words, n_progs, per_pass, c.chunk_cases);
+  const int64_t n_chunks64 = std::max<int64_t>(1, (n_words + chunk - 1) / chunk);
+  if (n_chunks64 * n_progs > 0x7fffffffLL) return gp_fail(GP_ERR_INVALID_ARG, "too many blocks");
+  Workspace* w = nullptr;
+  rc = get_workspace(s, 0, 0, &w);
+  if (rc) return rc;
+  cudaError_t e;
+  if (hits_out) {
+    e = cudaMemsetAsync(hits_out, 0, sizeof(uint64_t) * (size_t)n_progs, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing hits");
+  }
+  BoolArgs a;
+  a.programs = programs;
+  a.offsets = offsets;
+  a.lengths = lengths;
+  a.n_progs = n_progs;
+  a.case_bits = case_bits;
+  a.n_inputs = n_inputs;
+  a.n_cases = n_cases;
+  a.n_words = n_words;
+  a.target_bits = hits_out ? target_bits : nullptr;
+  a.hits_out = reinterpret_cast<unsigned long long*>(hits_out);
+  a.out_words = out_words;
+  a.status = w->status;
+  a.chunk_words = chunk;
+  a.n_chunks = (int32_t)n_chunks64;
+  a.aligned = aligned16(case_bits) && aligned16(target_bits) && (n_inputs <= 1 || n_words % 4 == 0);
+  e = launch_bool(a, c.k, c.block, (int)(n_progs * n_chunks64), s);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return GP_OK;
+}
+
+extern "C" int gp_eval_population_bool(const uint32_t* programs, const int64_t* offsets,
+                                       const int32_t* lengths, int32_t n_progs,
+                                       const uint32_t* case_bits, int32_t n_inputs,
+                                       int64_t n_cases, const uint32_t* target_bits,
+                                       uint64_t* hits_out, gp_stream_t stream) {
+  if (!hits_out) {
+    gp_clear_error();
+    return gp_fail(GP_ERR_INVALID_ARG, "null hits_out");
+  }
+  return gp_eval_population_bool_ex(programs, offsets, lengths, n_progs, case_bits, n_inputs,
+                                    n_cases, target_bits, hits_out, nullptr, nullptr, stream);
+}
+
+extern "C" int gp_last_error(gp_stream_t stream, int32_t* status) {
+  gp_clear_error();
+  if (!status) return gp_fail(GP_ERR_INVALID_ARG, "null status");
+  Workspace* w = nullptr;
+  int rc = get_workspace((cudaStream_t)stream, 0, 0, &w);
+  if (rc) return rc;
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, w->status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->status, 0, sizeof(int), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
+  *status = v;
+  return GP_OK;
+}
+
+extern "C" int gp_shutdown(void) {
+  gp_clear_error();
+  std::lock_guard<std::mutex> lk(g_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (Workspace* w : g_ws) {
+    cudaSetDevice(w->device);
+    cudaStreamSynchronize(w->stream);
+    if (w->partials) cudaFree(w->partials);
+    if (w->counters) cudaFree(w->counters);
+    if (w->status) cudaFree(w->status);
+    delete w;
+  }
+  g_ws.clear();
+  cudaSetDevice(cur);
+  return GP_OK;
+}

@@ -1,0 +1,11 @@
+// eval_float_k2.cu -- instantiation of the binary32 interpreters for K = 2
+// fitness cases per thread per pass.
+#include "launch.h"
+
+namespace gpdev {
+cudaError_t launch_float_k2(const FloatArgs& a, bool xreg, int block, int grid, cudaStream_t s) {
+  if (xreg) eval_float_kernel<2, true><<<grid, block, 0, s>>>(a);
+  else eval_float_kernel<2, false><<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace gpdev

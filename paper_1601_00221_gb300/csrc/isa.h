@@ -1,0 +1,94 @@
+// isa.h -- instruction codes of the encoded programs, shared by the host
+// encoder and the CUDA interpreters (both are product code).
+//
+// Every interpreter instruction is four uint32 words {code, pa, pb, pc}.  The
+// code is dense so that the interpreters dispatch with one jump table; it
+// folds together the function, the kind of each operand and the stack level
+// the instruction works on.  Stack levels are known statically for a
+// straight-line program (Sec. 5: the symbolic-stack conversion already knows,
+// at each function, which operands come from the stack), so the level is part
+// of the code and the register interpreters index their stack registers with
+// compile-time constants.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define GPISA_HD __host__ __device__
+#else
+#define GPISA_HD
+#endif
+
+namespace gpisa {
+
+constexpr int R = 8;            // stack levels held per case (GP_STACK_LEVELS)
+constexpr int MAX_INSTR = 1024; // GP_MAX_INSTR
+constexpr uint32_t VERSION = 1;
+
+enum Kind : uint32_t { K_SFORM = 1, K_RPN = 2, K_LINEAR = 3, K_BOOL = 4 };
+
+// float function index = user opcode - 1 (ADD, SUB, MUL, DIV)
+enum FOp : int { F_ADD = 0, F_SUB = 1, F_MUL = 2, F_DIV = 3 };
+
+// ---- float S-form (Sec. 5): operands X = input, C = constant, S0/S1 = the
+// stack level l / l+1; the result is written to level l.
+enum SForm : int {
+  SF_XX = 0, SF_XC, SF_CX, SF_CC,  // no stack operand
+  SF_SX, SF_XS, SF_SC, SF_CS,      // one stack operand at level l
+  SF_SS,                            // a = level l, b = level l+1
+  SF_SSR,                           // a = level l+1, b = level l
+  SF_MOVX, SF_MOVC,                 // a program that is a single terminal
+  SF_NFORMS
+};
+GPISA_HD constexpr int sform_code(int form, int level, int op) { return (form * R + level) * 4 + op; }
+constexpr int SF_NCODES = SF_NFORMS * R * 4;
+
+// ---- float RPN (Sec. 4): push a terminal to level l, or combine levels
+// l and l+1 into level l.
+enum RForm : int { RF_PUSHX = 0, RF_PUSHC, RF_OP, RF_OPR, RF_NFORMS };
+GPISA_HD constexpr int rpn_code(int form, int level, int op) { return (form * R + level) * 4 + op; }
+constexpr int RF_NCODES = RF_NFORMS * R * 4;
+
+// ---- register linear GP: code = (op, a, b); pa = destination register.
+constexpr int NREG = 8;
+GPISA_HD constexpr int lin_code(int op, int a, int b) { return (op * NREG + a) * NREG + b; }
+constexpr int LIN_NCODES = 4 * NREG * NREG;
+
+// ---- Boolean S-form.  Binary functions AND, OR, NAND, NOR (index 0..3).
+enum BOp : int { B_AND = 0, B_OR = 1, B_NAND = 2, B_NOR = 3 };
+enum BForm : int { BF_XX = 0, BF_XS, BF_SX, BF_SS, BF_SSR, BF_NFORMS };
+GPISA_HD constexpr int bool_bin_code(int form, int level, int op) { return (form * R + level) * 4 + op; }
+constexpr int BOOL_IF_BASE = BF_NFORMS * R * 4;  // 160
+// IF(c, a, b): each operand is X (0) or stack level l+0, l+1, l+2 (1, 2, 3);
+// the stack operands use exactly levels l .. l+m-1.  The 16 valid operand
+// descriptors are numbered in increasing order of (dc*16 + da*4 + db).
+GPISA_HD constexpr bool if_desc_valid(int dc, int da, int db) {
+  int m = (dc > 0) + (da > 0) + (db > 0);
+  bool used[3] = {false, false, false};
+  if (dc > 0) { if (dc - 1 >= m || used[dc - 1]) return false; used[dc - 1] = true; }
+  if (da > 0) { if (da - 1 >= m || used[da - 1]) return false; used[da - 1] = true; }
+  if (db > 0) { if (db - 1 >= m || used[db - 1]) return false; used[db - 1] = true; }
+  return true;
+}
+GPISA_HD constexpr int if_form_index(int dc, int da, int db) {
+  int idx = 0;
+  for (int t = 0; t < dc * 16 + da * 4 + db; ++t)
+    if (if_desc_valid(t / 16, (t / 4) % 4, t % 4)) ++idx;
+  return idx;
+}
+GPISA_HD constexpr int if_form_desc(int idx) {  // inverse: returns dc*16+da*4+db
+  int seen = 0;
+  for (int t = 0; t < 64; ++t)
+    if (if_desc_valid(t / 16, (t / 4) % 4, t % 4)) { if (seen == idx) return t; ++seen; }
+  return -1;
+}
+constexpr int BOOL_IF_FORMS = 16;
+GPISA_HD constexpr int bool_if_code(int iform, int level) { return BOOL_IF_BASE + iform * R + level; }
+constexpr int BOOL_MOVX = BOOL_IF_BASE + BOOL_IF_FORMS * R;  // 288
+constexpr int BOOL_NCODES = BOOL_MOVX + 1;
+
+// header word 0
+GPISA_HD constexpr uint32_t header0(uint32_t kind, uint32_t order) {
+  return kind | (order << 8) | (VERSION << 16);
+}
+
+}  // namespace gpisa

@@ -1,0 +1,148 @@
+"""Test-side reader of the encoded instruction streams (host, numpy binary32).
+
+It restates the documented layout of the encoded programs (header of four
+words, then four words per instruction: code, payloads) and runs them case by
+case with numpy float32 arithmetic, so that the host encoder can be checked
+against the CPU oracle without a GPU.  It is test code only.
+"""
+import numpy as np
+
+R = 8
+F_NAMES = "+-*/"
+SF_FORMS = ["XX", "XC", "CX", "CC", "SX", "XS", "SC", "CS", "SS", "SSR", "MOVX", "MOVC"]
+RF_FORMS = ["PUSHX", "PUSHC", "OP", "OPR"]
+BF_FORMS = ["XX", "XS", "SX", "SS", "SSR"]
+BOOL_IF_BASE = 5 * R * 4
+BOOL_MOVX = BOOL_IF_BASE + 16 * R
+
+
+def if_descs():
+    out = []
+    for t in range(64):
+        dc, da, db = t // 16, (t // 4) % 4, t % 4
+        m = (dc > 0) + (da > 0) + (db > 0)
+        used = []
+        ok = True
+        for d in (dc, da, db):
+            if d > 0:
+                if d - 1 >= m or (d - 1) in used:
+                    ok = False
+                used.append(d - 1)
+        if ok:
+            out.append((dc, da, db))
+    assert len(out) == 16
+    return out
+
+
+IF_DESCS = if_descs()
+
+
+def header(words):
+    w = np.asarray(words, np.uint32)
+    return {"kind": int(w[0]) & 0xFF, "order": (int(w[0]) >> 8) & 0xFF, "version": int(w[0]) >> 16,
+            "n_instr": int(w[1]), "n_nodes": int(w[2]), "max_depth": int(w[3]) & 0xFFFF,
+            "n_inputs_used": int(w[3]) >> 16}
+
+
+def instrs(words):
+    w = np.asarray(words, np.uint32)
+    n = int(w[1])
+    return [tuple(int(v) for v in w[4 + 4 * i: 8 + 4 * i]) for i in range(n)]
+
+
+def _f(bits):
+    return np.uint32(bits).view(np.float32)
+
+
+def _apply(op, a, b):
+    with np.errstate(all="ignore"):
+        if op == 0:
+            return (a + b).astype(np.float32)
+        if op == 1:
+            return (a - b).astype(np.float32)
+        if op == 2:
+            return (a * b).astype(np.float32)
+        safe = np.where(b == 0, np.float32(1), b)
+        return np.where(b == 0, np.float32(1), a / safe).astype(np.float32)
+
+
+def run_float(words, x):
+    """Per-case outputs of an encoded float program (S-form, RPN or register)."""
+    x = np.asarray(x, np.float32)
+    n_cases = x.shape[1]
+    h = header(words)
+    full = lambda v: np.full(n_cases, v, np.float32)
+    if h["kind"] == 3:
+        r = [x[i].copy() if i < x.shape[0] else full(0.0) for i in range(8)]
+        for code, d, _, _ in instrs(words):
+            op, a, b = code // 64, (code // 8) % 8, code % 8
+            r[d] = _apply(op, r[a], r[b])
+        return r[0]
+    S = [None] * R
+    for code, pa, pb, _ in instrs(words):
+        op, lvl, form = code & 3, (code >> 2) % R, (code >> 2) // R
+        if h["kind"] == 1:
+            name = SF_FORMS[form]
+            X = lambda v: x[v]
+            C = lambda bits: full(_f(bits))
+            if name == "MOVX":
+                S[0] = x[pa].copy(); continue
+            if name == "MOVC":
+                S[0] = C(pa); continue
+            src = {"X": None, "C": None}
+            if name in ("SS", "SSR"):
+                a, b = (S[lvl], S[lvl + 1]) if name == "SS" else (S[lvl + 1], S[lvl])
+            else:
+                ka, kb = name[0], name[1]
+                a = S[lvl] if ka == "S" else (X(pa) if ka == "X" else C(pa))
+                b = S[lvl] if kb == "S" else (X(pb) if kb == "X" else C(pb))
+            S[lvl] = _apply(op, a, b)
+        else:
+            name = RF_FORMS[form]
+            if name == "PUSHX":
+                S[lvl] = x[pa].copy()
+            elif name == "PUSHC":
+                S[lvl] = full(_f(pa))
+            elif name == "OP":
+                S[lvl] = _apply(op, S[lvl], S[lvl + 1])
+            else:
+                S[lvl] = _apply(op, S[lvl + 1], S[lvl])
+    return S[0]
+
+
+def run_bool(words, bits):
+    bits = np.asarray(bits, np.uint32)
+    S = [None] * R
+    for code, pa, pb, pc in instrs(words):
+        if code == BOOL_MOVX:
+            S[0] = bits[pa].copy(); continue
+        if code >= BOOL_IF_BASE:
+            f, lvl = (code - BOOL_IF_BASE) // R, (code - BOOL_IF_BASE) % R
+            ds = IF_DESCS[f]
+            vals = [bits[p] if d == 0 else S[lvl + d - 1] for d, p in zip(ds, (pa, pb, pc))]
+            c, a, b = vals
+            S[lvl] = ((c & a) | (~c & b)).astype(np.uint32)
+            continue
+        op, lvl, form = code & 3, (code >> 2) % R, (code >> 2) // R
+        name = BF_FORMS[form]
+        if name == "SS":
+            a, b = S[lvl], S[lvl + 1]
+        elif name == "SSR":
+            a, b = S[lvl + 1], S[lvl]
+        else:
+            a = S[lvl] if name[0] == "S" else bits[pa]
+            b = S[lvl] if name[1] == "S" else bits[pb]
+        v = [a & b, a | b, ~(a & b), ~(a | b)][op]
+        S[lvl] = np.asarray(v, np.uint32)
+    return S[0]
+
+
+def render_sform(words):
+    """Text of an encoded S-form program in the paper's notation, e.g. '+(XX) *(XS)'."""
+    out = []
+    for code, _, _, _ in instrs(words):
+        op, form = code & 3, (code >> 2) // R
+        name = SF_FORMS[form]
+        ops = {"SSR": "SS"}.get(name, name)
+        out.append(f"{F_NAMES[op]}({ops})")
+    return " ".join(out)

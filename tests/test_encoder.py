@@ -1,0 +1,222 @@
+"""Host encoder tests (CPU): the paper's worked example, stack-depth bounds,
+and encoded programs evaluated by the test-side reader against the oracle."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1601_00221_gb300 as gp
+from synth import ADD, SUB, MUL, DIV, VAR, CONST, tok, const_tokens
+import encoded_ref as ref
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sec5_worked_example.txt")
+
+
+def load_golden():
+    d = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            d[k.strip()] = v.strip()
+    return d
+
+
+def parse_rpn_text(s):
+    """'(A,B)op' nested RPN text of the paper -> prefix tokens (X = input 0)."""
+    ops = {"+": ADD, "-": SUB, "*": MUL, "/": DIV}
+    pos = 0
+
+    def elem():
+        nonlocal pos
+        if s[pos] == "X":
+            pos += 1
+            return [tok(VAR, 0)]
+        assert s[pos] == "("
+        pos += 1
+        a = elem()
+        assert s[pos] == ","
+        pos += 1
+        b = elem()
+        assert s[pos] == ")"
+        pos += 1
+        op = ops[s[pos]]
+        pos += 1
+        return [tok(op)] + a + b
+    t = elem()
+    assert pos == len(s)
+    return t
+
+
+def same_bits(a, b):
+    a = np.asarray(a, np.float32)
+    b = np.asarray(b, np.float32)
+    return np.all((a.view(np.uint32) == b.view(np.uint32)) | (np.isnan(a) & np.isnan(b)))
+
+
+def test_worked_example_sec5():
+    g = load_golden()
+    prog = parse_rpn_text(g["rpn"])
+    assert oracle.tree_nodes(prog) == int(g["nodes"])
+    w, info = gp.encode_tree(prog, gp.KIND_SFORM, gp.ORDER_PAPER)
+    assert ref.render_sform(w) == g["sform"]
+    assert info["n_instr"] == int(g["sform_instructions"])
+    assert info["n_instr"] + 2 * info["n_instr"] == int(g["sform_values"])  # functions + operands
+    assert info["stack_reads"] == int(g["sform_stack_fetches"])
+    assert info["max_depth"] == int(g["sform_max_stack"])
+    w, info = gp.encode_tree(prog, gp.KIND_RPN, gp.ORDER_PAPER)
+    assert info["n_instr"] == int(g["rpn_instructions"])
+    assert info["stack_reads"] == int(g["rpn_stack_fetches"])
+    assert info["max_depth"] == int(g["rpn_max_stack"])
+
+
+def postfix_depth(prog):
+    """Classical stack depth of the postfix order (children left to right)."""
+    d, best = 0, 0
+    # postfix = reverse of the right-to-left prefix scan's push sequence; scan
+    # recursively instead
+    pos = 0
+
+    def rec():
+        nonlocal pos, d, best
+        t = int(prog[pos]); op = t & 0xFF
+        pos += 2 if op == CONST else 1
+        if op in (VAR, CONST):
+            d += 1
+            best = max(best, d)
+            return
+        rec(); rec()
+        d -= 1
+    rec()
+    return best
+
+
+def sethi_ullman(prog):
+    """Registers needed when terminals need none and the bigger child goes first."""
+    pos = 0
+
+    def rec():
+        nonlocal pos
+        t = int(prog[pos]); op = t & 0xFF
+        pos += 2 if op == CONST else 1
+        if op in (VAR, CONST):
+            return 0
+        a, b = rec(), rec()
+        if a == 0 and b == 0:
+            return 1
+        return max(a, b) if a != b else a + 1
+    return rec()
+
+
+def test_depths_match_independent_counts():
+    progs = synth.ramped_half_and_half(51, 300, 2, 8, 255, n_inputs=2)
+    for p in progs:
+        _, info = gp.encode_tree(p, gp.KIND_RPN, gp.ORDER_PAPER)
+        assert info["max_depth"] == postfix_depth(p)
+        _, info = gp.encode_tree(p, gp.KIND_SFORM, gp.ORDER_MIN_DEPTH)
+        assert info["max_depth"] == max(1, sethi_ullman(p))
+        assert info["n_nodes"] == synth.count_nodes(p)
+
+
+def chain_tree(n_funcs):
+    """Right-leaning chain f(x, f(x, ...)): deep in paper order."""
+    t = []
+    for i in range(n_funcs):
+        t += [tok([ADD, SUB, MUL, DIV][i % 4]), tok(VAR, 0)]
+    return t + [tok(VAR, 0)]
+
+
+def balanced(depth):
+    if depth == 1:
+        return [tok(VAR, 0)]
+    return [tok(SUB)] + balanced(depth - 1) + balanced(depth - 1)
+
+
+def test_min_depth_fits_register_levels():
+    # a full tree of 255 functions (depth 9) needs 8 S-form levels
+    p = balanced(9)
+    _, info = gp.encode_tree(p, gp.KIND_SFORM, gp.ORDER_MIN_DEPTH)
+    assert info["max_depth"] == 8
+    # a left-deep-right chain is shallow in either order for S-form
+    _, info = gp.encode_tree(chain_tree(100), gp.KIND_SFORM, gp.ORDER_PAPER)
+    assert info["max_depth"] == 1
+    # in RPN paper order the chain is too deep for the register levels
+    with pytest.raises(gp.GPError) as e:
+        gp.encode_tree(chain_tree(20), gp.KIND_RPN, gp.ORDER_PAPER)
+    assert e.value.code == 2
+    _, info = gp.encode_tree(chain_tree(20), gp.KIND_RPN, gp.ORDER_MIN_DEPTH)
+    assert info["max_depth"] == 2
+
+
+@pytest.mark.parametrize("kind", [gp.KIND_SFORM, gp.KIND_RPN])
+@pytest.mark.parametrize("order", [gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH])
+def test_encoded_programs_match_oracle(kind, order):
+    w = synth.regression_small(seed=61, n_progs=120, n_cases=97)
+    x = w.cases.copy()
+    x[0, :3] = [0.0, -0.0, 1e-40]
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, kind, order)
+    assert enc.nodes == int(w.pop.nodes.sum())
+    for p in range(w.pop.n):
+        words = enc.words[enc.offsets[p]: enc.offsets[p] + enc.lengths[p]]
+        assert same_bits(ref.run_float(words, x), oracle.tree_outputs(w.pop.program(p), x))
+
+
+def test_encoded_multi_input_and_single_terminals():
+    progs = synth.ramped_half_and_half(62, 80, 2, 5, 64, n_inputs=3)
+    progs += [np.array([tok(VAR, 2)], np.uint32), np.array(const_tokens(0.625), np.uint32)]
+    x = synth.uniform_cases(63, 3, 33)
+    for kind in (gp.KIND_SFORM, gp.KIND_RPN):
+        for p in progs:
+            words, info = gp.encode_tree(p, kind, gp.ORDER_MIN_DEPTH)
+            assert same_bits(ref.run_float(words, x), oracle.tree_outputs(p, x))
+
+
+def test_encoded_bool_matches_oracle():
+    for kind, k in (("parity", 6), ("mux", 6), ("mux", 11)):
+        w = synth.boolean_problem(kind, k, seed=64, n_progs=60)
+        enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL,
+                                   gp.ORDER_MIN_DEPTH)
+        for p in range(w.pop.n):
+            words = enc.words[enc.offsets[p]: enc.offsets[p] + enc.lengths[p]]
+            got = ref.run_bool(words, w.case_bits)
+            exp = oracle.bool_outputs(w.pop.program(p), w.case_bits)
+            assert np.array_equal(got, exp)
+
+
+def test_encoded_linear_matches_oracle():
+    pop = synth.linear_programs(65, 40, 1, 60)
+    x = synth.normal_cases(66, 8, 41)
+    enc = gp.encode_linear_population(pop.instr, pop.offsets, pop.lengths)
+    assert enc.nodes == int(pop.lengths.sum())
+    for p in range(pop.n):
+        words = enc.words[enc.offsets[p]: enc.offsets[p] + enc.lengths[p]]
+        assert same_bits(ref.run_float(words, x), oracle.linear_outputs(pop.program(p), x))
+
+
+@pytest.mark.parametrize("bad", [
+    [tok(ADD), tok(VAR, 0)],                      # missing operand
+    [tok(VAR, 0), tok(VAR, 0)],                    # trailing tokens
+    [tok(77)],                                     # unknown opcode
+    [tok(CONST)],                                  # constant without value
+    [tok(synth.AND), tok(VAR, 0), tok(VAR, 1)],    # Boolean function in a float tree
+])
+def test_malformed_trees_rejected(bad):
+    with pytest.raises(gp.GPError) as e:
+        gp.encode_tree(bad, gp.KIND_SFORM)
+    assert e.value.code == 2
+
+
+def test_population_reports_bad_index():
+    progs = [np.array([tok(VAR, 0)], np.uint32)] * 3 + [np.array([tok(ADD)], np.uint32)]
+    pop = synth.pack(progs)
+    with pytest.raises(gp.GPError):
+        gp.encode_population(pop.words, pop.offsets, pop.lengths)
+
+
+def test_programs_are_16_byte_aligned():
+    w = synth.regression_small(n_progs=33, n_cases=8)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    assert enc.words.ctypes.data % 16 == 0
+    assert np.all(enc.offsets % 4 == 0) and np.all(enc.lengths % 4 == 0)

@@ -221,6 +221,16 @@ def even_parity_program(k):
     return e
 
 
+def even_parity_program_if(k):
+    """Even-k-parity with XOR(a, b) = IF(a, NOR(b, b), b): linear in k."""
+    # XNOR(x0, x1) = IF(x0, x1, NOR(x1, x1))
+    e = [tok(IF), tok(VAR, 0), tok(VAR, 1), tok(NOR), tok(VAR, 1), tok(VAR, 1)]
+    for i in range(2, k):
+        xi = tok(VAR, i)
+        e = [tok(IF)] + e + [tok(NOR), xi, xi, xi]
+    return e
+
+
 def mux_program_if(k):
     a = synth.mux_address_bits(k)
 
@@ -240,6 +250,13 @@ def test_even_parity_program_scores_all_hits(k):
     assert oracle.bool_hits(prog, cb, 1 << k, t) == 1 << k
     if k == 6:
         assert oracle.tree_nodes(prog) == 187  # the paper-sized XOR chain for 6 inputs
+
+
+@pytest.mark.parametrize("k", [6, 11, 20])
+def test_even_parity_if_program_scores_all_hits(k):
+    prog = even_parity_program_if(k)
+    assert oracle.bool_hits(prog, synth.bool_case_bits(k), 1 << k, synth.even_parity_target(k)) == 1 << k
+    assert oracle.tree_nodes(prog) == 6 + 5 * (k - 2)
 
 
 @pytest.mark.parametrize("k", [6, 11])

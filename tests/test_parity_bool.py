@@ -1,0 +1,97 @@
+"""GPU parity of the bit-packed Boolean interpreter: hit counts and output
+words bit-exact against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1601_00221_gb300 as gp
+from gpu_util import dev, upload
+from synth import AND, OR, NAND, NOR, IF, VAR, tok
+
+pytestmark = pytest.mark.gpu
+
+PROBLEMS = [("parity", 6), ("mux", 6), ("parity", 11), ("mux", 11)]
+
+
+def run(w, k, block=0, n_cases=None, words=None):
+    n_cases = w.n_cases if n_cases is None else n_cases
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL,
+                               gp.ORDER_MIN_DEPTH)
+    P, O, L = upload(enc)
+    cb = dev(w.case_bits.view(np.int32))
+    tb = dev(w.target_bits.view(np.int32))
+    cfg = gp.Config(gp.VARIANT_REGISTER, k, block, 0)
+    hits = gp.eval_population_bool(P, O, L, cb, n_cases, tb, config=cfg).cpu().numpy()
+    import torch
+    nw = (n_cases + 31) // 32
+    out = torch.zeros((w.pop.n, nw), dtype=torch.int32, device="cuda")
+    gp.eval_population_bool(P, O, L, cb, n_cases, tb, hits_out=None, out_words=out, config=cfg)
+    return hits.astype(np.uint64), out.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("kind,k_inputs", PROBLEMS)
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_boolean_problems(kind, k_inputs, k):
+    w = synth.boolean_problem(kind, k_inputs, n_progs=512)
+    hits, out = run(w, k)
+    exp = oracle.bool_population_hits(w.pop.words, w.pop.offsets, w.pop.lengths, w.case_bits,
+                                      w.n_cases, w.target_bits)
+    assert np.array_equal(hits, exp)
+    for p in range(0, w.pop.n, 17):
+        assert np.array_equal(out[p], oracle.bool_outputs(w.pop.program(p), w.case_bits))
+
+
+def test_known_correct_programs_score_all_hits():
+    from test_oracle_pins import even_parity_program, even_parity_program_if, mux_program_if
+    for k_inputs in (6, 11):
+        make = even_parity_program if k_inputs == 6 else even_parity_program_if
+        progs = [np.array(make(k_inputs), np.uint32)]
+        pop = synth.pack(progs)
+        w = synth.BooleanWorkload("p", pop, synth.bool_case_bits(k_inputs),
+                                  synth.even_parity_target(k_inputs), 1 << k_inputs)
+        hits, _ = run(w, 2)
+        assert hits[0] == 1 << k_inputs
+        pop = synth.pack([np.array(mux_program_if(k_inputs), np.uint32)])
+        w = synth.BooleanWorkload("m", pop, synth.bool_case_bits(k_inputs),
+                                  synth.mux_target(k_inputs), 1 << k_inputs)
+        hits, _ = run(w, 2)
+        assert hits[0] == 1 << k_inputs
+
+
+@pytest.mark.parametrize("n_cases", [1, 5, 31, 33, 100, 1000])
+def test_ragged_case_counts(n_cases):
+    """Cases that do not fill the last word: the unused bits never count."""
+    k_inputs = 10
+    w = synth.boolean_problem("parity", k_inputs, seed=81, n_progs=64)
+    nw = (n_cases + 31) // 32
+    cb = np.ascontiguousarray(w.case_bits[:, :nw])
+    tb = np.ascontiguousarray(w.target_bits[:nw])
+    w2 = synth.BooleanWorkload("r", w.pop, cb, tb, n_cases)
+    for k in (1, 4):
+        hits, out = run(w2, k, n_cases=n_cases)
+        exp = oracle.bool_population_hits(w.pop.words, w.pop.offsets, w.pop.lengths, cb, n_cases, tb)
+        assert np.array_equal(hits, exp)
+
+
+def test_large_multiplexer_sampled():
+    """20-multiplexer shape of the paper (2^20 cases = 32768 words)."""
+    w = synth.boolean_problem("mux", 20, n_progs=256)
+    hits, _ = run(w, 4)
+    for p in range(0, 256, 16):
+        exp = oracle.bool_hits(w.pop.program(p), w.case_bits, w.n_cases, w.target_bits)
+        assert hits[p] == exp
+
+
+def test_malformed_bool_program():
+    w = synth.boolean_problem("mux", 6, n_progs=4)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL)
+    words = enc.words.copy()
+    words[int(enc.offsets[1]) + 4] = 9999
+    P = dev(words.view(np.int32))
+    gp.last_error()
+    hits = gp.eval_population_bool(P, dev(enc.offsets), dev(enc.lengths),
+                                   dev(w.case_bits.view(np.int32)), w.n_cases,
+                                   dev(w.target_bits.view(np.int32))).cpu().numpy().view(np.uint64)
+    assert hits[1] == np.uint64(0xFFFFFFFFFFFFFFFF)
+    assert gp.last_error() == 2

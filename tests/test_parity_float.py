@@ -1,0 +1,222 @@
+"""GPU parity of the binary32 interpreters against the CPU oracle.
+
+Per-case outputs must match bit for bit (any NaN equals any NaN); fitness must
+lie within 1e-5 relative of the binary64 oracle (exactly equal when the oracle
+gives 0 or +inf).  Calls go through the C ABI (ctypes binding).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1601_00221_gb300 as gp
+from gpu_util import dev, upload, assert_bits, assert_fitness, oracle_outputs, rel_errors
+from synth import ADD, SUB, MUL, DIV, VAR, tok, const_tokens
+
+pytestmark = pytest.mark.gpu
+
+KS = [1, 2, 4, 8]
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = synth.regression_small()  # 256 trees, depth 2-6, 1024 cases
+    x = w.cases.copy()
+    x[0, :4] = [0.0, -0.0, 1e-40, -1.0]  # protected division and subnormals
+    y = synth.quartic_target(x[0])
+    ref = oracle_outputs(w.pop, x)
+    fit = oracle.population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, x, y)
+    return w, x, y, ref, fit
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("kind", [gp.KIND_SFORM, gp.KIND_RPN])
+@pytest.mark.parametrize("order", [gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH])
+def test_small_regression_all_k(small, k, kind, order):
+    w, x, y, ref, fit = small
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, kind, order)
+    P, O, L = upload(enc)
+    X, Y = dev(x), dev(y)
+    for block in (32, 128):
+        cfg = gp.Config(gp.VARIANT_REGISTER, k, block, 0)
+        out = gp.eval_outputs(P, O, L, X, config=cfg)
+        assert_bits(out.cpu().numpy(), ref, f"outputs k={k} block={block}")
+        f = gp.eval_population(P, O, L, X, Y, config=cfg)
+        assert_fitness(f.cpu().numpy(), fit, f"fitness k={k} block={block}")
+    assert gp.last_error() == 0
+
+
+def test_blockgp_local_stack(small):
+    w, x, y, ref, fit = small
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_RPN,
+                               gp.ORDER_PAPER)
+    P, O, L = upload(enc)
+    cfg = gp.Config(gp.VARIANT_LOCAL, 1, 256, 0)
+    out = gp.eval_outputs(P, O, L, dev(x), config=cfg)
+    assert_bits(out.cpu().numpy(), ref, "blockgp outputs")
+    f = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg)
+    assert_fitness(f.cpu().numpy(), fit, "blockgp fitness")
+
+
+@pytest.mark.parametrize("n_cases", [0, 1, 3, 31, 1000, 1027, 4099])
+@pytest.mark.parametrize("k", [1, 4, 8])
+def test_ragged_case_counts_and_chunks(n_cases, k):
+    w = synth.regression_small(seed=71, n_progs=40, n_cases=max(n_cases, 1))
+    x = w.cases[:, :n_cases].copy()
+    y = synth.quartic_target(x[0])
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    P, O, L = upload(enc)
+    # small chunks force many blocks per program and the fused cross-block sum
+    for chunk in (0, 64 * k):
+        cfg = gp.Config(gp.VARIANT_REGISTER, k, 64, chunk)
+        f = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy()
+        exp = oracle.population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, x, y)
+        assert_fitness(f, exp, f"n_cases={n_cases} chunk={chunk}")
+        if n_cases:
+            out = gp.eval_outputs(P, O, L, dev(x), config=cfg).cpu().numpy()
+            assert_bits(out, oracle_outputs(w.pop, x), f"outputs n_cases={n_cases}")
+
+
+@pytest.mark.parametrize("k", KS)
+def test_multi_input_programs(k):
+    progs = synth.ramped_half_and_half(72, 96, 2, 7, 127, n_inputs=5)
+    progs.append(np.array([tok(VAR, 4)], np.uint32))
+    progs.append(np.array(const_tokens(-0.375), np.uint32))
+    pop = synth.pack(progs)
+    x = synth.uniform_cases(73, 5, 2053)
+    y = synth.uniform_cases(74, 1, 2053)[0]
+    for kind in (gp.KIND_SFORM, gp.KIND_RPN):
+        enc = gp.encode_population(pop.words, pop.offsets, pop.lengths, kind, gp.ORDER_MIN_DEPTH)
+        P, O, L = upload(enc)
+        cfg = gp.Config(gp.VARIANT_REGISTER, k, 128, 0)
+        out = gp.eval_outputs(P, O, L, dev(x), config=cfg).cpu().numpy()
+        assert_bits(out, oracle_outputs(pop, x), f"multi-input kind={kind}")
+        f = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy()
+        assert_fitness(f, oracle.population_fitness(pop.words, pop.offsets, pop.lengths, x, y))
+
+
+def test_nonfinite_and_special_values():
+    big = const_tokens(3e38)
+    progs = [
+        [tok(MUL)] + big + big,                               # +inf everywhere
+        [tok(SUB), tok(MUL)] + big + big + [tok(MUL)] + big + big,  # NaN
+        [tok(DIV), tok(VAR, 0), tok(VAR, 0)],                  # 1 everywhere (protected at 0)
+        [tok(DIV)] + const_tokens(1.0) + [tok(VAR, 0)],        # 1/x: protected at +-0, +inf at 1e-45
+        [tok(SUB), tok(VAR, 0), tok(VAR, 0)],
+        list(synth.quartic_program()),
+    ]
+    pop = synth.pack([np.array(p, np.uint32) for p in progs])
+    x = synth.uniform_cases(75, 1, 777)
+    x[0, :5] = [0.0, -0.0, 1e-45, -1e-45, 3.4e38]
+    y = synth.quartic_target(x[0])
+    exp_out = oracle_outputs(pop, x)
+    exp_fit = oracle.population_fitness(pop.words, pop.offsets, pop.lengths, x, y)
+    assert np.isinf(exp_fit[0]) and np.isinf(exp_fit[1])
+    for k in KS:
+        enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+        P, O, L = upload(enc)
+        cfg = gp.Config(gp.VARIANT_REGISTER, k, 64, 0)
+        assert_bits(gp.eval_outputs(P, O, L, dev(x), config=cfg).cpu().numpy(), exp_out, f"k={k}")
+        f = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy()
+        assert_fitness(f, exp_fit, f"k={k}")
+
+
+def test_malformed_device_program_gives_nan_and_status():
+    w = synth.regression_small(n_progs=8, n_cases=256)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    words = enc.words.copy()
+    o = int(enc.offsets[3])
+    words[o + 4] = 0xFFFF          # unknown instruction code in program 3
+    o5 = int(enc.offsets[5])
+    words[o5 + 1] = 5000            # header claims more instructions than fit
+    P = dev(words.view(np.int32))
+    O, L = dev(enc.offsets), dev(enc.lengths)
+    gp.last_error()  # clear
+    f = gp.eval_population(P, O, L, dev(w.cases), dev(w.targets)).cpu().numpy()
+    assert np.isnan(f[3]) and np.isnan(f[5])
+    good = [p for p in range(8) if p not in (3, 5)]
+    exp = oracle.population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, w.cases, w.targets)
+    assert_fitness(f[good], exp[good])
+    assert gp.last_error() == 2
+    assert gp.last_error() == 0  # cleared by the read
+
+
+def test_input_index_beyond_n_inputs_is_rejected_on_device():
+    pop = synth.pack([np.array([tok(ADD), tok(VAR, 0), tok(VAR, 3)], np.uint32)])
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    P, O, L = upload(enc)
+    x = synth.uniform_cases(76, 2, 64)   # only 2 inputs
+    gp.last_error()
+    f = gp.eval_population(P, O, L, dev(x), dev(x[0])).cpu().numpy()
+    assert np.isnan(f[0])
+    assert gp.last_error() == 2
+
+
+@pytest.mark.parametrize("k", KS)
+def test_register_linear_gp(k):
+    w = synth.linear_workload(seed=77, n_progs=128, n_cases=4099)
+    x = w.cases.copy()
+    x[:, :2] = 0.0
+    enc = gp.encode_linear_population(w.pop.instr, w.pop.offsets, w.pop.lengths)
+    P, O, L = upload(enc)
+    cfg = gp.Config(gp.VARIANT_REGISTER, k, 128, 0)
+    out = gp.eval_outputs(P, O, L, dev(x), config=cfg).cpu().numpy()
+    exp = np.stack([oracle.linear_outputs(w.pop.program(p), x) for p in range(w.pop.n)])
+    assert_bits(out, exp, "linear outputs")
+    f = gp.eval_population(P, O, L, dev(x), dev(w.targets), config=cfg).cpu().numpy()
+    fit = oracle.linear_population_fitness(w.pop.instr, w.pop.offsets, w.pop.lengths, x, w.targets)
+    assert_fitness(f, fit, "linear fitness")
+
+
+def test_mixed_kinds_in_one_launch():
+    w = synth.regression_small(seed=78, n_progs=30, n_cases=515)
+    sf = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM)
+    rp = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_RPN)
+    words = np.concatenate([sf.words, rp.words])
+    offs = np.concatenate([sf.offsets, rp.offsets + sf.words.size])
+    lens = np.concatenate([sf.lengths, rp.lengths])
+    P = dev(words.view(np.int32))
+    f = gp.eval_population(P, dev(offs), dev(lens), dev(w.cases), dev(w.targets)).cpu().numpy()
+    exp = oracle.population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, w.cases, w.targets)
+    assert_fitness(f, np.concatenate([exp, exp]))
+    assert np.array_equal(f[:30], f[30:])  # same order of summation for both kinds
+
+
+def test_fitness_bit_identical_across_runs_and_streams():
+    import torch
+    w = synth.regression_small(seed=79, n_progs=64, n_cases=3000)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    P, O, L = upload(enc)
+    X, Y = dev(w.cases), dev(w.targets)
+    f0 = gp.eval_population(P, O, L, X, Y).cpu().numpy()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        f1 = gp.eval_population(P, O, L, X, Y, stream=s)
+    s.synchronize()
+    assert np.array_equal(f0, f1.cpu().numpy())
+
+
+@pytest.mark.parametrize("k", [1, 8])
+def test_full_size_regression_sampled(k):
+    """4096 trees (depth 2-8, <= 256 nodes) x 65536 cases, the benchmark's
+    configuration; the oracle checks a sample of 48 programs entirely."""
+    w = synth.regression_large()
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM,
+                               gp.ORDER_MIN_DEPTH)
+    P, O, L = upload(enc)
+    X, Y = dev(w.cases), dev(w.targets)
+    cfg = gp.Config(gp.VARIANT_REGISTER, k, 128, 0)
+    f = gp.eval_population(P, O, L, X, Y, config=cfg).cpu().numpy()
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(w.pop.n, 48, replace=False))
+    exp = np.array([oracle.tree_fitness(w.pop.program(int(p)), w.cases, w.targets)
+                    for p in sample])
+    assert_fitness(f[sample], exp, "full-size sample")
+    # per-case outputs of a few sampled programs
+    for p in sample[:6]:
+        sub = gp.EncodedPopulation(enc.words, enc.offsets[p:p + 1], enc.lengths[p:p + 1],
+                                   0, enc.kind, enc.order)
+        Pp, Op, Lp = upload(sub)
+        out = gp.eval_outputs(Pp, Op, Lp, X, config=cfg).cpu().numpy()[0]
+        assert_bits(out, oracle.tree_outputs(w.pop.program(int(p)), w.cases), f"program {p}")
+    assert np.all(np.isfinite(f) | np.isinf(f))

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import hashlib
+import importlib.util
 import os
 import shutil
 import subprocess
@@ -21,10 +22,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgpeval.so")
+GEN = os.path.join(BUILD, "gen")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-ftz=false", "-prec-div=true",
-           "-prec-sqrt=true", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I", INCLUDE]
+           "-prec-sqrt=true", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I", INCLUDE, "-I", GEN]
 
 
 def _nvcc() -> str:
@@ -45,6 +47,8 @@ def _digest() -> str:
             h.update(f.encode() + fh.read())
     with open(os.path.join(INCLUDE, "gpeval.h"), "rb") as fh:
         h.update(fh.read())
+    with open(os.path.join(HERE, "gen_interp.py"), "rb") as fh:
+        h.update(fh.read())
     h.update(" ".join(ARCH + NVFLAGS).encode())
     return h.hexdigest()
 
@@ -58,6 +62,11 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
             if fh.read().strip() == digest:
                 return LIB
     nvcc = _nvcc()
+    # the interpreter loops are generated PTX (gen_interp.py)
+    spec = importlib.util.spec_from_file_location("gen_interp", os.path.join(HERE, "gen_interp.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    gen.write(os.path.join(GEN, "gen_interp.h"))
     objs = []
 
     def compile_one(src: str) -> str:

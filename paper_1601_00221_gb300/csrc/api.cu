@@ -95,6 +95,10 @@ int sm_count() {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// dynamic shared memory left for staged input tiles next to the 16 KB
+// program buffer (227 KB per block on sm_103a)
+constexpr size_t kMaxTileBytes = 200 * 1024;
+
 // Fills zero fields of `c` from the default configuration and checks it.
 int resolve_config(const gp_config* user, gp_config* c) {
   {
@@ -212,12 +216,17 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   a.want_fitness = fitness_out != nullptr;
   const int grid = n_progs * n_chunks;
   const bool xreg = (n_inputs == 1);
+  const size_t smem = float_tile_bytes(c.k, c.block, n_inputs);
+  if (c.variant != GP_VARIANT_LOCAL && smem > kMaxTileBytes)
+    return gp_fail(GP_ERR_INVALID_ARG,
+                   "%d inputs need %zu bytes of staged inputs per block (max %zu): lower k or block",
+                   n_inputs, smem, kMaxTileBytes);
   cudaError_t e;
   if (c.variant == GP_VARIANT_LOCAL) e = launch_blockgp(a, c.block, grid, s);
-  else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, s);
-  else if (c.k == 2) e = launch_float_k2(a, xreg, c.block, grid, s);
-  else if (c.k == 4) e = launch_float_k4(a, xreg, c.block, grid, s);
-  else e = launch_float_k8(a, xreg, c.block, grid, s);
+  else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, smem, s);
+  else if (c.k == 2) e = launch_float_k2(a, xreg, c.block, grid, smem, s);
+  else if (c.k == 4) e = launch_float_k4(a, xreg, c.block, grid, smem, s);
+  else e = launch_float_k8(a, xreg, c.block, grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return GP_OK;
 }
@@ -299,7 +308,11 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   a.chunk_words = chunk;
   a.n_chunks = (int32_t)n_chunks64;
   a.aligned = aligned16(case_bits) && aligned16(target_bits) && (n_inputs <= 1 || n_words % 4 == 0);
-  e = launch_bool(a, c.k, c.block, (int)(n_progs * n_chunks64), s);
+  const size_t smem = bool_tile_bytes(c.k, c.block, n_inputs);
+  if (smem > kMaxTileBytes)
+    return gp_fail(GP_ERR_INVALID_ARG, "%d inputs need %zu bytes of staged inputs per block (max %zu)",
+                   n_inputs, smem, kMaxTileBytes);
+  e = launch_bool(a, c.k, c.block, (int)(n_progs * n_chunks64), smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return GP_OK;
 }

@@ -3,12 +3,19 @@
 #include "launch.h"
 
 namespace gpdev {
-cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, cudaStream_t s) {
+template <int K>
+static void launch_k(const BoolArgs& a, int block, int grid, size_t smem, cudaStream_t s) {
+  static std::atomic<size_t> configured{0};
+  ensure_dynamic_smem(eval_bool_kernel<K>, smem, configured);
+  eval_bool_kernel<K><<<grid, block, smem, s>>>(a);
+}
+
+cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s) {
   switch (k) {
-    case 1: eval_bool_kernel<1><<<grid, block, 0, s>>>(a); break;
-    case 2: eval_bool_kernel<2><<<grid, block, 0, s>>>(a); break;
-    case 4: eval_bool_kernel<4><<<grid, block, 0, s>>>(a); break;
-    default: eval_bool_kernel<8><<<grid, block, 0, s>>>(a); break;
+    case 1: launch_k<1>(a, block, grid, smem, s); break;
+    case 2: launch_k<2>(a, block, grid, smem, s); break;
+    case 4: launch_k<4>(a, block, grid, smem, s); break;
+    default: launch_k<8>(a, block, grid, smem, s); break;
   }
   return cudaGetLastError();
 }

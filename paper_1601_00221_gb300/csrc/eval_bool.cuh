@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gen_interp.h"
 #include "isa.h"
 
 namespace gpdev {
@@ -54,96 +55,23 @@ __device__ __forceinline__ void uload(UVec<K>& d, const uint32_t* __restrict__ s
   }
 }
 
-template <int OP, int K>
-__device__ __forceinline__ void bop(UVec<K>& d, const UVec<K>& a, const UVec<K>& b) {
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if constexpr (OP == gpisa::B_AND) d.w[j] = a.w[j] & b.w[j];
-    else if constexpr (OP == gpisa::B_OR) d.w[j] = a.w[j] | b.w[j];
-    else if constexpr (OP == gpisa::B_NAND) d.w[j] = ~(a.w[j] & b.w[j]);
-    else d.w[j] = ~(a.w[j] | b.w[j]);
-  }
-}
+// The interpreter loop is generated inline PTX (gen_interp.py): stack levels
+// are K-word registers at static levels, every function is one lop3 per word.
+#define GP_BO1(o) "=r"(o[0])
+#define GP_BO2(o) "=r"(o[0]), "=r"(o[1])
+#define GP_BO4(o) GP_BO2(o), "=r"(o[2]), "=r"(o[3])
+#define GP_BO8(o) GP_BO4(o), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7])
+#define GP_BOOL_ASM(MAC, KK) \
+  asm volatile(MAC : GP_BO##KK(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile) : "memory")
 
 template <int K>
-struct BSrc {
-  const uint32_t* bits;
-  int64_t n_words, w0;
-  bool vec_ok;
-  __device__ __forceinline__ void get(UVec<K>& d, uint32_t v) const {
-    uload<K>(d, bits + (int64_t)v * n_words, w0, n_words, vec_ok);
-  }
-};
-
-template <int BF, int L, int OP, int K>
-__device__ __forceinline__ void bool_bin(UVec<K> (&S)[gpisa::R], const BSrc<K>& X, const uint4& in) {
-  using namespace gpisa;
-  UVec<K> a, b;
-  if constexpr (BF == BF_XX) { X.get(a, in.y); X.get(b, in.z); bop<OP, K>(S[L], a, b); }
-  else if constexpr (BF == BF_XS) { X.get(a, in.y); bop<OP, K>(S[L], a, S[L]); }
-  else if constexpr (BF == BF_SX) { X.get(b, in.z); bop<OP, K>(S[L], S[L], b); }
-  else if constexpr (BF == BF_SS) { bop<OP, K>(S[L], S[L], S[(L + 1) % R]); }
-  else { bop<OP, K>(S[L], S[(L + 1) % R], S[L]); }
-}
-
-// IF(c, a, b) = (c & a) | (~c & b); operand descriptors from the form index
-template <int IFORM, int L, int K>
-__device__ __forceinline__ void bool_if(UVec<K> (&S)[gpisa::R], const BSrc<K>& X, const uint4& in) {
-  using namespace gpisa;
-  constexpr int desc = if_form_desc(IFORM);
-  constexpr int dc = desc / 16, da = (desc / 4) % 4, db = desc % 4;
-  UVec<K> c, a, b;
-  if constexpr (dc == 0) X.get(c, in.y); else c = S[(L + dc - 1) % R];
-  if constexpr (da == 0) X.get(a, in.z); else a = S[(L + da - 1) % R];
-  if constexpr (db == 0) X.get(b, in.w); else b = S[(L + db - 1) % R];
-#pragma unroll
-  for (int j = 0; j < K; ++j) S[L].w[j] = (c.w[j] & a.w[j]) | (~c.w[j] & b.w[j]);
-}
-
-#define GPB_OPS4(M, F, L) M(F, L, 0) M(F, L, 1) M(F, L, 2) M(F, L, 3)
-#define GPB_LEVELS(M, F) M(F, 0) M(F, 1) M(F, 2) M(F, 3) M(F, 4) M(F, 5) M(F, 6) M(F, 7)
-#define GPB_LEVELS7(M, F) M(F, 0) M(F, 1) M(F, 2) M(F, 3) M(F, 4) M(F, 5) M(F, 6)
-
-template <int K>
-__device__ __forceinline__ bool run_bool(const uint4* __restrict__ prog, int n, UVec<K> (&S)[gpisa::R],
-                                         const BSrc<K>& X) {
-  using namespace gpisa;
-  for (int i = 0; i < n; ++i) {
-    const uint4 in = prog[i];
-    switch (in.x) {
-#define B_CASE(F, L, OP) \
-  case bool_bin_code(F, L, OP): bool_bin<F, L, OP, K>(S, X, in); continue;
-#define B_LEVEL(F, L) GPB_OPS4(B_CASE, F, L)
-      GPB_LEVELS(B_LEVEL, BF_XX)
-      GPB_LEVELS(B_LEVEL, BF_XS)
-      GPB_LEVELS(B_LEVEL, BF_SX)
-      GPB_LEVELS7(B_LEVEL, BF_SS)
-      GPB_LEVELS7(B_LEVEL, BF_SSR)
-#undef B_LEVEL
-#undef B_CASE
-#define IF_CASE(F, L) case bool_if_code(F, L): bool_if<F, L, K>(S, X, in); continue;
-      GPB_LEVELS(IF_CASE, 0)
-      GPB_LEVELS(IF_CASE, 1)
-      GPB_LEVELS(IF_CASE, 2)
-      GPB_LEVELS(IF_CASE, 3)
-      GPB_LEVELS(IF_CASE, 4)
-      GPB_LEVELS(IF_CASE, 5)
-      GPB_LEVELS(IF_CASE, 6)
-      GPB_LEVELS(IF_CASE, 7)
-      GPB_LEVELS(IF_CASE, 8)
-      GPB_LEVELS(IF_CASE, 9)
-      GPB_LEVELS(IF_CASE, 10)
-      GPB_LEVELS(IF_CASE, 11)
-      GPB_LEVELS(IF_CASE, 12)
-      GPB_LEVELS(IF_CASE, 13)
-      GPB_LEVELS(IF_CASE, 14)
-      GPB_LEVELS(IF_CASE, 15)
-#undef IF_CASE
-      case BOOL_MOVX: X.get(S[0], in.y); continue;
-      default: return false;
-    }
-  }
-  return true;
+__device__ __forceinline__ bool run_bool(uint32_t prog, uint32_t n, uint32_t tile, uint32_t (&o)[K]) {
+  uint32_t bad;
+  if constexpr (K == 1) GP_BOOL_ASM(GP_PTX_BOOL_K1, 1);
+  else if constexpr (K == 2) GP_BOOL_ASM(GP_PTX_BOOL_K2, 2);
+  else if constexpr (K == 4) GP_BOOL_ASM(GP_PTX_BOOL_K4, 4);
+  else GP_BOOL_ASM(GP_PTX_BOOL_K8, 8);
+  return bad == 0;
 }
 
 __device__ __forceinline__ bool valid_bool_instr(const uint4& in, int n_inputs) {
@@ -175,6 +103,7 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   __shared__ uint4 prog_s[MAX_INSTR];
   __shared__ unsigned long long red_s[32];
   __shared__ int meta_s;
+  extern __shared__ uint4 btile_s[];  // [warp][input][32 lanes][K words]
 
   const int item = blockIdx.x;
   const int p = item / a.n_chunks;
@@ -223,17 +152,27 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   const uint32_t last_mask = tail ? ((1u << tail) - 1u) : 0xffffffffu;
   uint32_t* out_row = a.out_words ? a.out_words + (int64_t)p * a.n_words : nullptr;
   unsigned long long hits = 0;
+  bool bad_pass = false;
 
+  const uint32_t prog_addr = (uint32_t)__cvta_generic_to_shared(prog_s);
+  uint32_t* tile = reinterpret_cast<uint32_t*>(btile_s) + (size_t)warp * a.n_inputs * 32 * K + lane * K;
+  const uint32_t tile_addr = (uint32_t)__cvta_generic_to_shared(tile);
+#pragma unroll 1
   for (int64_t wb = w_begin + (int64_t)warp * 32 * K; wb < w_end; wb += (int64_t)nwarps * 32 * K) {
     const int64_t w0 = wb + (int64_t)lane * K;
     const bool full = w0 + K <= a.n_words;
-    BSrc<K> X{a.case_bits, a.n_words, w0, full && a.aligned};
-    UVec<K> S[R];
-    run_bool<K>(prog_s, n_instr, S, X);
+    for (int v = 0; v < a.n_inputs; ++v) {
+      UVec<K> t;
+      uload<K>(t, a.case_bits + (int64_t)v * a.n_words, w0, a.n_words, full && a.aligned);
+#pragma unroll
+      for (int j = 0; j < K; ++j) tile[v * 32 * K + j] = t.w[j];
+    }
+    uint32_t o[K];
+    if (!run_bool<K>(prog_addr, (uint32_t)n_instr, tile_addr, o)) bad_pass = true;
     if (out_row) {
 #pragma unroll
       for (int j = 0; j < K; ++j)
-        if (w0 + j < a.n_words) out_row[w0 + j] = S[0].w[j];
+        if (w0 + j < a.n_words) out_row[w0 + j] = o[j];
     }
     if (a.target_bits) {
       UVec<K> t;
@@ -243,10 +182,17 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
       for (int j = 0; j < K; ++j) {
         const int64_t w = w0 + j;
         uint32_t m = (w < a.n_words - 1) ? 0xffffffffu : (w == a.n_words - 1 ? last_mask : 0u);
-        h += __popc(~(S[0].w[j] ^ t.w[j]) & m);
+        h += __popc(~(o[j] ^ t.w[j]) & m);
       }
       hits += h;
     }
+  }
+  if (__syncthreads_or(bad_pass ? 1 : 0)) {
+    if (tid == 0) {
+      atomicOr(a.status, 2 /* GP_ERR_PROGRAM */);
+      if (a.hits_out) atomicExch(&a.hits_out[p], ~0ull);
+    }
+    return;
   }
   if (!a.hits_out || !a.target_bits) return;
   // integer sums are exact, so any order gives the same hit count
@@ -260,4 +206,10 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   }
 }
 
+}  // namespace gpdev
+
+namespace gpdev {
+inline size_t bool_tile_bytes(int k, int block, int n_inputs) {
+  return (size_t)(block / 32) * (size_t)n_inputs * 32u * (size_t)k * sizeof(uint32_t);
+}
 }  // namespace gpdev

@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "gen_interp.h"
 #include "isa.h"
 
 namespace gpdev {
@@ -58,179 +59,71 @@ struct FloatArgs {
   int32_t want_fitness;  // compute the fitness (targets may be null only if n_cases == 0)
 };
 
-// Source of input operands for one pass.  With a single input the K values
-// are loaded once per pass into registers; otherwise each input operand is a
-// (cached) global load of K consecutive cases.
-template <int K, bool XREG>
-struct XSrc {
-  Vec<K> xv;
-  const float* cases;
-  int64_t n_cases, c0;
-  bool vec_ok;
-  __device__ __forceinline__ void get(Vec<K>& d, uint32_t v) const {
-    if constexpr (XREG) d = xv;
-    else vload<K>(d, cases + (int64_t)v * n_cases, c0, n_cases, vec_ok);
+// ---------------------------------------------------------------------------
+// The interpreter loops are generated inline PTX (gen_interp.py): one
+// brx.idx jump per instruction straight into the body of its (function,
+// operand forms, stack level), stack levels in fixed registers, case pairs in
+// f32x2 registers.  These wrappers bind the operands of each block.
+//   prog  shared-memory address of instruction 0
+//   n     instruction count
+//   x     the K input values (single-input programs)
+//   tile  shared-memory address of this lane's staged inputs (input v at
+//         tile + v * 128 * K bytes)
+// Each returns true unless an unknown instruction code was met.
+// ---------------------------------------------------------------------------
+#define GP_O1(o) "=f"(o[0])
+#define GP_O2(o) "=f"(o[0]), "=f"(o[1])
+#define GP_O4(o) GP_O2(o), "=f"(o[2]), "=f"(o[3])
+#define GP_O8(o) GP_O4(o), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
+#define GP_I1(x) "f"(x[0])
+#define GP_I2(x) "f"(x[0]), "f"(x[1])
+#define GP_I4(x) GP_I2(x), "f"(x[2]), "f"(x[3])
+#define GP_I8(x) GP_I4(x), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7])
+
+#define GP_TREE_REG(MAC, KK) \
+  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), GP_I##KK(x) : "memory")
+#define GP_TREE_SMEM(MAC, KK) \
+  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile) : "memory")
+#define GP_LIN(MAC, KK) \
+  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile), "r"(nin) : "memory")
+
+template <int K, bool XREG, bool RPN>
+__device__ __forceinline__ bool run_tree(uint32_t prog, uint32_t n, const float (&x)[K], uint32_t tile,
+                                         float (&o)[K]) {
+  uint32_t bad;
+  if constexpr (XREG && !RPN) {
+    if constexpr (K == 1) GP_TREE_REG(GP_PTX_SFORM_K1_REG, 1);
+    else if constexpr (K == 2) GP_TREE_REG(GP_PTX_SFORM_K2_REG, 2);
+    else if constexpr (K == 4) GP_TREE_REG(GP_PTX_SFORM_K4_REG, 4);
+    else GP_TREE_REG(GP_PTX_SFORM_K8_REG, 8);
+  } else if constexpr (XREG && RPN) {
+    if constexpr (K == 1) GP_TREE_REG(GP_PTX_RPN_K1_REG, 1);
+    else if constexpr (K == 2) GP_TREE_REG(GP_PTX_RPN_K2_REG, 2);
+    else if constexpr (K == 4) GP_TREE_REG(GP_PTX_RPN_K4_REG, 4);
+    else GP_TREE_REG(GP_PTX_RPN_K8_REG, 8);
+  } else if constexpr (!RPN) {
+    if constexpr (K == 1) GP_TREE_SMEM(GP_PTX_SFORM_K1_SMEM, 1);
+    else if constexpr (K == 2) GP_TREE_SMEM(GP_PTX_SFORM_K2_SMEM, 2);
+    else if constexpr (K == 4) GP_TREE_SMEM(GP_PTX_SFORM_K4_SMEM, 4);
+    else GP_TREE_SMEM(GP_PTX_SFORM_K8_SMEM, 8);
+  } else {
+    if constexpr (K == 1) GP_TREE_SMEM(GP_PTX_RPN_K1_SMEM, 1);
+    else if constexpr (K == 2) GP_TREE_SMEM(GP_PTX_RPN_K2_SMEM, 2);
+    else if constexpr (K == 4) GP_TREE_SMEM(GP_PTX_RPN_K4_SMEM, 4);
+    else GP_TREE_SMEM(GP_PTX_RPN_K8_SMEM, 8);
   }
-};
-
-// ---------------------------------------------------------------------------
-// S-form instruction bodies.
-// ---------------------------------------------------------------------------
-template <int FORM, int L, int K, bool XREG>
-__device__ __forceinline__ void sf_fetch(Vec<K>& a, Vec<K>& b, Vec<K> (&S)[R], const XSrc<K, XREG>& X,
-                                         const uint4& in) {
-  using namespace gpisa;
-  if constexpr (FORM == SF_XX) { X.get(a, in.y); X.get(b, in.z); }
-  else if constexpr (FORM == SF_XC) { X.get(a, in.y); vbroadcast<K>(b, __uint_as_float(in.z)); }
-  else if constexpr (FORM == SF_CX) { vbroadcast<K>(a, __uint_as_float(in.y)); X.get(b, in.z); }
-  else if constexpr (FORM == SF_CC) { vbroadcast<K>(a, __uint_as_float(in.y)); vbroadcast<K>(b, __uint_as_float(in.z)); }
-  else if constexpr (FORM == SF_SX) { a = S[L]; X.get(b, in.z); }
-  else if constexpr (FORM == SF_XS) { X.get(a, in.y); b = S[L]; }
-  else if constexpr (FORM == SF_SC) { a = S[L]; vbroadcast<K>(b, __uint_as_float(in.z)); }
-  else if constexpr (FORM == SF_CS) { vbroadcast<K>(a, __uint_as_float(in.y)); b = S[L]; }
-  else if constexpr (FORM == SF_SS) { a = S[L]; b = S[(L + 1) % R]; }
-  else if constexpr (FORM == SF_SSR) { a = S[(L + 1) % R]; b = S[L]; }
+  return bad == 0;
 }
 
-template <int FORM, int L, int OP, int K, bool XREG>
-__device__ __forceinline__ void sf_exec(Vec<K> (&S)[R], const XSrc<K, XREG>& X, const uint4& in) {
-  Vec<K> a, b;
-  sf_fetch<FORM, L, K, XREG>(a, b, S, X, in);
-  vop<OP, K>(S[L], a, b);
-}
-
-// store a division result (or a register-GP result) into level/register `l`
 template <int K>
-__device__ __forceinline__ void store_level(Vec<K> (&S)[R], int l, const Vec<K>& q) {
-  switch (l) {
-    case 0: S[0] = q; break;
-    case 1: S[1] = q; break;
-    case 2: S[2] = q; break;
-    case 3: S[3] = q; break;
-    case 4: S[4] = q; break;
-    case 5: S[5] = q; break;
-    case 6: S[6] = q; break;
-    default: S[7] = q; break;
-  }
-}
-
-#define GP_OPS3(M, F, L) M(F, L, 0) M(F, L, 1) M(F, L, 2)
-#define GP_LEVELS(M, F) M(F, 0) M(F, 1) M(F, 2) M(F, 3) M(F, 4) M(F, 5) M(F, 6) M(F, 7)
-#define GP_LEVELS7(M, F) M(F, 0) M(F, 1) M(F, 2) M(F, 3) M(F, 4) M(F, 5) M(F, 6)
-
-// One pass of an S-form program over K cases per thread.  Returns false on an
-// unknown instruction code (validated before the first pass, so unreachable).
-template <int K, bool XREG>
-__device__ __forceinline__ bool run_sform(const uint4* __restrict__ prog, int n, Vec<K> (&S)[R],
-                                          const XSrc<K, XREG>& X) {
-  using namespace gpisa;
-  Vec<K> ta, tb;
-  int dl = 0;
-  for (int i = 0; i < n; ++i) {
-    const uint4 in = prog[i];
-    switch (in.x) {
-#define SF_CASE(F, L, OP) \
-  case sform_code(F, L, OP): sf_exec<F, L, OP, K, XREG>(S, X, in); continue;
-#define SF_DIV(F, L) \
-  case sform_code(F, L, F_DIV): sf_fetch<F, L, K, XREG>(ta, tb, S, X, in); dl = L; goto do_div;
-#define SF_LEVEL(F, L) GP_OPS3(SF_CASE, F, L) SF_DIV(F, L)
-      GP_LEVELS(SF_LEVEL, SF_XX)
-      GP_LEVELS(SF_LEVEL, SF_XC)
-      GP_LEVELS(SF_LEVEL, SF_CX)
-      GP_LEVELS(SF_LEVEL, SF_CC)
-      GP_LEVELS(SF_LEVEL, SF_SX)
-      GP_LEVELS(SF_LEVEL, SF_XS)
-      GP_LEVELS(SF_LEVEL, SF_SC)
-      GP_LEVELS(SF_LEVEL, SF_CS)
-      GP_LEVELS7(SF_LEVEL, SF_SS)
-      GP_LEVELS7(SF_LEVEL, SF_SSR)
-#undef SF_LEVEL
-#undef SF_DIV
-#undef SF_CASE
-      case sform_code(SF_MOVX, 0, 0): X.get(S[0], in.y); continue;
-      case sform_code(SF_MOVC, 0, 0): vbroadcast<K>(S[0], __uint_as_float(in.y)); continue;
-      default: return false;
-    }
-  do_div:
-    vop<F_DIV, K>(ta, ta, tb);
-    store_level<K>(S, dl, ta);
-  }
-  return true;
-}
-
-// ---------------------------------------------------------------------------
-// RPN (postfix) bodies: push a terminal to level l, or combine l and l+1.
-// ---------------------------------------------------------------------------
-template <int K, bool XREG>
-__device__ __forceinline__ bool run_rpn(const uint4* __restrict__ prog, int n, Vec<K> (&S)[R],
-                                        const XSrc<K, XREG>& X) {
-  using namespace gpisa;
-  Vec<K> ta, tb;
-  int dl = 0;
-  for (int i = 0; i < n; ++i) {
-    const uint4 in = prog[i];
-    switch (in.x) {
-#define RP_PUSH(F, L) \
-  case rpn_code(RF_PUSHX, L, 0): X.get(S[L], in.y); continue; \
-  case rpn_code(RF_PUSHC, L, 0): vbroadcast<K>(S[L], __uint_as_float(in.y)); continue;
-#define RP_OP(F, L, OP) \
-  case rpn_code(RF_OP, L, OP): vop<OP, K>(S[L], S[L], S[L + 1]); continue; \
-  case rpn_code(RF_OPR, L, OP): vop<OP, K>(S[L], S[L + 1], S[L]); continue;
-#define RP_LEVEL(F, L) GP_OPS3(RP_OP, F, L) \
-  case rpn_code(RF_OP, L, F_DIV): ta = S[L]; tb = S[L + 1]; dl = L; goto do_div; \
-  case rpn_code(RF_OPR, L, F_DIV): ta = S[L + 1]; tb = S[L]; dl = L; goto do_div;
-      GP_LEVELS(RP_PUSH, 0)
-      GP_LEVELS7(RP_LEVEL, 0)
-#undef RP_LEVEL
-#undef RP_OP
-#undef RP_PUSH
-      default: return false;
-    }
-  do_div:
-    vop<F_DIV, K>(ta, ta, tb);
-    store_level<K>(S, dl, ta);
-  }
-  return true;
-}
-
-// ---------------------------------------------------------------------------
-// Register linear GP: r[d] = r[a] op r[b]; the code selects (op, a, b), the
-// first payload word is d.
-// ---------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ bool run_linear(const uint4* __restrict__ prog, int n, Vec<K> (&r)[R]) {
-  using namespace gpisa;
-  Vec<K> t, tb;
-  for (int i = 0; i < n; ++i) {
-    const uint4 in = prog[i];
-    switch (in.x) {
-#define LN_CASE(OP, A, B) \
-  case lin_code(OP, A, B): vop<OP, K>(t, r[A], r[B]); goto do_store;
-#define LN_DIV(A, B) \
-  case lin_code(F_DIV, A, B): t = r[A]; tb = r[B]; goto do_div;
-#define LN_B(OP, A) LN_CASE(OP, A, 0) LN_CASE(OP, A, 1) LN_CASE(OP, A, 2) LN_CASE(OP, A, 3) \
-                    LN_CASE(OP, A, 4) LN_CASE(OP, A, 5) LN_CASE(OP, A, 6) LN_CASE(OP, A, 7)
-#define LN_BD(A) LN_DIV(A, 0) LN_DIV(A, 1) LN_DIV(A, 2) LN_DIV(A, 3) LN_DIV(A, 4) LN_DIV(A, 5) \
-                 LN_DIV(A, 6) LN_DIV(A, 7)
-#define LN_A(OP) LN_B(OP, 0) LN_B(OP, 1) LN_B(OP, 2) LN_B(OP, 3) LN_B(OP, 4) LN_B(OP, 5) \
-                 LN_B(OP, 6) LN_B(OP, 7)
-      LN_A(F_ADD)
-      LN_A(F_SUB)
-      LN_A(F_MUL)
-      LN_BD(0) LN_BD(1) LN_BD(2) LN_BD(3) LN_BD(4) LN_BD(5) LN_BD(6) LN_BD(7)
-#undef LN_A
-#undef LN_BD
-#undef LN_B
-#undef LN_DIV
-#undef LN_CASE
-      default: return false;
-    }
-  do_div:
-    vop<F_DIV, K>(t, t, tb);
-  do_store:
-    store_level<K>(r, (int)in.y, t);
-  }
-  return true;
+__device__ __forceinline__ bool run_linear(uint32_t prog, uint32_t n, uint32_t tile, uint32_t nin,
+                                           float (&o)[K]) {
+  uint32_t bad;
+  if constexpr (K == 1) GP_LIN(GP_PTX_LINEAR_K1, 1);
+  else if constexpr (K == 2) GP_LIN(GP_PTX_LINEAR_K2, 2);
+  else if constexpr (K == 4) GP_LIN(GP_PTX_LINEAR_K4, 4);
+  else GP_LIN(GP_PTX_LINEAR_K8, 8);
+  return bad == 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -273,6 +166,7 @@ __global__ void __launch_bounds__(256) eval_float_kernel(FloatArgs a) {
   __shared__ uint4 prog_s[MAX_INSTR];
   __shared__ Partial red_s[32];
   __shared__ int meta_s[2];  // n_instr (or -1 if bad), kind
+  extern __shared__ float4 tile_s[];  // [warp][input][32 lanes][K] when staged
 
   const int item = blockIdx.x;
   const int p = item / a.n_chunks;
@@ -323,32 +217,51 @@ __global__ void __launch_bounds__(256) eval_float_kernel(FloatArgs a) {
   int64_t c_end = c_begin + a.chunk_cases;
   if (c_end > a.n_cases) c_end = a.n_cases;
   float* out_row = a.outputs ? a.outputs + (int64_t)p * a.n_cases : nullptr;
+  const uint32_t prog_addr = (uint32_t)__cvta_generic_to_shared(prog_s);
+  // this lane's K staged values of input v live at tile + v * 32 * K floats
+  float* tile = reinterpret_cast<float*>(tile_s) + (size_t)warp * a.n_inputs * 32 * K + lane * K;
+  const uint32_t tile_addr = (uint32_t)__cvta_generic_to_shared(tile);
+  const bool staged = !XREG || kind == K_LINEAR;
 
   if (!bad) {
+#pragma unroll 1
     for (int64_t wb = c_begin + (int64_t)warp * 32 * K; wb < c_end; wb += (int64_t)nwarps * 32 * K) {
       const int64_t c0 = wb + (int64_t)lane * K;
       const bool full = c0 + K <= a.n_cases;
-      XSrc<K, XREG> X;
-      X.cases = a.cases;
-      X.n_cases = a.n_cases;
-      X.c0 = c0;
-      X.vec_ok = full && a.x_aligned;
-      Vec<K> S[R];
+      const bool vec_ok = full && a.x_aligned;
+      float x[K];
+      float o[K];
+      if (staged) {
+        for (int v = 0; v < a.n_inputs; ++v) {
+          Vec<K> t;
+          vload<K>(t, a.cases + (int64_t)v * a.n_cases, c0, a.n_cases, vec_ok);
+#pragma unroll
+          for (int j = 0; j < K; ++j) tile[v * 32 * K + j] = vget<K>(t, j);
+        }
+      }
+      if constexpr (XREG) {
+        Vec<K> t;
+        vload<K>(t, a.cases, c0, a.n_cases, vec_ok);
+#pragma unroll
+        for (int j = 0; j < K; ++j) x[j] = vget<K>(t, j);
+      } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) x[j] = 0.0f;
+      }
       bool ok;
       if (kind == K_LINEAR) {
-#pragma unroll
-        for (int v = 0; v < R; ++v) {
-          if (v < a.n_inputs) vload<K>(S[v], a.cases + (int64_t)v * a.n_cases, c0, a.n_cases, X.vec_ok);
-          else vbroadcast<K>(S[v], 0.0f);
-        }
-        ok = run_linear<K>(prog_s, n_instr, S);
+        ok = run_linear<K>(prog_addr, (uint32_t)n_instr, tile_addr,
+                           (uint32_t)(a.n_inputs < R ? a.n_inputs : R), o);
+      } else if (kind == K_SFORM) {
+        ok = run_tree<K, XREG, false>(prog_addr, (uint32_t)n_instr, x, tile_addr, o);
       } else {
-        if constexpr (XREG) vload<K>(X.xv, a.cases, c0, a.n_cases, X.vec_ok);
-        ok = (kind == K_SFORM) ? run_sform<K, XREG>(prog_s, n_instr, S, X)
-                               : run_rpn<K, XREG>(prog_s, n_instr, S, X);
+        ok = run_tree<K, XREG, true>(prog_addr, (uint32_t)n_instr, x, tile_addr, o);
       }
       if (!ok) flags |= FLAG_BAD;
-      if (out_row) vstore<K>(out_row, S[0], c0, a.n_cases, full && a.o_aligned);
+      Vec<K> ov;
+#pragma unroll
+      for (int j = 0; j < K; ++j) vset<K>(ov, j, o[j]);
+      if (out_row) vstore<K>(out_row, ov, c0, a.n_cases, full && a.o_aligned);
       if (a.want_fitness) {
         Vec<K> y;
         vload<K>(y, a.targets, c0, a.n_cases, full && a.y_aligned);
@@ -356,7 +269,7 @@ __global__ void __launch_bounds__(256) eval_float_kernel(FloatArgs a) {
         float e[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          float d = fabsf(__fsub_rn(vget<K>(S[0], j), vget<K>(y, j)));
+          float d = fabsf(__fsub_rn(o[j], vget<K>(y, j)));
           if (c0 + j >= a.n_cases) d = 0.0f;
           if (!(d <= 3.402823466e38f)) flags |= FLAG_NONFINITE;
           e[j] = d;
@@ -377,6 +290,11 @@ __global__ void __launch_bounds__(256) eval_float_kernel(FloatArgs a) {
     if (a.want_fitness || bad)
       finish_program(a.partials, a.counters, p, chunk, a.n_chunks, acc, flags, a.fitness_out);
   }
+}
+
+// dynamic shared memory of eval_float_kernel: the staged input tiles
+inline size_t float_tile_bytes(int k, int block, int n_inputs) {
+  return (size_t)(block / 32) * (size_t)n_inputs * 32u * (size_t)k * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------

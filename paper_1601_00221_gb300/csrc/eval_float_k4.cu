@@ -3,9 +3,16 @@
 #include "launch.h"
 
 namespace gpdev {
-cudaError_t launch_float_k4(const FloatArgs& a, bool xreg, int block, int grid, cudaStream_t s) {
-  if (xreg) eval_float_kernel<4, true><<<grid, block, 0, s>>>(a);
-  else eval_float_kernel<4, false><<<grid, block, 0, s>>>(a);
+cudaError_t launch_float_k4(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                            cudaStream_t s) {
+  static std::atomic<size_t> set_reg{0}, set_smem{0};
+  if (xreg) {
+    ensure_dynamic_smem(eval_float_kernel<4, true>, smem, set_reg);
+    eval_float_kernel<4, true><<<grid, block, smem, s>>>(a);
+  } else {
+    ensure_dynamic_smem(eval_float_kernel<4, false>, smem, set_smem);
+    eval_float_kernel<4, false><<<grid, block, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 }  // namespace gpdev

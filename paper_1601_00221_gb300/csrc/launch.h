@@ -5,14 +5,32 @@
 
 #include "eval_float.cuh"
 
+#include <atomic>
+
+namespace gpdev {
+// Raises a kernel's dynamic shared-memory limit the first time a launch
+// needs more than the default (static + dynamic > 48 KB needs the opt-in).
+template <typename F>
+inline void ensure_dynamic_smem(F* kernel, size_t bytes, std::atomic<size_t>& configured) {
+  if (bytes <= configured.load(std::memory_order_relaxed)) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  configured.store(bytes, std::memory_order_relaxed);
+}
+}  // namespace gpdev
+
 namespace gpdev {
 struct BoolArgs;
-// Float kernels: K in {1,2,4,8}; xreg = the single input is held in registers.
-cudaError_t launch_float_k1(const FloatArgs& a, bool xreg, int block, int grid, cudaStream_t s);
-cudaError_t launch_float_k2(const FloatArgs& a, bool xreg, int block, int grid, cudaStream_t s);
-cudaError_t launch_float_k4(const FloatArgs& a, bool xreg, int block, int grid, cudaStream_t s);
-cudaError_t launch_float_k8(const FloatArgs& a, bool xreg, int block, int grid, cudaStream_t s);
+// Float kernels: K in {1,2,4,8}; xreg = the single input is held in registers;
+// smem = dynamic shared memory (float_tile_bytes).
+cudaError_t launch_float_k1(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_float_k2(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_float_k4(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_float_k8(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                            cudaStream_t s);
 cudaError_t launch_blockgp(const FloatArgs& a, int block, int grid, cudaStream_t s);
 // Boolean kernels: K words per thread.
-cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, cudaStream_t s);
+cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s);
 }  // namespace gpdev

@@ -1,0 +1,555 @@
+"""Generates the inline-PTX interpreter loops of the CUDA library.
+
+Each interpreter is one PTX block: a loop that loads the next 16-byte
+instruction from shared memory (one broadcast load per warp), clamps its code
+and jumps through a ``brx.idx.uni`` jump table straight to the body of that
+(function, operand forms, stack level) combination.  The stack levels live in
+registers whose names are fixed in each body, so no body indexes a register
+at run time (Sec. 6.2 of the paper keeps low stack levels in registers behind
+a switch on the stack pointer; here the level is resolved by the encoder and
+the switch disappears into the jump).  Pairs of fitness cases are packed
+``.b64`` registers operated on by the f32x2 instructions of sm_100+
+(add/sub/mul.rn.f32x2), so a K-case body issues K/2 arithmetic instructions
+(Sec. 6.1's float2/float4 idea, with a wide ALU behind it on this GPU).
+Protected division shares one block per interpreter: operands are copied to
+temporaries, divided with ``div.rn.f32`` (IEEE, round to nearest, subnormals
+kept) and stored back through a second jump table on the level.
+
+The instruction codes follow ``csrc/isa.h``.  Output: ``gen_interp.h`` with
+one string macro per (interpreter, K, input mode), used by
+``csrc/eval_float.cuh`` and ``csrc/eval_bool.cuh``.
+
+Operand conventions of the generated asm (documented again in the header):
+  float S-form / RPN, XREG (single input in registers):
+     outputs %0..%{K-1} level-0 values (f32), %K bad flag (u32)
+     inputs  %{K+1} program address (shared, u32), %{K+2} instruction count,
+             %{K+3}..%{2K+2} the K input values (f32)
+  float S-form / RPN, XSMEM (inputs staged in shared memory):
+     inputs  %{K+1} program address, %{K+2} count, %{K+3} this lane's tile
+             address (u32): input v of this lane's K cases at
+             tile + v*128*K bytes
+  register linear GP (inputs always staged):
+     inputs  %{K+1} program address, %{K+2} count, %{K+3} tile address,
+             %{K+4} number of staged inputs (registers beyond start at 0)
+  Boolean (words): outputs %0..%{K-1} level-0 words (u32), %K bad;
+     inputs  %{K+1} program address, %{K+2} count, %{K+3} tile address
+"""
+from __future__ import annotations
+
+import os
+
+R = 8
+NREG = 8
+# csrc/isa.h
+SF_FORMS = ["XX", "XC", "CX", "CC", "SX", "XS", "SC", "CS", "SS", "SSR", "MOVX", "MOVC"]
+RF_FORMS = ["PUSHX", "PUSHC", "OP", "OPR"]
+BF_FORMS = ["XX", "XS", "SX", "SS", "SSR"]
+BOOL_IF_BASE = len(BF_FORMS) * R * 4
+BOOL_MOVX = BOOL_IF_BASE + 16 * R
+F32X2 = {0: "add.rn.f32x2", 1: "sub.rn.f32x2", 2: "mul.rn.f32x2"}
+F32 = {0: "add.rn.f32", 1: "sub.rn.f32", 2: "mul.rn.f32"}
+# lop3 truth tables with a = 0xF0, b = 0xCC, c = 0xAA
+LUT = {0: 0xC0, 1: 0xFC, 2: 0x3F, 3: 0x03}  # AND, OR, NAND, NOR of (a, b)
+LUT_IF = 0xCA                                 # (a & b) | (~a & c)
+
+
+def sform_code(form, level, op):
+    return (form * R + level) * 4 + op
+
+
+def rpn_code(form, level, op):
+    return (form * R + level) * 4 + op
+
+
+def lin_code(op, a, b):
+    return (op * NREG + a) * NREG + b
+
+
+def if_descs():
+    out = []
+    for t in range(64):
+        d = (t // 16, (t // 4) % 4, t % 4)
+        m = sum(1 for v in d if v > 0)
+        used, ok = [], True
+        for v in d:
+            if v > 0:
+                if v - 1 >= m or (v - 1) in used:
+                    ok = False
+                used.append(v - 1)
+        if ok:
+            out.append(d)
+    assert len(out) == 16
+    return out
+
+
+class Block:
+    def __init__(self):
+        self.lines = []
+
+    def __call__(self, s):
+        self.lines.append(s)
+
+    def macro(self, name, doc):
+        body = "".join(f'  "{ln}\\n\\t" \\\n' for ln in self.lines)
+        return f"// {doc}\n#define {name} \\\n{body}  \"\"\n"
+
+
+# ---------------------------------------------------------------------------
+# float interpreters
+# ---------------------------------------------------------------------------
+class FloatGen:
+    def __init__(self, K, xmode):
+        assert K in (1, 2, 4, 8) and xmode in ("reg", "smem")
+        self.K, self.xmode = K, xmode
+        self.H = 1 if K == 1 else K // 2   # register units per stack level
+        self.b = Block()
+        self.stride = 128 * K              # bytes between inputs in a lane's tile
+
+    # register unit names
+    def lev(self, l, i):
+        return f"s{l * self.H + i}"
+
+    def xreg(self, i):
+        return f"x{i}"
+
+    @property
+    def ty(self):
+        return "f32" if self.K == 1 else "b64"
+
+    def header(self, extra_regs=""):
+        K, H, b = self.K, self.H, self.b
+        b("{")
+        b(f".reg .{self.ty} s<{R * H}>, ta<{H}>, tb<{H}>, xA<{H}>, xB<{H}>, cA, cB;")
+        if self.xmode == "reg":
+            b(f".reg .{self.ty} x<{H}>;")
+        b(".reg .b32 code, pa, pb, pc, adr, end, dl, xa, xbase;")
+        b(".reg .f32 fa0, fa1, fb0, fb1, fq0, fq1;")
+        b(".reg .pred p, pz;")
+        if extra_regs:
+            b(extra_regs)
+        # Define every stack register before the loop: the jump table makes any
+        # of them readable at the loop head, so an undefined one would be live
+        # from the kernel's entry and could not share a physical register with
+        # the other interpreters of the same kernel.
+        zero = "0f00000000" if K == 1 else "0"
+        for r in range(R * H):
+            b(f"mov.{self.ty} s{r}, {zero};")
+
+    def load_x(self, dst, payload):
+        """Loads input `payload` (a b32 register) for this lane's K cases into
+        the register units `dst` (list of H names)."""
+        K, b = self.K, self.b
+        if self.xmode == "reg":
+            return [self.xreg(i) for i in range(self.H)]
+        b(f"mad.lo.u32 xa, {payload}, {self.stride}, xbase;")
+        if K == 1:
+            b(f"ld.shared.f32 {dst[0]}, [xa];")
+        elif K == 2:
+            b(f"ld.shared.b64 {dst[0]}, [xa];")
+        elif K == 4:
+            b(f"ld.shared.v2.b64 {{{dst[0]}, {dst[1]}}}, [xa];")
+        else:
+            b(f"ld.shared.v2.b64 {{{dst[0]}, {dst[1]}}}, [xa];")
+            b(f"ld.shared.v2.b64 {{{dst[2]}, {dst[3]}}}, [xa+16];")
+        return dst
+
+    def const(self, reg, payload):
+        if self.K == 1:
+            self.b(f"mov.b32 {reg}, {payload};")
+        else:
+            self.b(f"mov.b64 {reg}, {{{payload}, {payload}}};")
+        return [reg] * self.H
+
+    def vop(self, op, d, a, c):
+        for i in range(self.H):
+            if self.K == 1:
+                self.b(f"{F32[op]} {d[i]}, {a[i]}, {c[i]};")
+            else:
+                self.b(f"{F32X2[op]} {d[i]}, {a[i]}, {c[i]};")
+
+    def copy(self, d, a):
+        for i in range(self.H):
+            self.b(f"mov.{self.ty} {d[i]}, {a[i]};")
+
+    def div_block(self, store_label_prefix, store_targets):
+        """DIV: ta <- ta / tb (protected), then jump on `dl` to a store label."""
+        b, H = self.b, self.H
+        b("DIV:")
+        for i in range(H):
+            if self.K == 1:
+                b("setp.eq.f32 pz, tb0, 0f00000000;")
+                b("div.rn.f32 fq0, ta0, tb0;")
+                b("selp.f32 ta0, 0f3F800000, fq0, pz;")
+            else:
+                b(f"mov.b64 {{fa0, fa1}}, ta{i};")
+                b(f"mov.b64 {{fb0, fb1}}, tb{i};")
+                b("setp.eq.f32 pz, fb0, 0f00000000;")
+                b("div.rn.f32 fq0, fa0, fb0;")
+                b("selp.f32 fq0, 0f3F800000, fq0, pz;")
+                b("setp.eq.f32 pz, fb1, 0f00000000;")
+                b("div.rn.f32 fq1, fa1, fb1;")
+                b("selp.f32 fq1, 0f3F800000, fq1, pz;")
+                b(f"mov.b64 ta{i}, {{fq0, fq1}};")
+        b(f"brx.idx.uni dl, {store_label_prefix}TBL;")
+
+    def loop_head(self, n_codes, table):
+        """Table, prologue and the dispatch loop.  `table` maps code -> label."""
+        b, K = self.b, self.K
+        labels = [table.get(c, "CBAD") for c in range(n_codes)] + ["CBAD"]
+        b("TBL: .branchtargets " + ", ".join(labels) + ";")
+        b(f"mov.u32 adr, %{K + 1};")
+        b(f"mad.lo.u32 end, %{K + 2}, 16, adr;")
+        b(f"mov.u32 %{K}, 0;")
+
+    def dispatch(self, n_codes):
+        b = self.b
+        b("LOOP:")
+        b("setp.ge.u32 p, adr, end;")
+        b("@p bra.uni DONE;")
+        b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
+        b("add.u32 adr, adr, 16;")
+        b(f"min.u32 code, code, {n_codes};")
+        b("brx.idx.uni code, TBL;")
+
+    def epilogue(self, out_units):
+        b, K = self.b, self.K
+        b("CBAD:")
+        b(f"mov.u32 %{K}, 1;")
+        b("DONE:")
+        if K == 1:
+            b(f"mov.f32 %0, {out_units[0]};")
+        else:
+            for i in range(self.H):
+                b(f"mov.b64 {{%{2 * i}, %{2 * i + 1}}}, {out_units[i]};")
+        b("}")
+
+    def setup_inputs(self):
+        b, K = self.b, self.K
+        if self.xmode == "reg":
+            for i in range(self.H):
+                if K == 1:
+                    b(f"mov.f32 x0, %{K + 3};")
+                else:
+                    b(f"mov.b64 x{i}, {{%{K + 3 + 2 * i}, %{K + 4 + 2 * i}}};")
+        else:
+            b(f"mov.u32 xbase, %{K + 3};")
+
+    def store_table(self, prefix, units_of_level):
+        b = self.b
+        b(f"{prefix}TBL: .branchtargets " + ", ".join(f"{prefix}{l}" for l in range(R)) + ";")
+
+    def store_bodies(self, prefix, units_of_level, src):
+        b = self.b
+        for l in range(R):
+            b(f"{prefix}{l}:")
+            self.copy(units_of_level(l), src)
+            b("bra.uni LOOP;")
+
+    # ------------------------------------------------------------------
+    def sform(self):
+        K, H, b = self.K, self.H, self.b
+        self.header()
+        L = lambda l: [self.lev(l, i) for i in range(H)]
+        ta = [f"ta{i}" for i in range(H)]
+        tb = [f"tb{i}" for i in range(H)]
+        xA = [f"xA{i}" for i in range(H)]
+        xB = [f"xB{i}" for i in range(H)]
+        n_codes = len(SF_FORMS) * R * 4
+        table, bodies = {}, []
+        for f, name in enumerate(SF_FORMS):
+            for l in range(R):
+                for op in range(4):
+                    if name in ("SS", "SSR") and l + 1 >= R:
+                        continue
+                    if name in ("MOVX", "MOVC") and (l != 0 or op != 0):
+                        continue
+                    code = sform_code(f, l, op)
+                    table[code] = f"C{code}"
+                    bodies.append((code, name, l, op))
+        self.store_table("ST", L)
+        self.loop_head(n_codes, table)
+        self.setup_inputs()
+        self.dispatch(n_codes)
+        for code, name, l, op in bodies:
+            b(f"C{code}:")
+            if name == "MOVX":
+                src = self.load_x(xA, "pa")
+                self.copy(L(0), src)
+                b("bra.uni LOOP;")
+                continue
+            if name == "MOVC":
+                self.copy(L(0), self.const("cA", "pa"))
+                b("bra.uni LOOP;")
+                continue
+            if name == "SS":
+                a, c = L(l), L(l + 1)
+            elif name == "SSR":
+                a, c = L(l + 1), L(l)
+            else:
+                ka, kb = name[0], name[1]
+                a = L(l) if ka == "S" else (self.load_x(xA, "pa") if ka == "X" else self.const("cA", "pa"))
+                c = L(l) if kb == "S" else (self.load_x(xB, "pb") if kb == "X" else self.const("cB", "pb"))
+            if op == 3:
+                self.copy(ta, a)
+                self.copy(tb, c)
+                b(f"mov.u32 dl, {l};")
+                b("bra.uni DIV;")
+            else:
+                self.vop(op, L(l), a, c)
+                b("bra.uni LOOP;")
+        self.div_block("ST", None)
+        self.store_bodies("ST", L, ta)
+        self.epilogue(L(0))
+        return b
+
+    def rpn(self):
+        K, H, b = self.K, self.H, self.b
+        self.header()
+        L = lambda l: [self.lev(l, i) for i in range(H)]
+        ta = [f"ta{i}" for i in range(H)]
+        tb = [f"tb{i}" for i in range(H)]
+        n_codes = len(RF_FORMS) * R * 4
+        table, bodies = {}, []
+        for f, name in enumerate(RF_FORMS):
+            for l in range(R):
+                for op in range(4):
+                    if name in ("PUSHX", "PUSHC") and op != 0:
+                        continue
+                    if name in ("OP", "OPR") and l + 1 >= R:
+                        continue
+                    code = rpn_code(f, l, op)
+                    table[code] = f"C{code}"
+                    bodies.append((code, name, l, op))
+        self.store_table("ST", L)
+        self.loop_head(n_codes, table)
+        self.setup_inputs()
+        self.dispatch(n_codes)
+        for code, name, l, op in bodies:
+            b(f"C{code}:")
+            if name == "PUSHX":
+                if self.xmode == "reg":
+                    self.copy(L(l), [self.xreg(i) for i in range(H)])
+                else:
+                    self.load_x(L(l), "pa")
+                b("bra.uni LOOP;")
+                continue
+            if name == "PUSHC":
+                self.copy(L(l), self.const("cA", "pa"))
+                b("bra.uni LOOP;")
+                continue
+            a, c = (L(l), L(l + 1)) if name == "OP" else (L(l + 1), L(l))
+            if op == 3:
+                self.copy(ta, a)
+                self.copy(tb, c)
+                b(f"mov.u32 dl, {l};")
+                b("bra.uni DIV;")
+            else:
+                self.vop(op, L(l), a, c)
+                b("bra.uni LOOP;")
+        self.div_block("ST", None)
+        self.store_bodies("ST", L, ta)
+        self.epilogue(L(0))
+        return b
+
+    def linear(self):
+        """Register machine r[d] = r[a] op r[b]; registers start from the staged
+        inputs (register v < nin) or 0."""
+        K, H, b = self.K, self.H, self.b
+        assert self.xmode == "smem"
+        self.header(".reg .b32 nin;")
+        Rg = lambda r: [self.lev(r, i) for i in range(H)]
+        ta = [f"ta{i}" for i in range(H)]
+        tb = [f"tb{i}" for i in range(H)]
+        n_codes = 4 * NREG * NREG
+        table = {lin_code(op, a, c): f"C{lin_code(op, a, c)}"
+                 for op in range(4) for a in range(NREG) for c in range(NREG)}
+        self.store_table("ST", Rg)
+        self.loop_head(n_codes, table)
+        b(f"mov.u32 xbase, %{K + 3};")
+        b(f"mov.u32 nin, %{K + 4};")
+        zero = "0f00000000" if K == 1 else "0"
+        for r in range(NREG):
+            b(f"setp.lt.u32 p, {r}, nin;")
+            b(f"mov.u32 pa, {r};")
+            units = Rg(r)
+            # load when staged, else zero
+            b(f"@!p bra.uni Z{r};")
+            self.load_x(units, "pa")
+            b(f"bra.uni I{r};")
+            b(f"Z{r}:")
+            for u in units:
+                b(f"mov.{self.ty} {u}, {zero};")
+            b(f"I{r}:")
+        self.dispatch(n_codes)
+        for op in range(4):
+            for a in range(NREG):
+                for c in range(NREG):
+                    code = lin_code(op, a, c)
+                    b(f"C{code}:")
+                    if op == 3:
+                        self.copy(ta, Rg(a))
+                        self.copy(tb, Rg(c))
+                        b("bra.uni DIV;")
+                    else:
+                        self.vop(op, ta, Rg(a), Rg(c))
+                        b("bra.uni STORE;")
+        # DIV shares the destination jump with the other functions
+        b("DIV:")
+        for i in range(H):
+            if K == 1:
+                b("setp.eq.f32 pz, tb0, 0f00000000;")
+                b("div.rn.f32 fq0, ta0, tb0;")
+                b("selp.f32 ta0, 0f3F800000, fq0, pz;")
+            else:
+                b(f"mov.b64 {{fa0, fa1}}, ta{i};")
+                b(f"mov.b64 {{fb0, fb1}}, tb{i};")
+                b("setp.eq.f32 pz, fb0, 0f00000000;")
+                b("div.rn.f32 fq0, fa0, fb0;")
+                b("selp.f32 fq0, 0f3F800000, fq0, pz;")
+                b("setp.eq.f32 pz, fb1, 0f00000000;")
+                b("div.rn.f32 fq1, fa1, fb1;")
+                b("selp.f32 fq1, 0f3F800000, fq1, pz;")
+                b(f"mov.b64 ta{i}, {{fq0, fq1}};")
+        b("STORE:")
+        b(f"min.u32 dl, pa, {NREG - 1};")
+        b("brx.idx.uni dl, STTBL;")
+        self.store_bodies("ST", Rg, ta)
+        self.epilogue(Rg(0))
+        return b
+
+
+# ---------------------------------------------------------------------------
+# Boolean interpreter (K words per thread, 32 cases per word)
+# ---------------------------------------------------------------------------
+class BoolGen:
+    def __init__(self, K):
+        self.K = K
+        self.b = Block()
+        self.stride = 128 * K
+
+    def lev(self, l):
+        return [f"s{l * self.K + j}" for j in range(self.K)]
+
+    def load_x(self, dst, payload):
+        K, b = self.K, self.b
+        b(f"mad.lo.u32 xa, {payload}, {self.stride}, xbase;")
+        if K == 1:
+            b(f"ld.shared.b32 {dst[0]}, [xa];")
+        elif K == 2:
+            b(f"ld.shared.v2.b32 {{{dst[0]}, {dst[1]}}}, [xa];")
+        else:
+            for q in range(K // 4):
+                d = dst[4 * q: 4 * q + 4]
+                off = f"+{16 * q}" if q else ""
+                b(f"ld.shared.v4.b32 {{{', '.join(d)}}}, [xa{off}];")
+        return dst
+
+    def gen(self):
+        K, b = self.K, self.b
+        xA = [f"xA{j}" for j in range(K)]
+        xB = [f"xB{j}" for j in range(K)]
+        xC = [f"xC{j}" for j in range(K)]
+        b("{")
+        b(f".reg .b32 s<{R * K}>, xA<{K}>, xB<{K}>, xC<{K}>;")
+        b(".reg .b32 code, pa, pb, pc, adr, end, xa, xbase;")
+        b(".reg .pred p;")
+        for r in range(R * K):  # defined before the loop (see FloatGen.header)
+            b(f"mov.b32 s{r}, 0;")
+        n_codes = BOOL_MOVX + 1
+        table, bodies = {}, []
+        for f, name in enumerate(BF_FORMS):
+            for l in range(R):
+                for op in range(4):
+                    if name in ("SS", "SSR") and l + 1 >= R:
+                        continue
+                    code = (f * R + l) * 4 + op
+                    table[code] = f"C{code}"
+                    bodies.append((code, "bin", name, l, op))
+        for fi, d in enumerate(if_descs()):
+            m = sum(1 for v in d if v > 0)
+            for l in range(R):
+                if l + max(m - 1, 0) >= R:
+                    continue
+                code = BOOL_IF_BASE + fi * R + l
+                table[code] = f"C{code}"
+                bodies.append((code, "if", d, l, None))
+        table[BOOL_MOVX] = "CMOV"
+        labels = [table.get(c, "CBAD") for c in range(n_codes)] + ["CBAD"]
+        b("TBL: .branchtargets " + ", ".join(labels) + ";")
+        b(f"mov.u32 adr, %{K + 1};")
+        b(f"mad.lo.u32 end, %{K + 2}, 16, adr;")
+        b(f"mov.u32 %{K}, 0;")
+        b(f"mov.u32 xbase, %{K + 3};")
+        b("LOOP:")
+        b("setp.ge.u32 p, adr, end;")
+        b("@p bra.uni DONE;")
+        b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
+        b("add.u32 adr, adr, 16;")
+        b(f"min.u32 code, code, {n_codes};")
+        b("brx.idx.uni code, TBL;")
+        for code, kind, name, l, op in bodies:
+            b(f"C{code}:")
+            S = self.lev(l)
+            if kind == "bin":
+                if name == "SS":
+                    a, c = S, self.lev(l + 1)
+                elif name == "SSR":
+                    a, c = self.lev(l + 1), S
+                else:
+                    a = S if name[0] == "S" else self.load_x(xA, "pa")
+                    c = S if name[1] == "S" else self.load_x(xB, "pb")
+                for j in range(K):
+                    b(f"lop3.b32 {S[j]}, {a[j]}, {c[j]}, {c[j]}, 0x{LUT[op]:02X};")
+            else:
+                dc, da, db = name
+                ops = []
+                for dsc, pay, tmp in ((dc, "pa", xA), (da, "pb", xB), (db, "pc", xC)):
+                    ops.append(self.load_x(tmp, pay) if dsc == 0 else self.lev(l + dsc - 1))
+                cc, aa, bb = ops
+                for j in range(K):
+                    b(f"lop3.b32 {S[j]}, {cc[j]}, {aa[j]}, {bb[j]}, 0x{LUT_IF:02X};")
+            b("bra.uni LOOP;")
+        b("CMOV:")
+        src = self.load_x(xA, "pa")
+        S0 = self.lev(0)
+        for j in range(K):
+            b(f"mov.b32 {S0[j]}, {src[j]};")
+        b("bra.uni LOOP;")
+        b("CBAD:")
+        b(f"mov.u32 %{K}, 1;")
+        b("DONE:")
+        for j in range(K):
+            b(f"mov.b32 %{j}, s{j};")
+        b("}")
+        return b
+
+
+def generate() -> str:
+    parts = ["// gen_interp.h -- generated by paper_1601_00221_gb300/gen_interp.py; do not edit.\n",
+             "#pragma once\n"]
+    for K in (1, 2, 4, 8):
+        for xm in ("reg", "smem"):
+            X = xm.upper()
+            parts.append(FloatGen(K, xm).sform().macro(
+                f"GP_PTX_SFORM_K{K}_{X}", f"S-form interpreter, K={K}, inputs in {xm}"))
+            parts.append(FloatGen(K, xm).rpn().macro(
+                f"GP_PTX_RPN_K{K}_{X}", f"RPN interpreter, K={K}, inputs in {xm}"))
+        parts.append(FloatGen(K, "smem").linear().macro(
+            f"GP_PTX_LINEAR_K{K}", f"register linear-GP interpreter, K={K}"))
+        parts.append(BoolGen(K).gen().macro(f"GP_PTX_BOOL_K{K}", f"Boolean interpreter, K={K} words"))
+    return "".join(parts)
+
+
+def write(path: str) -> str:
+    text = generate()
+    old = open(path).read() if os.path.exists(path) else None
+    if old != text:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as fh:
+            fh.write(text)
+    return path
+
+
+if __name__ == "__main__":
+    import sys
+    print(write(sys.argv[1] if len(sys.argv) > 1 else "gen_interp.h"))

@@ -161,7 +161,7 @@ __device__ __forceinline__ bool valid_instr(uint32_t kind, const uint4& in, int 
 // program; each warp runs its own sequence of passes.
 // ---------------------------------------------------------------------------
 template <int K, bool XREG>
-__global__ void __launch_bounds__(256) eval_float_kernel(FloatArgs a) {
+__global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   using namespace gpisa;
   __shared__ uint4 prog_s[MAX_INSTR];
   __shared__ Partial red_s[32];

@@ -12,8 +12,9 @@ the switch disappears into the jump).  Pairs of fitness cases are packed
 (add/sub/mul.rn.f32x2), so a K-case body issues K/2 arithmetic instructions
 (Sec. 6.1's float2/float4 idea, with a wide ALU behind it on this GPU).
 Protected division shares one block per interpreter: operands are copied to
-temporaries, divided with ``div.rn.f32`` (IEEE, round to nearest, subnormals
-kept) and stored back through a second jump table on the level.
+temporaries, divided (emit_pdiv: a correctly rounded reciprocal-and-remainder
+sequence on case pairs, with ``div.rn.f32`` as the slow path for extreme
+operands) and stored back through a second jump table on the level.
 
 The instruction codes follow ``csrc/isa.h``.  Output: ``gen_interp.h`` with
 one string macro per (interpreter, K, input mode), used by
@@ -82,6 +83,118 @@ def if_descs():
     return out
 
 
+# bounds of the fast division path: 2^-100 and 2^100 as binary32 bit patterns
+DIV_LO = "0f0D800000"
+DIV_HI = "0f71800000"
+
+
+def emit_pdiv(b, K, A, B, Q, tag, group=2):
+    """Protected division Q = (B == 0) ? 1 : A / B, correctly rounded, for the
+    register units A, B, Q (K == 1: one f32 each; else b64 case pairs).
+
+    Fast path (no branch): reciprocal seed y0 = rcp.approx(b), one
+    Newton-Raphson step y1 = y0 + y0 (1 - b y0), the quotient q0 = a y1, the
+    exact remainder r = a - b q0 (one FMA) and Markstein's correction
+    q1 = q0 + r y1 (P. Markstein, IBM J. Res. Dev. 34(1), 1990), in
+    fma/mul.rn.f32x2, `group` pairs interleaved at a time.  An element is
+    right on this path when |a| >= 2^-100 and 2^-100 <= |q1| <= 2^100 (every
+    intermediate value stays normal, so the remainder is exact) or when its
+    denominator is zero (the final select gives 1).  A lane with any other
+    element takes the slow path, div.rn.f32, for all its elements; the
+    emit_pdiv_slow block must follow somewhere in the same asm block.
+    Scratch registers come from pdiv_regs().  Q may name the same registers
+    as A: quotients stay in dQ until the final selects."""
+    H = len(A)
+    if K == 1:
+        b(f"rcp.approx.ftz.f32 dY0, {B[0]};")
+        b(f"neg.f32 dN0, {B[0]};")
+        b("fma.rn.f32 dE0, dN0, dY0, 0f3F800000;")
+        b("fma.rn.f32 dY0, dY0, dE0, dY0;")
+        b(f"mul.rn.f32 dQ0, {A[0]}, dY0;")
+        b(f"fma.rn.f32 dE0, dN0, dQ0, {A[0]};")
+        b("fma.rn.f32 dQ0, dE0, dY0, dQ0;")
+        _emit_check(b, "dQ0", A[0], B[0], first=True)
+    else:
+        first = True
+        for g0 in range(0, H, group):
+            idx = list(range(g0, min(H, g0 + group)))
+            for i in idx:
+                b(f"mov.b64 {{dlo, dhi}}, {B[i]};")
+                b("rcp.approx.ftz.f32 dlo, dlo;")
+                b("rcp.approx.ftz.f32 dhi, dhi;")
+                b(f"mov.b64 dY{i}, {{dlo, dhi}};")
+                b(f"xor.b64 dN{i}, {B[i]}, 0x8000000080000000;")
+            for i in idx:
+                b(f"fma.rn.f32x2 dE{i}, dN{i}, dY{i}, one2;")
+            for i in idx:
+                b(f"fma.rn.f32x2 dY{i}, dY{i}, dE{i}, dY{i};")
+            for i in idx:
+                b(f"mul.rn.f32x2 dQ{i}, {A[i]}, dY{i};")
+            for i in idx:
+                b(f"fma.rn.f32x2 dE{i}, dN{i}, dQ{i}, {A[i]};")
+            for i in idx:
+                b(f"fma.rn.f32x2 dQ{i}, dE{i}, dY{i}, dQ{i};")
+            for i in idx:
+                b(f"mov.b64 {{dlo, dhi}}, dQ{i};")
+                b(f"mov.b64 {{dt, dt2}}, {A[i]};")
+                b(f"mov.b64 {{da, db}}, {B[i]};")
+                _emit_check(b, "dlo", "dt", "da", first)
+                first = False
+                _emit_check(b, "dhi", "dt2", "db", first)
+    b(f"@!dok bra {tag}SLOW;")
+    b(f"{tag}RET:")
+    if K == 1:
+        b(f"setp.eq.f32 dz, {B[0]}, 0f00000000;")
+        b(f"selp.f32 {Q[0]}, 0f3F800000, dQ0, dz;")
+        return
+    for i in range(H):
+        b(f"mov.b64 {{dlo, dhi}}, dQ{i};")
+        b(f"mov.b64 {{dt, dt2}}, {B[i]};")
+        b("setp.eq.f32 dz, dt, 0f00000000;")
+        b("selp.f32 dlo, 0f3F800000, dlo, dz;")
+        b("setp.eq.f32 dz, dt2, 0f00000000;")
+        b("selp.f32 dhi, 0f3F800000, dhi, dz;")
+        b(f"mov.b64 {Q[i]}, {{dlo, dhi}};")
+
+
+def _emit_check(b, q, a, den, first):
+    """dok (&)= the fast quotient q of a / den is right (see emit_pdiv)."""
+    b(f"abs.f32 dz0, {q};")
+    b(f"setp.ge.f32 dz, dz0, {DIV_LO};")
+    b(f"setp.le.and.f32 dz, dz0, {DIV_HI}, dz;")
+    b(f"abs.f32 dz0, {a};")
+    b(f"setp.ge.and.f32 dz, dz0, {DIV_LO}, dz;")
+    b(f"setp.eq.or.f32 dz, {den}, 0f00000000, dz;")
+    if first:
+        b("mov.pred dok, dz;")
+    else:
+        b("and.pred dok, dok, dz;")
+
+
+def emit_pdiv_slow(b, K, A, B, tag):
+    """Out-of-line slow path of emit_pdiv: IEEE division of every element
+    into dQ, then back to the selects."""
+    b(f"{tag}SLOW:")
+    if K == 1:
+        b(f"div.rn.f32 dQ0, {A[0]}, {B[0]};")
+    else:
+        for i in range(len(A)):
+            b(f"mov.b64 {{dlo, dhi}}, {A[i]};")
+            b(f"mov.b64 {{dt, dt2}}, {B[i]};")
+            b("div.rn.f32 dlo, dlo, dt;")
+            b("div.rn.f32 dhi, dhi, dt2;")
+            b(f"mov.b64 dQ{i}, {{dlo, dhi}};")
+    b(f"bra {tag}RET;")
+
+
+def pdiv_regs(K, H):
+    ty = "f32" if K == 1 else "b64"
+    return (f".reg .{ty} dY<{H}>, dE<{H}>, dN<{H}>, dQ<{H}>, one2;\n"
+            f".reg .f32 dlo, dhi, dt, dt2, da, db, dz0;\n"
+            f".reg .pred dok, dz;")
+
+
+
 class Block:
     def __init__(self):
         self.lines = []
@@ -125,6 +238,10 @@ class FloatGen:
         b(".reg .b32 code, pa, pb, pc, adr, end, dl, xa, xbase;")
         b(".reg .f32 fa0, fa1, fb0, fb1, fq0, fq1;")
         b(".reg .pred p, pz;")
+        for ln in pdiv_regs(K, H).split("\n"):
+            b(ln)
+        if K > 1:
+            b("mov.b64 one2, 0x3F8000003F800000;")
         if extra_regs:
             b(extra_regs)
         # Define every stack register before the loop: the jump table makes any
@@ -174,23 +291,12 @@ class FloatGen:
     def div_block(self, store_label_prefix, store_targets):
         """DIV: ta <- ta / tb (protected), then jump on `dl` to a store label."""
         b, H = self.b, self.H
+        ta = [f"ta{i}" for i in range(H)]
+        tb = [f"tb{i}" for i in range(H)]
         b("DIV:")
-        for i in range(H):
-            if self.K == 1:
-                b("setp.eq.f32 pz, tb0, 0f00000000;")
-                b("div.rn.f32 fq0, ta0, tb0;")
-                b("selp.f32 ta0, 0f3F800000, fq0, pz;")
-            else:
-                b(f"mov.b64 {{fa0, fa1}}, ta{i};")
-                b(f"mov.b64 {{fb0, fb1}}, tb{i};")
-                b("setp.eq.f32 pz, fb0, 0f00000000;")
-                b("div.rn.f32 fq0, fa0, fb0;")
-                b("selp.f32 fq0, 0f3F800000, fq0, pz;")
-                b("setp.eq.f32 pz, fb1, 0f00000000;")
-                b("div.rn.f32 fq1, fa1, fb1;")
-                b("selp.f32 fq1, 0f3F800000, fq1, pz;")
-                b(f"mov.b64 ta{i}, {{fq0, fq1}};")
+        emit_pdiv(b, self.K, ta, tb, ta, "D")
         b(f"brx.idx.uni dl, {store_label_prefix}TBL;")
+        emit_pdiv_slow(b, self.K, ta, tb, "D")
 
     def loop_head(self, n_codes, table):
         """Table, prologue and the dispatch loop.  `table` maps code -> label."""
@@ -395,21 +501,9 @@ class FloatGen:
                         b("bra.uni STORE;")
         # DIV shares the destination jump with the other functions
         b("DIV:")
-        for i in range(H):
-            if K == 1:
-                b("setp.eq.f32 pz, tb0, 0f00000000;")
-                b("div.rn.f32 fq0, ta0, tb0;")
-                b("selp.f32 ta0, 0f3F800000, fq0, pz;")
-            else:
-                b(f"mov.b64 {{fa0, fa1}}, ta{i};")
-                b(f"mov.b64 {{fb0, fb1}}, tb{i};")
-                b("setp.eq.f32 pz, fb0, 0f00000000;")
-                b("div.rn.f32 fq0, fa0, fb0;")
-                b("selp.f32 fq0, 0f3F800000, fq0, pz;")
-                b("setp.eq.f32 pz, fb1, 0f00000000;")
-                b("div.rn.f32 fq1, fa1, fb1;")
-                b("selp.f32 fq1, 0f3F800000, fq1, pz;")
-                b(f"mov.b64 ta{i}, {{fq0, fq1}};")
+        emit_pdiv(b, K, ta, tb, ta, "D")
+        b("bra.uni STORE;")
+        emit_pdiv_slow(b, K, ta, tb, "D")
         b("STORE:")
         b(f"min.u32 dl, pa, {NREG - 1};")
         b("brx.idx.uni dl, STTBL;")
@@ -524,9 +618,41 @@ class BoolGen:
         return b
 
 
+def pdiv_macro(K):
+    """Standalone protected division of K values (exactly the interpreters'
+    sequence), for the division checker: K == 1 operands %0 = q, %1 = a,
+    %2 = b (f32); K == 4 operands %0, %1 = q pairs, %2, %3 = a pairs,
+    %4, %5 = b pairs (b64)."""
+    b = Block()
+    H = 1 if K == 1 else K // 2
+    b("{")
+    for ln in pdiv_regs(K, H).split("\n"):
+        b(ln)
+    ty = "f32" if K == 1 else "b64"
+    b(f".reg .{ty} qa<{H}>, qb<{H}>;")
+    if K > 1:
+        b("mov.b64 one2, 0x3F8000003F800000;")
+    for i in range(H):
+        b(f"mov.{ty} qa{i}, %{H + i};")
+        b(f"mov.{ty} qb{i}, %{2 * H + i};")
+    # the quotient overwrites the numerator registers, as in the interpreters
+    qa = [f"qa{i}" for i in range(H)]
+    qb = [f"qb{i}" for i in range(H)]
+    emit_pdiv(b, K, qa, qb, qa, "P")
+    for i in range(H):
+        b(f"mov.{ty} %{i}, qa{i};")
+    b("bra.uni PEND;")
+    emit_pdiv_slow(b, K, qa, qb, "P")
+    b("PEND:")
+    b("}")
+    return b
+
+
 def generate() -> str:
     parts = ["// gen_interp.h -- generated by paper_1601_00221_gb300/gen_interp.py; do not edit.\n",
              "#pragma once\n"]
+    parts.append(pdiv_macro(1).macro("GP_PTX_PDIV_K1", "protected division, one value"))
+    parts.append(pdiv_macro(4).macro("GP_PTX_PDIV_K4", "protected division, two packed pairs"))
     for K in (1, 2, 4, 8):
         for xm in ("reg", "smem"):
             X = xm.upper()

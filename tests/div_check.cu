@@ -1,0 +1,183 @@
+// div_check.cu -- checks the library's protected division (the generated PTX
+// sequence GP_PTX_PDIV_K4 / GP_PTX_PDIV_K1, the same code the interpreters
+// run) against CUDA's correctly rounded division: q == (b == 0 ? 1 : a / b)
+// bit for bit, any NaN equal to any NaN.  Test tool, built by
+// tests/test_division.py.
+//
+// Modes (argv[1]):
+//   mant <slice> <nslices>   every pair of significands with a, b in [1, 2)
+//                            (all 2^46 pairs over nslices launches; this run
+//                            covers slice `slice` only, or all if slice < 0)
+//   rand <n_per_thread> <seed>  random bit patterns over every exponent,
+//                            including zeros, subnormals, infinities, NaN
+//   exps <n_per_thread> <seed>  random significands under every pair of
+//                            exponents (the fast path's range boundaries)
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+#include "gen_interp.h"
+
+__device__ unsigned long long g_bad;
+__device__ unsigned long long g_first[3];  // a bits, b bits, got bits
+
+__device__ __forceinline__ float ref_pdiv(float a, float b) {
+  return (b == 0.0f) ? 1.0f : __fdiv_rn(a, b);
+}
+
+__device__ __forceinline__ bool same(float x, float y) {
+  return (__float_as_uint(x) == __float_as_uint(y)) || (x != x && y != y);
+}
+
+__device__ __forceinline__ void report(float a, float b, float q) {
+  unsigned long long n = atomicAdd(&g_bad, 1ull);
+  if (n == 0) {
+    g_first[0] = __float_as_uint(a);
+    g_first[1] = __float_as_uint(b);
+    g_first[2] = __float_as_uint(q);
+  }
+}
+
+__device__ __forceinline__ void pdiv4(const float (&a)[4], const float (&b)[4], float (&q)[4]) {
+  unsigned long long a0, a1, b0, b1, q0, q1;
+  float2 t;
+  t = make_float2(a[0], a[1]); a0 = *reinterpret_cast<unsigned long long*>(&t);
+  t = make_float2(a[2], a[3]); a1 = *reinterpret_cast<unsigned long long*>(&t);
+  t = make_float2(b[0], b[1]); b0 = *reinterpret_cast<unsigned long long*>(&t);
+  t = make_float2(b[2], b[3]); b1 = *reinterpret_cast<unsigned long long*>(&t);
+  asm volatile(GP_PTX_PDIV_K4 : "=l"(q0), "=l"(q1) : "l"(a0), "l"(a1), "l"(b0), "l"(b1));
+  t = *reinterpret_cast<float2*>(&q0); q[0] = t.x; q[1] = t.y;
+  t = *reinterpret_cast<float2*>(&q1); q[2] = t.x; q[3] = t.y;
+}
+
+__device__ __forceinline__ float pdiv1(float a, float b) {
+  float q;
+  asm volatile(GP_PTX_PDIV_K1 : "=f"(q) : "f"(a), "f"(b));
+  return q;
+}
+
+__device__ __forceinline__ void check4(const float (&a)[4], const float (&b)[4]) {
+  float q[4];
+  pdiv4(a, b, q);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float r = ref_pdiv(a[j], b[j]);
+    if (!same(q[j], r)) report(a[j], b[j], q[j]);
+    const float s = pdiv1(a[j], b[j]);
+    if (!same(s, r)) report(a[j], b[j], s);
+  }
+}
+
+// every significand pair: thread = one b significand, loop over a slice of a
+__global__ void k_mant(uint32_t a_begin, uint32_t a_end) {
+  const uint32_t mb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mb >= (1u << 23)) return;
+  const float bv = __uint_as_float(0x3f800000u | mb);
+  const float b[4] = {bv, bv, bv, bv};
+  for (uint32_t ma = a_begin; ma < a_end; ma += 4) {
+    float a[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[j] = __uint_as_float(0x3f800000u | (ma + j));
+    check4(a, b);
+  }
+}
+
+__device__ __forceinline__ uint32_t xorshift(uint32_t& s) {
+  s ^= s << 13; s ^= s >> 17; s ^= s << 5;
+  return s;
+}
+
+__global__ void k_rand(uint32_t n, uint32_t seed) {
+  uint32_t s = seed ^ (0x9E3779B9u * (blockIdx.x * blockDim.x + threadIdx.x + 1));
+  for (int i = 0; i < 16; ++i) xorshift(s);
+  for (uint32_t it = 0; it < n; ++it) {
+    float a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t x = xorshift(s), y = xorshift(s);
+      // a quarter of the operands get special exponents (0, 255) or zero significands
+      const uint32_t sel = xorshift(s);
+      if ((sel & 7) == 0) x &= 0x807fffffu;
+      if ((sel & 7) == 1) x |= 0x7f800000u;
+      if ((sel & 7) == 2) x &= 0xff800000u;
+      if (((sel >> 3) & 7) == 0) y &= 0x807fffffu;
+      if (((sel >> 3) & 7) == 1) y |= 0x7f800000u;
+      if (((sel >> 3) & 7) == 2) y &= 0xff800000u;
+      a[j] = __uint_as_float(x);
+      b[j] = __uint_as_float(y);
+    }
+    check4(a, b);
+  }
+}
+
+// random significands under every exponent pair: block = (ea, eb)
+__global__ void k_exps(uint32_t n, uint32_t seed) {
+  const uint32_t ea = blockIdx.x, eb = blockIdx.y;
+  uint32_t s = seed ^ (0x9E3779B9u * (ea * 256 + eb + 1)) ^ (threadIdx.x * 0x85EBCA6Bu);
+  for (int i = 0; i < 8; ++i) xorshift(s);
+  for (uint32_t it = 0; it < n; ++it) {
+    float a[4], b[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t x = xorshift(s), y = xorshift(s);
+      a[j] = __uint_as_float((x & 0x807fffffu) | (ea << 23));
+      b[j] = __uint_as_float((y & 0x807fffffu) | (eb << 23));
+    }
+    check4(a, b);
+  }
+}
+
+static int finish(const char* what) {
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    printf("%s: CUDA error %s\n", what, cudaGetErrorString(e));
+    return 2;
+  }
+  unsigned long long bad = 0, first[3] = {0, 0, 0};
+  cudaMemcpyFromSymbol(&bad, g_bad, sizeof bad);
+  cudaMemcpyFromSymbol(first, g_first, sizeof first);
+  if (bad) {
+    float a, b, q;
+    uint32_t ab = (uint32_t)first[0], bb = (uint32_t)first[1], qb = (uint32_t)first[2];
+    memcpy(&a, &ab, 4); memcpy(&b, &bb, 4); memcpy(&q, &qb, 4);
+    printf("%s: %llu mismatches; first a=%a (0x%08x) b=%a (0x%08x) got %a (0x%08x)\n", what, bad, a, ab, b, bb, q, qb);
+    return 1;
+  }
+  printf("%s: 0 mismatches\n", what);
+  return 0;
+}
+
+int main(int argc, char** argv) {
+  if (argc < 2) {
+    fprintf(stderr, "usage: div_check mant <slice> <nslices> | rand <n> <seed> | exps <n> <seed>\n");
+    return 3;
+  }
+  unsigned long long zero = 0;
+  cudaMemcpyToSymbol(g_bad, &zero, sizeof zero);
+  const char* mode = argv[1];
+  if (!strcmp(mode, "mant")) {
+    const int slice = atoi(argv[2]), nslices = atoi(argv[3]);
+    const uint32_t per = (1u << 23) / (uint32_t)nslices;
+    if (per % 4 || per * (uint32_t)nslices != (1u << 23)) { fprintf(stderr, "bad slicing\n"); return 3; }
+    for (int s = (slice < 0 ? 0 : slice); s < (slice < 0 ? nslices : slice + 1); ++s) {
+      k_mant<<<(1u << 23) / 256, 256>>>(s * per, (s + 1) * per);
+      if (cudaDeviceSynchronize() != cudaSuccess) break;
+    }
+    char what[64];
+    snprintf(what, sizeof what, "significand pairs slice %d of %d", slice, nslices);
+    return finish(what);
+  }
+  if (!strcmp(mode, "rand")) {
+    k_rand<<<152 * 16, 256>>>((uint32_t)atoi(argv[2]), (uint32_t)atoi(argv[3]));
+    return finish("random bit patterns");
+  }
+  if (!strcmp(mode, "exps")) {
+    k_exps<<<dim3(256, 256), 32>>>((uint32_t)atoi(argv[2]), (uint32_t)atoi(argv[3]));
+    return finish("all exponent pairs");
+  }
+  fprintf(stderr, "unknown mode\n");
+  return 3;
+}

@@ -100,7 +100,7 @@ __device__ __forceinline__ bool valid_bool_instr(const uint4& in, int n_inputs) 
 template <int K>
 __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   using namespace gpisa;
-  __shared__ uint4 prog_s[MAX_INSTR];
+  __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
   __shared__ unsigned long long red_s[32];
   __shared__ int meta_s;
   extern __shared__ uint4 btile_s[];  // [warp][input][32 lanes][K words]
@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
       prog_s[i] = in;
       ok &= valid_bool_instr(in, a.n_inputs) ? 1 : 0;
     }
+    if (tid == 0) prog_s[n_instr] = make_uint4(BOOL_NCODES, 0u, 0u, 0u);  // end sentinel
     bad = !__syncthreads_and(ok);
   }
   if (bad) {

@@ -163,7 +163,7 @@ __device__ __forceinline__ bool valid_instr(uint32_t kind, const uint4& in, int 
 template <int K, bool XREG>
 __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   using namespace gpisa;
-  __shared__ uint4 prog_s[MAX_INSTR];
+  __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
   __shared__ Partial red_s[32];
   __shared__ int meta_s[2];  // n_instr (or -1 if bad), kind
   extern __shared__ float4 tile_s[];  // [warp][input][32 lanes][K] when staged
@@ -201,6 +201,10 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
       prog_s[i] = in;
       ok &= valid_instr(kind, in, a.n_inputs) ? 1 : 0;
     }
+    // the interpreters leave through the table entry one past the last code
+    if (tid == 0)
+      prog_s[n_instr] = make_uint4(kind == K_SFORM ? SF_NCODES : kind == K_RPN ? RF_NCODES : LIN_NCODES,
+                                   0u, 0u, 0u);
     bad = !__syncthreads_and(ok);
   }
 

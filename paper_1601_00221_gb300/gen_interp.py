@@ -1,9 +1,10 @@
 """Generates the inline-PTX interpreter loops of the CUDA library.
 
-Each interpreter is one PTX block: a loop that loads the next 16-byte
-instruction from shared memory (one broadcast load per warp), clamps its code
-and jumps through a ``brx.idx.uni`` jump table straight to the body of that
-(function, operand forms, stack level) combination.  The stack levels live in
+Each interpreter is one PTX block: every body loads the next 16-byte
+instruction from shared memory (one broadcast load per warp) as soon as it has
+read its own payloads, then returns to a single ``brx.idx.uni`` jump through a
+table straight to the body of the next (function, operand forms, stack level)
+combination; a sentinel instruction written after the program jumps out.  The stack levels live in
 registers whose names are fixed in each body, so no body indexes a register
 at run time (Sec. 6.2 of the paper keeps low stack levels in registers behind
 a switch on the stack pointer; here the level is resolved by the encoder and
@@ -96,14 +97,15 @@ def emit_pdiv(b, K, A, B, Q, tag, group=2):
     Newton-Raphson step y1 = y0 + y0 (1 - b y0), the quotient q0 = a y1, the
     exact remainder r = a - b q0 (one FMA) and Markstein's correction
     q1 = q0 + r y1 (P. Markstein, IBM J. Res. Dev. 34(1), 1990), in
-    fma/mul.rn.f32x2, `group` pairs interleaved at a time.  An element is
-    right on this path when |a| >= 2^-100 and 2^-100 <= |q1| <= 2^100 (every
-    intermediate value stays normal, so the remainder is exact) or when its
-    denominator is zero (the final select gives 1).  A lane with any other
-    element takes the slow path, div.rn.f32, for all its elements; the
-    emit_pdiv_slow block must follow somewhere in the same asm block.
-    Scratch registers come from pdiv_regs().  Q may name the same registers
-    as A: quotients stay in dQ until the final selects."""
+    fma/mul.rn.f32x2, `group` pairs interleaved at a time.  The fast result
+    of a lane is kept when, over all its elements, min(|q1|, |a|) >= 2^-100
+    and max |q1| <= 2^100 (NaN-propagating min/max, so a NaN anywhere fails):
+    every intermediate value is then normal and each remainder exact.  Any
+    other lane (a zero, subnormal, huge or non-finite operand, a zero
+    denominator) takes the slow path: div.rn.f32 and the protection select
+    for each element.  The emit_pdiv_slow block must follow in the same asm
+    block.  Scratch registers come from pdiv_regs().  Q may name the same
+    registers as A: quotients stay in dQ until the end."""
     H = len(A)
     if K == 1:
         b(f"rcp.approx.ftz.f32 dY0, {B[0]};")
@@ -113,16 +115,17 @@ def emit_pdiv(b, K, A, B, Q, tag, group=2):
         b(f"mul.rn.f32 dQ0, {A[0]}, dY0;")
         b(f"fma.rn.f32 dE0, dN0, dQ0, {A[0]};")
         b("fma.rn.f32 dQ0, dE0, dY0, dQ0;")
-        _emit_check(b, "dQ0", A[0], B[0], first=True)
+        b("abs.f32 dhi, dQ0;")
+        b(f"abs.f32 dt, {A[0]};")
+        b("min.NaN.f32 dlo, dhi, dt;")
     else:
-        first = True
         for g0 in range(0, H, group):
             idx = list(range(g0, min(H, g0 + group)))
             for i in idx:
-                b(f"mov.b64 {{dlo, dhi}}, {B[i]};")
-                b("rcp.approx.ftz.f32 dlo, dlo;")
-                b("rcp.approx.ftz.f32 dhi, dhi;")
-                b(f"mov.b64 dY{i}, {{dlo, dhi}};")
+                b(f"mov.b64 {{dt, dt2}}, {B[i]};")
+                b("rcp.approx.ftz.f32 dt, dt;")
+                b("rcp.approx.ftz.f32 dt2, dt2;")
+                b(f"mov.b64 dY{i}, {{dt, dt2}};")
                 b(f"xor.b64 dN{i}, {B[i]}, 0x8000000080000000;")
             for i in idx:
                 b(f"fma.rn.f32x2 dE{i}, dN{i}, dY{i}, one2;")
@@ -134,55 +137,52 @@ def emit_pdiv(b, K, A, B, Q, tag, group=2):
                 b(f"fma.rn.f32x2 dE{i}, dN{i}, dQ{i}, {A[i]};")
             for i in idx:
                 b(f"fma.rn.f32x2 dQ{i}, dE{i}, dY{i}, dQ{i};")
-            for i in idx:
-                b(f"mov.b64 {{dlo, dhi}}, dQ{i};")
-                b(f"mov.b64 {{dt, dt2}}, {A[i]};")
-                b(f"mov.b64 {{da, db}}, {B[i]};")
-                _emit_check(b, "dlo", "dt", "da", first)
-                first = False
-                _emit_check(b, "dhi", "dt2", "db", first)
+        for i in range(H):
+            b(f"mov.b64 {{dt, dt2}}, dQ{i};")
+            b("abs.f32 dt, dt;")
+            b("abs.f32 dt2, dt2;")
+            if i == 0:
+                b("max.NaN.f32 dhi, dt, dt2;")
+                b("min.NaN.f32 dlo, dt, dt2;")
+            else:
+                b("max.NaN.f32 dhi, dhi, dt;")
+                b("max.NaN.f32 dhi, dhi, dt2;")
+                b("min.NaN.f32 dlo, dlo, dt;")
+                b("min.NaN.f32 dlo, dlo, dt2;")
+            b(f"mov.b64 {{dt, dt2}}, {A[i]};")
+            b("abs.f32 dt, dt;")
+            b("abs.f32 dt2, dt2;")
+            b("min.NaN.f32 dlo, dlo, dt;")
+            b("min.NaN.f32 dlo, dlo, dt2;")
+    b(f"setp.ge.f32 dok, dlo, {DIV_LO};")
+    b(f"setp.le.and.f32 dok, dhi, {DIV_HI}, dok;")
     b(f"@!dok bra {tag}SLOW;")
     b(f"{tag}RET:")
     if K == 1:
-        b(f"setp.eq.f32 dz, {B[0]}, 0f00000000;")
-        b(f"selp.f32 {Q[0]}, 0f3F800000, dQ0, dz;")
-        return
-    for i in range(H):
-        b(f"mov.b64 {{dlo, dhi}}, dQ{i};")
-        b(f"mov.b64 {{dt, dt2}}, {B[i]};")
-        b("setp.eq.f32 dz, dt, 0f00000000;")
-        b("selp.f32 dlo, 0f3F800000, dlo, dz;")
-        b("setp.eq.f32 dz, dt2, 0f00000000;")
-        b("selp.f32 dhi, 0f3F800000, dhi, dz;")
-        b(f"mov.b64 {Q[i]}, {{dlo, dhi}};")
-
-
-def _emit_check(b, q, a, den, first):
-    """dok (&)= the fast quotient q of a / den is right (see emit_pdiv)."""
-    b(f"abs.f32 dz0, {q};")
-    b(f"setp.ge.f32 dz, dz0, {DIV_LO};")
-    b(f"setp.le.and.f32 dz, dz0, {DIV_HI}, dz;")
-    b(f"abs.f32 dz0, {a};")
-    b(f"setp.ge.and.f32 dz, dz0, {DIV_LO}, dz;")
-    b(f"setp.eq.or.f32 dz, {den}, 0f00000000, dz;")
-    if first:
-        b("mov.pred dok, dz;")
+        b(f"mov.f32 {Q[0]}, dQ0;")
     else:
-        b("and.pred dok, dok, dz;")
+        for i in range(H):
+            b(f"mov.b64 {Q[i]}, dQ{i};")
 
 
 def emit_pdiv_slow(b, K, A, B, tag):
-    """Out-of-line slow path of emit_pdiv: IEEE division of every element
-    into dQ, then back to the selects."""
+    """Out-of-line slow path of emit_pdiv: IEEE division and the protection
+    select (zero denominator -> 1) of every element into dQ, then back."""
     b(f"{tag}SLOW:")
     if K == 1:
         b(f"div.rn.f32 dQ0, {A[0]}, {B[0]};")
+        b(f"setp.eq.f32 dz, {B[0]}, 0f00000000;")
+        b("selp.f32 dQ0, 0f3F800000, dQ0, dz;")
     else:
         for i in range(len(A)):
             b(f"mov.b64 {{dlo, dhi}}, {A[i]};")
             b(f"mov.b64 {{dt, dt2}}, {B[i]};")
             b("div.rn.f32 dlo, dlo, dt;")
+            b("setp.eq.f32 dz, dt, 0f00000000;")
+            b("selp.f32 dlo, 0f3F800000, dlo, dz;")
             b("div.rn.f32 dhi, dhi, dt2;")
+            b("setp.eq.f32 dz, dt2, 0f00000000;")
+            b("selp.f32 dhi, 0f3F800000, dhi, dz;")
             b(f"mov.b64 dQ{i}, {{dlo, dhi}};")
     b(f"bra {tag}RET;")
 
@@ -190,7 +190,7 @@ def emit_pdiv_slow(b, K, A, B, tag):
 def pdiv_regs(K, H):
     ty = "f32" if K == 1 else "b64"
     return (f".reg .{ty} dY<{H}>, dE<{H}>, dN<{H}>, dQ<{H}>, one2;\n"
-            f".reg .f32 dlo, dhi, dt, dt2, da, db, dz0;\n"
+            f".reg .f32 dlo, dhi, dt, dt2;\n"
             f".reg .pred dok, dz;")
 
 
@@ -211,6 +211,15 @@ class Block:
 # float interpreters
 # ---------------------------------------------------------------------------
 class FloatGen:
+    """One dispatch site (LOOP: brx on the current code).  Every body loads
+    the next instruction right after reading its own payloads, so the
+    shared-memory load overlaps the body's arithmetic, and branches back to
+    LOOP.  (Ending each body with its own brx -- direct threading -- was
+    measured to be slower: several hundred indirect-branch sites.)  The kernel
+    writes a sentinel instruction (code n_codes) after the last one; its table
+    entry is DONE, so the loop needs no bound check.  Codes are validated when
+    the program is staged, so no code is clamped."""
+
     def __init__(self, K, xmode):
         assert K in (1, 2, 4, 8) and xmode in ("reg", "smem")
         self.K, self.xmode = K, xmode
@@ -235,19 +244,18 @@ class FloatGen:
         b(f".reg .{self.ty} s<{R * H}>, ta<{H}>, tb<{H}>, xA<{H}>, xB<{H}>, cA, cB;")
         if self.xmode == "reg":
             b(f".reg .{self.ty} x<{H}>;")
-        b(".reg .b32 code, pa, pb, pc, adr, end, dl, xa, xbase;")
-        b(".reg .f32 fa0, fa1, fb0, fb1, fq0, fq1;")
-        b(".reg .pred p, pz;")
+        b(".reg .b32 code, pa, pb, pc, adr, dl, xa, xbase;")
+        b(".reg .pred p;")
         for ln in pdiv_regs(K, H).split("\n"):
             b(ln)
         if K > 1:
             b("mov.b64 one2, 0x3F8000003F800000;")
         if extra_regs:
             b(extra_regs)
-        # Define every stack register before the loop: the jump table makes any
-        # of them readable at the loop head, so an undefined one would be live
-        # from the kernel's entry and could not share a physical register with
-        # the other interpreters of the same kernel.
+        # Define every stack register before the first jump: the jump table
+        # makes any of them readable at every body, so an undefined one would
+        # be live from the kernel's entry and could not share a physical
+        # register with the other interpreters of the same kernel.
         zero = "0f00000000" if K == 1 else "0"
         for r in range(R * H):
             b(f"mov.{self.ty} s{r}, {zero};")
@@ -288,34 +296,28 @@ class FloatGen:
         for i in range(self.H):
             self.b(f"mov.{self.ty} {d[i]}, {a[i]};")
 
-    def div_block(self, store_label_prefix, store_targets):
-        """DIV: ta <- ta / tb (protected), then jump on `dl` to a store label."""
-        b, H = self.b, self.H
-        ta = [f"ta{i}" for i in range(H)]
-        tb = [f"tb{i}" for i in range(H)]
-        b("DIV:")
-        emit_pdiv(b, self.K, ta, tb, ta, "D")
-        b(f"brx.idx.uni dl, {store_label_prefix}TBL;")
-        emit_pdiv_slow(b, self.K, ta, tb, "D")
+    # dispatch pieces
+    def fetch(self):
+        """Loads the next instruction (call after the payloads are consumed)."""
+        self.b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
+        self.b("add.u32 adr, adr, 16;")
 
-    def loop_head(self, n_codes, table):
-        """Table, prologue and the dispatch loop.  `table` maps code -> label."""
-        b, K = self.b, self.K
-        labels = [table.get(c, "CBAD") for c in range(n_codes)] + ["CBAD"]
-        b("TBL: .branchtargets " + ", ".join(labels) + ";")
+    def jump(self):
+        self.b("bra.uni LOOP;")
+
+    def table(self, n_codes, table):
+        labels = [table.get(c, "CBAD") for c in range(n_codes)] + ["DONE"]
+        self.b("TBL: .branchtargets " + ", ".join(labels) + ";")
+
+    def prologue(self):
+        K, b = self.K, self.b
         b(f"mov.u32 adr, %{K + 1};")
-        b(f"mad.lo.u32 end, %{K + 2}, 16, adr;")
         b(f"mov.u32 %{K}, 0;")
 
-    def dispatch(self, n_codes):
-        b = self.b
-        b("LOOP:")
-        b("setp.ge.u32 p, adr, end;")
-        b("@p bra.uni DONE;")
-        b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
-        b("add.u32 adr, adr, 16;")
-        b(f"min.u32 code, code, {n_codes};")
-        b("brx.idx.uni code, TBL;")
+    def start(self):
+        self.fetch()
+        self.b("LOOP:")
+        self.b("brx.idx.uni code, TBL;")
 
     def epilogue(self, out_units):
         b, K = self.b, self.K
@@ -340,16 +342,23 @@ class FloatGen:
         else:
             b(f"mov.u32 xbase, %{K + 3};")
 
-    def store_table(self, prefix, units_of_level):
-        b = self.b
-        b(f"{prefix}TBL: .branchtargets " + ", ".join(f"{prefix}{l}" for l in range(R)) + ";")
+    def store_table(self):
+        self.b("STTBL: .branchtargets " + ", ".join(f"ST{l}" for l in range(R)) + ";")
 
-    def store_bodies(self, prefix, units_of_level, src):
-        b = self.b
+    def store_bodies(self, units_of_level, src):
         for l in range(R):
-            b(f"{prefix}{l}:")
+            self.b(f"ST{l}:")
             self.copy(units_of_level(l), src)
-            b("bra.uni LOOP;")
+            self.jump()
+
+    def div_block(self, ta, tb, then_store=True):
+        """DIV: ta <- ta / tb (protected), then jump on `dl` to a store body."""
+        b = self.b
+        b("DIV:")
+        emit_pdiv(b, self.K, ta, tb, ta, "D")
+        b("STORE:")
+        b("brx.idx.uni dl, STTBL;")
+        emit_pdiv_slow(b, self.K, ta, tb, "D")
 
     # ------------------------------------------------------------------
     def sform(self):
@@ -372,20 +381,24 @@ class FloatGen:
                     code = sform_code(f, l, op)
                     table[code] = f"C{code}"
                     bodies.append((code, name, l, op))
-        self.store_table("ST", L)
-        self.loop_head(n_codes, table)
+        self.store_table()
+        self.table(n_codes, table)
+        self.prologue()
         self.setup_inputs()
-        self.dispatch(n_codes)
+        self.start()
         for code, name, l, op in bodies:
             b(f"C{code}:")
             if name == "MOVX":
                 src = self.load_x(xA, "pa")
+                self.fetch()
                 self.copy(L(0), src)
-                b("bra.uni LOOP;")
+                self.jump()
                 continue
             if name == "MOVC":
-                self.copy(L(0), self.const("cA", "pa"))
-                b("bra.uni LOOP;")
+                src = self.const("cA", "pa")
+                self.fetch()
+                self.copy(L(0), src)
+                self.jump()
                 continue
             if name == "SS":
                 a, c = L(l), L(l + 1)
@@ -399,12 +412,14 @@ class FloatGen:
                 self.copy(ta, a)
                 self.copy(tb, c)
                 b(f"mov.u32 dl, {l};")
+                self.fetch()
                 b("bra.uni DIV;")
             else:
+                self.fetch()
                 self.vop(op, L(l), a, c)
-                b("bra.uni LOOP;")
-        self.div_block("ST", None)
-        self.store_bodies("ST", L, ta)
+                self.jump()
+        self.div_block(ta, tb)
+        self.store_bodies(L, ta)
         self.epilogue(L(0))
         return b
 
@@ -426,24 +441,30 @@ class FloatGen:
                     code = rpn_code(f, l, op)
                     table[code] = f"C{code}"
                     bodies.append((code, name, l, op))
-        self.store_table("ST", L)
-        self.loop_head(n_codes, table)
+        self.store_table()
+        self.table(n_codes, table)
+        self.prologue()
         self.setup_inputs()
-        self.dispatch(n_codes)
+        self.start()
         for code, name, l, op in bodies:
             b(f"C{code}:")
             if name == "PUSHX":
                 if self.xmode == "reg":
+                    self.fetch()
                     self.copy(L(l), [self.xreg(i) for i in range(H)])
                 else:
                     self.load_x(L(l), "pa")
-                b("bra.uni LOOP;")
+                    self.fetch()
+                self.jump()
                 continue
             if name == "PUSHC":
-                self.copy(L(l), self.const("cA", "pa"))
-                b("bra.uni LOOP;")
+                src = self.const("cA", "pa")
+                self.fetch()
+                self.copy(L(l), src)
+                self.jump()
                 continue
             a, c = (L(l), L(l + 1)) if name == "OP" else (L(l + 1), L(l))
+            self.fetch()
             if op == 3:
                 self.copy(ta, a)
                 self.copy(tb, c)
@@ -451,15 +472,16 @@ class FloatGen:
                 b("bra.uni DIV;")
             else:
                 self.vop(op, L(l), a, c)
-                b("bra.uni LOOP;")
-        self.div_block("ST", None)
-        self.store_bodies("ST", L, ta)
+                self.jump()
+        self.div_block(ta, tb)
+        self.store_bodies(L, ta)
         self.epilogue(L(0))
         return b
 
     def linear(self):
         """Register machine r[d] = r[a] op r[b]; registers start from the staged
-        inputs (register v < nin) or 0."""
+        inputs (register v < nin) or 0.  The body computes into ta, then jumps
+        on d (the first payload) to the store of register d."""
         K, H, b = self.K, self.H, self.b
         assert self.xmode == "smem"
         self.header(".reg .b32 nin;")
@@ -469,8 +491,9 @@ class FloatGen:
         n_codes = 4 * NREG * NREG
         table = {lin_code(op, a, c): f"C{lin_code(op, a, c)}"
                  for op in range(4) for a in range(NREG) for c in range(NREG)}
-        self.store_table("ST", Rg)
-        self.loop_head(n_codes, table)
+        self.store_table()
+        self.table(n_codes, table)
+        self.prologue()
         b(f"mov.u32 xbase, %{K + 3};")
         b(f"mov.u32 nin, %{K + 4};")
         zero = "0f00000000" if K == 1 else "0"
@@ -478,7 +501,6 @@ class FloatGen:
             b(f"setp.lt.u32 p, {r}, nin;")
             b(f"mov.u32 pa, {r};")
             units = Rg(r)
-            # load when staged, else zero
             b(f"@!p bra.uni Z{r};")
             self.load_x(units, "pa")
             b(f"bra.uni I{r};")
@@ -486,12 +508,14 @@ class FloatGen:
             for u in units:
                 b(f"mov.{self.ty} {u}, {zero};")
             b(f"I{r}:")
-        self.dispatch(n_codes)
+        self.start()
         for op in range(4):
             for a in range(NREG):
                 for c in range(NREG):
                     code = lin_code(op, a, c)
                     b(f"C{code}:")
+                    b("mov.u32 dl, pa;")
+                    self.fetch()
                     if op == 3:
                         self.copy(ta, Rg(a))
                         self.copy(tb, Rg(c))
@@ -499,15 +523,8 @@ class FloatGen:
                     else:
                         self.vop(op, ta, Rg(a), Rg(c))
                         b("bra.uni STORE;")
-        # DIV shares the destination jump with the other functions
-        b("DIV:")
-        emit_pdiv(b, K, ta, tb, ta, "D")
-        b("bra.uni STORE;")
-        emit_pdiv_slow(b, K, ta, tb, "D")
-        b("STORE:")
-        b(f"min.u32 dl, pa, {NREG - 1};")
-        b("brx.idx.uni dl, STTBL;")
-        self.store_bodies("ST", Rg, ta)
+        self.div_block(ta, tb)
+        self.store_bodies(Rg, ta)
         self.epilogue(Rg(0))
         return b
 
@@ -516,6 +533,8 @@ class FloatGen:
 # Boolean interpreter (K words per thread, 32 cases per word)
 # ---------------------------------------------------------------------------
 class BoolGen:
+    """Same dispatch as FloatGen, over K-word registers."""
+
     def __init__(self, K):
         self.K = K
         self.b = Block()
@@ -538,6 +557,13 @@ class BoolGen:
                 b(f"ld.shared.v4.b32 {{{', '.join(d)}}}, [xa{off}];")
         return dst
 
+    def fetch(self):
+        self.b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
+        self.b("add.u32 adr, adr, 16;")
+
+    def jump(self):
+        self.b("bra.uni LOOP;")
+
     def gen(self):
         K, b = self.K, self.b
         xA = [f"xA{j}" for j in range(K)]
@@ -545,9 +571,8 @@ class BoolGen:
         xC = [f"xC{j}" for j in range(K)]
         b("{")
         b(f".reg .b32 s<{R * K}>, xA<{K}>, xB<{K}>, xC<{K}>;")
-        b(".reg .b32 code, pa, pb, pc, adr, end, xa, xbase;")
-        b(".reg .pred p;")
-        for r in range(R * K):  # defined before the loop (see FloatGen.header)
+        b(".reg .b32 code, pa, pb, pc, adr, xa, xbase;")
+        for r in range(R * K):  # defined before the first jump (see FloatGen.header)
             b(f"mov.b32 s{r}, 0;")
         n_codes = BOOL_MOVX + 1
         table, bodies = {}, []
@@ -568,18 +593,13 @@ class BoolGen:
                 table[code] = f"C{code}"
                 bodies.append((code, "if", d, l, None))
         table[BOOL_MOVX] = "CMOV"
-        labels = [table.get(c, "CBAD") for c in range(n_codes)] + ["CBAD"]
+        labels = [table.get(c, "CBAD") for c in range(n_codes)] + ["DONE"]
         b("TBL: .branchtargets " + ", ".join(labels) + ";")
         b(f"mov.u32 adr, %{K + 1};")
-        b(f"mad.lo.u32 end, %{K + 2}, 16, adr;")
         b(f"mov.u32 %{K}, 0;")
         b(f"mov.u32 xbase, %{K + 3};")
+        self.fetch()
         b("LOOP:")
-        b("setp.ge.u32 p, adr, end;")
-        b("@p bra.uni DONE;")
-        b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
-        b("add.u32 adr, adr, 16;")
-        b(f"min.u32 code, code, {n_codes};")
         b("brx.idx.uni code, TBL;")
         for code, kind, name, l, op in bodies:
             b(f"C{code}:")
@@ -592,6 +612,7 @@ class BoolGen:
                 else:
                     a = S if name[0] == "S" else self.load_x(xA, "pa")
                     c = S if name[1] == "S" else self.load_x(xB, "pb")
+                self.fetch()
                 for j in range(K):
                     b(f"lop3.b32 {S[j]}, {a[j]}, {c[j]}, {c[j]}, 0x{LUT[op]:02X};")
             else:
@@ -599,16 +620,18 @@ class BoolGen:
                 ops = []
                 for dsc, pay, tmp in ((dc, "pa", xA), (da, "pb", xB), (db, "pc", xC)):
                     ops.append(self.load_x(tmp, pay) if dsc == 0 else self.lev(l + dsc - 1))
+                self.fetch()
                 cc, aa, bb = ops
                 for j in range(K):
                     b(f"lop3.b32 {S[j]}, {cc[j]}, {aa[j]}, {bb[j]}, 0x{LUT_IF:02X};")
-            b("bra.uni LOOP;")
+            self.jump()
         b("CMOV:")
         src = self.load_x(xA, "pa")
+        self.fetch()
         S0 = self.lev(0)
         for j in range(K):
             b(f"mov.b32 {S0[j]}, {src[j]};")
-        b("bra.uni LOOP;")
+        self.jump()
         b("CBAD:")
         b(f"mov.u32 %{K}, 1;")
         b("DONE:")

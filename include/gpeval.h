@@ -192,6 +192,36 @@ int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets, const int3
                     float* outputs, const gp_config* cfg, gp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Float fitness without device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory -- for instance an application that gives the GPU's memory
+ * to its own fixed-size pool, or an evaluation loop that must not meet an
+ * allocation failure, or the synchronisation an allocation can imply, in the
+ * middle of a run.  It computes exactly what gp_eval_population computes
+ * (same arguments, same kernel, default configuration) but keeps the kernel's
+ * scratch (per-block partial sums, per-program counters, a status word) in a
+ * fixed array of about 1.25 MiB that every device loading the library holds
+ * until the process exits; it never calls cudaMalloc or cudaFree.
+ *   - n_progs may be at most GP_NOALLOC_MAX_PARTIALS; larger calls return
+ *     GP_ERR_INVALID_ARG.  Cases are split into fewer blocks when needed so
+ *     that the partial sums fit.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one array, which keeps the previous
+ *     call's contents; each call clears the parts it relies on.  Calls whose
+ *     work overlaps on the GPU (different streams, or host threads) race on
+ *     the array: serialise them.
+ *   - Malformed programs give NaN fitness as in gp_eval_population; the
+ *     status word is not reported (gp_last_error does not see it).
+ * ---------------------------------------------------------------------- */
+#define GP_NOALLOC_MAX_PARTIALS 65536
+int gp_eval_population_noalloc(const uint32_t* programs, const int64_t* offsets,
+                               const int32_t* lengths, int32_t n_progs, const float* cases,
+                               int32_t n_inputs, int64_t n_cases, const float* targets,
+                               double* fitness_out, gp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Bit-packed Boolean fitness (Sec. 4.2: 32 fitness cases per 32-bit word,
  * sub-machine-code GP).  programs: GP_KIND_BOOL.  case_bits uint32
  * [n_inputs][ceil(n_cases/32)]: case c of input v is bit (c & 31) of word

@@ -123,6 +123,7 @@ def kernel_source_digest() -> str:
     for f in sorted(os.listdir(d)):
         if f.startswith(("eval_float", "common", "isa")):
             h.update(open(os.path.join(d, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_1601_00221_gb300", "gen_interp.py"), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--k", type=int, default=0, help="force K (0 = tune)")
     ap.add_argument("--block", type=int, default=0, help="force the block size (0 = tune)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the Boolean, register-GP and serving measurements")
+    ap.add_argument("--serving-runs", type=int, default=64)
     return ap.parse_args()
 
 
@@ -177,7 +180,9 @@ def run_ours(args):
     gp.lib()
 
     # --- workload: each rank evaluates its own population (weak scaling) ---
-    w = synth.regression_large(seed=2 + 1000 * rank, n_progs=args.programs, n_cases=args.cases)
+    from paper_1601_00221_gb300 import dist as gdist
+    w = synth.regression_large(seed=gdist.population_seed(2, rank), n_progs=args.programs,
+                               n_cases=args.cases)
     enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM,
                                gp.ORDER_MIN_DEPTH)
     P, O, L = enc.to_device(device)
@@ -235,11 +240,7 @@ def run_ours(args):
     torch.cuda.synchronize(device)
     if world > 1:
         dist.barrier()
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = gdist.max_over_ranks(float(sum(times)), device)
     ms_step = total_ms / args.steps
     value = gpop_step * world * args.steps / (total_ms / 1e3) / 1e9
 
@@ -312,11 +313,7 @@ def run_ours(args):
                 e2e_times.append(t2 - t1)
             h2d = hw.numel() * 4 + ho.numel() * 8 + hl.numel() * 4
             d2h = host_fit.numel() * 8
-        e2e_s = sum(e2e_times)
-        if world > 1:
-            t = torch.tensor([e2e_s], device=device)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = gdist.max_over_ranks(sum(e2e_times), device)
         e2e = {"value": round(gpop_step * world * args.steps / e2e_s / 1e9, 2), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(e2e_s / args.steps * 1e3, 4),
@@ -327,6 +324,15 @@ def run_ours(args):
     err_stats = None
     if rank == 0 and not args.no_cpu:
         cpu_baseline, err_stats = cpu_oracle_baseline(w, fit.cpu().numpy(), n_cases)
+
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra["boolean"] = bench_boolean(gp, synth, torch, device)
+        lin, lin_fit, lin_w = bench_linear(gp, synth, torch, device)
+        if not args.no_cpu:
+            lin.update(cpu_oracle_linear(lin_w, lin_fit))  # CPU-baseline leg
+        extra["register_gp"] = lin
+        extra["serving"] = bench_serving(gp, synth, args.serving_runs)
 
     if rank != 0:
         if world > 1:
@@ -354,10 +360,169 @@ def run_ours(args):
         "fitness_rel_err_vs_fp64_oracle": err_stats,
         "wall_s_timed_region": round(wall, 3),
     }
+    if "serving" in extra:
+        sv = extra["serving"]
+        line["serving_p50_ms"] = sv.get("p50_ms")
+        line["serving_p99_ms"] = sv.get("p99_ms")
+    line.update(extra)
     print(json.dumps(line))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _time_events(torch, fn, steps=5, warmup=2):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(steps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / steps
+
+
+def bench_boolean(gp, synth, torch, device):
+    """Bit-packed Boolean problems: 4096 random trees (<= 256 nodes) each;
+    GPop counts cases as bits (32 per word), as the paper's 20-multiplexer does."""
+    import numpy as np
+    out = {}
+    for kind, k in (("parity", 6), ("mux", 6), ("parity", 11), ("mux", 11), ("mux", 20)):
+        n_progs = 4096 if k < 20 else 1024
+        w = synth.boolean_problem(kind, k, n_progs=n_progs)
+        enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL)
+        P, O, L = enc.to_device(device)
+        cb = torch.from_numpy(w.case_bits.view(np.int32)).to(device)
+        tb = torch.from_numpy(w.target_bits.view(np.int32)).to(device)
+        hits = torch.empty(w.pop.n, dtype=torch.int64, device=device)
+        best = None
+        for kk in (1, 2, 4, 8):
+            cfg = gp.Config(gp.VARIANT_REGISTER, kk, 0, 0)
+            ms = _time_events(torch, lambda: gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
+                                                                     hits_out=hits, config=cfg))
+            if best is None or ms < best[0]:
+                best = (ms, kk)
+        gpop = w.gpop
+        out[f"{kind}{k}"] = {"programs": w.pop.n, "cases": w.n_cases, "k": best[1],
+                             "ms": round(best[0], 4), "bit_GPop_per_s": round(gpop / best[0] / 1e6, 1)}
+    return out
+
+
+def bench_linear(gp, synth, torch, device):
+    """Register linear GP: 8 registers, 16-128 instructions, 8 inputs x 262144
+    cases (a 1024-program sample of the 8192-program population per launch)."""
+    w = synth.linear_workload(n_progs=1024)
+    enc = gp.encode_linear_population(w.pop.instr, w.pop.offsets, w.pop.lengths)
+    P, O, L = enc.to_device(device)
+    X = torch.from_numpy(w.cases).to(device)
+    Y = torch.from_numpy(w.targets).to(device)
+    fit = torch.empty(w.pop.n, dtype=torch.float64, device=device)
+    best = None
+    for k in (4, 8):
+        cfg = gp.Config(gp.VARIANT_REGISTER, k, 256, 0)
+        ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg),
+                          steps=2, warmup=1)
+        if best is None or ms < best[0]:
+            best = (ms, k)
+    return ({"programs": w.pop.n, "cases": int(w.cases.shape[1]),
+             "instructions": int(w.pop.lengths.sum()), "k": best[1], "ms": round(best[0], 3),
+             "GPop_per_s": round(w.gpop / best[0] / 1e6, 1)}, fit.cpu().numpy(), w)
+
+
+def cpu_oracle_linear(w, gpu_fit):
+    """CPU-baseline leg for the register programs: the oracle on a 16-program
+    sample (timed, threads over programs), and the GPU fitness error against it."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    sample = np.arange(0, w.pop.n, max(1, w.pop.n // 16))
+
+    def job(p):
+        return int(p), oracle.linear_population_fitness(w.pop.instr, w.pop.offsets, w.pop.lengths,
+                                                        w.cases, w.targets,
+                                                        p_range=(int(p), int(p) + 1))[int(p)]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        res = dict(ex.map(job, sample))
+    wall = time.perf_counter() - t0
+    exp = np.array([res[int(p)] for p in sample])
+    m = np.isfinite(exp) & (exp != 0)
+    rel = np.abs(gpu_fit[sample][m] - exp[m]) / np.abs(exp[m])
+    gpop = int(w.pop.lengths[sample].sum()) * int(w.cases.shape[1])
+    return {"cpu_baseline": {"value": round(gpop / wall / 1e9, 4), "unit": UNIT, "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{sample.size} programs x all {w.cases.shape[1]} cases"},
+            "fitness_rel_err_vs_fp64_oracle": {"programs_checked": int(sample.size),
+                                               "max": float(rel.max()) if rel.size else 0.0,
+                                               "bound": 1e-5}}
+
+
+def bench_serving(gp, synth, n_runs):
+    """Continuous batching: n_runs independent runs (mixed float regression and
+    Boolean, populations 128-2048, 2^10-2^20 cases) submit 4 generations each
+    with Poisson arrivals at 80% of the measured burst capacity."""
+    import numpy as np
+    runs = synth.serving_runs(n_runs=n_runs)
+    encs = []
+    for r in runs:
+        kind = gp.KIND_SFORM if r.kind == "float" else gp.KIND_BOOL
+        encs.append(gp.encode_population(r.pop.words, r.pop.offsets, r.pop.lengths, kind))
+    with gp.Server(n_streams=4, max_inflight=16) as srv:
+        ids = []
+        for r in runs:
+            if r.kind == "float":
+                ids.append(srv.register_run(r.cases, r.targets))
+            else:
+                ids.append(srv.register_run(r.cases, r.targets, kind=gp.RUN_BOOL, n_cases=r.n_cases))
+        kinds = [gp.RUN_FLOAT if r.kind == "float" else gp.RUN_BOOL for r in runs]
+
+        def burst():
+            t0 = time.perf_counter()
+            qs = [srv.submit(i, e, kind=k) for i, e, k in zip(ids, encs, kinds)]
+            for q in qs:
+                srv.wait(q)
+            return time.perf_counter() - t0
+
+        burst()  # warm-up (workspaces, pinned buffers)
+        t_burst = burst()
+        total_gpop = sum(r.gpop for r in runs)
+        capacity = total_gpop / t_burst
+        rng = np.random.default_rng(9)
+        gens = 4
+        order = [j for _ in range(gens) for j in rng.permutation(len(runs))]
+        mean_gpop = total_gpop / len(runs)
+        rate = 0.8 * capacity / mean_gpop  # requests per second
+        gaps = rng.exponential(1.0 / rate, size=len(order))
+        base = srv.stats()
+        qs = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for j, g in zip(order, gaps):
+            t_next += g
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                time.sleep(min(t_next - now, 0.0005))
+            qs.append(srv.submit(ids[j], encs[j], kind=kinds[j]))
+        infos = [srv.wait(q)[1] for q in qs]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    lat = np.sort(np.array([i.t_done_us - i.t_submit_us for i in infos])) / 1e3
+    pct = lambda q: float(lat[min(lat.size - 1, int(round(q * (lat.size - 1))))])
+    return {"runs": len(runs), "requests": len(qs), "generations_per_run": gens,
+            "float_runs": sum(r.kind == "float" for r in runs),
+            "bool_runs": sum(r.kind == "bool" for r in runs),
+            "offered_load": 0.8, "burst_capacity_GPop_per_s": round(capacity / 1e9, 1),
+            "p50_ms": round(pct(0.50), 3), "p99_ms": round(pct(0.99), 3),
+            "max_ms": round(float(lat[-1]), 3),
+            "sustained_GPop_per_s": round(sum(runs[j].gpop for j in order) / wall / 1e9, 1),
+            "launches": st["launches"] - base["launches"],
+            "note": "latency = submission to result in the caller's host buffer, over the "
+                    "requests of the Poisson phase"}
 
 
 def cpu_oracle_baseline(w, gpu_fit, n_cases, budget_s: float = 12.0):

@@ -46,7 +46,8 @@ typedef enum gp_status {
   GP_ERR_OOM = 4,             /* workspace or admission memory could not be had */
   GP_ERR_TIMEOUT = 5,         /* a bounded wait gave up */
   GP_ERR_NOT_IMPLEMENTED = 6,
-  GP_ERR_BUSY = 7             /* a serving queue is full */
+  GP_ERR_BUSY = 7,            /* a serving queue is full, or a request is not finished yet */
+  GP_ERR_CANCELLED = 8        /* a serving request was cancelled before it ran */
 } gp_status;
 
 /* ------------------------------------------------------------------------
@@ -242,6 +243,88 @@ int gp_eval_population_bool_ex(const uint32_t* programs, const int64_t* offsets,
                                const uint32_t* case_bits, int32_t n_inputs, int64_t n_cases,
                                const uint32_t* target_bits, uint64_t* hits_out,
                                uint32_t* out_words, const gp_config* cfg, gp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a continuously batched evaluation service for many independent GP
+ * runs (the paper evaluates one population per generation, Sec. 4.2; a
+ * server interleaves the generations of many runs).
+ *
+ * A run registers its fitness cases once; they stay resident on the device.
+ * Each submitted request (one population of one run, encoded programs in
+ * host memory) is queued, then admitted when an in-flight slot and enough of
+ * the server's memory budget are free; consecutive queued requests of the
+ * same run are merged into one launch; admitted work is spread over a pool
+ * of CUDA streams, so requests of different runs overlap on the GPU.  A
+ * host thread owned by the server issues the copies and launches and polls
+ * CUDA events for completion: no kernel ever waits on the host.  The case
+ * range of a run is split into blocks by its case count alone, so a
+ * request's result is bit-identical whether it runs alone or in any mix.
+ * All pointers here are host pointers.  Thread-safe: any host thread may
+ * submit, poll, wait or cancel.
+ * ---------------------------------------------------------------------- */
+typedef struct gp_server gp_server;
+
+enum { GP_RUN_FLOAT = 1, GP_RUN_BOOL = 2 };
+
+typedef struct gp_server_opts {
+  int32_t n_streams;      /* CUDA streams for admitted work (0 = 4) */
+  int32_t max_inflight;   /* admitted launches at once (0 = 16) */
+  int32_t max_queued;     /* requests waiting for admission (0 = 65536); more -> GP_ERR_BUSY */
+  int32_t max_merge;      /* programs merged into one launch (0 = 65536) */
+  int64_t memory_budget;  /* device bytes for admitted requests (0 = 1 GiB) */
+  gp_config config;       /* kernel configuration (zero fields = library default) */
+} gp_server_opts;
+
+typedef struct gp_request_info {
+  int32_t status;         /* GP_OK, or the error that ended the request */
+  int32_t n_progs;
+  int64_t gpop;           /* tree nodes x cases of the request */
+  double t_submit_us;     /* server clock, microseconds since gp_server_create */
+  double t_admit_us;
+  double t_done_us;
+} gp_request_info;
+
+typedef struct gp_server_stats {
+  int64_t submitted, completed, failed, cancelled, launches;
+  int64_t gpop_completed;
+  double p50_latency_us, p99_latency_us, max_latency_us; /* submission to completion */
+  double busy_s;          /* wall time between the first admission and the last completion */
+  double gpop_per_s;      /* gpop_completed / busy_s */
+} gp_server_stats;
+
+int gp_server_create(const gp_server_opts* opts, gp_server** out);
+
+/* Copies a run's cases to the device.  GP_RUN_FLOAT: cases binary32
+ * [n_inputs][n_cases], targets binary32 [n_cases].  GP_RUN_BOOL: cases uint32
+ * [n_inputs][ceil(n_cases/32)], targets uint32 [ceil(n_cases/32)]. */
+int gp_server_register_run(gp_server* srv, int32_t kind, const void* cases, int32_t n_inputs,
+                           int64_t n_cases, const void* targets, int32_t* run_id);
+
+/* Queues one population of encoded programs (copied before returning).
+ * `result` (host, caller-owned until the request is done, cancelled or failed)
+ * receives fitness as double[n_progs] (float runs) or hits as
+ * uint64_t[n_progs] (Boolean runs).  `n_nodes` is the request's total tree
+ * nodes (its GPop per case).  GP_ERR_BUSY when the queue is full, GP_ERR_OOM
+ * when the request alone exceeds the memory budget. */
+int gp_server_submit(gp_server* srv, int32_t run_id, const uint32_t* programs,
+                     const int64_t* offsets, const int32_t* lengths, int32_t n_progs,
+                     int64_t n_nodes, void* result, uint64_t* req_id);
+
+/* GP_OK and *info when the request is finished (done, failed or cancelled);
+ * GP_ERR_BUSY while it is queued or running. */
+int gp_server_poll(gp_server* srv, uint64_t req_id, gp_request_info* info);
+
+/* Blocks until the request is finished or `timeout_us` passes (GP_ERR_TIMEOUT). */
+int gp_server_wait(gp_server* srv, uint64_t req_id, int64_t timeout_us, gp_request_info* info);
+
+/* Cancels a request that is still queued (GP_OK); a request already admitted
+ * runs to completion (GP_ERR_BUSY). */
+int gp_server_cancel(gp_server* srv, uint64_t req_id);
+
+int gp_server_get_stats(gp_server* srv, gp_server_stats* stats);
+
+/* Waits for admitted work, drops queued requests (cancelled), frees everything. */
+int gp_server_destroy(gp_server* srv);
 
 /* ------------------------------------------------------------------------
  * Configuration, status and lifetime.

@@ -23,7 +23,8 @@ __all__ = [
     "GPError", "lib", "Config", "EncodedPopulation",
     "encode_tree", "encode_population", "encode_linear_population",
     "eval_population", "eval_outputs", "eval_population_bool",
-    "set_config", "get_config", "last_error", "shutdown", "version",
+    "set_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
+    "eval_population_noalloc",
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "ORDER_PAPER", "ORDER_MIN_DEPTH",
     "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL",
 ]
@@ -35,7 +36,9 @@ STACK_LEVELS = 8
 MAX_INSTR = 1024
 
 _STATUS = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_PROGRAM", 3: "GP_ERR_CUDA",
-           4: "GP_ERR_OOM", 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_NOT_IMPLEMENTED", 7: "GP_ERR_BUSY"}
+           4: "GP_ERR_OOM", 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_NOT_IMPLEMENTED", 7: "GP_ERR_BUSY",
+           8: "GP_ERR_CANCELLED"}
+RUN_FLOAT, RUN_BOOL = 1, 2
 
 
 class GPError(RuntimeError):
@@ -48,6 +51,31 @@ class _ProgInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("n_instr", ctypes.c_int32),
                 ("max_depth", ctypes.c_int32), ("stack_reads", ctypes.c_int32),
                 ("max_input", ctypes.c_int32), ("words", ctypes.c_int32)]
+
+
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("max_queued", ctypes.c_int32), ("max_merge", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("variant", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("block", ctypes.c_int32), ("chunk_cases", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n_progs", ctypes.c_int32), ("gpop", ctypes.c_int64),
+                ("t_submit_us", ctypes.c_double), ("t_admit_us", ctypes.c_double),
+                ("t_done_us", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("gpop_completed", ctypes.c_int64),
+                ("p50_latency_us", ctypes.c_double), ("p99_latency_us", ctypes.c_double),
+                ("max_latency_us", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("gpop_per_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Config(ctypes.Structure):
@@ -85,6 +113,15 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_get_config": [P],
         "gp_last_error": [P, P],
         "gp_shutdown": [],
+        "gp_eval_population_noalloc": [P, P, P, i32, P, i32, i64, P, P, P],
+        "gp_server_create": [P, P],
+        "gp_server_register_run": [P, i32, P, i32, i64, P, P],
+        "gp_server_submit": [P, i32, P, P, P, i32, i64, P, P],
+        "gp_server_poll": [P, ctypes.c_uint64, P],
+        "gp_server_wait": [P, ctypes.c_uint64, i64, P],
+        "gp_server_cancel": [P, ctypes.c_uint64],
+        "gp_server_get_stats": [P, P],
+        "gp_server_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -273,6 +310,102 @@ def eval_population_bool(programs, offsets, lengths, case_bits, n_cases, target_
                                             _tptr(target_bits), _tptr(hits_out),
                                             _tptr(out_words), _cfg(config), _stream(stream)))
     return hits_out
+
+
+def eval_population_noalloc(programs, offsets, lengths, cases, targets, fitness_out=None,
+                            stream=None):
+    """gp_eval_population_noalloc: same result as eval_population, with the
+    library's scratch in a fixed device array instead of allocated memory."""
+    import torch
+    n = int(lengths.numel())
+    n_inputs, n_cases = (int(cases.shape[0]), int(cases.shape[1])) if cases.dim() == 2 else (1, int(cases.numel()))
+    if fitness_out is None:
+        fitness_out = torch.empty(n, dtype=torch.float64, device=cases.device)
+    _check(lib().gp_eval_population_noalloc(_tptr(programs), _tptr(offsets), _tptr(lengths), n,
+                                            _tptr(cases), n_inputs, n_cases, _tptr(targets),
+                                            _tptr(fitness_out), _stream(stream)))
+    return fitness_out
+
+
+class Server:
+    """gp_server_*: continuously batched evaluation of many GP runs' populations.
+
+    Host numpy arrays in, host numpy arrays out; the server's own thread and
+    streams do the device work.  Use as a context manager or call close().
+    """
+
+    def __init__(self, n_streams=4, max_inflight=16, max_queued=65536, max_merge=65536,
+                 memory_budget=1 << 30, config: Optional[Config] = None):
+        c = config or Config()
+        opts = _ServerOpts(n_streams, max_inflight, max_queued, max_merge, memory_budget,
+                           c.variant, c.k, c.block, 0)
+        self._h = ctypes.c_void_p()
+        _check(lib().gp_server_create(ctypes.byref(opts), ctypes.byref(self._h)))
+        self._results = {}  # request id -> (buffer, keep-alive)
+
+    def register_run(self, cases, targets, kind=RUN_FLOAT, n_cases=None) -> int:
+        if kind == RUN_FLOAT:
+            x = np.ascontiguousarray(cases, np.float32)
+            x = x[None, :] if x.ndim == 1 else x
+            y = np.ascontiguousarray(targets, np.float32)
+            n_inputs, n = x.shape
+        else:
+            x = np.ascontiguousarray(cases, np.uint32)
+            x = x[None, :] if x.ndim == 1 else x
+            y = np.ascontiguousarray(targets, np.uint32)
+            n_inputs, n = x.shape[0], int(n_cases)
+        rid = ctypes.c_int32(-1)
+        _check(lib().gp_server_register_run(self._h, kind, _np_ptr(x), n_inputs, n, _np_ptr(y),
+                                            ctypes.byref(rid)))
+        return int(rid.value)
+
+    def submit(self, run_id: int, enc: "EncodedPopulation", n_nodes: Optional[int] = None,
+               kind=RUN_FLOAT) -> int:
+        n = enc.n
+        out = np.zeros(n, np.float64 if kind == RUN_FLOAT else np.uint64)
+        rid = ctypes.c_uint64(0)
+        words = np.ascontiguousarray(enc.words, np.uint32)
+        nodes = enc.nodes if n_nodes is None else n_nodes
+        _check(lib().gp_server_submit(self._h, run_id, _np_ptr(words), _np_ptr(enc.offsets),
+                                      _np_ptr(enc.lengths), n, nodes, _np_ptr(out),
+                                      ctypes.byref(rid)))
+        self._results[int(rid.value)] = out
+        return int(rid.value)
+
+    def wait(self, req_id: int, timeout_s: float = 60.0):
+        """(result array, RequestInfo); raises GPError on timeout or failure."""
+        info = RequestInfo()
+        _check(lib().gp_server_wait(self._h, req_id, int(timeout_s * 1e6), ctypes.byref(info)))
+        if info.status != 0:
+            raise GPError(info.status, f"request {req_id} ended with status {info.status}")
+        return self._results[req_id], info
+
+    def poll(self, req_id: int):
+        info = RequestInfo()
+        rc = lib().gp_server_poll(self._h, req_id, ctypes.byref(info))
+        if rc == 7:
+            return None
+        _check(rc)
+        return info
+
+    def cancel(self, req_id: int) -> int:
+        return int(lib().gp_server_cancel(self._h, req_id))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().gp_server_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            _check(lib().gp_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def set_config(variant=VARIANT_REGISTER, k=8, block=128):

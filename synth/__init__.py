@@ -351,3 +351,56 @@ def linear_workload(seed: int = 4, n_progs: int = 8192, n_cases: int = 262144,
     pop = linear_programs(seed, n_progs, len_lo, len_hi)
     x = normal_cases(seed + 1000, 8, n_cases)
     return LinearWorkload(f"linear-{n_progs}x{n_cases}", pop, x, poly3_target(x, seed + 2000))
+
+
+# --------------------------------------------------------------------------
+# serving: many independent GP runs submitting populations
+# --------------------------------------------------------------------------
+@dataclass
+class ServingRun:
+    kind: str              # "float" or "bool"
+    pop: Population
+    cases: np.ndarray      # float32 [n_inputs, n_cases] or uint32 [n_inputs, n_words]
+    targets: np.ndarray
+    n_cases: int
+
+    @property
+    def gpop(self) -> int:
+        return int(self.pop.nodes.sum()) * self.n_cases
+
+
+def serving_runs(seed: int = 5, n_runs: int = 64, pop_lo: int = 128, pop_hi: int = 2048,
+                 max_depth: int = 7, max_nodes: int = 255, log2_cases_lo: int = 10,
+                 log2_cases_hi: int = 20, p_bool: float = 0.25) -> List[ServingRun]:
+    """Independent runs of mixed kinds: float regression with 1 input (quartic
+    target) or 8 inputs (random cubic target), and Boolean k-multiplexer or
+    even-k-parity; population sizes U{pop_lo..pop_hi}; case counts 2^U{lo..hi}
+    (Boolean: k inputs, 2^k cases with k in the same range)."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for r in range(n_runs):
+        n_progs = int(rng.integers(pop_lo, pop_hi + 1))
+        s = int(rng.integers(0, 2**31 - 1))
+        lg = int(rng.integers(log2_cases_lo, log2_cases_hi + 1))
+        if rng.random() < p_bool:
+            kind = "mux" if rng.random() < 0.5 else "parity"
+            k = lg
+            if kind == "mux":  # nearest multiplexer size a + 2^a within the range
+                k = min((a + (1 << a) for a in range(2, 5)), key=lambda v: abs(v - lg))
+            funcs = BOOL_FUNCS + ((IF,) if kind == "mux" else ())
+            progs = ramped_half_and_half(s, n_progs, 2, max_depth, max_nodes, funcs=funcs,
+                                         n_inputs=k, p_const=0.0, full_fallback_to_grow=True)
+            target = even_parity_target(k) if kind == "parity" else mux_target(k)
+            runs.append(ServingRun("bool", pack(progs), bool_case_bits(k), target, 1 << k))
+        else:
+            n_inputs = 1 if rng.random() < 0.5 else 8
+            n_cases = 1 << lg
+            progs = ramped_half_and_half(s, n_progs, 2, max_depth, max_nodes, n_inputs=n_inputs)
+            if n_inputs == 1:
+                x = uniform_cases(s + 1, 1, n_cases)
+                y = quartic_target(x[0])
+            else:
+                x = normal_cases(s + 1, 8, n_cases)
+                y = poly3_target(x, s + 2)
+            runs.append(ServingRun("float", pack(progs), x, y, n_cases))
+    return runs

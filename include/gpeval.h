@@ -118,7 +118,10 @@ int gp_encode_tree(const uint32_t* prefix, int64_t n_words, int32_t kind, int32_
 
 /* Encodes programs p = 0..n_progs-1, program p being
  * words[offsets[p] .. offsets[p] + lengths[p]).  With out == NULL only the
- * sizes are computed: *total_words receives the encoded size.  Otherwise
+ * sizes are computed: *total_words receives the encoded size (a program never
+ * takes more than 4 + 4 * lengths[p] words, so that bound can size `out` for
+ * a single call).  Encoding runs on several host threads; the output is
+ * identical to a sequential encoding.  Otherwise
  * out_offsets[p] / out_lengths[p] (host, n_progs entries each) receive the
  * encoded word offset and length of program p, *total_nodes the sum of nodes.
  * `info` (may be NULL) receives n_progs entries.  Stops at the first bad
@@ -325,6 +328,25 @@ int gp_server_get_stats(gp_server* srv, gp_server_stats* stats);
 
 /* Waits for admitted work, drops queued requests (cancelled), frees everything. */
 int gp_server_destroy(gp_server* srv);
+
+/* ------------------------------------------------------------------------
+ * Autotuning.  The best K (the second dimension of the 2D stack) and block
+ * size depend on the hardware and the workload (Sec. 4.2: the paper's best K
+ * and thread count differ per problem, Tables of Sec. 4.2, 5 and 6).
+ * gp_autotune_population times every candidate configuration (k in
+ * {2, 4, 8} x block in {64, 128, 256}) on the given float population with CUDA
+ * events on `stream` (1 warm-up launch, `repeats` timed launches each, the
+ * minimum kept), writes the fastest to *best (may be NULL) and records it for
+ * the workload's shape: later float evaluations whose configuration leaves k
+ * and block at 0 and whose (single vs several inputs, floor(log2 n_cases),
+ * floor(log2 n_progs)) match use it.  Synchronises `stream`; allocates a
+ * temporary fitness buffer.  gp_autotune_clear forgets every record.
+ * ---------------------------------------------------------------------- */
+int gp_autotune_population(const uint32_t* programs, const int64_t* offsets,
+                           const int32_t* lengths, int32_t n_progs, const float* cases,
+                           int32_t n_inputs, int64_t n_cases, const float* targets,
+                           int32_t repeats, gp_config* best, gp_stream_t stream);
+int gp_autotune_clear(void);
 
 /* ------------------------------------------------------------------------
  * Configuration, status and lifetime.

@@ -24,7 +24,7 @@ __all__ = [
     "encode_tree", "encode_population", "encode_linear_population",
     "eval_population", "eval_outputs", "eval_population_bool",
     "set_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
-    "eval_population_noalloc",
+    "eval_population_noalloc", "autotune_population", "autotune_clear",
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "ORDER_PAPER", "ORDER_MIN_DEPTH",
     "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL",
 ]
@@ -122,6 +122,8 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_server_cancel": [P, ctypes.c_uint64],
         "gp_server_get_stats": [P, P],
         "gp_server_destroy": [P],
+        "gp_autotune_population": [P, P, P, i32, P, i32, i64, P, i32, P, P],
+        "gp_autotune_clear": [],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -185,33 +187,32 @@ def encode_tree(prefix, kind: int = KIND_SFORM, order: int = ORDER_MIN_DEPTH):
 
 
 def encode_population(words, offsets, lengths, kind: int = KIND_SFORM,
-                      order: int = ORDER_MIN_DEPTH, with_info: bool = False) -> EncodedPopulation:
+                      order: int = ORDER_MIN_DEPTH, with_info: bool = False,
+                      out: Optional[np.ndarray] = None) -> EncodedPopulation:
+    """Encodes a population in one call (the output is sized by the bound of
+    4 + 4 * lengths[p] words per program).  `out` (uint32, 16-byte aligned)
+    may supply the buffer, e.g. a pinned host array reused across calls."""
     w = np.ascontiguousarray(words, np.uint32)
     off = np.ascontiguousarray(offsets, np.int64)
     ln = np.ascontiguousarray(lengths, np.int32)
     n = int(ln.size)
+    cap = int(4 * n + 4 * int(ln.sum())) if n else 4
+    if out is None or out.size < cap:
+        out = _aligned_empty(max(cap, 4))
     total = ctypes.c_int64(0)
     nodes = ctypes.c_int64(0)
     bad = ctypes.c_int32(-1)
-    L = lib()
-    rc = L.gp_encode_population(_np_ptr(w), _np_ptr(off), _np_ptr(ln), n, kind, order, None, 0,
-                                None, None, ctypes.byref(total), ctypes.byref(nodes), None,
-                                ctypes.byref(bad))
-    _check(rc)
-    out = _aligned_empty(max(int(total.value), 4))
     out_off = np.zeros(n, np.int64)
     out_len = np.zeros(n, np.int32)
     info = (_ProgInfo * n)() if with_info else None
-    rc = L.gp_encode_population(_np_ptr(w), _np_ptr(off), _np_ptr(ln), n, kind, order,
-                                _np_ptr(out), out.size, _np_ptr(out_off), _np_ptr(out_len),
-                                ctypes.byref(total), ctypes.byref(nodes),
-                                ctypes.cast(info, ctypes.c_void_p) if info is not None else None,
-                                ctypes.byref(bad))
-    _check(rc)
-    arr = None
-    if info is not None:
-        arr = np.ctypeslib.as_array(info).copy()
-    return EncodedPopulation(out, out_off, out_len, int(nodes.value), kind, order, arr)
+    _check(lib().gp_encode_population(_np_ptr(w), _np_ptr(off), _np_ptr(ln), n, kind, order,
+                                      _np_ptr(out), out.size, _np_ptr(out_off), _np_ptr(out_len),
+                                      ctypes.byref(total), ctypes.byref(nodes),
+                                      ctypes.cast(info, ctypes.c_void_p) if info is not None else None,
+                                      ctypes.byref(bad)))
+    arr = np.ctypeslib.as_array(info).copy() if info is not None else None
+    return EncodedPopulation(out[:max(int(total.value), 4)], out_off, out_len, int(nodes.value),
+                             kind, order, arr)
 
 
 def encode_linear_population(instr, offsets, lengths) -> EncodedPopulation:
@@ -406,6 +407,22 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def autotune_population(programs, offsets, lengths, cases, targets, repeats=3, stream=None) -> Config:
+    """gp_autotune_population: times k x block candidates on this workload and
+    records the fastest for workloads of its shape; returns it."""
+    n = int(lengths.numel())
+    n_inputs, n_cases = (int(cases.shape[0]), int(cases.shape[1])) if cases.dim() == 2 else (1, int(cases.numel()))
+    best = Config()
+    _check(lib().gp_autotune_population(_tptr(programs), _tptr(offsets), _tptr(lengths), n,
+                                        _tptr(cases), n_inputs, n_cases, _tptr(targets), repeats,
+                                        ctypes.byref(best), _stream(stream)))
+    return best
+
+
+def autotune_clear():
+    _check(lib().gp_autotune_clear())
 
 
 def set_config(variant=VARIANT_REGISTER, k=8, block=128):

@@ -5,7 +5,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/gpeval.h"
@@ -33,6 +35,19 @@ struct Workspace {
   int* status = nullptr;
 };
 std::vector<Workspace*> g_ws;
+
+// autotuned configurations by workload shape
+using TuneKey = std::tuple<int, int, int>;  // several inputs?, log2 n_cases, log2 n_progs
+std::map<TuneKey, gp_config> g_tuned;
+
+int ilog2(int64_t v) {
+  int r = 0;
+  while (v > 1) { v >>= 1; ++r; }
+  return r;
+}
+TuneKey tune_key(int32_t n_inputs, int64_t n_cases, int32_t n_progs) {
+  return TuneKey(n_inputs > 1 ? 1 : 0, ilog2(std::max<int64_t>(n_cases, 1)), ilog2(std::max<int32_t>(n_progs, 1)));
+}
 
 int cuda_fail(cudaError_t e, const char* what) {
   return gp_fail(e == cudaErrorMemoryAllocation ? GP_ERR_OOM : GP_ERR_CUDA, "%s: %s", what,
@@ -124,6 +139,18 @@ int resolve_config(const gp_config* user, gp_config* c) {
   return GP_OK;
 }
 
+// The recorded tuned configuration for a float workload, if any, fills the
+// k and block fields the caller left at 0.
+void apply_tuned(const gp_config* user, gp_config* c, int32_t n_inputs, int64_t n_cases, int32_t n_progs) {
+  if (user && user->k && user->block) return;
+  if (c->variant != GP_VARIANT_REGISTER) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_tuned.find(tune_key(n_inputs, n_cases, n_progs));
+  if (it == g_tuned.end()) return;
+  if (!user || !user->k) c->k = it->second.k;
+  if (!user || !user->block) c->block = it->second.block;
+}
+
 // Cases (or words) per block: enough blocks to fill the GPU several times
 // over, each covering whole passes of the block.
 int64_t choose_chunk(int64_t n_units, int32_t n_progs, int per_pass, int64_t user_chunk) {
@@ -182,6 +209,9 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   gp_config c;
   int rc = resolve_config(cfg, &c);
   if (rc) return rc;
+  apply_tuned(cfg, &c, n_inputs, n_cases, n_progs);
+  if (c.chunk_cases % ((int64_t)c.k * c.block) != 0)
+    return gp_fail(GP_ERR_INVALID_ARG, "chunk_cases must be a multiple of k*block");
   cudaStream_t s = (cudaStream_t)stream;
 
   const int per_pass = c.k * c.block;
@@ -360,5 +390,69 @@ extern "C" int gp_shutdown(void) {
   }
   g_ws.clear();
   cudaSetDevice(cur);
+  return GP_OK;
+}
+
+extern "C" int gp_autotune_population(const uint32_t* programs, const int64_t* offsets,
+                                      const int32_t* lengths, int32_t n_progs, const float* cases,
+                                      int32_t n_inputs, int64_t n_cases, const float* targets,
+                                      int32_t repeats, gp_config* best, gp_stream_t stream) {
+  gp_clear_error();
+  if (n_progs <= 0 || n_cases <= 0) return gp_fail(GP_ERR_INVALID_ARG, "nothing to tune on");
+  if (repeats <= 0) repeats = 3;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* fit = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&fit, sizeof(double) * (size_t)n_progs, s);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune buffer");
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  gp_config best_c = {GP_VARIANT_REGISTER, 0, 0, 0};
+  float best_ms = 1e30f;
+  int rc = GP_OK;
+  static const int ks[] = {2, 4, 8};
+  static const int blocks[] = {64, 128, 256};
+  for (int k : ks) {
+    for (int blk : blocks) {
+      gp_config c = {GP_VARIANT_REGISTER, k, blk, 0};
+      rc = gp_eval_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases,
+                                 targets, fit, nullptr, &c, stream);
+      if (rc) break;
+      float ms_min = 1e30f;
+      for (int r = 0; r < repeats && rc == GP_OK; ++r) {
+        cudaEventRecord(t0, s);
+        rc = gp_eval_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases,
+                                   targets, fit, nullptr, &c, stream);
+        cudaEventRecord(t1, s);
+        e = cudaEventSynchronize(t1);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, t0, t1);
+        ms_min = std::min(ms_min, ms);
+      }
+      if (rc) break;
+      if (ms_min < best_ms) {
+        best_ms = ms_min;
+        best_c = c;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaFreeAsync(fit, s);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tuned[tune_key(n_inputs, n_cases, n_progs)] = best_c;
+  }
+  if (best) *best = best_c;
+  return GP_OK;
+}
+
+extern "C" int gp_autotune_clear(void) {
+  gp_clear_error();
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_tuned.clear();
   return GP_OK;
 }

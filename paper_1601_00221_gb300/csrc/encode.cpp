@@ -22,6 +22,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/gpeval.h"
@@ -258,6 +260,27 @@ extern "C" int gp_encode_tree(const uint32_t* prefix, int64_t n_words, int32_t k
   return GP_OK;
 }
 
+// Population encoding runs on several host threads: programs are split into
+// contiguous ranges, each thread encodes its range into its own buffer, and
+// the buffers are laid out in program order.  The result is identical to a
+// sequential encoding.
+namespace {
+struct Piece {
+  std::vector<uint32_t> words;
+  std::vector<int32_t> lengths;
+  int64_t nodes = 0;
+  int rc = GP_OK;
+  int32_t bad = -1;
+  std::string msg;
+};
+
+int encode_threads(int32_t n_progs) {
+  unsigned hc = std::thread::hardware_concurrency();
+  int t = (int)std::min<unsigned>(hc ? hc : 1, 32);
+  return std::max(1, std::min<int>(t, n_progs / 128));
+}
+}  // namespace
+
 extern "C" int gp_encode_population(const uint32_t* words, const int64_t* offsets,
                                     const int32_t* lengths, int32_t n_progs, int32_t kind,
                                     int32_t order, uint32_t* out, int64_t cap_words,
@@ -270,32 +293,63 @@ extern "C" int gp_encode_population(const uint32_t* words, const int64_t* offset
     return gp_fail(GP_ERR_INVALID_ARG, "bad population arguments");
   if (out && (!out_offsets || !out_lengths))
     return gp_fail(GP_ERR_INVALID_ARG, "out_offsets and out_lengths are required with out");
-  std::vector<uint32_t> buf;
+  const int nt = encode_threads(n_progs);
+  std::vector<Piece> pieces(nt);
+  auto work = [&](int t) {
+    const int32_t b = (int32_t)((int64_t)n_progs * t / nt), e = (int32_t)((int64_t)n_progs * (t + 1) / nt);
+    Piece& pc = pieces[t];
+    std::vector<uint32_t> buf;
+    for (int32_t p = b; p < e; ++p) {
+      gp_prog_info inf{};
+      int rc;
+      if (lengths[p] <= 0 || offsets[p] < 0)
+        rc = gp_fail(GP_ERR_PROGRAM, "program %d has no words", p);
+      else
+        rc = encode_one(words + offsets[p], lengths[p], kind, order, buf, &inf);
+      if (info) info[p] = inf;
+      if (rc) {
+        pc.rc = rc;
+        pc.bad = p;
+        pc.msg = gp_error_string();
+        return;
+      }
+      pc.words.insert(pc.words.end(), buf.begin(), buf.end());
+      pc.lengths.push_back((int32_t)buf.size());
+      pc.nodes += inf.n_nodes;
+    }
+  };
+  if (nt == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+  }
   int64_t pos = 0, nodes = 0;
-  for (int32_t p = 0; p < n_progs; ++p) {
-    gp_prog_info inf{};
-    if (lengths[p] <= 0 || offsets[p] < 0) {
-      if (bad_prog) *bad_prog = p;
-      return gp_fail(GP_ERR_PROGRAM, "program %d has no words", p);
+  for (int t = 0; t < nt; ++t) {
+    if (pieces[t].rc) {  // the first bad program in program order
+      if (bad_prog) *bad_prog = pieces[t].bad;
+      return gp_fail(pieces[t].rc, "%s", pieces[t].msg.c_str());
     }
-    int rc = encode_one(words + offsets[p], lengths[p], kind, order, buf, &inf);
-    if (info) info[p] = inf;
-    if (rc) {
-      if (bad_prog) *bad_prog = p;
-      return rc;
-    }
-    if (out) {
-      if (pos + (int64_t)buf.size() > cap_words)
-        return gp_fail(GP_ERR_INVALID_ARG, "output capacity %lld too small", (long long)cap_words);
-      memcpy(out + pos, buf.data(), buf.size() * sizeof(uint32_t));
-      out_offsets[p] = pos;
-      out_lengths[p] = (int32_t)buf.size();
-    }
-    pos += (int64_t)buf.size();
-    nodes += inf.n_nodes;
+    pos += (int64_t)pieces[t].words.size();
+    nodes += pieces[t].nodes;
   }
   if (total_words) *total_words = pos;
   if (total_nodes) *total_nodes = nodes;
+  if (!out) return GP_OK;
+  if (pos > cap_words)
+    return gp_fail(GP_ERR_INVALID_ARG, "output capacity %lld < %lld words", (long long)cap_words, (long long)pos);
+  int64_t w = 0;
+  int32_t p = 0;
+  for (int t = 0; t < nt; ++t) {
+    memcpy(out + w, pieces[t].words.data(), pieces[t].words.size() * sizeof(uint32_t));
+    for (int32_t len : pieces[t].lengths) {
+      out_offsets[p] = w;
+      out_lengths[p] = len;
+      w += len;
+      ++p;
+    }
+  }
   return GP_OK;
 }
 

@@ -137,23 +137,28 @@ def emit_pdiv(b, K, A, B, Q, tag, group=2):
                 b(f"fma.rn.f32x2 dE{i}, dN{i}, dQ{i}, {A[i]};")
             for i in idx:
                 b(f"fma.rn.f32x2 dQ{i}, dE{i}, dY{i}, dQ{i};")
+        # per pair: lo = min(|q0|, |q1|, |a0|, |a1|), hi = max(|q0|, |q1|);
+        # then a tree over the pairs (a short dependency chain)
         for i in range(H):
             b(f"mov.b64 {{dt, dt2}}, dQ{i};")
             b("abs.f32 dt, dt;")
             b("abs.f32 dt2, dt2;")
-            if i == 0:
-                b("max.NaN.f32 dhi, dt, dt2;")
-                b("min.NaN.f32 dlo, dt, dt2;")
-            else:
-                b("max.NaN.f32 dhi, dhi, dt;")
-                b("max.NaN.f32 dhi, dhi, dt2;")
-                b("min.NaN.f32 dlo, dlo, dt;")
-                b("min.NaN.f32 dlo, dlo, dt2;")
+            b(f"max.NaN.f32 dh{i}, dt, dt2;")
+            b(f"min.NaN.f32 dl{i}, dt, dt2;")
             b(f"mov.b64 {{dt, dt2}}, {A[i]};")
             b("abs.f32 dt, dt;")
             b("abs.f32 dt2, dt2;")
-            b("min.NaN.f32 dlo, dlo, dt;")
-            b("min.NaN.f32 dlo, dlo, dt2;")
+            b("min.NaN.f32 dt, dt, dt2;")
+            b(f"min.NaN.f32 dl{i}, dl{i}, dt;")
+        w = H
+        while w > 1:
+            half = (w + 1) // 2
+            for i in range(w // 2):
+                b(f"min.NaN.f32 dl{i}, dl{i}, dl{i + half};")
+                b(f"max.NaN.f32 dh{i}, dh{i}, dh{i + half};")
+            w = half
+        b("mov.f32 dlo, dl0;")
+        b("mov.f32 dhi, dh0;")
     b(f"setp.ge.f32 dok, dlo, {DIV_LO};")
     b(f"setp.le.and.f32 dok, dhi, {DIV_HI}, dok;")
     b(f"@!dok bra {tag}SLOW;")
@@ -190,7 +195,7 @@ def emit_pdiv_slow(b, K, A, B, tag):
 def pdiv_regs(K, H):
     ty = "f32" if K == 1 else "b64"
     return (f".reg .{ty} dY<{H}>, dE<{H}>, dN<{H}>, dQ<{H}>, one2;\n"
-            f".reg .f32 dlo, dhi, dt, dt2;\n"
+            f".reg .f32 dlo, dhi, dt, dt2, dl<{H}>, dh<{H}>;\n"
             f".reg .pred dok, dz;")
 
 
@@ -360,6 +365,15 @@ class FloatGen:
         b("brx.idx.uni dl, STTBL;")
         emit_pdiv_slow(b, self.K, ta, tb, "D")
 
+    def div_blocks_per_level(self, ta, tb, units_of_level):
+        """DIV_l, one per stack level: level l <- ta / tb (protected), written
+        straight into the level's registers (no store jump, no copy back)."""
+        for l in range(R):
+            self.b(f"DIV{l}:")
+            emit_pdiv(self.b, self.K, ta, tb, units_of_level(l), f"D{l}_")
+            self.jump()
+            emit_pdiv_slow(self.b, self.K, ta, tb, f"D{l}_")
+
     # ------------------------------------------------------------------
     def sform(self):
         K, H, b = self.K, self.H, self.b
@@ -381,7 +395,6 @@ class FloatGen:
                     code = sform_code(f, l, op)
                     table[code] = f"C{code}"
                     bodies.append((code, name, l, op))
-        self.store_table()
         self.table(n_codes, table)
         self.prologue()
         self.setup_inputs()
@@ -411,15 +424,13 @@ class FloatGen:
             if op == 3:
                 self.copy(ta, a)
                 self.copy(tb, c)
-                b(f"mov.u32 dl, {l};")
                 self.fetch()
-                b("bra.uni DIV;")
+                b(f"bra.uni DIV{l};")
             else:
                 self.fetch()
                 self.vop(op, L(l), a, c)
                 self.jump()
-        self.div_block(ta, tb)
-        self.store_bodies(L, ta)
+        self.div_blocks_per_level(ta, tb, L)
         self.epilogue(L(0))
         return b
 
@@ -441,7 +452,6 @@ class FloatGen:
                     code = rpn_code(f, l, op)
                     table[code] = f"C{code}"
                     bodies.append((code, name, l, op))
-        self.store_table()
         self.table(n_codes, table)
         self.prologue()
         self.setup_inputs()
@@ -468,13 +478,11 @@ class FloatGen:
             if op == 3:
                 self.copy(ta, a)
                 self.copy(tb, c)
-                b(f"mov.u32 dl, {l};")
-                b("bra.uni DIV;")
+                b(f"bra.uni DIV{l};")
             else:
                 self.vop(op, L(l), a, c)
                 self.jump()
-        self.div_block(ta, tb)
-        self.store_bodies(L, ta)
+        self.div_blocks_per_level(ta, tb, L)
         self.epilogue(L(0))
         return b
 

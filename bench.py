@@ -42,7 +42,7 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--programs", type=int, default=4096)
@@ -75,7 +75,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -227,10 +227,11 @@ def run_ours(args):
     # the library's autotuner chooses the configuration the timed steps use
     if args.k or args.block:
         _, best_k, best_b = cands[0]
+        best_chunk = 0
     else:
         tuned = gp.autotune_population(P, O, L, X, Y, repeats=3)
-        best_k, best_b = int(tuned.k), int(tuned.block)
-    cfg = gp.Config(gp.VARIANT_REGISTER, best_k, best_b, 0)
+        best_k, best_b, best_chunk = int(tuned.k), int(tuned.block), int(tuned.chunk_cases)
+    cfg = gp.Config(gp.VARIANT_REGISTER, best_k, best_b, best_chunk)
 
     # --- timed region ---
     if world > 1:
@@ -381,7 +382,8 @@ def run_ours(args):
                                f"{{+,-,*,pdiv}}) x {n_cases} fp32 cases",
                    "programs": w.pop.n, "cases": n_cases, "tree_nodes": nodes,
                    "function_nodes": funcs, "kind": "sform", "order": "min_depth",
-                   "k": best_k, "block": best_b, "variant": "register 2D stack",
+                   "k": best_k, "block": best_b, "chunk_cases": best_chunk,
+                   "variant": "register 2D stack",
                    "tuned_by": "gp_autotune_population" if not (args.k or args.block) else "flags",
                    "l2": "flushed between timed steps (512 MiB write outside the CUDA-event pair)",
                    "parallelism": f"population sharded over {world} GPU(s), no collective"},

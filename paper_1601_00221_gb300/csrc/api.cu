@@ -149,6 +149,7 @@ void apply_tuned(const gp_config* user, gp_config* c, int32_t n_inputs, int64_t 
   if (it == g_tuned.end()) return;
   if (!user || !user->k) c->k = it->second.k;
   if (!user || !user->block) c->block = it->second.block;
+  if (!user || !user->chunk_cases) c->chunk_cases = it->second.chunk_cases;
 }
 
 // Cases (or words) per block: enough blocks to fill the GPU several times
@@ -412,9 +413,12 @@ extern "C" int gp_autotune_population(const uint32_t* programs, const int64_t* o
   int rc = GP_OK;
   static const int ks[] = {2, 4, 8};
   static const int blocks[] = {64, 128, 256};
+  static const int chunks[] = {0, 4096, 8192, 16384, 32768};
   for (int k : ks) {
     for (int blk : blocks) {
-      gp_config c = {GP_VARIANT_REGISTER, k, blk, 0};
+     for (int ch : chunks) {
+      if (ch && (ch % (k * blk) || ch >= n_cases)) continue;
+      gp_config c = {GP_VARIANT_REGISTER, k, blk, ch};
       rc = gp_eval_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases,
                                  targets, fit, nullptr, &c, stream);
       if (rc) break;
@@ -435,6 +439,8 @@ extern "C" int gp_autotune_population(const uint32_t* programs, const int64_t* o
         best_ms = ms_min;
         best_c = c;
       }
+     }
+     if (rc) break;
     }
     if (rc) break;
   }

@@ -20,9 +20,11 @@ def test_autotune_records_and_applies_the_fastest_configuration():
     gp.autotune_clear()
     best = gp.autotune_population(P, O, L, X, Y, repeats=2)
     assert best.k in (2, 4, 8) and best.block in (64, 128, 256)
+    assert best.chunk_cases == 0 or best.chunk_cases % (best.k * best.block) == 0
     tuned = gp.eval_population(P, O, L, X, Y).cpu().numpy()  # default config -> the tuned one
     explicit = gp.eval_population(P, O, L, X, Y, config=gp.Config(gp.VARIANT_REGISTER, best.k,
-                                                                    best.block, 0)).cpu().numpy()
+                                                                    best.block,
+                                                                    best.chunk_cases)).cpu().numpy()
     assert np.array_equal(tuned.view(np.uint64), explicit.view(np.uint64))
     assert_fitness(tuned, oracle.population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths,
                                                     w.cases, w.targets))

@@ -421,12 +421,15 @@ def _time_events(torch, fn, steps=5, warmup=2):
 
 
 def bench_boolean(gp, synth, torch, device):
-    """Bit-packed Boolean problems: 4096 random trees (<= 256 nodes) each;
-    GPop counts cases as bits (32 per word), as the paper's 20-multiplexer does."""
+    """Bit-packed Boolean problems, random trees (<= 256 nodes): 32768 trees for
+    the 6-input problems (64 cases), 4096 for 11 inputs, 1024 for the
+    20-multiplexer; GPop counts cases as bits (32 per word), as the paper's
+    20-multiplexer figure does."""
     import numpy as np
     out = {}
     for kind, k in (("parity", 6), ("mux", 6), ("parity", 11), ("mux", 11), ("mux", 20)):
-        n_progs = 4096 if k < 20 else 1024
+        # tiny case sets need a large population to fill the GPU
+        n_progs = {6: 32768, 11: 4096, 20: 1024}[k]
         w = synth.boolean_problem(kind, k, n_progs=n_progs)
         enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL)
         P, O, L = enc.to_device(device)
@@ -434,12 +437,15 @@ def bench_boolean(gp, synth, torch, device):
         tb = torch.from_numpy(w.target_bits.view(np.int32)).to(device)
         hits = torch.empty(w.pop.n, dtype=torch.int64, device=device)
         best = None
-        for kk in (1, 2, 4, 8):
-            cfg = gp.Config(gp.VARIANT_REGISTER, kk, 0, 0)
+        cands = [(gp.VARIANT_REGISTER, kk) for kk in (1, 2, 4, 8)]
+        if (w.n_cases + 31) // 32 <= 4:
+            cands.append((gp.VARIANT_LANES, 0))
+        for var, kk in cands:
+            cfg = gp.Config(var, kk, 0, 0)
             ms = _time_events(torch, lambda: gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
                                                                      hits_out=hits, config=cfg))
             if best is None or ms < best[0]:
-                best = (ms, kk)
+                best = (ms, kk if var == gp.VARIANT_REGISTER else "lane per program")
         gpop = w.gpop
         out[f"{kind}{k}"] = {"programs": w.pop.n, "cases": w.n_cases, "k": best[1],
                              "ms": round(best[0], 4), "bit_GPop_per_s": round(gpop / best[0] / 1e6, 1)}

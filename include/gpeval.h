@@ -149,8 +149,10 @@ int gp_encode_linear_population(const uint8_t* instr, const int64_t* offsets,
 typedef enum gp_variant {
   GP_VARIANT_AUTO = 0,      /* the tuned default for the workload */
   GP_VARIANT_REGISTER = 1,  /* stack levels in registers, K cases per thread */
-  GP_VARIANT_LOCAL = 2      /* BlockGP-style one-case-per-thread stack in local memory
+  GP_VARIANT_LOCAL = 2,     /* BlockGP-style one-case-per-thread stack in local memory
                                (Sec. 3 prior art), GP_KIND_RPN programs only */
+  GP_VARIANT_LANES = 3      /* Boolean only: one program per lane over at most 4 words
+                               (128 cases); GP_VARIANT_AUTO picks it for such case sets */
 } gp_variant;
 
 typedef struct gp_config {

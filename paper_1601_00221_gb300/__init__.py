@@ -26,12 +26,12 @@ __all__ = [
     "set_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
     "eval_population_noalloc", "autotune_population", "autotune_clear",
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "ORDER_PAPER", "ORDER_MIN_DEPTH",
-    "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL",
+    "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL", "VARIANT_LANES",
 ]
 
 KIND_SFORM, KIND_RPN, KIND_LINEAR, KIND_BOOL = 1, 2, 3, 4
 ORDER_PAPER, ORDER_MIN_DEPTH = 0, 1
-VARIANT_AUTO, VARIANT_REGISTER, VARIANT_LOCAL = 0, 1, 2
+VARIANT_AUTO, VARIANT_REGISTER, VARIANT_LOCAL, VARIANT_LANES = 0, 1, 2, 3
 STACK_LEVELS = 8
 MAX_INSTR = 1024
 

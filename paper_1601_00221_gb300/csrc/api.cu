@@ -126,7 +126,8 @@ int resolve_config(const gp_config* user, gp_config* c) {
     if (user->block) c->block = user->block;
     c->chunk_cases = user->chunk_cases;
   }
-  if (c->variant != GP_VARIANT_REGISTER && c->variant != GP_VARIANT_LOCAL && c->variant != GP_VARIANT_AUTO)
+  if (c->variant != GP_VARIANT_REGISTER && c->variant != GP_VARIANT_LOCAL &&
+      c->variant != GP_VARIANT_AUTO && c->variant != GP_VARIANT_LANES)
     return gp_fail(GP_ERR_INVALID_ARG, "unknown variant %d", c->variant);
   if (c->variant == GP_VARIANT_AUTO) c->variant = GP_VARIANT_REGISTER;
   if (c->k != 1 && c->k != 2 && c->k != 4 && c->k != 8)
@@ -302,10 +303,41 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   const int64_t n_words = (n_cases + 31) / 32;
   if (n_words > 0 && n_inputs > 0 && !case_bits) return gp_fail(GP_ERR_INVALID_ARG, "null case_bits");
   if (hits_out && n_words > 0 && !target_bits) return gp_fail(GP_ERR_INVALID_ARG, "null target_bits");
+  // program per lane for tiny case sets unless a variant is forced
+  const bool lanes = (cfg && cfg->variant == GP_VARIANT_LANES) ||
+                     ((!cfg || cfg->variant == GP_VARIANT_AUTO) && n_words > 0 && n_words <= 4);
+  if (lanes) {
+    if (n_words > 4) return gp_fail(GP_ERR_INVALID_ARG, "the per-lane variant takes at most 4 words (128 cases)");
+    Workspace* wl = nullptr;
+    int rc0 = get_workspace((cudaStream_t)stream, 0, 0, &wl);
+    if (rc0) return rc0;
+    const int w = n_words <= 1 ? 1 : (n_words <= 2 ? 2 : 4);
+    BoolArgs a;
+    a.programs = programs;
+    a.offsets = offsets;
+    a.lengths = lengths;
+    a.n_progs = n_progs;
+    a.case_bits = case_bits;
+    a.n_inputs = n_inputs;
+    a.n_cases = n_cases;
+    a.n_words = n_words;
+    a.target_bits = hits_out ? target_bits : nullptr;
+    a.hits_out = reinterpret_cast<unsigned long long*>(hits_out);
+    a.out_words = out_words;
+    a.status = wl->status;
+    a.chunk_words = 0;
+    a.n_chunks = 1;
+    a.aligned = 0;
+    const size_t smem = bool_lanes_smem(w, 32, n_inputs);
+    if (smem > 48 * 1024) return gp_fail(GP_ERR_INVALID_ARG, "too many inputs for the per-lane variant");
+    cudaError_t el = launch_bool_lanes(a, w, (n_progs + 31) / 32, smem, (cudaStream_t)stream);
+    if (el != cudaSuccess) return cuda_fail(el, "kernel launch");
+    return GP_OK;
+  }
   gp_config c;
   int rc = resolve_config(cfg, &c);
   if (rc) return rc;
-  if (c.variant != GP_VARIANT_REGISTER) return gp_fail(GP_ERR_INVALID_ARG, "Boolean programs use the register variant");
+  if (c.variant != GP_VARIANT_REGISTER) return gp_fail(GP_ERR_INVALID_ARG, "Boolean programs use the register or per-lane variant");
   if (!cfg || !cfg->block) {  // small case sets: do not launch idle warps
     int64_t need = (n_words + c.k - 1) / c.k;
     c.block = (int)std::min<int64_t>(c.block, std::max<int64_t>(32, ((need + 31) / 32) * 32));

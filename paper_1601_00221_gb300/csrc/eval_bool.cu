@@ -19,4 +19,12 @@ cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, size_t sm
   }
   return cudaGetLastError();
 }
+cudaError_t launch_bool_lanes(const BoolArgs& a, int w, int grid, size_t smem, cudaStream_t s) {
+  switch (w) {
+    case 1: eval_bool_lanes_kernel<1><<<grid, 32, smem, s>>>(a); break;
+    case 2: eval_bool_lanes_kernel<2><<<grid, 32, smem, s>>>(a); break;
+    default: eval_bool_lanes_kernel<4><<<grid, 32, smem, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
 }  // namespace gpdev

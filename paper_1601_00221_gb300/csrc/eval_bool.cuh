@@ -214,3 +214,139 @@ inline size_t bool_tile_bytes(int k, int block, int n_inputs) {
   return (size_t)(block / 32) * (size_t)n_inputs * 32u * (size_t)k * sizeof(uint32_t);
 }
 }  // namespace gpdev
+
+namespace gpdev {
+
+// ---------------------------------------------------------------------------
+// Program per lane, for tiny case sets (at most 4 words = 128 cases per
+// input; the 6-input problems have 2 words).  A warp per program would leave
+// most lanes idle; here each lane runs its own program over all W words
+// (the paper's ThreadGP layout, Sec. 3), and branch-free decoding keeps the
+// lanes of a warp on one instruction stream even though their programs
+// differ: operand slots are computed, AND / OR / IF are all computed and one
+// is selected, NAND / NOR are a negation mask.  Stack levels live in shared
+// memory [level][lane][W], the staged inputs [input][W] are shared by the
+// block.  Instructions are read per lane from global memory (L1-cached), one
+// ahead of the one being computed.  One warp per block, so that small
+// populations still spread over every SM.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(32) eval_bool_lanes_kernel(BoolArgs a) {
+  using namespace gpisa;
+  extern __shared__ uint32_t lane_smem[];
+  __shared__ uint32_t if_desc_s[BOOL_IF_FORMS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t* inp_s = lane_smem;                                   // [n_inputs][W]
+  uint32_t* lvl_s = lane_smem + a.n_inputs * W + warp * (R * 32 * W);  // [R][32][W]
+  if (tid < BOOL_IF_FORMS) if_desc_s[tid] = (uint32_t)if_form_desc(tid);
+  for (int i = tid; i < a.n_inputs * W; i += blockDim.x) {
+    const int v = i / W, w = i % W;
+    inp_s[i] = (w < a.n_words) ? a.case_bits[(int64_t)v * a.n_words + w] : 0u;
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + tid;
+  if (p >= a.n_progs) return;
+
+  int n = -1;
+  const uint4* prog = nullptr;
+  {
+    const int64_t off = a.offsets[p];
+    const int32_t len = a.lengths[p];
+    if ((off & 3) == 0 && len >= 4) {
+      prog = reinterpret_cast<const uint4*>(a.programs + off);
+      const uint4 h = __ldg(prog);
+      const int cnt = (int)h.y;
+      if ((h.x & 0xffu) == K_BOOL && (h.x >> 16) == VERSION && cnt >= 1 && cnt <= MAX_INSTR &&
+          4 + 4 * (int64_t)cnt <= len)
+        n = cnt;
+    }
+  }
+  bool bad = n < 0;
+  const uint32_t nin = (uint32_t)a.n_inputs;
+  // address (in words) of a slot: input v, or stack level l of this lane
+  auto in_addr = [&](uint32_t v, bool& b) -> uint32_t {
+    if (v >= nin) { b = true; v = 0; }
+    return v * W;
+  };
+  auto lv_addr = [&](uint32_t l, bool& b) -> uint32_t {
+    if (l >= (uint32_t)R) { b = true; l = 0; }
+    return (uint32_t)(a.n_inputs * W + warp * (R * 32 * W)) + (l * 32 + (uint32_t)lane) * W;
+  };
+  // the next instruction is loaded while the current one is computed
+  uint4 next = bad ? make_uint4(0, 0, 0, 0) : __ldg(prog + 1);
+  for (int i = 0; i < (bad ? 0 : n); ++i) {
+    const uint4 in = next;
+    if (i + 1 < n) next = __ldg(prog + 2 + i);
+    const uint32_t code = in.x;
+    uint32_t sa, sb, sc, dst;
+    uint32_t is_or = 0, is_if = 0, neg = 0;
+    if (code < (uint32_t)BOOL_IF_BASE) {
+      const uint32_t op = code & 3u, l = (code >> 2) & 7u, form = code >> 5;
+      dst = l;
+      // XX, XS, SX, SS, SSR
+      sa = (form == BF_XX || form == BF_XS) ? in_addr(in.y, bad)
+                                            : lv_addr(form == BF_SSR ? l + 1 : l, bad);
+      sb = (form == BF_XX || form == BF_SX) ? in_addr(in.z, bad)
+                                            : lv_addr(form == BF_SS ? l + 1 : l, bad);
+      sc = sb;
+      is_or = (op == B_OR || op == B_NOR) ? 1u : 0u;
+      neg = (op == B_NAND || op == B_NOR) ? 0xffffffffu : 0u;
+    } else if (code < (uint32_t)BOOL_MOVX) {
+      const uint32_t f = (code - BOOL_IF_BASE) >> 3, l = (code - BOOL_IF_BASE) & 7u;
+      const uint32_t d = if_desc_s[f & 15u];
+      const uint32_t dc = d >> 4, da = (d >> 2) & 3u, db = d & 3u;
+      dst = l;
+      sa = dc ? lv_addr(l + dc - 1, bad) : in_addr(in.y, bad);
+      sb = da ? lv_addr(l + da - 1, bad) : in_addr(in.z, bad);
+      sc = db ? lv_addr(l + db - 1, bad) : in_addr(in.w, bad);
+      is_if = 1u;
+    } else {
+      if (code != (uint32_t)BOOL_MOVX) bad = true;
+      dst = 0;
+      sa = in_addr(in.y, bad);
+      sb = sa;  // AND(a, a) = a
+      sc = sa;
+    }
+    const uint32_t da_ = lv_addr(dst, bad);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const uint32_t x = lane_smem[sa + w], y = lane_smem[sb + w], z = lane_smem[sc + w];
+      uint32_t r = is_or ? (x | y) : (x & y);
+      r ^= neg;
+      const uint32_t f3 = (x & y) | (~x & z);
+      lane_smem[da_ + w] = is_if ? f3 : r;
+    }
+  }
+  uint32_t out[W];
+  const uint32_t base0 = (uint32_t)(a.n_inputs * W + warp * (R * 32 * W)) + (uint32_t)lane * W;
+#pragma unroll
+  for (int w = 0; w < W; ++w) out[w] = lane_smem[base0 + w];
+  if (bad) {
+    atomicOr(a.status, 2 /* GP_ERR_PROGRAM */);
+    if (a.hits_out) a.hits_out[p] = ~0ull;
+    return;
+  }
+  if (a.out_words) {
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+      if (w < a.n_words) a.out_words[(int64_t)p * a.n_words + w] = out[w];
+  }
+  if (a.hits_out && a.target_bits) {
+    const uint32_t tail = (uint32_t)(a.n_cases & 31);
+    const uint32_t last_mask = tail ? ((1u << tail) - 1u) : 0xffffffffu;
+    unsigned long long h = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      if (w >= a.n_words) break;
+      const uint32_t m = (w < a.n_words - 1) ? 0xffffffffu : last_mask;
+      h += __popc(~(out[w] ^ __ldg(a.target_bits + w)) & m);
+    }
+    a.hits_out[p] = h;
+  }
+}
+
+inline size_t bool_lanes_smem(int w, int block, int n_inputs) {
+  return sizeof(uint32_t) * ((size_t)n_inputs * w + (size_t)(block / 32) * gpisa::R * 32 * w);
+}
+
+}  // namespace gpdev

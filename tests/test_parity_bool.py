@@ -95,3 +95,52 @@ def test_malformed_bool_program():
                                    dev(w.target_bits.view(np.int32))).cpu().numpy().view(np.uint64)
     assert hits[1] == np.uint64(0xFFFFFFFFFFFFFFFF)
     assert gp.last_error() == 2
+
+
+@pytest.mark.parametrize("kind,k_inputs", [("parity", 5), ("mux", 6), ("parity", 6), ("parity", 7)])
+def test_program_per_lane_variant(kind, k_inputs):
+    """Tiny case sets (<= 4 words): one program per lane, bit-exact hits and words."""
+    if kind == "mux":
+        w = synth.boolean_problem(kind, k_inputs, seed=121, n_progs=1000)
+    else:
+        progs = synth.ramped_half_and_half(122 + k_inputs, 1000, 2, 8, 256,
+                                           funcs=synth.BOOL_FUNCS + (IF,), n_inputs=k_inputs,
+                                           p_const=0.0, full_fallback_to_grow=True)
+        w = synth.BooleanWorkload("p", synth.pack(progs), synth.bool_case_bits(k_inputs),
+                                  synth.even_parity_target(k_inputs), 1 << k_inputs)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL)
+    P, O, L = upload(enc)
+    cb = dev(w.case_bits.view(np.int32))
+    tb = dev(w.target_bits.view(np.int32))
+    import torch
+    nw = (w.n_cases + 31) // 32
+    for cfg in (gp.Config(gp.VARIANT_LANES, 0, 0, 0), None):  # forced, and chosen automatically
+        hits = gp.eval_population_bool(P, O, L, cb, w.n_cases, tb, config=cfg).cpu().numpy()
+        exp = oracle.bool_population_hits(w.pop.words, w.pop.offsets, w.pop.lengths, w.case_bits,
+                                          w.n_cases, w.target_bits)
+        assert np.array_equal(hits.astype(np.uint64), exp)
+        out = torch.zeros((w.pop.n, nw), dtype=torch.int32, device="cuda")
+        gp.eval_population_bool(P, O, L, cb, w.n_cases, tb, hits_out=None, out_words=out, config=cfg)
+        out = out.cpu().numpy().view(np.uint32)
+        for p in range(0, w.pop.n, 37):
+            exp_w = oracle.bool_outputs(w.pop.program(p), w.case_bits)
+            if w.n_cases % 32:
+                m = np.uint32((1 << (w.n_cases % 32)) - 1)
+                assert np.array_equal(out[p][:-1], exp_w[:-1]) and (out[p][-1] & m) == (exp_w[-1] & m)
+            else:
+                assert np.array_equal(out[p], exp_w)
+
+
+@pytest.mark.parametrize("n_cases", [1, 17, 32, 33, 64, 100, 128])
+def test_program_per_lane_ragged(n_cases):
+    w = synth.boolean_problem("parity", 7, seed=123, n_progs=300)
+    nw = (n_cases + 31) // 32
+    cb = np.ascontiguousarray(w.case_bits[:, :nw])
+    tb = np.ascontiguousarray(w.target_bits[:nw])
+    w2 = synth.BooleanWorkload("r", w.pop, cb, tb, n_cases)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL)
+    P, O, L = upload(enc)
+    hits = gp.eval_population_bool(P, O, L, dev(cb.view(np.int32)), n_cases, dev(tb.view(np.int32)),
+                                   config=gp.Config(gp.VARIANT_LANES, 0, 0, 0)).cpu().numpy()
+    exp = oracle.bool_population_hits(w.pop.words, w.pop.offsets, w.pop.lengths, cb, n_cases, tb)
+    assert np.array_equal(hits.astype(np.uint64), exp)

@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--k", type=int, default=0, help="force K (0 = tune)")
     ap.add_argument("--block", type=int, default=0, help="force the block size (0 = tune)")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="cases per block when --k/--block force the configuration (0 = library default)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the Boolean, register-GP and serving measurements")
     ap.add_argument("--serving-runs", type=int, default=64)
@@ -227,7 +229,7 @@ def run_ours(args):
     # the library's autotuner chooses the configuration the timed steps use
     if args.k or args.block:
         _, best_k, best_b = cands[0]
-        best_chunk = 0
+        best_chunk = args.chunk
     else:
         tuned = gp.autotune_population(P, O, L, X, Y, repeats=3)
         best_k, best_b, best_chunk = int(tuned.k), int(tuned.block), int(tuned.chunk_cases)

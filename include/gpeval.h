@@ -59,11 +59,27 @@ typedef enum gp_status {
  * binary32 quotient rounded to nearest even.  SUB(a,b) = a - b and
  * DIV(a,b) = a / b where a is the first child.  Boolean trees use VAR and the
  * bitwise functions AND, OR, NAND, NOR and IF(c,a,b) = (c&a)|(~c&b).
+ *
+ * Float trees may also use the rest of the function sets of the paper's float
+ * problems (Sec. 4.2: sextic regression {*,/,+,-,Sin,Cos,Log,Exp}; Shuttle
+ * {*,/,+,-,>,<,==,AND,OR,IF}; KDDcup all of them).  The paper names these
+ * functions only; this library defines them as:
+ *   SIN, COS, EXP  binary32 sine, cosine (radians), e^a: CUDA's sinf, cosf
+ *                  and expf (documented maximum error 2 ulp each).
+ *   LOG(a)         0 if a == 0 (either sign), else logf(|a|) (1 ulp).
+ *   GT, LT, EQ     1.0f if a > b (a < b, a == b), else 0.0f; IEEE compares,
+ *                  so a NaN operand gives 0.0f and -0 == +0.
+ *   AND, OR        1.0f if a != 0 and (or) b != 0, else 0.0f; NaN != 0.
+ *   IF(c, a, b)    a if c != 0, else b (NaN != 0 selects a).
+ * A float tree that uses any of them needs GP_VARIANT_EXTENDED and the
+ * S-form (gp_prog_info.extended tells).
  * ---------------------------------------------------------------------- */
 enum {
   GP_OP_ADD = 1, GP_OP_SUB = 2, GP_OP_MUL = 3, GP_OP_DIV = 4,
   GP_OP_VAR = 5, GP_OP_CONST = 6,
-  GP_OP_AND = 7, GP_OP_OR = 8, GP_OP_NAND = 9, GP_OP_NOR = 10, GP_OP_IF = 11
+  GP_OP_AND = 7, GP_OP_OR = 8, GP_OP_NAND = 9, GP_OP_NOR = 10, GP_OP_IF = 11,
+  GP_OP_SIN = 12, GP_OP_COS = 13, GP_OP_EXP = 14, GP_OP_LOG = 15,
+  GP_OP_GT = 16, GP_OP_LT = 17, GP_OP_EQ = 18
 };
 
 /* Encoded program kinds (the interpreter a program is compiled for). */
@@ -72,7 +88,9 @@ typedef enum gp_kind {
                          instruction per function, operands input/constant/stack */
   GP_KIND_RPN = 2,    /* postfix reverse-Polish form of a float tree (Sec. 4, 4.1) */
   GP_KIND_LINEAR = 3, /* register linear GP r[d] = r[a] op r[b], 8 registers */
-  GP_KIND_BOOL = 4    /* S-form of a bit-packed Boolean tree (Sec. 4.2) */
+  GP_KIND_BOOL = 4,   /* S-form of a bit-packed Boolean tree (Sec. 4.2) */
+  GP_KIND_SFORM_EXT = 5 /* written by the encoder, never requested: the S-form
+                           of a float tree that uses the extended functions */
 } gp_kind;
 
 /* Evaluation order of the children of a tree node when it is encoded. */
@@ -96,6 +114,7 @@ typedef struct gp_prog_info {
   int32_t stack_reads;  /* operands taken from the stack */
   int32_t max_input;    /* largest input index referenced, -1 if none */
   int32_t words;        /* encoded size in uint32 words */
+  int32_t extended;     /* 1 if the tree uses SIN..EQ or float AND/OR/IF */
 } gp_prog_info;
 
 /* ------------------------------------------------------------------------
@@ -107,7 +126,9 @@ typedef struct gp_prog_info {
  * GP_KIND_BOOL) with child order `order`.  `info` (may be NULL) receives the
  * counts.  Returns GP_ERR_PROGRAM for a malformed tree or one that needs more
  * than GP_STACK_LEVELS levels or GP_MAX_INSTR instructions, GP_ERR_INVALID_ARG
- * if `out` is too small (info->words still tells the size needed).
+ * if `out` is too small (info->words still tells the size needed),
+ * GP_ERR_NOT_IMPLEMENTED for an extended-function float tree requested as
+ * GP_KIND_RPN (the extended functions are encoded in S-form only).
  *
  * Encoded layout (uint32 words, every program a multiple of 4 words):
  *   header {kind | order<<8, n_instr, n_nodes, max_depth | (max_input+1)<<16}
@@ -151,22 +172,35 @@ typedef enum gp_variant {
   GP_VARIANT_REGISTER = 1,  /* stack levels in registers, K cases per thread */
   GP_VARIANT_LOCAL = 2,     /* BlockGP-style one-case-per-thread stack in local memory
                                (Sec. 3 prior art), GP_KIND_RPN programs only */
-  GP_VARIANT_LANES = 3      /* Boolean only: one program per lane over at most 4 words
+  GP_VARIANT_LANES = 3,     /* Boolean only: one program per lane over at most 4 words
                                (128 cases); GP_VARIANT_AUTO picks it for such case sets */
+  GP_VARIANT_EXTENDED = 4   /* the S-form interpreter with the extended float functions
+                               (runs GP_KIND_SFORM and GP_KIND_SFORM_EXT programs) */
 } gp_variant;
+
+/* Fitness measure of a float program (Sec. 4.2 parameter table: mean squared
+ * error for regression, the number of incorrect classifications for
+ * classification; the default is the sum of absolute errors). */
+typedef enum gp_fitness {
+  GP_FITNESS_SUM_ABS = 0,  /* sum over cases of |o - y| (binary32 error) */
+  GP_FITNESS_MSE = 1,      /* (sum of d*d, d = o - y, binary32) / n_cases */
+  GP_FITNESS_CLASS = 2     /* number of cases with rint(o) != y (y holds class labels) */
+} gp_fitness;
 
 typedef struct gp_config {
   int32_t variant;
   int32_t k;            /* 1, 2, 4 or 8 (0 = tuned) */
   int32_t block;        /* 32..1024, multiple of 32 (0 = tuned) */
   int32_t chunk_cases;  /* 0 = choose; else a multiple of k*block */
+  int32_t fitness;      /* gp_fitness (0 = GP_FITNESS_SUM_ABS) */
 } gp_config;
 
 /* ------------------------------------------------------------------------
  * Float fitness of a population (device pointers).
  *   programs     encoded words (gp_encode_*), GP_KIND_SFORM, GP_KIND_RPN or
- *                GP_KIND_LINEAR, any mix; offsets[p] (int64, multiple of 4)
- *                and lengths[p] (int32) in words.
+ *                GP_KIND_LINEAR, any mix (GP_VARIANT_EXTENDED: GP_KIND_SFORM
+ *                and GP_KIND_SFORM_EXT only); offsets[p] (int64, multiple of
+ *                4) and lengths[p] (int32) in words.
  *   cases        binary32 [n_inputs][n_cases], structure of arrays:
  *                input v of case c at cases[v * n_cases + c].
  *   targets      binary32 [n_cases].
@@ -176,6 +210,11 @@ typedef struct gp_config {
  *                accumulated with compensated binary32 sums per thread and
  *                summed in binary64 across blocks in a fixed order; +inf if any
  *                per-case error is not finite, NaN for a malformed program.
+ *                With cfg->fitness = GP_FITNESS_MSE the binary64 sum of the
+ *                binary32 squares d*d (d = o - y, binary32) divided by
+ *                n_cases; GP_FITNESS_CLASS counts the cases whose output,
+ *                rounded to the nearest integer (ties to even), differs from
+ *                the target label (NaN never matches; never +inf).
  * The result depends only on (program, cases, config), never on what else
  * runs on the GPU.  n_cases may be 0 (fitness 0).  Sec. 4.1, Listing 1/2.
  * ---------------------------------------------------------------------- */

@@ -72,6 +72,7 @@ static float frec(fctx* k, int64_t* pos) {
   *pos += 1;
   if (op == ORC_VAR) {
     if ((int64_t)arg >= k->n_inputs) { k->err = -4; return 0.0f; }
+    if (!k->cases) return 0.0f; /* no cases: validation only */
     return k->cases[(int64_t)arg * k->n_cases + k->c];
   }
   if (op == ORC_CONST) {
@@ -102,8 +103,7 @@ int oracle_tree_outputs(const uint32_t* prog, int64_t len, const float* cases,
     out[c] = v;
   }
   if (n_cases == 0) { /* still validate the program */
-    float dummy = 0.0f;
-    fctx k = {prog, len, &dummy, n_inputs, 1, 0, 0};
+    fctx k = {prog, len, NULL, n_inputs, 0, 0, 0};
     int64_t pos = 0;
     (void)frec(&k, &pos);
     if (k.err) return k.err;

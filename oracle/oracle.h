@@ -54,8 +54,14 @@ extern "C" {
 enum {
   ORC_ADD = 1, ORC_SUB = 2, ORC_MUL = 3, ORC_DIV = 4,
   ORC_VAR = 5, ORC_CONST = 6,
-  ORC_AND = 7, ORC_OR = 8, ORC_NAND = 9, ORC_NOR = 10, ORC_IF = 11
+  ORC_AND = 7, ORC_OR = 8, ORC_NAND = 9, ORC_NOR = 10, ORC_IF = 11,
+  /* the rest of the float function sets of Sec. 4.2 (oracle_fset.c) */
+  ORC_SIN = 12, ORC_COS = 13, ORC_EXP = 14, ORC_LOG = 15,
+  ORC_GT = 16, ORC_LT = 17, ORC_EQ = 18
 };
+
+/* fitness measures */
+enum { ORC_FIT_ABS = 0, ORC_FIT_MSE = 1, ORC_FIT_CLASS = 2 };
 
 /* Single binary32 operation as the oracle defines it (pinned against numpy). */
 float oracle_apply_op(int op, float a, float b);
@@ -113,6 +119,68 @@ int oracle_linear_population_fitness(const uint8_t* instr, const int64_t* offset
                                      int32_t p_end, const float* cases,
                                      int32_t n_inputs, int64_t n_cases,
                                      const float* targets, double* fitness_out);
+
+/* ------------------------------------------------------------------------
+ * Full float function sets (oracle_fset.c).  Sec. 4.2 names the sets of the
+ * float problems -- sextic regression {+,-,*,/,Sin,Cos,Log,Exp}; Shuttle
+ * {+,-,*,/,>,<,==,AND,OR,IF}; KDDcup both together -- and defines none of
+ * them beyond the name.  Readings (each pinned by a test):
+ *   SIN, COS, EXP  binary32 sine, cosine (radians) and e^a.
+ *   LOG(a)         0 if a == 0 (either sign), else the natural log of |a|.
+ *   GT, LT, EQ     1.0f if a > b (a < b, a == b) else 0.0f; IEEE comparisons,
+ *                  so a NaN operand gives 0.0f and -0 == +0.
+ *   AND, OR        1.0f if a != 0 and (or) b != 0, else 0.0f; a NaN counts as
+ *                  non-zero (it is != 0).
+ *   IF(c, a, b)    a if c != 0 else b (a NaN condition selects a).
+ * Fitness measures (the paper's parameter table: mean squared error for
+ * regression, the number of incorrect classifications for classification):
+ *   ORC_FIT_ABS    sum of |o - y| (binary32 error, binary64 sum).
+ *   ORC_FIT_MSE    (sum of d*d, d = o - y, both binary32; binary64 sum) / n.
+ *   ORC_FIT_CLASS  number of cases whose output, rounded to the nearest
+ *                  integer (ties to even), differs from the target label.
+ * A non-finite binary32 error (ABS, MSE) makes the fitness +inf; n = 0
+ * gives 0.
+ *
+ * There is no single correct binary32 sine: implementations differ by an
+ * ulp or two.  The point evaluator takes the binary32 value nearest the
+ * binary64 libm result.  The enclosure evaluator instead bounds EVERY
+ * implementation that rounds +,-,*,/ correctly, takes the comparisons, logic
+ * and IF exactly, and returns sin, cos and exp within 2 ulp and log within
+ * 1 ulp of the correctly rounded value (the documented maximum errors of
+ * CUDA's sinf, cosf, expf and logf): the output of any such implementation
+ * lies in [lo, hi], or is NaN where may_nan is set.  Without a transcendental
+ * node, lo == hi is the exact output (up to the sign of zero).
+ * ------------------------------------------------------------------------ */
+
+/* Arity of a float function of the full sets (0 for a terminal, -1 unknown). */
+int oracle_fset_arity(int op);
+
+/* Per-case outputs of a tree over the full function sets (point evaluation). */
+int oracle_fset_outputs(const uint32_t* prog, int64_t len, const float* cases,
+                        int32_t n_inputs, int64_t n_cases, float* out);
+
+/* Per-case enclosures: lo[c] <= output <= hi[c], or NaN if may_nan[c]. */
+int oracle_fset_enclosure(const uint32_t* prog, int64_t len, const float* cases,
+                          int32_t n_inputs, int64_t n_cases, float* lo, float* hi,
+                          uint8_t* may_nan);
+
+/* Fitness of per-case outputs under a measure. */
+int oracle_fitness_of_outputs(const float* out, const float* targets, int64_t n_cases,
+                              int32_t kind, double* fitness);
+
+/* Fitness bounds from per-case enclosures: every output inside its enclosure
+ * gives a fitness in [f_lo, f_hi] (before the binary64 sum's rounding), or
+ * +inf where *may_inf; *must_inf when every choice gives +inf. */
+int oracle_fitness_enclosure(const float* lo, const float* hi, const uint8_t* may_nan,
+                             const float* targets, int64_t n_cases, int32_t kind,
+                             double* f_lo, double* f_hi, int32_t* may_inf,
+                             int32_t* must_inf);
+
+/* Population over the full function sets, point evaluation, any measure. */
+int oracle_fset_population_fitness(const uint32_t* programs, const int64_t* offsets,
+                                   const int32_t* lengths, int32_t p_begin, int32_t p_end,
+                                   const float* cases, int32_t n_inputs, int64_t n_cases,
+                                   const float* targets, int32_t kind, double* fitness_out);
 
 #ifdef __cplusplus
 }

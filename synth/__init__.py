@@ -26,6 +26,19 @@ Workload recipes (all seeded, numpy PCG64):
   uniform over 8 registers and {+,-,*,/}; inputs ~N(0,1); target a seeded
   random polynomial of total degree <= 3 in 8 variables (all 165 monomials,
   coefficients U[-1,1]) evaluated in binary64 and rounded once to binary32.
+* the paper's float problems (Sec. 4.2), synthetic stand-ins of the same
+  shape (the Shuttle and KDDcup data sets are not available):
+  - sextic regression: x ~ U[-1,1], 100000 cases, y = x^6 - 2x^4 + x^2
+    (binary64, rounded once); trees over {*,/,+,-,sin,cos,log,exp} with
+    terminals {x, U[-1,1] constants}; fitness mean squared error.
+  - Shuttle-shaped classification: 9 integer-valued inputs U{-100..100},
+    58000 cases, 10 class labels 1..10 with 75% of the cases in class 1 (the
+    rest uniform); trees over {*,/,+,-,>,<,==,AND,OR,IF}, constants
+    U[-200,200]; fitness = incorrect classifications.
+  - KDDcup-shaped classification: 41 inputs (a third integer counts
+    floor(Exp(mean 100)), a third rates in [0,1] in steps of 0.01, a third
+    0/1 flags), 494021 cases, 22 labels 0..21 with P(label i) proportional to
+    2^-i; trees over all 14 functions, constants U[-20000,20000].
 """
 from __future__ import annotations
 
@@ -37,9 +50,15 @@ import numpy as np
 # user token format: bits 0..7 opcode, bits 8..31 operand; CONST is followed
 # by one word with the binary32 bit pattern of the constant.
 ADD, SUB, MUL, DIV, VAR, CONST, AND, OR, NAND, NOR, IF = range(1, 12)
+SIN, COS, EXP, LOG, GT, LT, EQ = range(12, 19)
 FLOAT_FUNCS = (ADD, SUB, MUL, DIV)
 BOOL_FUNCS = (AND, OR, NAND, NOR)
-ARITY = {ADD: 2, SUB: 2, MUL: 2, DIV: 2, AND: 2, OR: 2, NAND: 2, NOR: 2, IF: 3}
+# the float function sets of Sec. 4.2 (AND, OR, IF act on floats in float trees)
+SEXTIC_FUNCS = (MUL, DIV, ADD, SUB, SIN, COS, LOG, EXP)
+SHUTTLE_FUNCS = (MUL, DIV, ADD, SUB, GT, LT, EQ, AND, OR, IF)
+KDD_FUNCS = (ADD, SUB, MUL, DIV, GT, LT, EQ, AND, OR, IF, SIN, COS, LOG, EXP)
+ARITY = {ADD: 2, SUB: 2, MUL: 2, DIV: 2, AND: 2, OR: 2, NAND: 2, NOR: 2, IF: 3,
+         SIN: 1, COS: 1, EXP: 1, LOG: 1, GT: 2, LT: 2, EQ: 2}
 
 
 def tok(op: int, arg: int = 0) -> int:
@@ -404,3 +423,63 @@ def serving_runs(seed: int = 5, n_runs: int = 64, pop_lo: int = 128, pop_hi: int
                 y = poly3_target(x, s + 2)
             runs.append(ServingRun("float", pack(progs), x, y, n_cases))
     return runs
+
+
+# --------------------------------------------------------------------------
+# the paper's float problems (Sec. 4.2), synthetic stand-ins
+# --------------------------------------------------------------------------
+def sextic_target(x: np.ndarray) -> np.ndarray:
+    """x^6 - 2x^4 + x^2 in binary64, rounded once to binary32."""
+    x64 = np.asarray(x, np.float64)
+    return (x64 ** 6 - 2.0 * x64 ** 4 + x64 ** 2).astype(np.float32)
+
+
+@dataclass
+class FunctionSetWorkload:
+    name: str
+    pop: Population
+    cases: np.ndarray       # float32 [n_inputs, n_cases]
+    targets: np.ndarray     # float32 [n_cases] (class labels for classification)
+    fitness: int            # 0 sum |e|, 1 mean squared error, 2 incorrect classifications
+    funcs: tuple
+
+    @property
+    def gpop(self) -> float:
+        return float(self.pop.nodes.sum()) * self.cases.shape[1]
+
+
+def sextic_problem(seed: int = 6, n_progs: int = 4096, n_cases: int = 100000,
+                   depth_lo: int = 2, depth_hi: int = 8, max_nodes: int = 256) -> FunctionSetWorkload:
+    progs = ramped_half_and_half(seed, n_progs, depth_lo, depth_hi, max_nodes, funcs=SEXTIC_FUNCS)
+    x = uniform_cases(seed + 1000, 1, n_cases)
+    return FunctionSetWorkload("sextic", pack(progs), x, sextic_target(x[0]), 1, SEXTIC_FUNCS)
+
+
+def shuttle_like_problem(seed: int = 7, n_progs: int = 4096, n_cases: int = 58000,
+                         depth_lo: int = 2, depth_hi: int = 8,
+                         max_nodes: int = 256) -> FunctionSetWorkload:
+    progs = ramped_half_and_half(seed, n_progs, depth_lo, depth_hi, max_nodes, funcs=SHUTTLE_FUNCS,
+                                 n_inputs=9, const_lo=-200.0, const_hi=200.0)
+    rng = np.random.default_rng(seed + 1000)
+    x = rng.integers(-100, 101, (9, n_cases)).astype(np.float32)
+    labels = np.where(rng.random(n_cases) < 0.75, 1, rng.integers(2, 11, n_cases)).astype(np.float32)
+    return FunctionSetWorkload("shuttle-like", pack(progs), x, labels, 2, SHUTTLE_FUNCS)
+
+
+def kdd_like_problem(seed: int = 8, n_progs: int = 1024, n_cases: int = 494021,
+                     depth_lo: int = 2, depth_hi: int = 8,
+                     max_nodes: int = 256) -> FunctionSetWorkload:
+    progs = ramped_half_and_half(seed, n_progs, depth_lo, depth_hi, max_nodes, funcs=KDD_FUNCS,
+                                 n_inputs=41, const_lo=-20000.0, const_hi=20000.0)
+    rng = np.random.default_rng(seed + 1000)
+    x = np.empty((41, n_cases), np.float32)
+    for v in range(41):
+        if v % 3 == 0:
+            x[v] = np.floor(rng.exponential(100.0, n_cases))
+        elif v % 3 == 1:
+            x[v] = rng.integers(0, 101, n_cases) / np.float32(100)
+        else:
+            x[v] = rng.integers(0, 2, n_cases)
+    p = 2.0 ** -np.arange(22)
+    labels = rng.choice(22, n_cases, p=p / p.sum()).astype(np.float32)
+    return FunctionSetWorkload("kdd-like", pack(progs), x, labels, 2, KDD_FUNCS)

@@ -243,7 +243,8 @@ int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets, const int3
  * to its own fixed-size pool, or an evaluation loop that must not meet an
  * allocation failure, or the synchronisation an allocation can imply, in the
  * middle of a run.  It computes exactly what gp_eval_population computes
- * (same arguments, same kernel, default configuration) but keeps the kernel's
+ * (same arguments, same kernel, default configuration: its variant, register
+ * or extended, and its fitness measure) but keeps the kernel's
  * scratch (per-block partial sums, per-program counters, a status word) in a
  * fixed array of about 1.25 MiB that every device loading the library holds
  * until the process exits; it never calls cudaMalloc or cudaFree.

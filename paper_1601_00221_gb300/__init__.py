@@ -25,13 +25,15 @@ __all__ = [
     "eval_population", "eval_outputs", "eval_population_bool",
     "set_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
     "eval_population_noalloc", "autotune_population", "autotune_clear",
-    "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "ORDER_PAPER", "ORDER_MIN_DEPTH",
-    "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL", "VARIANT_LANES",
+    "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "ORDER_PAPER",
+    "ORDER_MIN_DEPTH", "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL", "VARIANT_LANES",
+    "VARIANT_EXTENDED", "FITNESS_SUM_ABS", "FITNESS_MSE", "FITNESS_CLASS",
 ]
 
-KIND_SFORM, KIND_RPN, KIND_LINEAR, KIND_BOOL = 1, 2, 3, 4
+KIND_SFORM, KIND_RPN, KIND_LINEAR, KIND_BOOL, KIND_SFORM_EXT = 1, 2, 3, 4, 5
 ORDER_PAPER, ORDER_MIN_DEPTH = 0, 1
-VARIANT_AUTO, VARIANT_REGISTER, VARIANT_LOCAL, VARIANT_LANES = 0, 1, 2, 3
+VARIANT_AUTO, VARIANT_REGISTER, VARIANT_LOCAL, VARIANT_LANES, VARIANT_EXTENDED = 0, 1, 2, 3, 4
+FITNESS_SUM_ABS, FITNESS_MSE, FITNESS_CLASS = 0, 1, 2
 STACK_LEVELS = 8
 MAX_INSTR = 1024
 
@@ -50,14 +52,16 @@ class GPError(RuntimeError):
 class _ProgInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("n_instr", ctypes.c_int32),
                 ("max_depth", ctypes.c_int32), ("stack_reads", ctypes.c_int32),
-                ("max_input", ctypes.c_int32), ("words", ctypes.c_int32)]
+                ("max_input", ctypes.c_int32), ("words", ctypes.c_int32),
+                ("extended", ctypes.c_int32)]
 
 
 class _ServerOpts(ctypes.Structure):
     _fields_ = [("n_streams", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("max_queued", ctypes.c_int32), ("max_merge", ctypes.c_int32),
                 ("memory_budget", ctypes.c_int64), ("variant", ctypes.c_int32),
-                ("k", ctypes.c_int32), ("block", ctypes.c_int32), ("chunk_cases", ctypes.c_int32)]
+                ("k", ctypes.c_int32), ("block", ctypes.c_int32), ("chunk_cases", ctypes.c_int32),
+                ("fitness", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -79,12 +83,14 @@ class ServerStats(ctypes.Structure):
 
 
 class Config(ctypes.Structure):
-    """gp_config: variant, k (cases per thread per pass), block, chunk_cases (0 = choose)."""
+    """gp_config: variant, k (cases per thread per pass), block, chunk_cases
+    (0 = choose), fitness (FITNESS_SUM_ABS, FITNESS_MSE or FITNESS_CLASS)."""
     _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("chunk_cases", ctypes.c_int32)]
+                ("chunk_cases", ctypes.c_int32), ("fitness", ctypes.c_int32)]
 
     def __repr__(self):
-        return f"Config(variant={self.variant}, k={self.k}, block={self.block}, chunk_cases={self.chunk_cases})"
+        return (f"Config(variant={self.variant}, k={self.k}, block={self.block}, "
+                f"chunk_cases={self.chunk_cases}, fitness={self.fitness})")
 
 
 _lib = None
@@ -166,6 +172,20 @@ class EncodedPopulation:
     @property
     def n(self) -> int:
         return int(self.lengths.size)
+
+    @property
+    def extended(self) -> bool:
+        """Some program uses the extended float functions (needs VARIANT_EXTENDED)."""
+        if self.kind != KIND_SFORM or self.n == 0:
+            return False
+        return bool(np.any((self.words[self.offsets] & 0xFF) == KIND_SFORM_EXT))
+
+    def config(self, fitness: int = FITNESS_SUM_ABS, k: int = 0, block: int = 0,
+               chunk_cases: int = 0) -> "Config":
+        """A configuration that can run this population with the given fitness
+        measure: the extended interpreter when some program needs it."""
+        variant = VARIANT_EXTENDED if self.extended else VARIANT_AUTO
+        return Config(variant, k, block, chunk_cases, fitness)
 
     def to_device(self, device="cuda"):
         import torch
@@ -339,7 +359,7 @@ class Server:
                  memory_budget=1 << 30, config: Optional[Config] = None):
         c = config or Config()
         opts = _ServerOpts(n_streams, max_inflight, max_queued, max_merge, memory_budget,
-                           c.variant, c.k, c.block, 0)
+                           c.variant, c.k, c.block, 0, c.fitness)
         self._h = ctypes.c_void_p()
         _check(lib().gp_server_create(ctypes.byref(opts), ctypes.byref(self._h)))
         self._results = {}  # request id -> (buffer, keep-alive)

@@ -20,7 +20,7 @@ using namespace gpdev;
 namespace {
 
 std::mutex g_mu;
-gp_config g_default = {GP_VARIANT_REGISTER, 8, 128, 0};
+gp_config g_default = {GP_VARIANT_REGISTER, 8, 128, 0, GP_FITNESS_SUM_ABS};
 
 // Internal workspace of one (device, stream): per-block partial sums, the
 // per-program arrival counters of the fused reduction (zero between
@@ -125,10 +125,14 @@ int resolve_config(const gp_config* user, gp_config* c) {
     if (user->k) c->k = user->k;
     if (user->block) c->block = user->block;
     c->chunk_cases = user->chunk_cases;
+    if (user->fitness) c->fitness = user->fitness;
   }
   if (c->variant != GP_VARIANT_REGISTER && c->variant != GP_VARIANT_LOCAL &&
-      c->variant != GP_VARIANT_AUTO && c->variant != GP_VARIANT_LANES)
+      c->variant != GP_VARIANT_AUTO && c->variant != GP_VARIANT_LANES &&
+      c->variant != GP_VARIANT_EXTENDED)
     return gp_fail(GP_ERR_INVALID_ARG, "unknown variant %d", c->variant);
+  if (c->fitness != GP_FITNESS_SUM_ABS && c->fitness != GP_FITNESS_MSE && c->fitness != GP_FITNESS_CLASS)
+    return gp_fail(GP_ERR_INVALID_ARG, "unknown fitness measure %d", c->fitness);
   if (c->variant == GP_VARIANT_AUTO) c->variant = GP_VARIANT_REGISTER;
   if (c->k != 1 && c->k != 2 && c->k != 4 && c->k != 8)
     return gp_fail(GP_ERR_INVALID_ARG, "k must be 1, 2, 4 or 8 (got %d)", c->k);
@@ -246,6 +250,7 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   a.y_aligned = aligned16(targets);
   a.o_aligned = aligned16(outputs) && (n_progs == 1 || n_cases % 4 == 0);
   a.want_fitness = fitness_out != nullptr;
+  a.fitness_kind = c.fitness;
   const int grid = n_progs * n_chunks;
   const bool xreg = (n_inputs == 1);
   const size_t smem = float_tile_bytes(c.k, c.block, n_inputs);
@@ -255,7 +260,12 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
                    n_inputs, smem, kMaxTileBytes);
   cudaError_t e;
   if (c.variant == GP_VARIANT_LOCAL) e = launch_blockgp(a, c.block, grid, s);
-  else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, smem, s);
+  else if (c.variant == GP_VARIANT_EXTENDED) {
+    if (c.k == 1) e = launch_floatx_k1(a, xreg, c.block, grid, smem, s);
+    else if (c.k == 2) e = launch_floatx_k2(a, xreg, c.block, grid, smem, s);
+    else if (c.k == 4) e = launch_floatx_k4(a, xreg, c.block, grid, smem, s);
+    else e = launch_floatx_k8(a, xreg, c.block, grid, smem, s);
+  } else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, smem, s);
   else if (c.k == 2) e = launch_float_k2(a, xreg, c.block, grid, smem, s);
   else if (c.k == 4) e = launch_float_k4(a, xreg, c.block, grid, smem, s);
   else e = launch_float_k8(a, xreg, c.block, grid, smem, s);
@@ -337,6 +347,7 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   gp_config c;
   int rc = resolve_config(cfg, &c);
   if (rc) return rc;
+  if (c.variant == GP_VARIANT_EXTENDED) c.variant = GP_VARIANT_REGISTER;  // a float-only choice
   if (c.variant != GP_VARIANT_REGISTER) return gp_fail(GP_ERR_INVALID_ARG, "Boolean programs use the register or per-lane variant");
   if (!cfg || !cfg->block) {  // small case sets: do not launch idle warps
     int64_t need = (n_words + c.k - 1) / c.k;

@@ -214,10 +214,11 @@ __device__ __forceinline__ void block_reduce(CSum& v, uint32_t& flags, Partial* 
 __device__ __forceinline__ void finish_program(Partial* __restrict__ partials,
                                                unsigned* __restrict__ counters, int p,
                                                int chunk, int n_chunks, CSum v, uint32_t flags,
-                                               double* __restrict__ fitness_out) {
+                                               double* __restrict__ fitness_out,
+                                               double divisor = 1.0) {
   if (n_chunks == 1) {
     if (fitness_out) {
-      double f = (double)v.s + (double)v.c;
+      double f = ((double)v.s + (double)v.c) / divisor;
       if (flags & FLAG_BAD) f = __longlong_as_double(0x7ff8000000000000ll);
       else if (flags & FLAG_NONFINITE) f = __longlong_as_double(0x7ff0000000000000ll);
       fitness_out[p] = f;
@@ -239,10 +240,26 @@ __device__ __forceinline__ void finish_program(Partial* __restrict__ partials,
   }
   counters[p] = 0u;  // ready for the next launch
   if (fitness_out) {
+    f = f / divisor;
     if (fl & FLAG_BAD) f = __longlong_as_double(0x7ff8000000000000ll);
     else if (fl & FLAG_NONFINITE) f = __longlong_as_double(0x7ff0000000000000ll);
     fitness_out[p] = f;
   }
+}
+
+// Per-case error of the fitness measures (gp_fitness; Sec. 4.2 parameter
+// table): 0 |o - y|, 1 (o - y)^2, 2 a misclassification (the output rounded
+// to the nearest integer, ties to even, differs from the label).  Every step
+// is one binary32 operation.
+constexpr int FIT_SUM_ABS = 0, FIT_MSE = 1, FIT_CLASS = 2;
+__device__ __forceinline__ float case_error(float o, float y, int kind) {
+  if (kind == FIT_CLASS) return (rintf(o) == y) ? 0.0f : 1.0f;
+  const float d = __fsub_rn(o, y);
+  return kind == FIT_MSE ? __fmul_rn(d, d) : fabsf(d);
+}
+// the binary64 divisor of the summed errors
+__host__ __device__ __forceinline__ double fitness_divisor(int kind, int64_t n_cases) {
+  return (kind == FIT_MSE && n_cases > 0) ? (double)n_cases : 1.0;
 }
 
 }  // namespace gpdev

@@ -44,15 +44,32 @@ struct Node {
 
 bool is_float_fn(uint32_t op) { return op >= GP_OP_ADD && op <= GP_OP_DIV; }
 bool is_bool_fn(uint32_t op) { return op >= GP_OP_AND && op <= GP_OP_IF; }
-int arity(uint32_t op) { return op == GP_OP_IF ? 3 : 2; }
+// the extended float functions (Sec. 4.2 function sets); AND, OR and IF are
+// float functions in a float tree
+bool is_float_unary(uint32_t op) { return op >= GP_OP_SIN && op <= GP_OP_LOG; }
+bool is_float_ext(uint32_t op) {
+  return is_float_unary(op) || (op >= GP_OP_GT && op <= GP_OP_EQ) || op == GP_OP_AND ||
+         op == GP_OP_OR || op == GP_OP_IF;
+}
+int arity(uint32_t op) { return op == GP_OP_IF ? 3 : is_float_unary(op) ? 1 : 2; }
+int xbin_index(uint32_t op) {
+  switch (op) {
+    case GP_OP_GT: return XB_GT;
+    case GP_OP_LT: return XB_LT;
+    case GP_OP_EQ: return XB_EQ;
+    case GP_OP_AND: return XB_AND;
+    default: return XB_OR;
+  }
+}
 
 constexpr int64_t kMaxTokens = 16 * MAX_INSTR;
 
 // Parses prefix tokens into nodes (index 0 = root; children after parents).
 int parse_prefix(const uint32_t* w, int64_t n, bool boolean, std::vector<Node>& nodes,
-                 int* max_input) {
+                 int* max_input, bool* extended) {
   nodes.clear();
   *max_input = -1;
+  *extended = false;
   if (!w || n <= 0) return gp_fail(GP_ERR_PROGRAM, "empty program");
   if (n > kMaxTokens) return gp_fail(GP_ERR_PROGRAM, "program longer than %lld words", (long long)kMaxTokens);
   struct Open { int node; int filled; };
@@ -75,6 +92,10 @@ int parse_prefix(const uint32_t* w, int64_t n, bool boolean, std::vector<Node>& 
       i += 2;
     } else if ((boolean && is_bool_fn(nd.op)) || (!boolean && is_float_fn(nd.op))) {
       nd.nchild = arity(nd.op);
+      i += 1;
+    } else if (!boolean && is_float_ext(nd.op)) {
+      nd.nchild = arity(nd.op);
+      *extended = true;
       i += 1;
     } else {
       return gp_fail(GP_ERR_PROGRAM, "opcode %u not allowed at word %lld", nd.op, (long long)i);
@@ -146,7 +167,7 @@ struct Emitter {
       const Node& ch = nodes[n.child[c]];
       if (lvl[c] < 0) pay[c] = ch.payload; else ++stack_reads;
     }
-    auto kindof = [&](int c) -> int {  // 0 X, 1 C, 2 S0, 3 S1
+    auto kindof = [&](int c) -> int {  // 0 X, 1 C, 2 + j stack level l + j
       const Node& ch = nodes[n.child[c]];
       if (lvl[c] >= 0) return 2 + lvl[c];
       return ch.op == GP_OP_CONST ? 1 : 0;
@@ -167,6 +188,17 @@ struct Emitter {
       put(bool_bin_code(form, l, (int)(n.op - GP_OP_AND)), pay[0], pay[1], 0);
       return;
     }
+    if (n.nchild == 1) {  // SIN, COS, EXP, LOG
+      const int k = kindof(0);
+      const int uform = k == 0 ? UF_X : k == 1 ? UF_C : UF_S;
+      put(sfx_un_code(uform, l, (int)(n.op - GP_OP_SIN)), pay[0], 0, 0);
+      return;
+    }
+    if (n.nchild == 3) {  // float IF: descriptors X 0, C 1, stack level l+j 2+j
+      const int d0 = kindof(0), d1 = kindof(1), d2 = kindof(2);
+      put(sfx_if_code(xif_form_index(d0, d1, d2), l), pay[0], pay[1], pay[2]);
+      return;
+    }
     static const int table[4][4] = {
         // b:   X       C       S0      S1
         {SF_XX, SF_XC, SF_XS, -1},      // a = X
@@ -175,7 +207,8 @@ struct Emitter {
         {-1, -1, SF_SSR, -1},           // a = S1
     };
     int form = table[kindof(0)][kindof(1)];
-    put(sform_code(form, l, (int)(n.op - GP_OP_ADD)), pay[0], pay[1], 0);
+    if (is_float_fn(n.op)) put(sform_code(form, l, (int)(n.op - GP_OP_ADD)), pay[0], pay[1], 0);
+    else put(sfx_bin_code(form, l, xbin_index(n.op)), pay[0], pay[1], 0);
   }
 
   // postfix (RPN): the value of node n ends on level l
@@ -203,9 +236,12 @@ int encode_one(const uint32_t* prefix, int64_t n_words, int32_t kind, int32_t or
     return gp_fail(GP_ERR_INVALID_ARG, "unknown order %d", order);
   std::vector<Node> nodes;
   int max_input = -1;
-  int rc = parse_prefix(prefix, n_words, kind == K_BOOL, nodes, &max_input);
+  bool extended = false;
+  int rc = parse_prefix(prefix, n_words, kind == K_BOOL, nodes, &max_input, &extended);
   if (rc) return rc;
   const bool rpn = (kind == K_RPN);
+  if (extended && rpn)
+    return gp_fail(GP_ERR_NOT_IMPLEMENTED, "the extended float functions are encoded in S-form only");
   compute_needs(nodes, order, rpn);
   Emitter em{nodes, order, (uint32_t)kind, {}, 0};
   em.ins.reserve(16 * nodes.size());
@@ -230,13 +266,14 @@ int encode_one(const uint32_t* prefix, int64_t n_words, int32_t kind, int32_t or
   inf.stack_reads = em.stack_reads;
   inf.max_input = max_input;
   inf.words = 4 + 4 * n_instr;
+  inf.extended = extended ? 1 : 0;
   if (info) *info = inf;
   if (depth > R)
     return gp_fail(GP_ERR_PROGRAM, "program needs %d stack levels, more than %d (encode with GP_ORDER_MIN_DEPTH)", depth, R);
   if (n_instr > MAX_INSTR)
     return gp_fail(GP_ERR_PROGRAM, "program has %d instructions, more than %d", n_instr, MAX_INSTR);
   out.clear();
-  out.push_back(header0((uint32_t)kind, (uint32_t)order));
+  out.push_back(header0(extended ? (uint32_t)K_SFORMX : (uint32_t)kind, (uint32_t)order));
   out.push_back((uint32_t)n_instr);
   out.push_back((uint32_t)inf.n_nodes);
   out.push_back((uint32_t)depth | ((uint32_t)(max_input + 1) << 16));

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
       const float o = stack[0];
       if (out_row) out_row[c] = o;
       if (a.want_fitness) {
-        const float d = fabsf(__fsub_rn(o, __ldg(a.targets + c)));
+        const float d = case_error(o, __ldg(a.targets + c), a.fitness_kind);
         if (!(d <= 3.402823466e38f)) flags |= FLAG_NONFINITE;
         csum_add(acc, d);
       }
@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
   if (tid == 0) {
     if (flags & FLAG_BAD) atomicOr(a.status, 2 /* GP_ERR_PROGRAM */);
     if (a.want_fitness || (flags & FLAG_BAD))
-      finish_program(a.partials, a.counters, p, chunk, a.n_chunks, acc, flags, a.fitness_out);
+      finish_program(a.partials, a.counters, p, chunk, a.n_chunks, acc, flags, a.fitness_out,
+                     fitness_divisor(a.fitness_kind, a.n_cases));
   }
 }
 

@@ -57,6 +57,7 @@ struct FloatArgs {
   int32_t y_aligned;     // targets 16-byte aligned
   int32_t o_aligned;     // outputs + p*n_cases 16-byte aligned for every p
   int32_t want_fitness;  // compute the fitness (targets may be null only if n_cases == 0)
+  int32_t fitness_kind;  // FIT_SUM_ABS, FIT_MSE or FIT_CLASS
 };
 
 // ---------------------------------------------------------------------------
@@ -127,6 +128,107 @@ __device__ __forceinline__ bool run_linear(uint32_t prog, uint32_t n, uint32_t t
 }
 
 // ---------------------------------------------------------------------------
+// Extended S-form (the full float function sets of Sec. 4.2).  The generated
+// block keeps the stack in asm operands and returns whenever it meets SIN,
+// COS, EXP or LOG, with the operand's K values in t; this loop applies CUDA's
+// binary32 function (sinf, cosf, expf: 2 ulp; logf: 1 ulp, documented) and
+// enters the block again, which stores t into the level and goes on.  The
+// program is warp-uniform, so every exit and the function chosen are too.
+// ---------------------------------------------------------------------------
+constexpr uint32_t SFX_EXIT = 16;  // status >= SFX_EXIT: 16 + fn * 8 + level
+
+template <int K>
+struct SfxUnit {  // register unit of the extended interpreter's operands
+  using type = unsigned long long;  // a pair of binary32 cases
+};
+template <>
+struct SfxUnit<1> {
+  using type = float;
+};
+
+template <int K>
+__device__ __forceinline__ void sfx_unpack(const typename SfxUnit<K>::type* u, float (&v)[K]) {
+  if constexpr (K == 1) {
+    v[0] = u[0];
+  } else {
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) {
+      v[2 * i] = __uint_as_float((unsigned)(u[i] & 0xffffffffull));
+      v[2 * i + 1] = __uint_as_float((unsigned)(u[i] >> 32));
+    }
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void sfx_pack(const float (&v)[K], typename SfxUnit<K>::type* u) {
+  if constexpr (K == 1) {
+    u[0] = v[0];
+  } else {
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i)
+      u[i] = ((unsigned long long)__float_as_uint(v[2 * i + 1]) << 32) | __float_as_uint(v[2 * i]);
+  }
+}
+
+// protected log: 0 at a zero operand (either sign), else the log of |a|
+__device__ __forceinline__ float protected_logf(float a) { return a == 0.0f ? 0.0f : logf(fabsf(a)); }
+
+template <int K>
+__device__ __forceinline__ void sfx_apply(uint32_t fn, typename SfxUnit<K>::type* t) {
+  float v[K];
+  sfx_unpack<K>(t, v);
+  if (fn == gpisa::XU_SIN) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = sinf(v[j]);
+  } else if (fn == gpisa::XU_COS) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = cosf(v[j]);
+  } else if (fn == gpisa::XU_EXP) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = expf(v[j]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = protected_logf(v[j]);
+  }
+  sfx_pack<K>(v, t);
+}
+
+#define GP_SFX(K_, X_) \
+  asm volatile(GP_PTX_SFORMX_K##K_##_##X_ : GP_SFX_OUT_K##K_##_##X_ : GP_SFX_IN_K##K_##_##X_ : "memory")
+
+template <int K, bool XREG>
+__device__ __forceinline__ bool run_tree_ext(uint32_t prog, const float (&x)[K], uint32_t tile,
+                                             float (&o)[K]) {
+  using U = typename SfxUnit<K>::type;
+  constexpr int H = K == 1 ? 1 : K / 2;
+  U s[R * H];
+  U t[H];
+#pragma unroll
+  for (int i = 0; i < R * H; ++i) s[i] = U(0);
+#pragma unroll
+  for (int i = 0; i < H; ++i) t[i] = U(0);
+  uint32_t adr = prog, st = 0;
+#pragma unroll 1
+  for (;;) {
+    if constexpr (XREG) {
+      if constexpr (K == 1) GP_SFX(1, REG);
+      else if constexpr (K == 2) GP_SFX(2, REG);
+      else if constexpr (K == 4) GP_SFX(4, REG);
+      else GP_SFX(8, REG);
+    } else {
+      if constexpr (K == 1) GP_SFX(1, SMEM);
+      else if constexpr (K == 2) GP_SFX(2, SMEM);
+      else if constexpr (K == 4) GP_SFX(4, SMEM);
+      else GP_SFX(8, SMEM);
+    }
+    if (st < SFX_EXIT) break;
+    sfx_apply<K>((st - SFX_EXIT) >> 3, t);
+  }
+  sfx_unpack<K>(s, o);
+  return st == 0;
+}
+
+// ---------------------------------------------------------------------------
 // Instruction validation (once per block, before the first pass): every code
 // known, every input index below n_inputs, every level pair in range.
 // ---------------------------------------------------------------------------
@@ -156,11 +258,42 @@ __device__ __forceinline__ bool valid_instr(uint32_t kind, const uint4& in, int 
   return false;
 }
 
+// the extended S-form's codes (a superset of the basic S-form's)
+__device__ __forceinline__ bool valid_instr_ext(const uint4& in, int n_inputs) {
+  using namespace gpisa;
+  const uint32_t nin = (uint32_t)n_inputs;
+  if (in.x < (uint32_t)SF_NCODES) return valid_instr(K_SFORM, in, n_inputs);
+  if (in.x >= (uint32_t)SFX_NCODES) return false;
+  if (in.x < (uint32_t)SFX_UN_BASE) {
+    const int c = (int)in.x - SFX_BIN_BASE;
+    const int level = (c / XB_NOPS) % R, form = (c / XB_NOPS) / R;
+    if ((form == SF_SS || form == SF_SSR) && level + 1 >= R) return false;
+    const bool xa = form == SF_XX || form == SF_XC || form == SF_XS;
+    const bool xb = form == SF_XX || form == SF_CX || form == SF_SX;
+    return !(xa && in.y >= nin) && !(xb && in.z >= nin);
+  }
+  if (in.x < (uint32_t)SFX_IF_BASE) {
+    const int uform = ((int)in.x - SFX_UN_BASE) / XU_NOPS / R;
+    return !(uform == UF_X && in.y >= nin);
+  }
+  const int c = (int)in.x - SFX_IF_BASE;
+  const int level = c % R, desc = xif_form_desc(c / R);
+  const int d[3] = {desc / 25, (desc / 5) % 5, desc % 5};
+  const uint32_t pay[3] = {in.y, in.z, in.w};
+  int m = 0;
+  for (int i = 0; i < 3; ++i) {
+    if (d[i] >= 2) ++m;
+    if (d[i] == 0 && pay[i] >= nin) return false;
+  }
+  return level + (m > 0 ? m - 1 : 0) < R;
+}
+
 // ---------------------------------------------------------------------------
 // The kernel: block = (program p, chunk of cases).  Shared memory holds the
 // program; each warp runs its own sequence of passes.
 // ---------------------------------------------------------------------------
-template <int K, bool XREG>
+// EXT: the extended S-form interpreter (K_SFORM and K_SFORMX programs only).
+template <int K, bool XREG, bool EXT = false>
 __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   using namespace gpisa;
   __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
@@ -181,7 +314,8 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
       const uint4 h = *reinterpret_cast<const uint4*>(a.programs + off);
       kind = (int)(h.x & 0xffu);
       const int n = (int)h.y;
-      const bool kind_ok = kind == K_SFORM || kind == K_RPN || kind == K_LINEAR;
+      const bool kind_ok = EXT ? (kind == K_SFORM || kind == K_SFORMX)
+                               : (kind == K_SFORM || kind == K_RPN || kind == K_LINEAR);
       const bool ver_ok = (h.x >> 16) == VERSION;
       const bool n_ok = n >= (kind == K_LINEAR ? 0 : 1) && n <= MAX_INSTR && 4 + 4 * (int64_t)n <= len;
       if (kind_ok && ver_ok && n_ok) n_instr = n;
@@ -199,11 +333,15 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
     for (int i = tid; i < n_instr; i += blockDim.x) {
       const uint4 in = g[i];
       prog_s[i] = in;
-      ok &= valid_instr(kind, in, a.n_inputs) ? 1 : 0;
+      if constexpr (EXT) ok &= valid_instr_ext(in, a.n_inputs) ? 1 : 0;
+      else ok &= valid_instr(kind, in, a.n_inputs) ? 1 : 0;
     }
     // the interpreters leave through the table entry one past the last code
     if (tid == 0)
-      prog_s[n_instr] = make_uint4(kind == K_SFORM ? SF_NCODES : kind == K_RPN ? RF_NCODES : LIN_NCODES,
+      prog_s[n_instr] = make_uint4(EXT ? SFX_NCODES
+                                       : kind == K_SFORM ? SF_NCODES
+                                       : kind == K_RPN   ? RF_NCODES
+                                                         : LIN_NCODES,
                                    0u, 0u, 0u);
     bad = !__syncthreads_and(ok);
   }
@@ -225,7 +363,7 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   // this lane's K staged values of input v live at tile + v * 32 * K floats
   float* tile = reinterpret_cast<float*>(tile_s) + (size_t)warp * a.n_inputs * 32 * K + lane * K;
   const uint32_t tile_addr = (uint32_t)__cvta_generic_to_shared(tile);
-  const bool staged = !XREG || kind == K_LINEAR;
+  const bool staged = !XREG || (!EXT && kind == K_LINEAR);
 
   if (!bad) {
 #pragma unroll 1
@@ -253,7 +391,9 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
         for (int j = 0; j < K; ++j) x[j] = 0.0f;
       }
       bool ok;
-      if (kind == K_LINEAR) {
+      if constexpr (EXT) {
+        ok = run_tree_ext<K, XREG>(prog_addr, x, tile_addr, o);
+      } else if (kind == K_LINEAR) {
         ok = run_linear<K>(prog_addr, (uint32_t)n_instr, tile_addr,
                            (uint32_t)(a.n_inputs < R ? a.n_inputs : R), o);
       } else if (kind == K_SFORM) {
@@ -269,11 +409,11 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
       if (a.want_fitness) {
         Vec<K> y;
         vload<K>(y, a.targets, c0, a.n_cases, full && a.y_aligned);
-        // pass sum of the K absolute errors, then one compensated add
+        // pass sum of the K errors, then one compensated add
         float e[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-          float d = fabsf(__fsub_rn(o[j], vget<K>(y, j)));
+          float d = case_error(o[j], vget<K>(y, j), a.fitness_kind);
           if (c0 + j >= a.n_cases) d = 0.0f;
           if (!(d <= 3.402823466e38f)) flags |= FLAG_NONFINITE;
           e[j] = d;
@@ -292,7 +432,8 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   if (tid == 0) {
     if (flags & FLAG_BAD) atomicOr(a.status, 2 /* GP_ERR_PROGRAM */);
     if (a.want_fitness || bad)
-      finish_program(a.partials, a.counters, p, chunk, a.n_chunks, acc, flags, a.fitness_out);
+      finish_program(a.partials, a.counters, p, chunk, a.n_chunks, acc, flags, a.fitness_out,
+                     fitness_divisor(a.fitness_kind, a.n_cases));
   }
 }
 

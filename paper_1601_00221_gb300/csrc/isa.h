@@ -24,7 +24,7 @@ constexpr int R = 8;            // stack levels held per case (GP_STACK_LEVELS)
 constexpr int MAX_INSTR = 1024; // GP_MAX_INSTR
 constexpr uint32_t VERSION = 1;
 
-enum Kind : uint32_t { K_SFORM = 1, K_RPN = 2, K_LINEAR = 3, K_BOOL = 4 };
+enum Kind : uint32_t { K_SFORM = 1, K_RPN = 2, K_LINEAR = 3, K_BOOL = 4, K_SFORMX = 5 };
 
 // float function index = user opcode - 1 (ADD, SUB, MUL, DIV)
 enum FOp : int { F_ADD = 0, F_SUB = 1, F_MUL = 2, F_DIV = 3 };
@@ -41,6 +41,58 @@ enum SForm : int {
 };
 GPISA_HD constexpr int sform_code(int form, int level, int op) { return (form * R + level) * 4 + op; }
 constexpr int SF_NCODES = SF_NFORMS * R * 4;
+
+// ---- extended float S-form (the function sets of Sec. 4.2's float
+// problems).  Its code space starts with the basic S-form's codes, unchanged,
+// so the extended interpreter also runs basic programs; the extended codes
+// follow.  Comparisons and logic GT, LT, EQ, AND, OR take the ten binary
+// operand forms SF_XX..SF_SSR; the unary functions SIN, COS, EXP, LOG take an
+// input, a constant or the stack level l as operand; IF(c, a, b) takes each
+// operand as an input (0), a constant (1) or stack level l + j (2 + j), the
+// stack operands using exactly the levels l .. l + m - 1.  Every result goes
+// to level l.
+enum XBin : int { XB_GT = 0, XB_LT, XB_EQ, XB_AND, XB_OR, XB_NOPS };
+enum XUn : int { XU_SIN = 0, XU_COS, XU_EXP, XU_LOG, XU_NOPS };
+enum UForm : int { UF_X = 0, UF_C, UF_S, UF_NFORMS };
+constexpr int SFX_BIN_BASE = SF_NFORMS * R * 4;  // 384
+GPISA_HD constexpr int sfx_bin_code(int form, int level, int op) {
+  return SFX_BIN_BASE + (form * R + level) * XB_NOPS + op;  // form SF_XX..SF_SSR
+}
+constexpr int SFX_UN_BASE = SFX_BIN_BASE + (SF_SSR + 1) * R * XB_NOPS;  // 784
+GPISA_HD constexpr int sfx_un_code(int uform, int level, int fn) {
+  return SFX_UN_BASE + (uform * R + level) * XU_NOPS + fn;
+}
+constexpr int SFX_IF_BASE = SFX_UN_BASE + UF_NFORMS * R * XU_NOPS;  // 880
+// operand descriptor d in 0..4 (X, C, S0, S1, S2); valid when the stack
+// operands use exactly levels l .. l+m-1, each once
+GPISA_HD constexpr bool xif_desc_valid(int dc, int da, int db) {
+  int m = (dc >= 2) + (da >= 2) + (db >= 2);
+  bool used[3] = {false, false, false};
+  const int d[3] = {dc, da, db};
+  for (int i = 0; i < 3; ++i) {
+    if (d[i] < 2) continue;
+    const int j = d[i] - 2;
+    if (j >= m || used[j]) return false;
+    used[j] = true;
+  }
+  return true;
+}
+// descriptors numbered in increasing order of dc*25 + da*5 + db
+GPISA_HD constexpr int xif_form_index(int dc, int da, int db) {
+  int idx = 0;
+  for (int t = 0; t < dc * 25 + da * 5 + db; ++t)
+    if (xif_desc_valid(t / 25, (t / 5) % 5, t % 5)) ++idx;
+  return idx;
+}
+GPISA_HD constexpr int xif_form_desc(int idx) {  // inverse: dc*25 + da*5 + db
+  int seen = 0;
+  for (int t = 0; t < 125; ++t)
+    if (xif_desc_valid(t / 25, (t / 5) % 5, t % 5)) { if (seen == idx) return t; ++seen; }
+  return -1;
+}
+constexpr int SFX_IF_FORMS = 38;
+GPISA_HD constexpr int sfx_if_code(int iform, int level) { return SFX_IF_BASE + iform * R + level; }
+constexpr int SFX_NCODES = SFX_IF_BASE + SFX_IF_FORMS * R;  // 1184
 
 // ---- float RPN (Sec. 4): push a terminal to level l, or combine levels
 // l and l+1 into level l.

@@ -30,10 +30,18 @@ cudaError_t launch_float_k4(const FloatArgs& a, bool xreg, int block, int grid, 
                             cudaStream_t s);
 cudaError_t launch_float_k8(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
                             cudaStream_t s);
+// The extended S-form interpreter (the full float function sets), same shapes.
+cudaError_t launch_floatx_k1(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                             cudaStream_t s);
+cudaError_t launch_floatx_k2(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                             cudaStream_t s);
+cudaError_t launch_floatx_k4(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                             cudaStream_t s);
+cudaError_t launch_floatx_k8(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                             cudaStream_t s);
 cudaError_t launch_blockgp(const FloatArgs& a, int block, int grid, cudaStream_t s);
 // Boolean kernels: K words per thread.
 cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s);
-// Boolean, one program per lane over w <= 4 words (blocks of 128 threads).
 // Boolean, one program per lane over w <= 4 words (one warp per block).
 cudaError_t launch_bool_lanes(const BoolArgs& a, int w, int grid, size_t smem, cudaStream_t s);
 }  // namespace gpdev

@@ -91,7 +91,7 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   gp_config c;
   int rc = gp_get_config(&c);
   if (rc) return rc;
-  if (c.variant != GP_VARIANT_REGISTER) c.variant = GP_VARIANT_REGISTER;
+  if (c.variant != GP_VARIANT_EXTENDED) c.variant = GP_VARIANT_REGISTER;
 
   NoallocScratch* scratch = nullptr;
   rc = scratch_on_current_device(&scratch);
@@ -140,9 +140,15 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   a.y_aligned = ((uintptr_t)targets & 15u) == 0;
   a.o_aligned = 0;
   a.want_fitness = 1;
+  a.fitness_kind = c.fitness;
   const int grid = (int)(n_progs * n_chunks);
   const bool xreg = (n_inputs == 1);
-  if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, smem, s);
+  if (c.variant == GP_VARIANT_EXTENDED) {
+    if (c.k == 1) e = launch_floatx_k1(a, xreg, c.block, grid, smem, s);
+    else if (c.k == 2) e = launch_floatx_k2(a, xreg, c.block, grid, smem, s);
+    else if (c.k == 4) e = launch_floatx_k4(a, xreg, c.block, grid, smem, s);
+    else e = launch_floatx_k8(a, xreg, c.block, grid, smem, s);
+  } else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, smem, s);
   else if (c.k == 2) e = launch_float_k2(a, xreg, c.block, grid, smem, s);
   else if (c.k == 4) e = launch_float_k4(a, xreg, c.block, grid, smem, s);
   else e = launch_float_k8(a, xreg, c.block, grid, smem, s);

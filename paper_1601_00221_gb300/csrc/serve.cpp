@@ -348,6 +348,7 @@ extern "C" int gp_server_create(const gp_server_opts* opts, gp_server** out) {
   if (!o.config.variant) o.config.variant = def.variant;
   if (!o.config.k) o.config.k = def.k;
   if (!o.config.block) o.config.block = def.block;
+  if (!o.config.fitness) o.config.fitness = def.fitness;
   o.config.chunk_cases = 0;
   s->opts = o;
   cudaError_t e = cudaGetDevice(&s->device);

@@ -538,6 +538,290 @@ class FloatGen:
 
 
 # ---------------------------------------------------------------------------
+# extended float S-form (the full function sets of Sec. 4.2)
+# ---------------------------------------------------------------------------
+SFX_BIN_BASE = len(SF_FORMS) * R * 4              # 384
+XB_OPS = ["GT", "LT", "EQ", "AND", "OR"]
+SFX_UN_BASE = SFX_BIN_BASE + 10 * R * len(XB_OPS)  # 784
+UF_FORMS = ["X", "C", "S"]
+SFX_IF_BASE = SFX_UN_BASE + len(UF_FORMS) * R * 4  # 880
+
+
+def xif_descs():
+    """IF operand descriptors (c, a, b), each 0 = input, 1 = constant,
+    2 + j = stack level l + j, numbered as in csrc/isa.h."""
+    out = []
+    for t in range(125):
+        d = (t // 25, (t // 5) % 5, t % 5)
+        m = sum(1 for v in d if v >= 2)
+        used, ok = set(), True
+        for v in d:
+            if v >= 2:
+                if v - 2 >= m or (v - 2) in used:
+                    ok = False
+                used.add(v - 2)
+        if ok:
+            out.append(d)
+    assert len(out) == 38
+    return out
+
+
+SFX_NCODES = SFX_IF_BASE + 38 * R                  # 1184
+# exit status of the extended interpreter: 0 done, 1 bad code, else
+# XEXIT + fn * 8 + level (apply unary function fn to t, store to level)
+XEXIT = 16
+
+
+class FloatGenX(FloatGen):
+    """S-form interpreter over the full float function sets.  The stack
+    registers, the unary-function operand t, the instruction address and the
+    status are asm in/out operands, so the loop can leave the PTX block: a
+    SIN, COS, EXP or LOG instruction copies its operand into t, records the
+    function and the destination level in the status and exits; the caller
+    applies CUDA's binary32 function to the K values and enters again, and the
+    block first stores t into the level, then goes on with the next
+    instruction.  Operands:
+        %0 .. %{RH-1}       stack units (f32 for K = 1, b64 case pairs else)
+        %{RH} .. %{RH+H-1}  t units
+        %{RH+H}             shared address of the next instruction (u32)
+        %{RH+H+1}           status: 0 on the first entry, as above on exit
+        %{RH+H+2} ..        the K input values (f32, single input in
+                            registers) or this lane's tile address (u32)"""
+
+    def __init__(self, K, xmode):
+        super().__init__(K, xmode)
+        self.RH = R * self.H
+        self.o_adr = self.RH + self.H
+        self.o_st = self.RH + self.H + 1
+        self.o_in = self.RH + self.H + 2
+
+    def lev(self, l, i):
+        return f"%{l * self.H + i}"
+
+    def t(self):
+        return [f"%{self.RH + i}" for i in range(self.H)]
+
+    def setup_inputs(self):
+        b, K = self.b, self.K
+        if self.xmode == "reg":
+            for i in range(self.H):
+                if K == 1:
+                    b(f"mov.f32 x0, %{self.o_in};")
+                else:
+                    b(f"mov.b64 x{i}, {{%{self.o_in + 2 * i}, %{self.o_in + 2 * i + 1}}};")
+        else:
+            b(f"mov.u32 xbase, %{self.o_in};")
+
+    def elementwise(self, d, srcs, emit):
+        """d[i] <- emit(elements of srcs[*][i]) one binary32 element at a time."""
+        b = self.b
+        if self.K == 1:
+            for i in range(self.H):
+                emit(d[i], [s_[i] for s_ in srcs])
+            return
+        for i in range(self.H):
+            names = []
+            for j, s_ in enumerate(srcs):
+                b(f"mov.b64 {{e{2 * j}, e{2 * j + 1}}}, {s_[i]};")
+                names.append((f"e{2 * j}", f"e{2 * j + 1}"))
+            emit("e6", [n[0] for n in names])
+            emit("e7", [n[1] for n in names])
+            b(f"mov.b64 {d[i]}, {{e6, e7}};")
+
+    def cmp_emit(self, op):
+        b = self.b
+
+        def emit(dst, ops):
+            a, c = ops
+            if op == "GT":
+                b(f"setp.gt.f32 q, {a}, {c};")
+            elif op == "LT":
+                b(f"setp.lt.f32 q, {a}, {c};")
+            elif op == "EQ":
+                b(f"setp.eq.f32 q, {a}, {c};")
+            elif op == "AND":   # NaN != 0 counts as true: unordered compare
+                b(f"setp.neu.f32 q, {a}, 0f00000000;")
+                b(f"setp.neu.and.f32 q, {c}, 0f00000000, q;")
+            else:
+                b(f"setp.neu.f32 q, {a}, 0f00000000;")
+                b(f"setp.neu.or.f32 q, {c}, 0f00000000, q;")
+            b(f"selp.f32 {dst}, 0f3F800000, 0f00000000, q;")
+        return emit
+
+    def if_emit(self):
+        b = self.b
+
+        def emit(dst, ops):
+            c, a, e = ops
+            b(f"setp.neu.f32 q, {c}, 0f00000000;")
+            b(f"selp.f32 {dst}, {a}, {e}, q;")
+        return emit
+
+    def operand(self, kind, l, payload, xreg_units, creg):
+        """Register units of an operand: 'X' input, 'C' constant, or a level."""
+        if kind == "X":
+            return self.load_x(xreg_units, payload)
+        if kind == "C":
+            return self.const(creg, payload)
+        return [self.lev(kind, i) for i in range(self.H)]
+
+    def sform_ext(self):
+        K, H, b = self.K, self.H, self.b
+        ty = self.ty
+        b("{")
+        b(f".reg .{ty} ta<{H}>, tb<{H}>, xA<{H}>, xB<{H}>, xC<{H}>, cA, cB, cC;")
+        if self.xmode == "reg":
+            b(f".reg .{ty} x<{H}>;")
+        b(".reg .b32 code, pa, pb, pc, adr, dl, xa, xbase;")
+        b(".reg .f32 e<8>;")
+        b(".reg .pred p, q;")
+        for ln in pdiv_regs(K, H).split("\n"):
+            b(ln)
+        if K > 1:
+            b("mov.b64 one2, 0x3F8000003F800000;")
+        L = lambda l: [self.lev(l, i) for i in range(H)]
+        ta = [f"ta{i}" for i in range(H)]
+        tb = [f"tb{i}" for i in range(H)]
+        xA = [f"xA{i}" for i in range(H)]
+        xB = [f"xB{i}" for i in range(H)]
+        xC = [f"xC{i}" for i in range(H)]
+        T = self.t()
+        table, bodies = {}, []
+        # basic S-form codes (same numbers as the basic interpreter)
+        for f, name in enumerate(SF_FORMS):
+            for l in range(R):
+                for op in range(4):
+                    if name in ("SS", "SSR") and l + 1 >= R:
+                        continue
+                    if name in ("MOVX", "MOVC") and (l != 0 or op != 0):
+                        continue
+                    code = sform_code(f, l, op)
+                    table[code] = f"C{code}"
+                    bodies.append((code, "basic", name, l, op))
+        for f, name in enumerate(SF_FORMS[:10]):
+            for l in range(R):
+                for op in range(len(XB_OPS)):
+                    if name in ("SS", "SSR") and l + 1 >= R:
+                        continue
+                    code = SFX_BIN_BASE + (f * R + l) * len(XB_OPS) + op
+                    table[code] = f"C{code}"
+                    bodies.append((code, "cmp", name, l, op))
+        for uf, name in enumerate(UF_FORMS):
+            for l in range(R):
+                for fn in range(4):
+                    code = SFX_UN_BASE + (uf * R + l) * 4 + fn
+                    table[code] = f"C{code}"
+                    bodies.append((code, "un", name, l, fn))
+        for fi, d in enumerate(xif_descs()):
+            m = sum(1 for v in d if v >= 2)
+            for l in range(R):
+                if l + max(m - 1, 0) >= R:
+                    continue
+                code = SFX_IF_BASE + fi * R + l
+                table[code] = f"C{code}"
+                bodies.append((code, "if", d, l, None))
+        assert max(table) < SFX_NCODES
+        self.table(SFX_NCODES, table)
+        b("RSTBL: .branchtargets " + ", ".join(f"RS{l}" for l in range(R)) + ";")
+        b(f"mov.u32 adr, %{self.o_adr};")
+        self.setup_inputs()
+        # resume: store t (the function's result) into its level
+        b(f"setp.lt.u32 p, %{self.o_st}, {XEXIT};")
+        b("@p bra.uni START;")
+        b(f"and.b32 dl, %{self.o_st}, 7;")
+        b("brx.idx.uni dl, RSTBL;")
+        for l in range(R):
+            b(f"RS{l}:")
+            self.copy(L(l), T)
+            b("bra.uni START;")
+        b("START:")
+        self.fetch()
+        b("LOOP:")
+        b("brx.idx.uni code, TBL;")
+        for code, kind, name, l, op in bodies:
+            b(f"C{code}:")
+            if kind == "un":
+                if name == "S":
+                    self.copy(T, L(l))
+                elif name == "X":
+                    src = self.load_x(xA, "pa")
+                    self.copy(T, src)
+                else:
+                    self.copy(T, self.const("cA", "pa"))
+                b(f"mov.u32 %{self.o_st}, {XEXIT + op * 8 + l};")
+                b("bra.uni EXIT;")
+                continue
+            if kind == "if":
+                ops = []
+                for dsc, pay, xr, cr in zip(name, ("pa", "pb", "pc"), (xA, xB, xC), ("cA", "cB", "cC")):
+                    if dsc == 0:
+                        ops.append(self.load_x(xr, pay))
+                    elif dsc == 1:
+                        ops.append(self.const(cr, pay))
+                    else:
+                        ops.append(L(l + dsc - 2))
+                self.fetch()
+                self.elementwise(L(l), ops, self.if_emit())
+                self.jump()
+                continue
+            if name == "MOVX":
+                src = self.load_x(xA, "pa")
+                self.fetch()
+                self.copy(L(0), src)
+                self.jump()
+                continue
+            if name == "MOVC":
+                src = self.const("cA", "pa")
+                self.fetch()
+                self.copy(L(0), src)
+                self.jump()
+                continue
+            if name == "SS":
+                a, c = L(l), L(l + 1)
+            elif name == "SSR":
+                a, c = L(l + 1), L(l)
+            else:
+                ka, kb = name[0], name[1]
+                a = L(l) if ka == "S" else (self.load_x(xA, "pa") if ka == "X" else self.const("cA", "pa"))
+                c = L(l) if kb == "S" else (self.load_x(xB, "pb") if kb == "X" else self.const("cB", "pb"))
+            if kind == "cmp":
+                self.fetch()
+                self.elementwise(L(l), [a, c], self.cmp_emit(XB_OPS[op]))
+                self.jump()
+            elif op == 3:
+                self.copy(ta, a)
+                self.copy(tb, c)
+                self.fetch()
+                b(f"bra.uni DIV{l};")
+            else:
+                self.fetch()
+                self.vop(op, L(l), a, c)
+                self.jump()
+        self.div_blocks_per_level(ta, tb, L)
+        b("CBAD:")
+        b(f"mov.u32 %{self.o_st}, 1;")
+        b("bra.uni EXIT;")
+        b("DONE:")
+        b(f"mov.u32 %{self.o_st}, 0;")
+        b("EXIT:")
+        b(f"mov.u32 %{self.o_adr}, adr;")
+        b("}")
+        return b
+
+    def operand_macros(self):
+        """C++ operand lists of the asm statement (outputs and inputs)."""
+        K, H = self.K, self.H
+        c = "f" if K == 1 else "l"
+        outs = [f'"+{c}"(s[{i}])' for i in range(self.RH)] + [f'"+{c}"(t[{i}])' for i in range(H)]
+        outs += ['"+r"(adr)', '"+r"(st)']
+        if self.xmode == "reg":
+            ins = [f'"f"(x[{j}])' for j in range(K)]
+        else:
+            ins = ['"r"(tile)']
+        return ", ".join(outs), ", ".join(ins)
+
+
+# ---------------------------------------------------------------------------
 # Boolean interpreter (K words per thread, 32 cases per word)
 # ---------------------------------------------------------------------------
 class BoolGen:
@@ -693,6 +977,13 @@ def generate() -> str:
                 f"GP_PTX_RPN_K{K}_{X}", f"RPN interpreter, K={K}, inputs in {xm}"))
         parts.append(FloatGen(K, "smem").linear().macro(
             f"GP_PTX_LINEAR_K{K}", f"register linear-GP interpreter, K={K}"))
+        for xm in ("reg", "smem"):
+            X = xm.upper()
+            g = FloatGenX(K, xm)
+            parts.append(g.sform_ext().macro(
+                f"GP_PTX_SFORMX_K{K}_{X}", f"extended S-form interpreter, K={K}, inputs in {xm}"))
+            outs, ins = g.operand_macros()
+            parts.append(f"#define GP_SFX_OUT_K{K}_{X} {outs}\n#define GP_SFX_IN_K{K}_{X} {ins}\n")
         parts.append(BoolGen(K).gen().macro(f"GP_PTX_BOOL_K{K}", f"Boolean interpreter, K={K} words"))
     return "".join(parts)
 

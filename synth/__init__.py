@@ -31,7 +31,9 @@ Workload recipes (all seeded, numpy PCG64):
   - sextic regression: x ~ U[-1,1], 100000 cases, y = x^6 - 2x^4 + x^2
     (binary64, rounded once); trees over {*,/,+,-,sin,cos,log,exp} with
     terminals {x, U[-1,1] constants}; fitness mean squared error.
-  - Shuttle-shaped classification: 9 integer-valued inputs U{-100..100},
+  - Shuttle-shaped classification (a full tree over the node cap -- IF has
+    three children -- is replaced by a grow tree, as for the multiplexers):
+    9 integer-valued inputs U{-100..100},
     58000 cases, 10 class labels 1..10 with 75% of the cases in class 1 (the
     rest uniform); trees over {*,/,+,-,>,<,==,AND,OR,IF}, constants
     U[-200,200]; fitness = incorrect classifications.
@@ -459,7 +461,8 @@ def shuttle_like_problem(seed: int = 7, n_progs: int = 4096, n_cases: int = 5800
                          depth_lo: int = 2, depth_hi: int = 8,
                          max_nodes: int = 256) -> FunctionSetWorkload:
     progs = ramped_half_and_half(seed, n_progs, depth_lo, depth_hi, max_nodes, funcs=SHUTTLE_FUNCS,
-                                 n_inputs=9, const_lo=-200.0, const_hi=200.0)
+                                 n_inputs=9, const_lo=-200.0, const_hi=200.0,
+                                 full_fallback_to_grow=True)
     rng = np.random.default_rng(seed + 1000)
     x = rng.integers(-100, 101, (9, n_cases)).astype(np.float32)
     labels = np.where(rng.random(n_cases) < 0.75, 1, rng.integers(2, 11, n_cases)).astype(np.float32)
@@ -470,7 +473,8 @@ def kdd_like_problem(seed: int = 8, n_progs: int = 1024, n_cases: int = 494021,
                      depth_lo: int = 2, depth_hi: int = 8,
                      max_nodes: int = 256) -> FunctionSetWorkload:
     progs = ramped_half_and_half(seed, n_progs, depth_lo, depth_hi, max_nodes, funcs=KDD_FUNCS,
-                                 n_inputs=41, const_lo=-20000.0, const_hi=20000.0)
+                                 n_inputs=41, const_lo=-20000.0, const_hi=20000.0,
+                                 full_fallback_to_grow=True)
     rng = np.random.default_rng(seed + 1000)
     x = np.empty((41, n_cases), np.float32)
     for v in range(41):

@@ -36,6 +36,43 @@ def if_descs():
 
 IF_DESCS = if_descs()
 
+# extended S-form codes (kind 5): comparisons/logic, unary functions, IF
+SFX_BIN_BASE = len(SF_FORMS) * R * 4
+XB_NAMES = ["GT", "LT", "EQ", "AND", "OR"]
+SFX_UN_BASE = SFX_BIN_BASE + 10 * R * 5
+UF_FORMS = ["X", "C", "S"]
+SFX_IF_BASE = SFX_UN_BASE + 3 * R * 4
+
+
+def xif_descs():
+    out = []
+    for t in range(125):
+        d = (t // 25, (t // 5) % 5, t % 5)
+        m = sum(1 for v in d if v >= 2)
+        js = [v - 2 for v in d if v >= 2]
+        if sorted(js) == list(range(m)):
+            out.append(d)
+    assert len(out) == 38
+    return out
+
+
+XIF_DESCS = xif_descs()
+
+
+def _unary_ref(fn, a):
+    """A valid binary32 implementation: the value nearest the binary64 result."""
+    a64 = a.astype(np.float64)
+    with np.errstate(all="ignore"):
+        if fn == 3:
+            return np.where(a == 0, np.float32(0), np.log(np.abs(a64)).astype(np.float32))
+        return [np.sin, np.cos, np.exp][fn](a64).astype(np.float32)
+
+
+def _xbin(op, a, b):
+    with np.errstate(all="ignore"):
+        v = [a > b, a < b, a == b, (a != 0) & (b != 0), (a != 0) | (b != 0)][op]
+    return v.astype(np.float32)
+
 
 def header(words):
     w = np.asarray(words, np.uint32)
@@ -67,7 +104,8 @@ def _apply(op, a, b):
 
 
 def run_float(words, x):
-    """Per-case outputs of an encoded float program (S-form, RPN or register)."""
+    """Per-case outputs of an encoded float program (S-form, extended S-form,
+    RPN or register)."""
     x = np.asarray(x, np.float32)
     n_cases = x.shape[1]
     h = header(words)
@@ -79,9 +117,34 @@ def run_float(words, x):
             r[d] = _apply(op, r[a], r[b])
         return r[0]
     S = [None] * R
-    for code, pa, pb, _ in instrs(words):
+    for code, pa, pb, pc in instrs(words):
         op, lvl, form = code & 3, (code >> 2) % R, (code >> 2) // R
-        if h["kind"] == 1:
+        if h["kind"] == 5 and code >= SFX_BIN_BASE:
+            X = lambda v: x[v]
+            C = lambda bits: full(_f(bits))
+            if code >= SFX_IF_BASE:
+                f, lvl = (code - SFX_IF_BASE) // R, (code - SFX_IF_BASE) % R
+                vals = [x[p_] if d == 0 else C(p_) if d == 1 else S[lvl + d - 2]
+                        for d, p_ in zip(XIF_DESCS[f], (pa, pb, pc))]
+                c, a, b = vals
+                S[lvl] = np.where(c != 0, a, b).astype(np.float32)
+            elif code >= SFX_UN_BASE:
+                c = code - SFX_UN_BASE
+                fn, lvl, uf = c % 4, (c // 4) % R, (c // 4) // R
+                a = {"X": lambda: X(pa), "C": lambda: C(pa), "S": lambda: S[lvl]}[UF_FORMS[uf]]()
+                S[lvl] = _unary_ref(fn, a)
+            else:
+                c = code - SFX_BIN_BASE
+                xop, lvl, form = c % 5, (c // 5) % R, (c // 5) // R
+                name = SF_FORMS[form]
+                if name in ("SS", "SSR"):
+                    a, b = (S[lvl], S[lvl + 1]) if name == "SS" else (S[lvl + 1], S[lvl])
+                else:
+                    a = S[lvl] if name[0] == "S" else (X(pa) if name[0] == "X" else C(pa))
+                    b = S[lvl] if name[1] == "S" else (X(pb) if name[1] == "X" else C(pb))
+                S[lvl] = _xbin(xop, a, b)
+            continue
+        if h["kind"] in (1, 5):
             name = SF_FORMS[form]
             X = lambda v: x[v]
             C = lambda bits: full(_f(bits))

@@ -200,7 +200,7 @@ def test_encoded_linear_matches_oracle():
     [tok(VAR, 0), tok(VAR, 0)],                    # trailing tokens
     [tok(77)],                                     # unknown opcode
     [tok(CONST)],                                  # constant without value
-    [tok(synth.AND), tok(VAR, 0), tok(VAR, 1)],    # Boolean function in a float tree
+    [tok(synth.NAND), tok(VAR, 0), tok(VAR, 1)],   # Boolean-only function in a float tree
 ])
 def test_malformed_trees_rejected(bad):
     with pytest.raises(gp.GPError) as e:
@@ -220,3 +220,93 @@ def test_programs_are_16_byte_aligned():
     enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
     assert enc.words.ctypes.data % 16 == 0
     assert np.all(enc.offsets % 4 == 0) and np.all(enc.lengths % 4 == 0)
+
+
+# ---------------------------------------------------------------------------
+# the full float function sets (Sec. 4.2): extended S-form encoding
+# ---------------------------------------------------------------------------
+EXACT_SETS = (synth.SHUTTLE_FUNCS,)
+ALL_SET = synth.KDD_FUNCS
+
+
+def test_extended_trees_encode_with_the_extended_kind():
+    progs = synth.ramped_half_and_half(81, 60, 2, 6, 64, funcs=ALL_SET, n_inputs=3)
+    pop = synth.pack(progs)
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths, with_info=True)
+    kinds = enc.words[enc.offsets] & 0xFF
+    uses = np.array([any((int(t) & 0xFF) in (synth.SIN, synth.COS, synth.EXP, synth.LOG, synth.GT,
+                                             synth.LT, synth.EQ, synth.AND, synth.OR, synth.IF)
+                         for t in _tokens(p)) for p in progs])
+    assert np.array_equal(kinds == gp.KIND_SFORM_EXT, uses)
+    assert np.array_equal(enc.info["extended"] == 1, uses)
+    assert enc.extended == bool(uses.any())
+    basic = synth.pack(synth.ramped_half_and_half(82, 20, 2, 5, 40))
+    assert not gp.encode_population(basic.words, basic.offsets, basic.lengths).extended
+
+
+def _tokens(p):
+    """Opcode tokens of a prefix tree (constant payload words skipped)."""
+    out, i = [], 0
+    while i < len(p):
+        out.append(p[i])
+        i += 2 if (int(p[i]) & 0xFF) == synth.CONST else 1
+    return out
+
+
+@pytest.mark.parametrize("order", [gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH])
+def test_encoded_exact_extended_programs_match_oracle(order):
+    """No transcendental function: the encoded program reproduces the oracle
+    bit for bit (NaN == NaN)."""
+    progs = synth.ramped_half_and_half(83, 150, 2, 6, 64, funcs=synth.SHUTTLE_FUNCS, n_inputs=4,
+                                       const_lo=-200.0, const_hi=200.0)
+    rng = np.random.default_rng(84)
+    x = rng.integers(-100, 101, (4, 97)).astype(np.float32)
+    x[:, :5] = np.array([0.0, -0.0, np.nan, np.inf, 1e-45], np.float32)
+    for p in progs:
+        words, info = gp.encode_tree(p, gp.KIND_SFORM, order)
+        got = ref.run_float(words, x)
+        exp = oracle.fset_outputs(p, x)
+        assert same_bits(got, exp), p.tolist()
+
+
+def test_encoded_transcendental_programs_inside_enclosures():
+    progs = synth.ramped_half_and_half(85, 120, 2, 6, 64, funcs=ALL_SET, n_inputs=2)
+    x = synth.uniform_cases(86, 2, 64, -3.0, 3.0)
+    for p in progs:
+        words, _ = gp.encode_tree(p, gp.KIND_SFORM, gp.ORDER_MIN_DEPTH)
+        got = ref.run_float(words, x)
+        lo, hi, nan = oracle.fset_enclosure(p, x)
+        ok = np.where(np.isnan(got), nan, (lo <= got) & (got <= hi))
+        assert ok.all(), p.tolist()
+
+
+def test_extended_rpn_is_not_implemented_and_nand_is_rejected():
+    p = np.array([synth.SIN, synth.tok(synth.VAR, 0)], np.uint32)
+    with pytest.raises(gp.GPError) as e:
+        gp.encode_tree(p, gp.KIND_RPN)
+    assert e.value.code == 6
+    with pytest.raises(gp.GPError) as e:
+        gp.encode_tree(np.array([synth.NAND, synth.tok(synth.VAR, 0), synth.tok(synth.VAR, 0)],
+                                np.uint32), gp.KIND_SFORM)
+    assert e.value.code == 2
+
+
+def test_if_forms_cover_every_operand_mix():
+    """IF with each operand an input, a constant or a subtree, in all 27 mixes,
+    and every evaluation order of three subtrees."""
+    X = synth.tok(synth.VAR, 0)
+    Cc = synth.const_tokens(0.75)
+    sub = [synth.SUB, X, *synth.const_tokens(0.5)]          # needs one level
+    deep = [synth.MUL, *sub, synth.ADD, X, *sub]            # needs two levels
+    parts = {"X": [X], "C": Cc, "S": sub, "D": deep}
+    x = synth.uniform_cases(87, 1, 33, -2.0, 2.0)
+    x[0, :3] = np.array([0.5, 0.0, np.nan], np.float32)
+    import itertools
+    seen = set()
+    for combo in itertools.product("XCSD", repeat=3):
+        p = np.array([synth.IF] + parts[combo[0]] + parts[combo[1]] + parts[combo[2]], np.uint32)
+        for order in (gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH):
+            words, info = gp.encode_tree(p, gp.KIND_SFORM, order)
+            seen.add(int(words[4 + 4 * (info["n_instr"] - 1)]))
+            assert same_bits(ref.run_float(words, x), oracle.fset_outputs(p, x)), (combo, order)
+    assert len(seen) >= 20

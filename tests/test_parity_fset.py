@@ -1,0 +1,248 @@
+"""GPU parity of the extended S-form interpreter (the full float function sets
+of Sec. 4.2) and of the fitness measures, against the CPU oracle.
+
+* Programs without a transcendental function (the Shuttle set: *, /, +, -,
+  >, <, ==, AND, OR, IF): per-case outputs bit-exact (any NaN equals any NaN).
+* Programs with SIN, COS, EXP, LOG: there is no unique binary32 answer, so
+  every per-case output must lie inside the oracle's enclosure of all
+  admissible implementations (CUDA's documented bounds: sinf, cosf, expf
+  2 ulp, logf 1 ulp), and most enclosures must be tight (so that the check
+  has teeth); each single function is also held to its documented bound
+  directly.
+* Fitness: sum |e|, mean squared error, classification errors; within 1e-5
+  relative of the binary64 oracle (classification counts exactly) for exact
+  programs, inside the oracle's fitness enclosure widened by 1e-5 otherwise.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1601_00221_gb300 as gp
+from gpu_util import dev, upload, assert_bits, assert_fitness, REL_TOL
+from synth import SIN, COS, EXP, LOG, VAR, tok
+
+pytestmark = pytest.mark.gpu
+
+KS = [1, 2, 4, 8]
+FITS = [gp.FITNESS_SUM_ABS, gp.FITNESS_MSE, gp.FITNESS_CLASS]
+
+
+def ext_cfg(k, block=128, chunk=0, fitness=gp.FITNESS_SUM_ABS):
+    return gp.Config(gp.VARIANT_EXTENDED, k, block, chunk, fitness)
+
+
+def oracle_fset_outputs(pop, x):
+    return np.stack([oracle.fset_outputs(pop.program(p), x) for p in range(pop.n)])
+
+
+def enclosures(pop, x):
+    lo, hi, nan = zip(*(oracle.fset_enclosure(pop.program(p), x) for p in range(pop.n)))
+    return np.stack(lo), np.stack(hi), np.stack(nan)
+
+
+def assert_inside(got, lo, hi, nan, what):
+    ok = np.where(np.isnan(got), nan, (lo <= got) & (got <= hi))
+    if not ok.all():
+        i = np.argwhere(~ok)[0]
+        raise AssertionError(f"{what}: {int((~ok).sum())} outputs outside, first {i.tolist()}: "
+                             f"{got[tuple(i)]!r} not in [{lo[tuple(i)]!r}, {hi[tuple(i)]!r}]")
+
+
+def tight_fraction(lo, hi):
+    fin = lo <= hi
+    mag = np.maximum(np.abs(lo), np.abs(hi)).astype(np.float32)
+    with np.errstate(invalid="ignore"):
+        w = (hi.astype(np.float64) - lo) / np.maximum(np.spacing(mag), 1e-45)
+    return float(np.mean(fin & (w <= 64)))
+
+
+def assert_fitness_inside(got, pop, x, y, kind, lo, hi, nan, what):
+    for p in range(pop.n):
+        f_lo, f_hi, may_inf, must_inf = oracle.fitness_enclosure(lo[p], hi[p], nan[p], y, kind)
+        g = float(got[p])
+        if g == np.inf:
+            assert may_inf, f"{what} program {p}: +inf not admissible"
+            continue
+        assert not must_inf, f"{what} program {p}: got {g}, must be +inf"
+        if kind == gp.FITNESS_CLASS:
+            assert f_lo <= g <= f_hi, f"{what} program {p}: {g} not in [{f_lo}, {f_hi}]"
+        else:
+            assert f_lo * (1 - REL_TOL) - 1e-30 <= g <= f_hi * (1 + REL_TOL) + 1e-30, \
+                f"{what} program {p}: {g} not in [{f_lo}, {f_hi}]"
+
+
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def exact_set():
+    """Shuttle-set trees on 9 integer inputs (zeros, so protected division and
+    false conditions occur), ragged case count, with specials."""
+    w = synth.shuttle_like_problem(seed=101, n_progs=96, n_cases=1500)
+    x = w.cases.copy()
+    x[:, :6] = np.array([0.0, -0.0, np.nan, np.inf, -np.inf, 1e-45], np.float32)[None, :]
+    return w, x, oracle_fset_outputs(w.pop, x)
+
+
+@pytest.mark.parametrize("k", KS)
+def test_exact_extended_programs_bit_exact(exact_set, k):
+    w, x, ref = exact_set
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    assert enc.extended
+    P, O, L = upload(enc)
+    for block in (64, 256):
+        out = gp.eval_outputs(P, O, L, dev(x), config=ext_cfg(k, block))
+        assert_bits(out.cpu().numpy(), ref, f"k={k} block={block}")
+    assert gp.last_error() == 0
+
+
+@pytest.mark.parametrize("k", KS)
+def test_exact_extended_single_input_in_registers(k):
+    progs = synth.ramped_half_and_half(102, 80, 2, 7, 128, funcs=synth.SHUTTLE_FUNCS,
+                                       const_lo=-2.0, const_hi=2.0, full_fallback_to_grow=True)
+    pop = synth.pack(progs)
+    x = synth.uniform_cases(103, 1, 2051, -2.0, 2.0)
+    x[0, :4] = np.array([0.0, -0.0, np.nan, 1.0], np.float32)
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    P, O, L = upload(enc)
+    out = gp.eval_outputs(P, O, L, dev(x), config=ext_cfg(k))
+    assert_bits(out.cpu().numpy(), oracle_fset_outputs(pop, x), f"k={k}")
+
+
+@pytest.fixture(scope="module")
+def trans_set():
+    """All fourteen functions (the KDDcup set) on 3 inputs, x ~ U[-3, 3]."""
+    progs = synth.ramped_half_and_half(104, 120, 2, 8, 256, funcs=synth.KDD_FUNCS, n_inputs=3,
+                                       const_lo=-2.0, const_hi=2.0, full_fallback_to_grow=True)
+    pop = synth.pack(progs)
+    x = synth.uniform_cases(105, 3, 777, -3.0, 3.0)
+    x[:, :3] = np.array([0.0, 1e-45, np.nan], np.float32)[None, :]
+    lo, hi, nan = enclosures(pop, x)
+    return pop, x, lo, hi, nan
+
+
+@pytest.mark.parametrize("k", KS)
+def test_transcendental_outputs_inside_enclosures(trans_set, k):
+    pop, x, lo, hi, nan = trans_set
+    assert tight_fraction(lo, hi) >= 0.8
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    P, O, L = upload(enc)
+    out = gp.eval_outputs(P, O, L, dev(x), config=ext_cfg(k)).cpu().numpy()
+    assert_inside(out, lo, hi, nan, f"k={k}")
+    assert gp.last_error() == 0
+
+
+@pytest.mark.parametrize("k", [2, 8])
+def test_sextic_single_input_inside_enclosures(k):
+    w = synth.sextic_problem(seed=106, n_progs=100, n_cases=3000)
+    lo, hi, nan = enclosures(w.pop, w.cases)
+    assert tight_fraction(lo, hi) >= 0.8
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    P, O, L = upload(enc)
+    X, Y = dev(w.cases), dev(w.targets)
+    out = gp.eval_outputs(P, O, L, X, config=ext_cfg(k)).cpu().numpy()
+    assert_inside(out, lo, hi, nan, f"sextic k={k}")
+    f = gp.eval_population(P, O, L, X, Y, config=ext_cfg(k, fitness=gp.FITNESS_MSE)).cpu().numpy()
+    assert_fitness_inside(f, w.pop, w.cases, w.targets, gp.FITNESS_MSE, lo, hi, nan, "sextic MSE")
+
+
+def _ulps(a, b):
+    """Distance in binary32 steps between finite a and b."""
+    def key(v):
+        i = v.view(np.int32).astype(np.int64)
+        return np.where(i < 0, -(i & 0x7FFFFFFF), i)
+    return np.abs(key(a) - key(b))
+
+
+@pytest.mark.parametrize("op,bound", [(SIN, 2), (COS, 2), (EXP, 2), (LOG, 1)])
+def test_unary_functions_within_documented_ulps(op, bound):
+    rng = np.random.default_rng(110 + op)
+    n = 1 << 18
+    bits = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    x = bits.view(np.float32).copy()
+    x[: n // 2] = rng.uniform(-100, 100, n // 2).astype(np.float32)   # the common range
+    x[:8] = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-45, 88.7, -103.0], np.float32)
+    X = x[None, :]
+    pop = synth.pack([np.array([op, tok(VAR, 0)], np.uint32)])
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    P, O, L = upload(enc)
+    got = gp.eval_outputs(P, O, L, dev(X), config=ext_cfg(8)).cpu().numpy()[0]
+    lo, hi, nan = oracle.fset_enclosure(pop.program(0), X)
+    assert_inside(got[None], lo[None], hi[None], nan[None], f"op {op}")
+    ref = oracle.fset_outputs(pop.program(0), X)        # nearest binary32 to the binary64 value
+    both = np.isfinite(got) & np.isfinite(ref)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    assert np.array_equal(got[np.isinf(ref)], ref[np.isinf(ref)]) or op == EXP
+    assert _ulps(got[both], ref[both]).max() <= bound
+
+
+def test_basic_programs_identical_on_both_interpreters():
+    w = synth.regression_small(seed=107, n_progs=128, n_cases=999)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    assert not enc.extended
+    P, O, L = upload(enc)
+    X = dev(w.cases)
+    for k in KS:
+        a = gp.eval_outputs(P, O, L, X, config=gp.Config(gp.VARIANT_REGISTER, k, 128, 0)).cpu().numpy()
+        b = gp.eval_outputs(P, O, L, X, config=ext_cfg(k)).cpu().numpy()
+        assert_bits(b, a, f"k={k}")
+
+
+def test_extended_program_needs_the_extended_variant(exact_set):
+    w, x, ref = exact_set
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    P, O, L = upload(enc)
+    kinds = enc.words[enc.offsets] & 0xFF
+    f = gp.eval_population(P, O, L, dev(x), dev(w.targets), config=gp.Config(gp.VARIANT_REGISTER, 8, 128, 0))
+    f = f.cpu().numpy()
+    assert np.all(np.isnan(f[kinds == gp.KIND_SFORM_EXT]))
+    assert gp.last_error() == 2
+    assert gp.last_error() == 0
+
+
+# ---------------------------------------------------------------------------
+# fitness measures
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("fit", FITS)
+@pytest.mark.parametrize("variant,kind", [(gp.VARIANT_REGISTER, gp.KIND_SFORM),
+                                          (gp.VARIANT_REGISTER, gp.KIND_RPN),
+                                          (gp.VARIANT_LOCAL, gp.KIND_RPN),
+                                          (gp.VARIANT_EXTENDED, gp.KIND_SFORM)])
+def test_fitness_measures_basic_programs(fit, variant, kind):
+    w = synth.regression_small(seed=108, n_progs=96, n_cases=3001)
+    x = w.cases.copy()
+    y = w.targets.copy()
+    if fit == gp.FITNESS_CLASS:
+        y = np.rint(y * 2).astype(np.float32)      # integer labels in -2..8
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, kind)
+    P, O, L = upload(enc)
+    exp = oracle.fset_population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, x, y, fit)
+    for chunk in (0, 512):
+        k = 1 if variant == gp.VARIANT_LOCAL else 4
+        cfg = gp.Config(variant, k, 128 if variant != gp.VARIANT_LOCAL else 256, chunk, fit)
+        got = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy()
+        if fit == gp.FITNESS_CLASS:
+            assert np.array_equal(got, exp), f"chunk={chunk}"
+        else:
+            assert_fitness(got, exp, f"fit={fit} chunk={chunk}")
+
+
+@pytest.mark.parametrize("fit", FITS)
+def test_fitness_measures_extended_programs(trans_set, fit):
+    pop, x, lo, hi, nan = trans_set
+    y = np.rint(np.random.default_rng(109).uniform(-1, 3, x.shape[1])).astype(np.float32)
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    P, O, L = upload(enc)
+    for chunk in (0, 256):
+        got = gp.eval_population(P, O, L, dev(x), dev(y), config=ext_cfg(4, 64, chunk, fit)).cpu().numpy()
+        assert_fitness_inside(got, pop, x, y, fit, lo, hi, nan, f"fit={fit} chunk={chunk}")
+
+
+def test_fitness_measures_no_cases_and_noalloc():
+    w = synth.regression_small(seed=111, n_progs=16, n_cases=0)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    P, O, L = upload(enc)
+    X = dev(np.zeros((1, 0), np.float32))
+    Y = dev(np.zeros(0, np.float32))
+    for fit in FITS:
+        f = gp.eval_population(P, O, L, X, Y, config=gp.Config(gp.VARIANT_REGISTER, 8, 128, 0, fit))
+        assert np.all(f.cpu().numpy() == 0)

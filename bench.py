@@ -369,6 +369,11 @@ def run_ours(args):
             lin.update(cpu_oracle_linear(lin_w, lin_fit))  # CPU-baseline leg
         extra["register_gp"] = lin
         extra["serving"] = bench_serving(gp, synth, args.serving_runs)
+        fsets, fset_data = bench_function_sets(gp, synth, torch, device)
+        if not args.no_cpu:
+            for name, d in fset_data.items():
+                fsets[name].update(cpu_oracle_function_set(*d))  # CPU-baseline leg
+        extra["function_sets"] = fsets
 
     if rank != 0:
         if world > 1:
@@ -502,6 +507,95 @@ def cpu_oracle_linear(w, gpu_fit):
             "fitness_rel_err_vs_fp64_oracle": {"programs_checked": int(sample.size),
                                                "max": float(rel.max()) if rel.size else 0.0,
                                                "bound": 1e-5}}
+
+
+# the paper's best GPop/s per problem (Sec. 6.2's last table: 2D LGP, float4,
+# register-file stack; GTX 670, whole GP runs) -- context, not a target
+PAPER_BEST = {"sextic": 53.193, "shuttle-like": 55.734, "kdd-like": 48.811}
+
+
+def bench_function_sets(gp, synth, torch, device):
+    """The paper's float problems with their full function sets (Sec. 4.2),
+    synthetic stand-ins of the same shape: sextic regression (4096 trees x
+    100000 cases, mean squared error), Shuttle-shaped (4096 trees x 58000
+    cases x 9 inputs, classification errors), KDDcup-shaped (1024 trees x
+    494021 cases x 41 inputs, classification errors).  The extended S-form
+    interpreter; the staged-input tile holds the largest number of inputs any
+    tree reads.  Returns the results and, per problem, what the CPU leg needs."""
+    import numpy as np
+    out, data = {}, {}
+    for make in (synth.sextic_problem, synth.shuttle_like_problem, synth.kdd_like_problem):
+        w = make()
+        enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+        P, O, L = enc.to_device(device)
+        X = torch.from_numpy(w.cases).to(device)
+        Y = torch.from_numpy(w.targets).to(device)
+        fit = torch.empty(w.pop.n, dtype=torch.float64, device=device)
+        best = None
+        for k in (2, 4, 8):
+            for block in (128, 256):
+                cfg = enc.config(fitness=w.fitness, k=k, block=block)
+                try:
+                    ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit,
+                                                                        config=cfg), steps=3, warmup=1)
+                except gp.GPError:  # the tile does not fit this shape
+                    continue
+                if best is None or ms < best[0]:
+                    best = (ms, cfg)
+        ms, cfg = best
+        gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg)
+        sample = np.arange(0, w.pop.n, w.pop.n // 4)[:4]
+        outs = gp.eval_outputs(P, O, L, X, config=cfg)[torch.from_numpy(sample).to(device)]
+        out[w.name] = {"programs": w.pop.n, "cases": int(w.cases.shape[1]),
+                       "inputs": int(w.cases.shape[0]), "mean_nodes": round(float(w.pop.nodes.mean()), 2),
+                       "fitness": ["sum_abs", "mse", "class_errors"][w.fitness],
+                       "k": int(cfg.k), "block": int(cfg.block), "tile_inputs": int(cfg.tile_inputs),
+                       "ms": round(ms, 3), "GPop_per_s": round(w.gpop / ms / 1e6, 1),
+                       "paper_best_GPop_per_s_context": PAPER_BEST[w.name]}
+        data[w.name] = (w, sample, fit.cpu().numpy(), outs.cpu().numpy())
+    return out, data
+
+
+def cpu_oracle_function_set(w, sample, gpu_fit, gpu_outs):
+    """CPU-baseline leg of a function-set problem: the oracle's point
+    evaluation of the sampled programs (timed, threads over programs), and the
+    GPU's per-case outputs and fitness of those programs checked against the
+    oracle's enclosures of every admissible implementation."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    progs = [int(p) for p in sample]
+    n_timed = 16 if w.cases.shape[1] > 200000 else 64
+    timed = [int(p) for p in np.arange(0, w.pop.n, w.pop.n // n_timed)[:n_timed]]
+    cores = min(len(os.sched_getaffinity(0)), len(timed))
+
+    def point(p):
+        return oracle.fset_population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, w.cases,
+                                              w.targets, w.fitness, p_range=(p, p + 1))[p]
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(point, timed))
+    wall = time.perf_counter() - t0
+
+    def check(i_p):
+        i, p = i_p
+        lo, hi, nan = oracle.fset_enclosure(w.pop.program(p), w.cases)
+        o = gpu_outs[i]
+        inside = np.where(np.isnan(o), nan, (lo <= o) & (o <= hi))
+        f_lo, f_hi, may_inf, must_inf = oracle.fitness_enclosure(lo, hi, nan, w.targets, w.fitness)
+        g = float(gpu_fit[p])
+        f_ok = (may_inf if g == np.inf else
+                (not must_inf and f_lo * (1 - 1e-5) <= g <= f_hi * (1 + 1e-5)))
+        return bool(inside.all()), bool(f_ok)
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        res = list(ex.map(check, enumerate(progs)))
+    gpop = int(w.pop.nodes[timed].sum()) * int(w.cases.shape[1])
+    return {"cpu_baseline": {"value": round(gpop / wall / 1e9, 4), "unit": UNIT, "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{len(timed)} programs x all {w.cases.shape[1]} cases"},
+            "parity_sample": {"programs": len(progs),
+                              "outputs_inside_enclosure": all(r[0] for r in res),
+                              "fitness_inside_enclosure": all(r[1] for r in res)}}
 
 
 def bench_serving(gp, synth, n_runs):

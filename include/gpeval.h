@@ -115,6 +115,7 @@ typedef struct gp_prog_info {
   int32_t max_input;    /* largest input index referenced, -1 if none */
   int32_t words;        /* encoded size in uint32 words */
   int32_t extended;     /* 1 if the tree uses SIN..EQ or float AND/OR/IF */
+  int32_t inputs_used;  /* distinct input indices the tree reads */
 } gp_prog_info;
 
 /* ------------------------------------------------------------------------
@@ -193,6 +194,11 @@ typedef struct gp_config {
   int32_t block;        /* 32..1024, multiple of 32 (0 = tuned) */
   int32_t chunk_cases;  /* 0 = choose; else a multiple of k*block */
   int32_t fitness;      /* gp_fitness (0 = GP_FITNESS_SUM_ABS) */
+  int32_t tile_inputs;  /* inputs per case the shared-memory tile holds (0 = n_inputs).  A
+                           tree stages only the inputs it reads, so the largest
+                           gp_prog_info.inputs_used of the population is enough (register
+                           programs need min(n_inputs, 8)); a program that needs more
+                           fails as malformed.  Smaller tiles leave room for more warps. */
 } gp_config;
 
 /* ------------------------------------------------------------------------

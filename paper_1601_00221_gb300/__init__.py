@@ -53,7 +53,7 @@ class _ProgInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("n_instr", ctypes.c_int32),
                 ("max_depth", ctypes.c_int32), ("stack_reads", ctypes.c_int32),
                 ("max_input", ctypes.c_int32), ("words", ctypes.c_int32),
-                ("extended", ctypes.c_int32)]
+                ("extended", ctypes.c_int32), ("inputs_used", ctypes.c_int32)]
 
 
 class _ServerOpts(ctypes.Structure):
@@ -61,7 +61,7 @@ class _ServerOpts(ctypes.Structure):
                 ("max_queued", ctypes.c_int32), ("max_merge", ctypes.c_int32),
                 ("memory_budget", ctypes.c_int64), ("variant", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("block", ctypes.c_int32), ("chunk_cases", ctypes.c_int32),
-                ("fitness", ctypes.c_int32)]
+                ("fitness", ctypes.c_int32), ("tile_inputs", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -84,13 +84,16 @@ class ServerStats(ctypes.Structure):
 
 class Config(ctypes.Structure):
     """gp_config: variant, k (cases per thread per pass), block, chunk_cases
-    (0 = choose), fitness (FITNESS_SUM_ABS, FITNESS_MSE or FITNESS_CLASS)."""
+    (0 = choose), fitness (FITNESS_SUM_ABS, FITNESS_MSE or FITNESS_CLASS),
+    tile_inputs (inputs per case the shared-memory tile holds, 0 = all)."""
     _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("chunk_cases", ctypes.c_int32), ("fitness", ctypes.c_int32)]
+                ("chunk_cases", ctypes.c_int32), ("fitness", ctypes.c_int32),
+                ("tile_inputs", ctypes.c_int32)]
 
     def __repr__(self):
         return (f"Config(variant={self.variant}, k={self.k}, block={self.block}, "
-                f"chunk_cases={self.chunk_cases}, fitness={self.fitness})")
+                f"chunk_cases={self.chunk_cases}, fitness={self.fitness}, "
+                f"tile_inputs={self.tile_inputs})")
 
 
 _lib = None
@@ -180,12 +183,21 @@ class EncodedPopulation:
             return False
         return bool(np.any((self.words[self.offsets] & 0xFF) == KIND_SFORM_EXT))
 
+    @property
+    def max_inputs_used(self) -> int:
+        """The most distinct inputs any tree reads (0 if unknown or none)."""
+        if self.info is None or self.n == 0 or "inputs_used" not in self.info.dtype.names:
+            return 0
+        return int(self.info["inputs_used"].max())
+
     def config(self, fitness: int = FITNESS_SUM_ABS, k: int = 0, block: int = 0,
                chunk_cases: int = 0) -> "Config":
         """A configuration that can run this population with the given fitness
-        measure: the extended interpreter when some program needs it."""
+        measure: the extended interpreter when some program needs it, and a
+        staged-input tile no larger than the population needs."""
         variant = VARIANT_EXTENDED if self.extended else VARIANT_AUTO
-        return Config(variant, k, block, chunk_cases, fitness)
+        tile = max(self.max_inputs_used, 1) if self.kind in (KIND_SFORM, KIND_RPN) else 0
+        return Config(variant, k, block, chunk_cases, fitness, tile)
 
     def to_device(self, device="cuda"):
         import torch
@@ -211,7 +223,9 @@ def encode_population(words, offsets, lengths, kind: int = KIND_SFORM,
                       out: Optional[np.ndarray] = None) -> EncodedPopulation:
     """Encodes a population in one call (the output is sized by the bound of
     4 + 4 * lengths[p] words per program).  `out` (uint32, 16-byte aligned)
-    may supply the buffer, e.g. a pinned host array reused across calls."""
+    may supply the buffer, e.g. a pinned host array reused across calls.
+    The per-program info is always kept (`with_info` is accepted for older
+    callers)."""
     w = np.ascontiguousarray(words, np.uint32)
     off = np.ascontiguousarray(offsets, np.int64)
     ln = np.ascontiguousarray(lengths, np.int32)
@@ -224,13 +238,13 @@ def encode_population(words, offsets, lengths, kind: int = KIND_SFORM,
     bad = ctypes.c_int32(-1)
     out_off = np.zeros(n, np.int64)
     out_len = np.zeros(n, np.int32)
-    info = (_ProgInfo * n)() if with_info else None
+    info = (_ProgInfo * n)()
     _check(lib().gp_encode_population(_np_ptr(w), _np_ptr(off), _np_ptr(ln), n, kind, order,
                                       _np_ptr(out), out.size, _np_ptr(out_off), _np_ptr(out_len),
                                       ctypes.byref(total), ctypes.byref(nodes),
-                                      ctypes.cast(info, ctypes.c_void_p) if info is not None else None,
+                                      ctypes.cast(info, ctypes.c_void_p),
                                       ctypes.byref(bad)))
-    arr = np.ctypeslib.as_array(info).copy() if info is not None else None
+    arr = np.ctypeslib.as_array(info).copy() if n else None
     return EncodedPopulation(out[:max(int(total.value), 4)], out_off, out_len, int(nodes.value),
                              kind, order, arr)
 
@@ -359,7 +373,7 @@ class Server:
                  memory_budget=1 << 30, config: Optional[Config] = None):
         c = config or Config()
         opts = _ServerOpts(n_streams, max_inflight, max_queued, max_merge, memory_budget,
-                           c.variant, c.k, c.block, 0, c.fitness)
+                           c.variant, c.k, c.block, 0, c.fitness, c.tile_inputs)
         self._h = ctypes.c_void_p()
         _check(lib().gp_server_create(ctypes.byref(opts), ctypes.byref(self._h)))
         self._results = {}  # request id -> (buffer, keep-alive)

@@ -20,7 +20,7 @@ using namespace gpdev;
 namespace {
 
 std::mutex g_mu;
-gp_config g_default = {GP_VARIANT_REGISTER, 8, 128, 0, GP_FITNESS_SUM_ABS};
+gp_config g_default = {GP_VARIANT_REGISTER, 8, 128, 0, GP_FITNESS_SUM_ABS, 0};
 
 // Internal workspace of one (device, stream): per-block partial sums, the
 // per-program arrival counters of the fused reduction (zero between
@@ -126,7 +126,9 @@ int resolve_config(const gp_config* user, gp_config* c) {
     if (user->block) c->block = user->block;
     c->chunk_cases = user->chunk_cases;
     if (user->fitness) c->fitness = user->fitness;
+    c->tile_inputs = user->tile_inputs;
   }
+  if (c->tile_inputs < 0) return gp_fail(GP_ERR_INVALID_ARG, "negative tile_inputs");
   if (c->variant != GP_VARIANT_REGISTER && c->variant != GP_VARIANT_LOCAL &&
       c->variant != GP_VARIANT_AUTO && c->variant != GP_VARIANT_LANES &&
       c->variant != GP_VARIANT_EXTENDED)
@@ -251,13 +253,15 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   a.o_aligned = aligned16(outputs) && (n_progs == 1 || n_cases % 4 == 0);
   a.want_fitness = fitness_out != nullptr;
   a.fitness_kind = c.fitness;
+  a.tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
   const int grid = n_progs * n_chunks;
   const bool xreg = (n_inputs == 1);
-  const size_t smem = float_tile_bytes(c.k, c.block, n_inputs);
+  const size_t smem = float_tile_bytes(c.k, c.block, a.tile_inputs);
   if (c.variant != GP_VARIANT_LOCAL && smem > kMaxTileBytes)
     return gp_fail(GP_ERR_INVALID_ARG,
-                   "%d inputs need %zu bytes of staged inputs per block (max %zu): lower k or block",
-                   n_inputs, smem, kMaxTileBytes);
+                   "a tile of %d inputs needs %zu bytes of shared memory per block (max %zu): "
+                   "lower k, block or tile_inputs",
+                   a.tile_inputs, smem, kMaxTileBytes);
   cudaError_t e;
   if (c.variant == GP_VARIANT_LOCAL) e = launch_blockgp(a, c.block, grid, s);
   else if (c.variant == GP_VARIANT_EXTENDED) {

@@ -267,6 +267,13 @@ int encode_one(const uint32_t* prefix, int64_t n_words, int32_t kind, int32_t or
   inf.max_input = max_input;
   inf.words = 4 + 4 * n_instr;
   inf.extended = extended ? 1 : 0;
+  {
+    std::vector<uint32_t> vars;
+    for (const Node& nd : nodes)
+      if (nd.op == GP_OP_VAR) vars.push_back(nd.payload);
+    std::sort(vars.begin(), vars.end());
+    inf.inputs_used = (int32_t)(std::unique(vars.begin(), vars.end()) - vars.begin());
+  }
   if (info) *info = inf;
   if (depth > R)
     return gp_fail(GP_ERR_PROGRAM, "program needs %d stack levels, more than %d (encode with GP_ORDER_MIN_DEPTH)", depth, R);

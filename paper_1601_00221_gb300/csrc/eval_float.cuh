@@ -58,7 +58,32 @@ struct FloatArgs {
   int32_t o_aligned;     // outputs + p*n_cases 16-byte aligned for every p
   int32_t want_fitness;  // compute the fitness (targets may be null only if n_cases == 0)
   int32_t fitness_kind;  // FIT_SUM_ABS, FIT_MSE or FIT_CLASS
+  int32_t tile_inputs;   // inputs per case the staged tile holds (<= n_inputs)
 };
+
+// Trees whose cases have at most this many inputs stage only the inputs the
+// program reads (see compact_inputs); with more, every input is staged.
+constexpr int GP_COMPACT_MAX_INPUTS = 4096;
+
+// which payload words of an instruction are input indices: bit 0 = y,
+// bit 1 = z, bit 2 = w (codes already validated)
+__device__ __forceinline__ uint32_t input_fields(uint32_t kind, uint32_t code) {
+  using namespace gpisa;
+  auto bin = [](int form) -> uint32_t {
+    switch (form) {
+      case SF_XX: return 3u;
+      case SF_XC: case SF_XS: case SF_MOVX: return 1u;
+      case SF_CX: case SF_SX: return 2u;
+      default: return 0u;
+    }
+  };
+  if (kind == K_RPN) return ((code >> 2) / R) == RF_PUSHX ? 1u : 0u;
+  if (code < (uint32_t)SF_NCODES) return bin((int)((code >> 2) / R));
+  if (code < (uint32_t)SFX_UN_BASE) return bin(((int)code - SFX_BIN_BASE) / XB_NOPS / R);
+  if (code < (uint32_t)SFX_IF_BASE) return ((int)code - SFX_UN_BASE) / XU_NOPS / R == UF_X ? 1u : 0u;
+  const int desc = xif_form_desc(((int)code - SFX_IF_BASE) / R);
+  return (desc / 25 == 0 ? 1u : 0u) | ((desc / 5) % 5 == 0 ? 2u : 0u) | (desc % 5 == 0 ? 4u : 0u);
+}
 
 // ---------------------------------------------------------------------------
 // The interpreter loops are generated inline PTX (gen_interp.py): one
@@ -299,7 +324,12 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
   __shared__ Partial red_s[32];
   __shared__ int meta_s[2];  // n_instr (or -1 if bad), kind
-  extern __shared__ float4 tile_s[];  // [warp][input][32 lanes][K] when staged
+  // dynamic: the staged inputs' list [tile_inputs, padded to 4 words], then
+  // the tiles [warp][slot][32 lanes][K] when staged
+  extern __shared__ float4 tile_s[];
+  __shared__ uint32_t used_s[GP_COMPACT_MAX_INPUTS / 32];  // bitmap of the inputs read
+  __shared__ uint32_t before_s[GP_COMPACT_MAX_INPUTS / 32];  // set bits in earlier words
+  __shared__ int n_stage_s;
 
   const int item = blockIdx.x;
   const int p = item / a.n_chunks;
@@ -346,6 +376,67 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
     bad = !__syncthreads_and(ok);
   }
 
+  // Inputs to stage.  A tree stages only the inputs it reads: they are listed
+  // in increasing order (slot s holds input list_s[s]) and the program's
+  // input payloads, in shared memory, become slots.  Register programs stage
+  // their first min(n_inputs, 8) inputs.
+  uint32_t* list_s = reinterpret_cast<uint32_t*>(tile_s);
+  const bool staged = !XREG || (!EXT && kind == K_LINEAR);
+  int n_stage = 0;
+  if (!bad && staged) {
+    if (kind == K_LINEAR || a.n_inputs > GP_COMPACT_MAX_INPUTS) {
+      n_stage = kind == K_LINEAR ? (a.n_inputs < R ? a.n_inputs : R) : a.n_inputs;
+      if (n_stage <= a.tile_inputs)
+        for (int v = tid; v < n_stage; v += blockDim.x) list_s[v] = (uint32_t)v;
+    } else {
+      const int nw = (a.n_inputs + 31) >> 5;
+      for (int i = tid; i < nw; i += blockDim.x) used_s[i] = 0u;
+      __syncthreads();
+      for (int i = tid; i < n_instr; i += blockDim.x) {
+        const uint4 in = prog_s[i];
+        const uint32_t f = input_fields(kind, in.x);
+        if (f & 1u) atomicOr(&used_s[in.y >> 5], 1u << (in.y & 31));
+        if (f & 2u) atomicOr(&used_s[in.z >> 5], 1u << (in.z & 31));
+        if (f & 4u) atomicOr(&used_s[in.w >> 5], 1u << (in.w & 31));
+      }
+      __syncthreads();
+      if (tid == 0) {
+        uint32_t c = 0;
+        for (int i = 0; i < nw; ++i) {
+          before_s[i] = c;
+          c += (uint32_t)__popc(used_s[i]);
+        }
+        n_stage_s = (int)c;
+      }
+      __syncthreads();
+      n_stage = n_stage_s;
+      auto slot = [&](uint32_t v) {
+        return before_s[v >> 5] + (uint32_t)__popc(used_s[v >> 5] & ((1u << (v & 31)) - 1u));
+      };
+      if (n_stage <= a.tile_inputs) {
+        for (int i = tid; i < n_instr; i += blockDim.x) {
+          uint4 in = prog_s[i];
+          const uint32_t f = input_fields(kind, in.x);
+          if (f & 1u) in.y = slot(in.y);
+          if (f & 2u) in.z = slot(in.z);
+          if (f & 4u) in.w = slot(in.w);
+          prog_s[i] = in;
+        }
+        for (int i = tid; i < nw; i += blockDim.x) {
+          uint32_t m = used_s[i];
+          uint32_t s0 = before_s[i];
+          while (m) {
+            const int b = __ffs(m) - 1;
+            list_s[s0++] = (uint32_t)(i * 32 + b);
+            m &= m - 1u;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (n_stage > a.tile_inputs) bad = true;  // the tile was sized too small
+  }
+
   CSum acc = {0.0f, 0.0f};
   uint32_t flags = 0;
   if (bad) {
@@ -360,10 +451,10 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   if (c_end > a.n_cases) c_end = a.n_cases;
   float* out_row = a.outputs ? a.outputs + (int64_t)p * a.n_cases : nullptr;
   const uint32_t prog_addr = (uint32_t)__cvta_generic_to_shared(prog_s);
-  // this lane's K staged values of input v live at tile + v * 32 * K floats
-  float* tile = reinterpret_cast<float*>(tile_s) + (size_t)warp * a.n_inputs * 32 * K + lane * K;
+  // this lane's K staged values of slot v live at tile + v * 32 * K floats
+  float* tile = reinterpret_cast<float*>(tile_s) + ((a.tile_inputs + 3) & ~3) +
+                (size_t)warp * a.tile_inputs * 32 * K + lane * K;
   const uint32_t tile_addr = (uint32_t)__cvta_generic_to_shared(tile);
-  const bool staged = !XREG || (!EXT && kind == K_LINEAR);
 
   if (!bad) {
 #pragma unroll 1
@@ -374,9 +465,9 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
       float x[K];
       float o[K];
       if (staged) {
-        for (int v = 0; v < a.n_inputs; ++v) {
+        for (int v = 0; v < n_stage; ++v) {
           Vec<K> t;
-          vload<K>(t, a.cases + (int64_t)v * a.n_cases, c0, a.n_cases, vec_ok);
+          vload<K>(t, a.cases + (int64_t)list_s[v] * a.n_cases, c0, a.n_cases, vec_ok);
 #pragma unroll
           for (int j = 0; j < K; ++j) tile[v * 32 * K + j] = vget<K>(t, j);
         }
@@ -437,9 +528,11 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   }
 }
 
-// dynamic shared memory of eval_float_kernel: the staged input tiles
-inline size_t float_tile_bytes(int k, int block, int n_inputs) {
-  return (size_t)(block / 32) * (size_t)n_inputs * 32u * (size_t)k * sizeof(float);
+// dynamic shared memory of eval_float_kernel: the list of staged inputs and
+// the staged input tiles, for tile_inputs inputs per case
+inline size_t float_tile_bytes(int k, int block, int tile_inputs) {
+  return sizeof(float) * ((size_t)((tile_inputs + 3) & ~3) +
+                          (size_t)(block / 32) * (size_t)tile_inputs * 32u * (size_t)k);
 }
 
 // ---------------------------------------------------------------------------

@@ -110,9 +110,11 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   if (n_chunks > 1 && n_chunks * n_progs > kMaxPartials)
     return gp_fail(GP_ERR_INVALID_ARG, "%lld partial sums exceed the fixed scratch of %lld",
                    (long long)(n_chunks * n_progs), (long long)kMaxPartials);
-  const size_t smem = float_tile_bytes(c.k, c.block, n_inputs);
+  const int32_t tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
+  const size_t smem = float_tile_bytes(c.k, c.block, tile_inputs);
   if (smem > 200 * 1024)
-    return gp_fail(GP_ERR_INVALID_ARG, "%d inputs need %zu bytes of staged inputs per block", n_inputs, smem);
+    return gp_fail(GP_ERR_INVALID_ARG, "a tile of %d inputs needs %zu bytes of shared memory per block",
+                   tile_inputs, smem);
 
   // the array keeps the previous call's contents: clear the counters this
   // call relies on and the status word
@@ -141,6 +143,7 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   a.o_aligned = 0;
   a.want_fitness = 1;
   a.fitness_kind = c.fitness;
+  a.tile_inputs = tile_inputs;
   const int grid = (int)(n_progs * n_chunks);
   const bool xreg = (n_inputs == 1);
   if (c.variant == GP_VARIANT_EXTENDED) {

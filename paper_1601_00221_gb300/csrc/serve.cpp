@@ -349,6 +349,7 @@ extern "C" int gp_server_create(const gp_server_opts* opts, gp_server** out) {
   if (!o.config.k) o.config.k = def.k;
   if (!o.config.block) o.config.block = def.block;
   if (!o.config.fitness) o.config.fitness = def.fitness;
+  if (!o.config.tile_inputs) o.config.tile_inputs = def.tile_inputs;
   o.config.chunk_cases = 0;
   s->opts = o;
   cudaError_t e = cudaGetDevice(&s->device);

@@ -246,3 +246,49 @@ def test_fitness_measures_no_cases_and_noalloc():
     for fit in FITS:
         f = gp.eval_population(P, O, L, X, Y, config=gp.Config(gp.VARIANT_REGISTER, 8, 128, 0, fit))
         assert np.all(f.cpu().numpy() == 0)
+
+
+# ---------------------------------------------------------------------------
+# staged-input compaction: a tree stages only the inputs it reads
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def wide():
+    """Shuttle-set trees over 41 inputs (the KDDcup shape), ragged cases."""
+    progs = synth.ramped_half_and_half(120, 128, 2, 7, 128, funcs=synth.SHUTTLE_FUNCS, n_inputs=41,
+                                       const_lo=-50.0, const_hi=50.0, full_fallback_to_grow=True)
+    pop = synth.pack(progs)
+    rng = np.random.default_rng(121)
+    x = rng.integers(-20, 21, (41, 2999)).astype(np.float32)
+    return pop, x, oracle_fset_outputs(pop, x)
+
+
+@pytest.mark.parametrize("k,block", [(8, 256), (4, 128), (1, 64)])
+def test_compacted_tiles_bit_exact(wide, k, block):
+    pop, x, ref = wide
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    used = enc.info["inputs_used"]
+    assert 0 < enc.max_inputs_used < 41
+    P, O, L = upload(enc)
+    cfg = enc.config(k=k, block=block)
+    assert cfg.tile_inputs == enc.max_inputs_used
+    out = gp.eval_outputs(P, O, L, dev(x), config=cfg)
+    assert_bits(out.cpu().numpy(), ref, f"k={k} block={block}")
+    assert gp.last_error() == 0
+
+
+def test_tile_smaller_than_a_program_needs(wide):
+    pop, x, ref = wide
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    used = enc.info["inputs_used"]
+    cap = int(np.median(used))
+    P, O, L = upload(enc)
+    cfg = enc.config(k=4, block=128)
+    cfg.tile_inputs = cap
+    y = np.zeros(x.shape[1], np.float32)
+    f = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy()
+    assert np.all(np.isnan(f[used > cap]))
+    assert not np.any(np.isnan(f[used <= cap]))
+    assert gp.last_error() == 2
+    out = gp.eval_outputs(P, O, L, dev(x), config=cfg).cpu().numpy()
+    assert_bits(out[used <= cap], ref[used <= cap], "programs that fit")
+    gp.last_error()

@@ -196,9 +196,11 @@ typedef struct gp_config {
   int32_t fitness;      /* gp_fitness (0 = GP_FITNESS_SUM_ABS) */
   int32_t tile_inputs;  /* inputs per case the shared-memory tile holds (0 = n_inputs).  A
                            tree stages only the inputs it reads, so the largest
-                           gp_prog_info.inputs_used of the population is enough (register
-                           programs need min(n_inputs, 8)); a program that needs more
-                           fails as malformed.  Smaller tiles leave room for more warps. */
+                           gp_prog_info.inputs_used of the population is enough (a tree
+                           reading more than 256 distinct inputs, or cases with more than
+                           4096 inputs, stage every input; register programs need
+                           min(n_inputs, 8)); a program that needs more fails as
+                           malformed.  Smaller tiles leave room for more warps. */
 } gp_config;
 
 /* ------------------------------------------------------------------------

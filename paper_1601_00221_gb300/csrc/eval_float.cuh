@@ -61,9 +61,11 @@ struct FloatArgs {
   int32_t tile_inputs;   // inputs per case the staged tile holds (<= n_inputs)
 };
 
-// Trees whose cases have at most this many inputs stage only the inputs the
-// program reads (see compact_inputs); with more, every input is staged.
+// Trees whose cases have at most GP_COMPACT_MAX_INPUTS inputs stage only the
+// inputs the program reads, at most GP_COMPACT_MAX_LIST of them; otherwise
+// (and for register programs) the first inputs are staged in order.
 constexpr int GP_COMPACT_MAX_INPUTS = 4096;
+constexpr int GP_COMPACT_MAX_LIST = 256;
 
 // which payload words of an instruction are input indices: bit 0 = y,
 // bit 1 = z, bit 2 = w (codes already validated)
@@ -324,9 +326,9 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
   __shared__ Partial red_s[32];
   __shared__ int meta_s[2];  // n_instr (or -1 if bad), kind
-  // dynamic: the staged inputs' list [tile_inputs, padded to 4 words], then
-  // the tiles [warp][slot][32 lanes][K] when staged
+  // dynamic: the tiles [warp][slot][32 lanes][K] when staged
   extern __shared__ float4 tile_s[];
+  __shared__ uint32_t list_s[GP_COMPACT_MAX_LIST];  // input of each staged slot
   __shared__ uint32_t used_s[GP_COMPACT_MAX_INPUTS / 32];  // bitmap of the inputs read
   __shared__ uint32_t before_s[GP_COMPACT_MAX_INPUTS / 32];  // set bits in earlier words
   __shared__ int n_stage_s;
@@ -380,15 +382,16 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   // in increasing order (slot s holds input list_s[s]) and the program's
   // input payloads, in shared memory, become slots.  Register programs stage
   // their first min(n_inputs, 8) inputs.
-  uint32_t* list_s = reinterpret_cast<uint32_t*>(tile_s);
   const bool staged = !XREG || (!EXT && kind == K_LINEAR);
-  int n_stage = 0;
+  // (the count is read back from shared memory where it is used, so no
+  // register holds it across the interpreter loop)
   if (!bad && staged) {
-    if (kind == K_LINEAR || a.n_inputs > GP_COMPACT_MAX_INPUTS) {
+    int n_stage;
+    if (XREG || kind == K_LINEAR || a.n_inputs > GP_COMPACT_MAX_INPUTS) {
+      // (a kernel with the input in registers stages register programs only)
       n_stage = kind == K_LINEAR ? (a.n_inputs < R ? a.n_inputs : R) : a.n_inputs;
-      if (n_stage <= a.tile_inputs)
-        for (int v = tid; v < n_stage; v += blockDim.x) list_s[v] = (uint32_t)v;
-    } else {
+      if (tid == 0) n_stage_s = n_stage;
+    } else if constexpr (!XREG) {
       const int nw = (a.n_inputs + 31) >> 5;
       for (int i = tid; i < nw; i += blockDim.x) used_s[i] = 0u;
       __syncthreads();
@@ -413,7 +416,11 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
       auto slot = [&](uint32_t v) {
         return before_s[v >> 5] + (uint32_t)__popc(used_s[v >> 5] & ((1u << (v & 31)) - 1u));
       };
-      if (n_stage <= a.tile_inputs) {
+      if (n_stage > GP_COMPACT_MAX_LIST) {  // too many to list: stage every input in order
+        n_stage = a.n_inputs;
+        __syncthreads();
+        if (tid == 0) n_stage_s = n_stage;
+      } else if (n_stage <= a.tile_inputs) {
         for (int i = tid; i < n_instr; i += blockDim.x) {
           uint4 in = prog_s[i];
           const uint32_t f = input_fields(kind, in.x);
@@ -452,8 +459,7 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   float* out_row = a.outputs ? a.outputs + (int64_t)p * a.n_cases : nullptr;
   const uint32_t prog_addr = (uint32_t)__cvta_generic_to_shared(prog_s);
   // this lane's K staged values of slot v live at tile + v * 32 * K floats
-  float* tile = reinterpret_cast<float*>(tile_s) + ((a.tile_inputs + 3) & ~3) +
-                (size_t)warp * a.tile_inputs * 32 * K + lane * K;
+  float* tile = reinterpret_cast<float*>(tile_s) + (size_t)warp * a.tile_inputs * 32 * K + lane * K;
   const uint32_t tile_addr = (uint32_t)__cvta_generic_to_shared(tile);
 
   if (!bad) {
@@ -465,9 +471,14 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
       float x[K];
       float o[K];
       if (staged) {
+        // a kernel with the input in registers has one input (register programs)
+        const int n_stage = XREG ? a.n_inputs : n_stage_s;
+        const bool listed = !XREG && kind != K_LINEAR && a.n_inputs <= GP_COMPACT_MAX_INPUTS &&
+                            n_stage <= GP_COMPACT_MAX_LIST;
         for (int v = 0; v < n_stage; ++v) {
           Vec<K> t;
-          vload<K>(t, a.cases + (int64_t)list_s[v] * a.n_cases, c0, a.n_cases, vec_ok);
+          const int64_t src = listed ? (int64_t)list_s[v] : (int64_t)v;
+          vload<K>(t, a.cases + src * a.n_cases, c0, a.n_cases, vec_ok);
 #pragma unroll
           for (int j = 0; j < K; ++j) tile[v * 32 * K + j] = vget<K>(t, j);
         }
@@ -528,11 +539,10 @@ __global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
   }
 }
 
-// dynamic shared memory of eval_float_kernel: the list of staged inputs and
-// the staged input tiles, for tile_inputs inputs per case
+// dynamic shared memory of eval_float_kernel: the staged input tiles, for
+// tile_inputs inputs per case
 inline size_t float_tile_bytes(int k, int block, int tile_inputs) {
-  return sizeof(float) * ((size_t)((tile_inputs + 3) & ~3) +
-                          (size_t)(block / 32) * (size_t)tile_inputs * 32u * (size_t)k);
+  return sizeof(float) * (size_t)(block / 32) * (size_t)tile_inputs * 32u * (size_t)k;
 }
 
 // ---------------------------------------------------------------------------

@@ -292,3 +292,24 @@ def test_tile_smaller_than_a_program_needs(wide):
     out = gp.eval_outputs(P, O, L, dev(x), config=cfg).cpu().numpy()
     assert_bits(out[used <= cap], ref[used <= cap], "programs that fit")
     gp.last_error()
+
+
+def test_tree_reading_more_inputs_than_the_list_holds():
+    """A chain over 300 distinct inputs (more than the 256 a block lists):
+    every input is staged in order, and the outputs stay exact."""
+    n_in = 300
+    chain = []
+    for v in range(n_in - 1):
+        chain += [synth.ADD, tok(VAR, v)]
+    chain.append(tok(VAR, n_in - 1))
+    other = [synth.MUL, tok(VAR, 7), tok(VAR, 299)]
+    pop = synth.pack([np.array(chain, np.uint32), np.array(other, np.uint32)])
+    x = synth.uniform_cases(130, n_in, 100, -1.0, 1.0)
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    assert enc.max_inputs_used == n_in
+    P, O, L = upload(enc)
+    for k in (1, 2):
+        out = gp.eval_outputs(P, O, L, dev(x), config=gp.Config(gp.VARIANT_REGISTER, k, 32, 0))
+        exp = np.stack([oracle.tree_outputs(pop.program(p), x) for p in range(2)])
+        assert_bits(out.cpu().numpy(), exp, f"k={k}")
+    assert gp.last_error() == 0

@@ -125,6 +125,7 @@ int64_t oracle_tree_nodes(const uint32_t* prog, int64_t len) {
     if (op == ORC_VAR) { i += 1; continue; }
     if (is_float_fn(op)) owed += 2;
     else if (is_bool_fn(op)) owed += bool_arity(op);
+    else if (oracle_fset_arity(op) > 0) owed += oracle_fset_arity(op); /* SIN .. EQ */
     else return -1;
     i += 1;
   }

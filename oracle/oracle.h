@@ -75,7 +75,8 @@ int oracle_tree_outputs(const uint32_t* prog, int64_t len, const float* cases,
 int oracle_tree_outputs_stack(const uint32_t* prog, int64_t len, const float* cases,
                               int32_t n_inputs, int64_t n_cases, float* out);
 
-/* Number of nodes (functions + terminals) of a prefix tree; <0 on error. */
+/* Number of nodes (functions + terminals) of a prefix tree, over every
+ * function of oracle.h (Boolean and the full float sets); <0 on error. */
 int64_t oracle_tree_nodes(const uint32_t* prog, int64_t len);
 
 /* Sum |o-y| in binary64 over the per-case binary32 errors (+inf if any is

@@ -400,6 +400,104 @@ int gp_autotune_population(const uint32_t* programs, const int64_t* offsets,
 int gp_autotune_clear(void);
 
 /* ------------------------------------------------------------------------
+ * Device-side encoder.  The S-form encoding of gp_encode_population (float
+ * trees, basic or extended functions; Sec. 5 symbolic stack), run on the GPU
+ * with one thread per tree, so that a generation loop needs no host
+ * conversion between generations (the paper converts on the host, Sec. 5).
+ * Output words are identical to gp_encode_population's for the same trees.
+ *   words, offsets, lengths   device: the trees in the user token format.
+ *   out, out_offsets          device: program p is written at
+ *                             out[out_offsets[p] ..]; the slot must hold
+ *                             4 + 4 * lengths[p] words (the same bound as on
+ *                             the host) and start on a multiple of 4 words.
+ *   out_lengths               device: the encoded length of each program.
+ * Trees of at most GP_DEVICE_ENCODE_MAX_NODES nodes.  A malformed tree, a
+ * larger one, or one that needs more than GP_STACK_LEVELS levels is written as
+ * a 4-word header of kind 0, which every evaluation reports as malformed
+ * (fitness NaN).  Asynchronous on `stream`.
+ * ---------------------------------------------------------------------- */
+#define GP_DEVICE_ENCODE_MAX_NODES 256
+int gp_encode_population_device(const uint32_t* words, const int64_t* offsets,
+                                const int32_t* lengths, int32_t n_progs, int32_t order,
+                                uint32_t* out, const int64_t* out_offsets, int32_t* out_lengths,
+                                gp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * On-device generation loop.  A GP run (Sec. 4.2 parameter table: population
+ * 1000, tournament selection of size 7, crossover 0.95, mutation 0.2) evolves
+ * the population on the GPU: each generation is one variation kernel
+ * (selection, subtree crossover, subtree mutation; one thread per offspring),
+ * the device encoder and the fitness evaluation, captured once as a CUDA
+ * graph and replayed, with the cases resident.  The paper names the
+ * operators only; this library defines them as:
+ *   draws        Philox4x32-10 (Salmon et al., SC'11): offspring i of
+ *                generation g reads the output words of the counters
+ *                (i, g, 0, 0), (i, g, 1, 0), ... in order under the key
+ *                (seed & 0xffffffff, seed >> 32).
+ *   uniform(n)   (u * n) >> 32 of a draw u; an event of probability p happens
+ *                when u < floor(p * 2^32) (capped at 2^32 - 1).
+ *   tournament   `tournament` uniform picks; the first is the provisional
+ *                winner and a later pick wins only with a strictly lower
+ *                fitness (NaN counts as +inf).
+ *   offspring    parent A by tournament; then with p_crossover parent B by
+ *                tournament, a node of A and a node of B uniformly (prefix
+ *                order) and the child is A with that subtree replaced by B's,
+ *                or A if the result has more than max_nodes nodes; then with
+ *                p_mutation a node of the child uniformly, replaced by a grown
+ *                subtree, unless that exceeds max_nodes.
+ *   grow(D)      a node at depth d (the root at 1) is a terminal if d >= D;
+ *                otherwise, below the root, one draw makes it a terminal with
+ *                probability 1/2; else a function uniformly from `funcs`,
+ *                children grown at depth d + 1.  A terminal is a constant with
+ *                probability p_const (a second draw u gives
+ *                const_lo + (const_hi - const_lo) * ((u >> 8) * 2^-24), each
+ *                step one binary32 operation), else an input uniformly.
+ * max_nodes is at most 255, which keeps every tree within GP_STACK_LEVELS
+ * register levels.  Generation 0 is the population given to
+ * gp_evolve_create; each gp_evolve_run generation produces the next one and
+ * its fitness.
+ * ---------------------------------------------------------------------- */
+typedef struct gp_evolve_params {
+  int32_t pop_size;
+  int32_t max_nodes;       /* tree size cap, 1..255 */
+  int32_t tournament;      /* tournament size, >= 1 (the paper: 7) */
+  float p_crossover;       /* the paper: 0.95 */
+  float p_mutation;        /* the paper: 0.2 */
+  int32_t mutation_depth;  /* depth cap D of a grown subtree, 1..4 */
+  int32_t n_funcs;         /* 1..16 */
+  int32_t funcs[16];       /* float function opcodes (GP_OP_ADD .. GP_OP_EQ, AND, OR, IF) */
+  float p_const;           /* probability that a grown terminal is a constant */
+  float const_lo, const_hi;
+  uint64_t seed;
+  gp_config eval;          /* evaluation: variant (GP_VARIANT_AUTO becomes
+                              GP_VARIANT_EXTENDED when funcs has an extended
+                              function), k, block, fitness, tile_inputs */
+} gp_evolve_params;
+
+typedef struct gp_evolver gp_evolver;
+
+/* Creates a run: copies the initial population (host, user token format,
+ * pop_size trees of at most max_nodes nodes) to the device, encodes and
+ * evaluates it (generation 0) on `stream`.  cases / targets are device
+ * arrays ([n_inputs][n_cases] and [n_cases]) that must stay valid and
+ * unchanged until gp_evolve_destroy; grown inputs are drawn from
+ * 0 .. n_inputs - 1.  The run owns its device buffers and its own stream. */
+int gp_evolve_create(const gp_evolve_params* params, const uint32_t* words,
+                     const int64_t* offsets, const int32_t* lengths, const float* cases,
+                     int32_t n_inputs, int64_t n_cases, const float* targets,
+                     gp_evolver** out);
+/* Enqueues `generations` generations (graph replays); asynchronous. */
+int gp_evolve_run(gp_evolver* ev, int32_t generations);
+/* Waits for the run, then copies the current population (host: words with
+ * room for pop_size * 2 * max_nodes words, tree p at p * 2 * max_nodes;
+ * lengths pop_size), its fitness (pop_size doubles), the generation index and
+ * the tree nodes evaluated so far over all generations (generation 0
+ * included; times n_cases gives the GP operations).  Any pointer may be NULL. */
+int gp_evolve_read(gp_evolver* ev, uint32_t* words, int32_t* lengths, double* fitness,
+                   int32_t* generation, int64_t* nodes_evaluated);
+int gp_evolve_destroy(gp_evolver* ev);
+
+/* ------------------------------------------------------------------------
  * Configuration, status and lifetime.
  * ---------------------------------------------------------------------- */
 /* Default configuration used when cfg is NULL or a field is 0. */

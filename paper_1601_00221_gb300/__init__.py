@@ -28,6 +28,7 @@ __all__ = [
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "ORDER_PAPER",
     "ORDER_MIN_DEPTH", "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL", "VARIANT_LANES",
     "VARIANT_EXTENDED", "FITNESS_SUM_ABS", "FITNESS_MSE", "FITNESS_CLASS",
+    "encode_population_device", "EvolveParams", "Evolver",
 ]
 
 KIND_SFORM, KIND_RPN, KIND_LINEAR, KIND_BOOL, KIND_SFORM_EXT = 1, 2, 3, 4, 5
@@ -133,6 +134,11 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_server_destroy": [P],
         "gp_autotune_population": [P, P, P, i32, P, i32, i64, P, i32, P, P],
         "gp_autotune_clear": [],
+        "gp_encode_population_device": [P, P, P, i32, i32, P, P, P, P],
+        "gp_evolve_create": [P, P, P, P, P, i32, i64, P, P],
+        "gp_evolve_run": [P, i32],
+        "gp_evolve_read": [P, P, P, P, P, P],
+        "gp_evolve_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -477,3 +483,110 @@ def last_error(stream=None) -> int:
 
 def shutdown():
     _check(lib().gp_shutdown())
+
+
+# ---------------------------------------------------------------------------
+# device-side encoder and the on-device generation loop
+# ---------------------------------------------------------------------------
+def encode_population_device(words, offsets, lengths, order: int = ORDER_MIN_DEPTH, stream=None):
+    """gp_encode_population_device on CUDA tensors (user-format trees).
+    Returns (out words, out offsets, out lengths) as CUDA tensors; program p
+    is written at out_offsets[p], slots laid out back to back with room for
+    4 + 4 * lengths[p] words."""
+    import torch
+    n = int(lengths.numel())
+    slot = 4 + 4 * lengths.to(torch.int64)
+    out_off = torch.zeros(n, dtype=torch.int64, device=lengths.device)
+    if n > 1:
+        out_off[1:] = torch.cumsum(slot, 0)[:-1]
+    total = int(slot.sum().item()) if n else 4
+    out = torch.zeros(max(total, 4), dtype=torch.int32, device=lengths.device)
+    out_len = torch.zeros(n, dtype=torch.int32, device=lengths.device)
+    _check(lib().gp_encode_population_device(_tptr(words), _tptr(offsets), _tptr(lengths), n, order,
+                                             _tptr(out), _tptr(out_off), _tptr(out_len),
+                                             _stream(stream)))
+    return out, out_off, out_len
+
+
+class EvolveParams(ctypes.Structure):
+    """gp_evolve_params (include/gpeval.h)."""
+    _fields_ = [("pop_size", ctypes.c_int32), ("max_nodes", ctypes.c_int32),
+                ("tournament", ctypes.c_int32), ("p_crossover", ctypes.c_float),
+                ("p_mutation", ctypes.c_float), ("mutation_depth", ctypes.c_int32),
+                ("n_funcs", ctypes.c_int32), ("funcs", ctypes.c_int32 * 16),
+                ("p_const", ctypes.c_float), ("const_lo", ctypes.c_float),
+                ("const_hi", ctypes.c_float), ("seed", ctypes.c_uint64), ("eval", Config)]
+
+    @classmethod
+    def make(cls, pop_size, funcs, max_nodes=255, tournament=7, p_crossover=0.95, p_mutation=0.2,
+             mutation_depth=4, p_const=0.5, const_lo=-1.0, const_hi=1.0, seed=1, config=None):
+        p = cls()
+        p.pop_size, p.max_nodes, p.tournament = pop_size, max_nodes, tournament
+        p.p_crossover, p.p_mutation, p.mutation_depth = p_crossover, p_mutation, mutation_depth
+        p.n_funcs = len(funcs)
+        for i, f in enumerate(funcs):
+            p.funcs[i] = int(f)
+        p.p_const, p.const_lo, p.const_hi, p.seed = p_const, const_lo, const_hi, seed
+        if config is not None:
+            p.eval = config
+        return p
+
+
+class Evolver:
+    """gp_evolve_*: a GP run whose generations (variation, device encoding,
+    evaluation) run on the GPU as CUDA-graph replays.  The initial population
+    is host user-format trees; cases and targets are CUDA tensors kept alive
+    by the run."""
+
+    def __init__(self, params: EvolveParams, words, offsets, lengths, cases, targets):
+        w = np.ascontiguousarray(words, np.uint32)
+        off = np.ascontiguousarray(offsets, np.int64)
+        ln = np.ascontiguousarray(lengths, np.int32)
+        if ln.size != params.pop_size:
+            raise ValueError("the initial population must have pop_size trees")
+        self.params = params
+        self._keep = (cases, targets)
+        n_inputs, n_cases = (int(cases.shape[0]), int(cases.shape[1])) if cases.dim() == 2 else (1, int(cases.numel()))
+        self._h = ctypes.c_void_p()
+        _check(lib().gp_evolve_create(ctypes.byref(params), _np_ptr(w), _np_ptr(off), _np_ptr(ln),
+                                      _tptr(cases), n_inputs, n_cases, _tptr(targets),
+                                      ctypes.byref(self._h)))
+        self.slot = 2 * params.max_nodes
+
+    def run(self, generations: int = 1):
+        _check(lib().gp_evolve_run(self._h, int(generations)))
+
+    def read(self):
+        """(list of token arrays, fitness float64 [n], generation index)."""
+        n = self.params.pop_size
+        words = np.zeros(n * self.slot, np.uint32)
+        lens = np.zeros(n, np.int32)
+        fit = np.zeros(n, np.float64)
+        gen = ctypes.c_int32(0)
+        _check(lib().gp_evolve_read(self._h, _np_ptr(words), _np_ptr(lens), _np_ptr(fit),
+                                    ctypes.byref(gen), None))
+        trees = [words[p * self.slot: p * self.slot + lens[p]].copy() for p in range(n)]
+        return trees, fit, int(gen.value)
+
+    def nodes_evaluated(self) -> int:
+        """Tree nodes evaluated over all generations so far (waits for the run)."""
+        v = ctypes.c_int64(0)
+        _check(lib().gp_evolve_read(self._h, None, None, None, None, ctypes.byref(v)))
+        return int(v.value)
+
+    def close(self):
+        if self._h:
+            lib().gp_evolve_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -44,3 +44,32 @@ def test_host_side_argument_checks_without_gpu():
     bad = gp.Config(variant=1, k=3, block=128, chunk_cases=0)
     assert L.gp_set_config(ctypes.byref(bad)) == 1
     assert b"k must be" in L.gp_error_string()
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets (the header compiled by the host C compiler)."""
+    import subprocess
+    import sys
+    mirrors = {"gp_config": gp.Config, "gp_prog_info": gp._ProgInfo,
+               "gp_server_opts": gp._ServerOpts, "gp_evolve_params": gp.EvolveParams,
+               "gp_request_info": gp.RequestInfo, "gp_server_stats": gp.ServerStats}
+    nested = {"gp_server_opts": {"variant", "k", "block", "chunk_cases", "fitness", "tile_inputs"}}
+
+    def member(cname, fname):  # the binding flattens gp_server_opts.config
+        return f"config.{fname}" if fname in nested.get(cname, ()) else fname
+    lines = ["#include <stdio.h>", "#include <stddef.h>", f'#include "{HEADER}"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {member(cname, fname)}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-std=c11", str(src), "-o", str(exe)])
+    out = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, py in mirrors.items():
+        assert int(out[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(out[f"{cname}.{fname}"]) == getattr(py, fname).offset, f"{cname}.{fname}"

@@ -12,6 +12,12 @@ encoder) and replays the graph: one launch instead of five calls.
 The graph copies the whole capacity of the program buffer every replay (the
 size is fixed at capture); the words past the population's encoding are not
 read by the kernel.
+
+With `device_encode=True` the host encodes nothing: the graph copies the
+user-format trees themselves and runs the device-side encoder
+(gp_encode_population_device) before the evaluation, so the host's work per
+generation is one copy of the trees into pinned memory (trees of at most
+GP_DEVICE_ENCODE_MAX_NODES nodes, S-form).
 """
 from __future__ import annotations
 
@@ -23,10 +29,13 @@ import numpy as np
 from . import (Config, KIND_SFORM, ORDER_MIN_DEPTH, VARIANT_REGISTER, _check, _stream, _tptr,
                encode_population, lib)
 
+DEVICE_ENCODE_MAX_NODES = 256  # GP_DEVICE_ENCODE_MAX_NODES
+
 
 class GenerationGraph:
     def __init__(self, n_progs: int, max_tokens: int, cases, targets, config: Optional[Config] = None,
-                 kind: int = KIND_SFORM, order: int = ORDER_MIN_DEPTH, device="cuda"):
+                 kind: int = KIND_SFORM, order: int = ORDER_MIN_DEPTH, device="cuda",
+                 device_encode: bool = False):
         """n_progs: population size; max_tokens: the largest total number of
         user-format words of any population to be evaluated; cases/targets:
         host arrays, binary32 [n_inputs, n_cases] and [n_cases]."""
@@ -34,6 +43,10 @@ class GenerationGraph:
         self.torch = torch
         self.n = int(n_progs)
         self.kind, self.order = kind, order
+        self.device_encode = bool(device_encode)
+        if self.device_encode and kind != KIND_SFORM:
+            raise ValueError("the device-side encoder writes the S-form only")
+        self.max_tokens = int(max_tokens)
         self.device = torch.device(device)
         x = np.ascontiguousarray(cases, np.float32)
         x = x[None, :] if x.ndim == 1 else x
@@ -54,19 +67,66 @@ class GenerationGraph:
         self.stream = torch.cuda.Stream(device=self.device)
         self.graph = None
         self.nodes = 0
+        if self.device_encode:
+            # trees in, encoded programs in fixed slots of 4 + 4 * lengths[p] words
+            self.h_tok = pin(max(self.max_tokens, 1), torch.int32)
+            self.h_eoff = pin(self.n, torch.int64)
+            self.d_tok = torch.zeros(max(self.max_tokens, 1), dtype=torch.int32, device=self.device)
+            self.d_eoff = torch.zeros(self.n, dtype=torch.int64, device=self.device)
+            self.d_elen = torch.full((self.n,), 4, dtype=torch.int32, device=self.device)
 
     def _device_work(self):
         torch = self.torch
-        self.d_words.copy_(self.h_words, non_blocking=True)
-        self.d_off.copy_(self.h_off, non_blocking=True)
-        self.d_len.copy_(self.h_len, non_blocking=True)
+        stream = _stream(torch.cuda.current_stream())
+        if self.device_encode:
+            self.d_tok.copy_(self.h_tok, non_blocking=True)
+            self.d_off.copy_(self.h_off, non_blocking=True)
+            self.d_len.copy_(self.h_len, non_blocking=True)
+            self.d_eoff.copy_(self.h_eoff, non_blocking=True)
+            _check(lib().gp_encode_population_device(
+                _tptr(self.d_tok), _tptr(self.d_off), _tptr(self.d_len), self.n, self.order,
+                _tptr(self.d_words), _tptr(self.d_eoff), _tptr(self.d_elen), stream))
+            words, off, ln = self.d_words, self.d_eoff, self.d_elen
+        else:
+            self.d_words.copy_(self.h_words, non_blocking=True)
+            self.d_off.copy_(self.h_off, non_blocking=True)
+            self.d_len.copy_(self.h_len, non_blocking=True)
+            words, off, ln = self.d_words, self.d_off, self.d_len
         _check(lib().gp_eval_population_ex(
-            _tptr(self.d_words), _tptr(self.d_off), _tptr(self.d_len), self.n, _tptr(self.X),
-            self.n_inputs, self.n_cases, _tptr(self.Y), _tptr(self.d_fit), None,
-            ctypes.byref(self.cfg), _stream(torch.cuda.current_stream())))
+            _tptr(words), _tptr(off), _tptr(ln), self.n, _tptr(self.X), self.n_inputs,
+            self.n_cases, _tptr(self.Y), _tptr(self.d_fit), None, ctypes.byref(self.cfg), stream))
         self.h_fit.copy_(self.d_fit, non_blocking=True)
 
+    def _stage_trees(self, words, offsets, lengths):
+        """Device encoding: the trees, packed back to back, into pinned memory."""
+        w = np.ascontiguousarray(words, np.uint32)
+        off = np.ascontiguousarray(offsets, np.int64)
+        ln = np.ascontiguousarray(lengths, np.int32)
+        total = int(ln.sum())
+        if total > self.max_tokens:
+            raise ValueError("the population has more words than the graph's capacity")
+        dense = bool(np.array_equal(off[1:], np.cumsum(ln[:-1], dtype=np.int64))) and \
+            (ln.size == 0 or off[0] == 0)
+        tok = self.h_tok.numpy().view(np.uint32)
+        if dense:
+            tok[:total] = w[:total]
+            self.h_off.numpy()[:] = off
+        else:
+            pos = 0
+            for p in range(ln.size):
+                tok[pos:pos + ln[p]] = w[off[p]:off[p] + ln[p]]
+                self.h_off.numpy()[p] = pos
+                pos += int(ln[p])
+        self.h_len.numpy()[:] = ln
+        slot = 4 + 4 * ln.astype(np.int64)
+        eoff = self.h_eoff.numpy()
+        eoff[0] = 0
+        eoff[1:] = np.cumsum(slot[:-1])
+
     def _encode(self, words, offsets, lengths):
+        if self.device_encode:
+            self._stage_trees(words, offsets, lengths)
+            return None
         out = self.h_words.numpy().view(np.uint32)
         enc = encode_population(words, offsets, lengths, self.kind, self.order, out=out)
         if enc.words.ctypes.data != out.ctypes.data:

@@ -37,3 +37,32 @@ def test_graph_rejects_a_population_too_large_for_its_capacity():
     gg.run(small.words, small.offsets, small.lengths)
     with pytest.raises(ValueError):
         gg.run(big.words, big.offsets, big.lengths)
+
+
+@pytest.mark.parametrize("funcs,n_inputs,fitness", [(synth.FLOAT_FUNCS, 1, gp.FITNESS_SUM_ABS),
+                                                    (synth.SHUTTLE_FUNCS, 9, gp.FITNESS_CLASS)])
+def test_device_encoding_graph_matches_host_encoding(funcs, n_inputs, fitness):
+    """The graph that copies the trees and encodes them on the device gives
+    bit-identical fitness to host encoding, generation after generation (also
+    for trees that are not packed back to back)."""
+    n, n_cases = 300, 5000
+    x = synth.uniform_cases(203, n_inputs, n_cases, -3.0, 3.0)
+    y = np.rint(synth.uniform_cases(204, 1, n_cases, 0.0, 4.0)[0]).astype(np.float32)
+    pops = [synth.pack(synth.ramped_half_and_half(320 + g, n, 1, 8, 255, funcs=funcs,
+                                                  n_inputs=n_inputs, full_fallback_to_grow=True))
+            for g in range(3)]
+    max_tokens = max(int(p.lengths.sum()) for p in pops) + 64
+    variant = gp.VARIANT_EXTENDED if funcs is synth.SHUTTLE_FUNCS else gp.VARIANT_REGISTER
+    cfg = gp.Config(variant, 4, 128, 0, fitness)
+    gh = GenerationGraph(n, max_tokens, x, y, config=cfg)
+    gd = GenerationGraph(n, max_tokens, x, y, config=cfg, device_encode=True)
+    for g, pop in enumerate(pops):
+        words, offsets = pop.words, pop.offsets
+        if g == 2:  # gaps between the trees
+            words = np.zeros(pop.words.size + 2 * n, np.uint32)
+            offsets = pop.offsets + 2 * np.arange(n)
+            for p in range(n):
+                words[offsets[p]: offsets[p] + pop.lengths[p]] = pop.program(p)
+        a = gh.run(words, offsets, pop.lengths)
+        b = gd.run(words, offsets, pop.lengths)
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), g

@@ -221,14 +221,18 @@ __global__ void bump_generation(int32_t* g) { *g += 1; }
 // device encoder: one thread per tree, scratch in shared memory
 // ---------------------------------------------------------------------------
 struct EncScratch {  // per thread
+  uint32_t tok[2 * GP_DEVICE_ENCODE_MAX_NODES];  // the tree's words
   uint16_t pos[GP_DEVICE_ENCODE_MAX_NODES];   // word position of each node
   uint16_t cnt[GP_DEVICE_ENCODE_MAX_NODES];   // nodes in its subtree
+  uint8_t op[GP_DEVICE_ENCODE_MAX_NODES];     // opcode
   uint8_t need[GP_DEVICE_ENCODE_MAX_NODES];   // stack levels its subtree needs
+  uint8_t ord[GP_DEVICE_ENCODE_MAX_NODES];    // function children in evaluation order:
+                                              // child ranks in bits 0-1, 2-3, 4-5, count in 6-7
   uint16_t fnode[GP_DEVICE_ENCODE_MAX_NODES]; // stack: node (parse: open node; emit: frame)
-  uint8_t fk[GP_DEVICE_ENCODE_MAX_NODES];     // stack: remaining children / next child rank
+  uint8_t fk[GP_DEVICE_ENCODE_MAX_NODES];     // stack: remaining children / next child
   uint8_t flevel[GP_DEVICE_ENCODE_MAX_NODES]; // stack: level of the frame's result
 };
-constexpr int kEncThreads = 32;
+constexpr int kEncThreads = 16;  // small blocks spread the trees over every SM
 
 struct EncArgs {
   const uint32_t* words;
@@ -242,28 +246,10 @@ struct EncArgs {
   unsigned long long* node_total;  // may be null: adds the nodes of every tree encoded
 };
 
-// children of function node v (node indices) and their evaluation order:
-// function children only, by decreasing need (stable) for GP_ORDER_MIN_DEPTH
-__device__ int enc_children(const uint32_t* t, const EncScratch& s, int v, int order, int* ch,
-                            int* perm, int* np) {
-  const int ar = fn_arity(t[s.pos[v]] & 0xffu);
+__device__ __forceinline__ int child_at(const EncScratch& s, int v, int rank) {
   int c = v + 1;
-  for (int k = 0; k < ar; ++k) {
-    ch[k] = c;
-    c += s.cnt[c];
-  }
-  int m = 0;
-  for (int k = 0; k < ar; ++k)
-    if (fn_arity(t[s.pos[ch[k]]] & 0xffu) > 0) perm[m++] = k;
-  if (order == GP_ORDER_MIN_DEPTH)  // insertion sort: stable
-    for (int x = 1; x < m; ++x)
-      for (int y = x; y > 0 && s.need[ch[perm[y]]] > s.need[ch[perm[y - 1]]]; --y) {
-        const int tmp = perm[y];
-        perm[y] = perm[y - 1];
-        perm[y - 1] = tmp;
-      }
-  *np = m;
-  return ar;
+  for (int k = 0; k < rank; ++k) c += s.cnt[c];
+  return c;
 }
 
 __device__ int xbin(uint32_t op) {
@@ -271,26 +257,39 @@ __device__ int xbin(uint32_t op) {
                                 : op == GP_OP_AND ? XB_AND : XB_OR;
 }
 
+// One tree per thread: (1) copy its words to shared memory and parse them into
+// nodes (positions, opcodes, subtree sizes); (2) from the leaves up, the levels
+// each subtree needs and the evaluation order of each node's function
+// children (by decreasing need, stable, for GP_ORDER_MIN_DEPTH; left to right
+// for GP_ORDER_PAPER); (3) emit the S-form post-order: a node's function
+// children at levels l, l + 1, ... in that order, then the node at level l.
+// The words are the host encoder's (encode.cpp) for the same tree.
 __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncArgs a) {
   extern __shared__ EncScratch enc_s[];
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.n_progs) return;
   EncScratch& s = enc_s[threadIdx.x];
-  const uint32_t* t = a.words + a.offsets[p];
   const int len = a.lengths[p];
   uint32_t* o = a.out + a.out_offsets[p];
   bool ok = len > 0 && len <= 2 * GP_DEVICE_ENCODE_MAX_NODES;
+  if (ok) {
+    const uint32_t* g = a.words + a.offsets[p];
+#pragma unroll 8
+    for (int w = 0; w < len; ++w) s.tok[w] = g[w];
+  }
   bool extended = false;
   int max_input = -1, n = 0, top = 0, w = 0;
-  // 1. parse: node positions and subtree sizes
+  // 1. parse
   while (ok && w < len) {
     if (n > 0 && top == 0) { ok = false; break; }          // trailing tokens
     if (n >= GP_DEVICE_ENCODE_MAX_NODES) { ok = false; break; }
-    const uint32_t op = t[w] & 0xffu;
+    const uint32_t tk = s.tok[w];
+    const uint32_t op = tk & 0xffu;
     int ar = 0;
     s.pos[n] = (uint16_t)w;
+    s.op[n] = (uint8_t)op;
     if (op == GP_OP_VAR) {
-      if ((int)(t[w] >> 8) > max_input) max_input = (int)(t[w] >> 8);
+      if ((int)(tk >> 8) > max_input) max_input = (int)(tk >> 8);
       w += 1;
     } else if (op == GP_OP_CONST) {
       if (w + 1 >= len) { ok = false; break; }
@@ -316,18 +315,34 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncArgs a) {
     }
   }
   if (ok && (top != 0 || n == 0)) ok = false;                // missing operands
-  // 2. stack levels each subtree needs (children follow their parent)
+  // 2. needs and child orders (children follow their parent in prefix order)
   int depth = 1;
   if (ok) {
     for (int v = n - 1; v >= 0; --v) {
-      if (fn_arity(t[s.pos[v]] & 0xffu) <= 0) { s.need[v] = 0; continue; }
-      int ch[3], perm[3], np;
-      enc_children(t, s, v, a.order, ch, perm, &np);
+      const int ar = fn_arity(s.op[v]);
+      if (ar <= 0) { s.need[v] = 0; s.ord[v] = 0; continue; }
+      int rk[3], nd[3], m = 0;
+      int c = v + 1;
+      for (int k = 0; k < ar; ++k) {
+        if (fn_arity(s.op[c]) > 0) { rk[m] = k; nd[m] = s.need[c]; ++m; }
+        c += s.cnt[c];
+      }
+      if (a.order == GP_ORDER_MIN_DEPTH)  // insertion sort by decreasing need: stable
+        for (int x = 1; x < m; ++x)
+          for (int y = x; y > 0 && nd[y] > nd[y - 1]; --y) {
+            int t0 = rk[y]; rk[y] = rk[y - 1]; rk[y - 1] = t0;
+            t0 = nd[y]; nd[y] = nd[y - 1]; nd[y - 1] = t0;
+          }
       int need = 1;
-      for (int k = 0; k < np; ++k) need = max(need, k + (int)s.need[ch[perm[k]]]);
+      uint32_t packed = (uint32_t)m << 6;
+      for (int k = 0; k < m; ++k) {
+        need = max(need, k + nd[k]);
+        packed |= (uint32_t)rk[k] << (2 * k);
+      }
       s.need[v] = (uint8_t)min(need, 255);
+      s.ord[v] = (uint8_t)packed;
     }
-    depth = fn_arity(t[0] & 0xffu) > 0 ? s.need[0] : 1;
+    depth = fn_arity(s.op[0]) > 0 ? s.need[0] : 1;
     if (depth > R) ok = false;
   }
   if (!ok) {  // a header of kind 0: every evaluation reports the program as malformed
@@ -335,13 +350,13 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncArgs a) {
     a.out_lengths[p] = 4;
     return;
   }
-  // 3. emit the S-form: children first (in their order, at levels l + k), then the node
+  // 3. emit
   int ni = 0;
   uint32_t* ins = o + 4;
-  if (fn_arity(t[0] & 0xffu) <= 0) {  // a single terminal: one move to level 0
-    const bool cst = (t[0] & 0xffu) == GP_OP_CONST;
+  if (fn_arity(s.op[0]) <= 0) {  // a single terminal: one move to level 0
+    const bool cst = s.op[0] == GP_OP_CONST;
     ins[0] = (uint32_t)sform_code(cst ? SF_MOVC : SF_MOVX, 0, 0);
-    ins[1] = cst ? t[1] : (t[0] >> 8);
+    ins[1] = cst ? s.tok[1] : (s.tok[0] >> 8);
     ins[2] = 0u;
     ins[3] = 0u;
     ni = 1;
@@ -350,25 +365,28 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncArgs a) {
     s.fnode[top] = 0; s.flevel[top] = 0; s.fk[top] = 0; ++top;
     while (top) {
       const int v = s.fnode[top - 1], l = s.flevel[top - 1], k = s.fk[top - 1];
-      int ch[3], perm[3], np;
-      const int ar = enc_children(t, s, v, a.order, ch, perm, &np);
+      const uint32_t od = s.ord[v];
+      const int np = (int)(od >> 6);
       if (k < np) {  // next function child, at level l + k
         s.fk[top - 1] = (uint8_t)(k + 1);
-        s.fnode[top] = (uint16_t)ch[perm[k]]; s.flevel[top] = (uint8_t)(l + k); s.fk[top] = 0;
+        s.fnode[top] = (uint16_t)child_at(s, v, (int)((od >> (2 * k)) & 3u));
+        s.flevel[top] = (uint8_t)(l + k);
+        s.fk[top] = 0;
         ++top;
         continue;
       }
       --top;
+      const uint32_t op = s.op[v];
+      const int ar = fn_arity(op);
       int kind[3] = {0, 0, 0};   // 0 input, 1 constant, 2 + j stack level l + j
       uint32_t pay[3] = {0u, 0u, 0u};
-      for (int c = 0; c < ar; ++c) {
-        const uint32_t tok = t[s.pos[ch[c]]];
-        const uint32_t cop = tok & 0xffu;
-        if (cop == GP_OP_VAR) { kind[c] = 0; pay[c] = tok >> 8; }
-        else if (cop == GP_OP_CONST) { kind[c] = 1; pay[c] = t[s.pos[ch[c]] + 1]; }
+      int c = v + 1;
+      for (int q = 0; q < ar; ++q) {
+        if (s.op[c] == GP_OP_VAR) { kind[q] = 0; pay[q] = s.tok[s.pos[c]] >> 8; }
+        else if (s.op[c] == GP_OP_CONST) { kind[q] = 1; pay[q] = s.tok[s.pos[c] + 1]; }
+        c += s.cnt[c];
       }
-      for (int r = 0; r < np; ++r) kind[perm[r]] = 2 + r;
-      const uint32_t op = t[s.pos[v]] & 0xffu;
+      for (int r = 0; r < np; ++r) kind[(od >> (2 * r)) & 3u] = 2 + r;
       uint32_t code;
       if (ar == 1) {
         const int uf = kind[0] == 0 ? UF_X : kind[0] == 1 ? UF_C : UF_S;

@@ -219,7 +219,7 @@ def run_ours(args):
     # --- tune K and block for the 2D stack (short sweep) ---
     cands = []
     ks = [args.k] if args.k else [2, 4, 8]
-    blocks = [args.block] if args.block else [64, 128, 256]
+    blocks = [args.block] if args.block else [64, 128, 256, 512]
     for k in ks:
         for b in blocks:
             cfg = gp.Config(gp.VARIANT_REGISTER, k, b, 0)

@@ -191,7 +191,8 @@ typedef enum gp_fitness {
 typedef struct gp_config {
   int32_t variant;
   int32_t k;            /* 1, 2, 4 or 8 (0 = tuned) */
-  int32_t block;        /* 32..1024, multiple of 32 (0 = tuned) */
+  int32_t block;        /* threads per block: a multiple of 32, at most 512 (256 for the
+                           local-memory variant; Boolean launches use at most 256); 0 = tuned */
   int32_t chunk_cases;  /* 0 = choose; else a multiple of k*block */
   int32_t fitness;      /* gp_fitness (0 = GP_FITNESS_SUM_ABS) */
   int32_t tile_inputs;  /* inputs per case the shared-memory tile holds (0 = n_inputs).  A
@@ -384,7 +385,7 @@ int gp_server_destroy(gp_server* srv);
  * size depend on the hardware and the workload (Sec. 4.2: the paper's best K
  * and thread count differ per problem, Tables of Sec. 4.2, 5 and 6).
  * gp_autotune_population times every candidate configuration (k in
- * {2, 4, 8} x block in {64, 128, 256} x cases per block in {chosen, 4096,
+ * {2, 4, 8} x block in {64, 128, 256, 512} x cases per block in {chosen, 4096,
  * 8192, 16384, 32768}) on the given float population with CUDA
  * events on `stream` (1 warm-up launch, `repeats` timed launches each, the
  * minimum kept), writes the fastest to *best (may be NULL) and records it for

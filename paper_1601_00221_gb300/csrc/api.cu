@@ -139,8 +139,10 @@ int resolve_config(const gp_config* user, gp_config* c) {
   if (c->k != 1 && c->k != 2 && c->k != 4 && c->k != 8)
     return gp_fail(GP_ERR_INVALID_ARG, "k must be 1, 2, 4 or 8 (got %d)", c->k);
   if (c->variant == GP_VARIANT_LOCAL) c->k = 1;
-  if (c->block < 32 || c->block > 256 || c->block % 32)
-    return gp_fail(GP_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 256] (got %d)", c->block);
+  if (c->block < 32 || c->block > 512 || c->block % 32)
+    return gp_fail(GP_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 512] (got %d)", c->block);
+  if (c->block > 256 && c->variant == GP_VARIANT_LOCAL)
+    return gp_fail(GP_ERR_INVALID_ARG, "the local-memory variant takes at most 256 threads per block");
   if (c->chunk_cases < 0 || (c->chunk_cases % ((int64_t)c->k * c->block)) != 0)
     return gp_fail(GP_ERR_INVALID_ARG, "chunk_cases must be a multiple of k*block");
   return GP_OK;
@@ -353,6 +355,7 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   if (rc) return rc;
   if (c.variant == GP_VARIANT_EXTENDED) c.variant = GP_VARIANT_REGISTER;  // a float-only choice
   if (c.variant != GP_VARIANT_REGISTER) return gp_fail(GP_ERR_INVALID_ARG, "Boolean programs use the register or per-lane variant");
+  if (c.block > 256) c.block = 256;  // the Boolean kernel's block limit
   if (!cfg || !cfg->block) {  // small case sets: do not launch idle warps
     int64_t need = (n_words + c.k - 1) / c.k;
     c.block = (int)std::min<int64_t>(c.block, std::max<int64_t>(32, ((need + 31) / 32) * 32));
@@ -459,7 +462,7 @@ extern "C" int gp_autotune_population(const uint32_t* programs, const int64_t* o
   float best_ms = 1e30f;
   int rc = GP_OK;
   static const int ks[] = {2, 4, 8};
-  static const int blocks[] = {64, 128, 256};
+  static const int blocks[] = {64, 128, 256, 512};
   static const int chunks[] = {0, 4096, 8192, 16384, 32768};
   for (int k : ks) {
     for (int blk : blocks) {

@@ -320,8 +320,10 @@ __device__ __forceinline__ bool valid_instr_ext(const uint4& in, int n_inputs) {
 // program; each warp runs its own sequence of passes.
 // ---------------------------------------------------------------------------
 // EXT: the extended S-form interpreter (K_SFORM and K_SFORMX programs only).
+// Up to 512 threads per block at 128 registers: the warps of an SM interpret
+// as few distinct programs as possible (every block holds one program).
 template <int K, bool XREG, bool EXT = false>
-__global__ void __launch_bounds__(256, 2) eval_float_kernel(FloatArgs a) {
+__global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
   using namespace gpisa;
   __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
   __shared__ Partial red_s[32];

@@ -159,3 +159,23 @@ def test_malformed_program_only_affects_its_request(runs):
     mask = np.arange(b.size) != 5
     assert np.array_equal(a.view(np.uint64)[mask], b.view(np.uint64)[mask])
     assert np.array_equal(a.view(np.uint64), c.view(np.uint64))
+
+
+def test_extended_functions_and_fitness_measures_are_served():
+    """A server configured with the extended interpreter and classification
+    fitness serves Shuttle-set runs; each result equals the direct evaluation
+    and the oracle's exact counts."""
+    import torch
+    cfg = gp.Config(gp.VARIANT_EXTENDED, 4, 128, 0, gp.FITNESS_CLASS)
+    runs = [synth.shuttle_like_problem(seed=140 + i, n_progs=64 + 32 * i, n_cases=900 + 500 * i)
+            for i in range(3)]
+    with gp.Server(config=cfg) as srv:
+        ids = [srv.register_run(w.cases, w.targets) for w in runs]
+        encs = [gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths) for w in runs]
+        reqs = [srv.submit(i, e) for i, e in zip(ids, encs)]
+        for q, w, e in zip(reqs, runs, encs):
+            out, info = srv.wait(q)
+            assert info.status == 0
+            exp = oracle.fset_population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, w.cases,
+                                                 w.targets, oracle.FIT_CLASS)
+            assert np.array_equal(out, exp)

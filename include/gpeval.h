@@ -202,6 +202,9 @@ typedef struct gp_config {
                            4096 inputs, stage every input; register programs need
                            min(n_inputs, 8)); a program that needs more fails as
                            malformed.  Smaller tiles leave room for more warps. */
+  int32_t stack_registers; /* stack levels held in registers: 0 (or 8) = all; 4 = levels 4..7
+                              in shared memory, fewer registers per thread (k = 8, the register
+                              variant, GP_KIND_SFORM programs only; others fail as malformed) */
 } gp_config;
 
 /* ------------------------------------------------------------------------

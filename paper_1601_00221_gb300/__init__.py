@@ -62,7 +62,8 @@ class _ServerOpts(ctypes.Structure):
                 ("max_queued", ctypes.c_int32), ("max_merge", ctypes.c_int32),
                 ("memory_budget", ctypes.c_int64), ("variant", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("block", ctypes.c_int32), ("chunk_cases", ctypes.c_int32),
-                ("fitness", ctypes.c_int32), ("tile_inputs", ctypes.c_int32)]
+                ("fitness", ctypes.c_int32), ("tile_inputs", ctypes.c_int32),
+                ("stack_registers", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -89,12 +90,12 @@ class Config(ctypes.Structure):
     tile_inputs (inputs per case the shared-memory tile holds, 0 = all)."""
     _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("chunk_cases", ctypes.c_int32), ("fitness", ctypes.c_int32),
-                ("tile_inputs", ctypes.c_int32)]
+                ("tile_inputs", ctypes.c_int32), ("stack_registers", ctypes.c_int32)]
 
     def __repr__(self):
         return (f"Config(variant={self.variant}, k={self.k}, block={self.block}, "
                 f"chunk_cases={self.chunk_cases}, fitness={self.fitness}, "
-                f"tile_inputs={self.tile_inputs})")
+                f"tile_inputs={self.tile_inputs}, stack_registers={self.stack_registers})")
 
 
 _lib = None
@@ -379,7 +380,7 @@ class Server:
                  memory_budget=1 << 30, config: Optional[Config] = None):
         c = config or Config()
         opts = _ServerOpts(n_streams, max_inflight, max_queued, max_merge, memory_budget,
-                           c.variant, c.k, c.block, 0, c.fitness, c.tile_inputs)
+                           c.variant, c.k, c.block, 0, c.fitness, c.tile_inputs, c.stack_registers)
         self._h = ctypes.c_void_p()
         _check(lib().gp_server_create(ctypes.byref(opts), ctypes.byref(self._h)))
         self._results = {}  # request id -> (buffer, keep-alive)

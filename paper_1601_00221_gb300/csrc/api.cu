@@ -20,7 +20,7 @@ using namespace gpdev;
 namespace {
 
 std::mutex g_mu;
-gp_config g_default = {GP_VARIANT_REGISTER, 8, 128, 0, GP_FITNESS_SUM_ABS, 0};
+gp_config g_default = {GP_VARIANT_REGISTER, 8, 128, 0, GP_FITNESS_SUM_ABS, 0, 0};
 
 // Internal workspace of one (device, stream): per-block partial sums, the
 // per-program arrival counters of the fused reduction (zero between
@@ -127,7 +127,11 @@ int resolve_config(const gp_config* user, gp_config* c) {
     c->chunk_cases = user->chunk_cases;
     if (user->fitness) c->fitness = user->fitness;
     c->tile_inputs = user->tile_inputs;
+    c->stack_registers = user->stack_registers;
   }
+  if (c->stack_registers == gpisa::R) c->stack_registers = 0;
+  if (c->stack_registers != 0 && c->stack_registers != 4)
+    return gp_fail(GP_ERR_INVALID_ARG, "stack_registers must be 0, 4 or 8 (got %d)", c->stack_registers);
   if (c->tile_inputs < 0) return gp_fail(GP_ERR_INVALID_ARG, "negative tile_inputs");
   if (c->variant != GP_VARIANT_REGISTER && c->variant != GP_VARIANT_LOCAL &&
       c->variant != GP_VARIANT_AUTO && c->variant != GP_VARIANT_LANES &&
@@ -258,7 +262,11 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   a.tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
   const int grid = n_progs * n_chunks;
   const bool xreg = (n_inputs == 1);
-  const size_t smem = float_tile_bytes(c.k, c.block, a.tile_inputs);
+  const bool rl4 = c.stack_registers == 4;
+  if (rl4 && (c.k != 8 || c.variant != GP_VARIANT_REGISTER))
+    return gp_fail(GP_ERR_INVALID_ARG, "stack_registers = 4 needs k = 8 and the register variant");
+  const size_t smem = float_tile_bytes(c.k, c.block, a.tile_inputs) +
+                      (rl4 ? (size_t)(c.block / 32) * spill_bytes_per_warp<8, 4>() : 0);
   if (c.variant != GP_VARIANT_LOCAL && smem > kMaxTileBytes)
     return gp_fail(GP_ERR_INVALID_ARG,
                    "a tile of %d inputs needs %zu bytes of shared memory per block (max %zu): "
@@ -266,6 +274,7 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
                    a.tile_inputs, smem, kMaxTileBytes);
   cudaError_t e;
   if (c.variant == GP_VARIANT_LOCAL) e = launch_blockgp(a, c.block, grid, s);
+  else if (rl4) e = launch_float_k8_rl4(a, xreg, c.block, grid, smem, s);
   else if (c.variant == GP_VARIANT_EXTENDED) {
     if (c.k == 1) e = launch_floatx_k1(a, xreg, c.block, grid, smem, s);
     else if (c.k == 2) e = launch_floatx_k2(a, xreg, c.block, grid, smem, s);

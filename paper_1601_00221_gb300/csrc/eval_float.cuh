@@ -143,6 +143,26 @@ __device__ __forceinline__ bool run_tree(uint32_t prog, uint32_t n, const float 
   return bad == 0;
 }
 
+// S-form with stack levels 4..7 in shared memory (K = 8): `sbase` is this
+// lane's spill address (per warp [level][16-byte chunk][lane])
+#define GP_TREE_REG_SP(MAC, KK) \
+  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), GP_I##KK(x), "r"(sbase) : "memory")
+#define GP_TREE_SMEM_SP(MAC, KK) \
+  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile), "r"(sbase) : "memory")
+
+template <bool XREG>
+__device__ __forceinline__ bool run_tree_rl4(uint32_t prog, uint32_t n, const float (&x)[8], uint32_t tile,
+                                             uint32_t sbase, float (&o)[8]) {
+  uint32_t bad;
+  if constexpr (XREG) GP_TREE_REG_SP(GP_PTX_SFORM_K8_REG_RL4, 8);
+  else GP_TREE_SMEM_SP(GP_PTX_SFORM_K8_SMEM_RL4, 8);
+  return bad == 0;
+}
+
+// shared-memory bytes of the levels RL.. of one warp
+template <int K, int RL>
+__host__ __device__ constexpr int spill_bytes_per_warp() { return (gpisa::R - RL) * 4 * K * 32; }
+
 template <int K>
 __device__ __forceinline__ bool run_linear(uint32_t prog, uint32_t n, uint32_t tile, uint32_t nin,
                                            float (&o)[K]) {
@@ -320,9 +340,10 @@ __device__ __forceinline__ bool valid_instr_ext(const uint4& in, int n_inputs) {
 // program; each warp runs its own sequence of passes.
 // ---------------------------------------------------------------------------
 // EXT: the extended S-form interpreter (K_SFORM and K_SFORMX programs only).
+// RL < R: stack levels RL.. in shared memory (K = 8, RL = 4; K_SFORM only).
 // Up to 512 threads per block at 128 registers: the warps of an SM interpret
 // as few distinct programs as possible (every block holds one program).
-template <int K, bool XREG, bool EXT = false>
+template <int K, bool XREG, bool EXT = false, int RL = gpisa::R>
 __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
   using namespace gpisa;
   __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
@@ -348,8 +369,9 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
       const uint4 h = *reinterpret_cast<const uint4*>(a.programs + off);
       kind = (int)(h.x & 0xffu);
       const int n = (int)h.y;
-      const bool kind_ok = EXT ? (kind == K_SFORM || kind == K_SFORMX)
-                               : (kind == K_SFORM || kind == K_RPN || kind == K_LINEAR);
+      const bool kind_ok = EXT         ? (kind == K_SFORM || kind == K_SFORMX)
+                           : RL < R    ? kind == K_SFORM
+                                       : (kind == K_SFORM || kind == K_RPN || kind == K_LINEAR);
       const bool ver_ok = (h.x >> 16) == VERSION;
       const bool n_ok = n >= (kind == K_LINEAR ? 0 : 1) && n <= MAX_INSTR && 4 + 4 * (int64_t)n <= len;
       if (kind_ok && ver_ok && n_ok) n_instr = n;
@@ -463,6 +485,12 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
   // this lane's K staged values of slot v live at tile + v * 32 * K floats
   float* tile = reinterpret_cast<float*>(tile_s) + (size_t)warp * a.tile_inputs * 32 * K + lane * K;
   const uint32_t tile_addr = (uint32_t)__cvta_generic_to_shared(tile);
+  // levels RL.. of this lane, after the staged tiles
+  uint32_t sbase = 0;
+  if constexpr (RL < R)
+    sbase = (uint32_t)__cvta_generic_to_shared(tile_s) +
+            (uint32_t)(sizeof(float) * (size_t)nwarps * a.tile_inputs * 32 * K) +
+            (uint32_t)(warp * spill_bytes_per_warp<K, RL>() + lane * 16);
 
   if (!bad) {
 #pragma unroll 1
@@ -497,6 +525,9 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
       bool ok;
       if constexpr (EXT) {
         ok = run_tree_ext<K, XREG>(prog_addr, x, tile_addr, o);
+      } else if constexpr (RL < R) {
+        static_assert(K == 8 && RL == 4, "shared-memory levels are generated for K = 8, RL = 4");
+        ok = run_tree_rl4<XREG>(prog_addr, (uint32_t)n_instr, x, tile_addr, sbase, o);
       } else if (kind == K_LINEAR) {
         ok = run_linear<K>(prog_addr, (uint32_t)n_instr, tile_addr,
                            (uint32_t)(a.n_inputs < R ? a.n_inputs : R), o);

@@ -92,6 +92,7 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   int rc = gp_get_config(&c);
   if (rc) return rc;
   if (c.variant != GP_VARIANT_EXTENDED) c.variant = GP_VARIANT_REGISTER;
+  c.stack_registers = 0;  // every level in registers
 
   NoallocScratch* scratch = nullptr;
   rc = scratch_on_current_device(&scratch);

@@ -225,12 +225,17 @@ class FloatGen:
     entry is DONE, so the loop needs no bound check.  Codes are validated when
     the program is staged, so no code is clamped."""
 
-    def __init__(self, K, xmode):
-        assert K in (1, 2, 4, 8) and xmode in ("reg", "smem")
+    def __init__(self, K, xmode, rl=R):
+        assert K in (1, 2, 4, 8) and xmode in ("reg", "smem") and 1 <= rl <= R
         self.K, self.xmode = K, xmode
         self.H = 1 if K == 1 else K // 2   # register units per stack level
         self.b = Block()
         self.stride = 128 * K              # bytes between inputs in a lane's tile
+        # levels rl .. R-1 live in shared memory: per warp [level][chunk][lane]
+        # with 16-byte chunks (K >= 4), so a warp's access is conflict-free
+        self.rl = rl
+        self.chunk = min(16, 4 * K)        # bytes of one lane's chunk
+        self.nchunk = 4 * K // self.chunk  # chunks per lane per level
 
     # register unit names
     def lev(self, l, i):
@@ -246,7 +251,10 @@ class FloatGen:
     def header(self, extra_regs=""):
         K, H, b = self.K, self.H, self.b
         b("{")
-        b(f".reg .{self.ty} s<{R * H}>, ta<{H}>, tb<{H}>, xA<{H}>, xB<{H}>, cA, cB;")
+        b(f".reg .{self.ty} s<{self.rl * H}>, ta<{H}>, tb<{H}>, xA<{H}>, xB<{H}>, cA, cB;")
+        if self.rl < R:
+            b(f".reg .{self.ty} sA<{H}>, sB<{H}>;")
+            b(".reg .b32 sbase;")
         if self.xmode == "reg":
             b(f".reg .{self.ty} x<{H}>;")
         b(".reg .b32 code, pa, pb, pc, adr, dl, xa, xbase;")
@@ -262,8 +270,35 @@ class FloatGen:
         # be live from the kernel's entry and could not share a physical
         # register with the other interpreters of the same kernel.
         zero = "0f00000000" if K == 1 else "0"
-        for r in range(R * H):
+        for r in range(self.rl * H):
             b(f"mov.{self.ty} s{r}, {zero};")
+
+    # levels in shared memory (rl <= l < R)
+    def spill_off(self, l, q):
+        return ((l - self.rl) * self.nchunk + q) * 32 * self.chunk
+
+    def spill_load(self, l, dst):
+        b, K = self.b, self.K
+        for q in range(self.nchunk):
+            off = self.spill_off(l, q)
+            if K == 1:
+                b(f"ld.shared.f32 {dst[0]}, [sbase+{off}];")
+            elif K == 2:
+                b(f"ld.shared.b64 {dst[0]}, [sbase+{off}];")
+            else:
+                b(f"ld.shared.v2.b64 {{{dst[2 * q]}, {dst[2 * q + 1]}}}, [sbase+{off}];")
+        return dst
+
+    def spill_store(self, l, src):
+        b, K = self.b, self.K
+        for q in range(self.nchunk):
+            off = self.spill_off(l, q)
+            if K == 1:
+                b(f"st.shared.f32 [sbase+{off}], {src[0]};")
+            elif K == 2:
+                b(f"st.shared.b64 [sbase+{off}], {src[0]};")
+            else:
+                b(f"st.shared.v2.b64 [sbase+{off}], {{{src[2 * q]}, {src[2 * q + 1]}}};")
 
     def load_x(self, dst, payload):
         """Loads input `payload` (a b32 register) for this lane's K cases into
@@ -376,13 +411,19 @@ class FloatGen:
 
     # ------------------------------------------------------------------
     def sform(self):
+        """S-form interpreter.  With rl < R the levels rl.. are in shared
+        memory: a body loads a spilled operand into sA/sB and stores a spilled
+        result back (one more asm operand, the lane's spill address)."""
         K, H, b = self.K, self.H, self.b
         self.header()
+        rl = self.rl
         L = lambda l: [self.lev(l, i) for i in range(H)]
         ta = [f"ta{i}" for i in range(H)]
         tb = [f"tb{i}" for i in range(H)]
         xA = [f"xA{i}" for i in range(H)]
         xB = [f"xB{i}" for i in range(H)]
+        sA = [f"sA{i}" for i in range(H)]
+        sB = [f"sB{i}" for i in range(H)]
         n_codes = len(SF_FORMS) * R * 4
         table, bodies = {}, []
         for f, name in enumerate(SF_FORMS):
@@ -398,7 +439,10 @@ class FloatGen:
         self.table(n_codes, table)
         self.prologue()
         self.setup_inputs()
+        if rl < R:
+            b(f"mov.u32 sbase, %{self.sbase_operand()};")
         self.start()
+        opnd = lambda l, tmp: L(l) if l < rl else self.spill_load(l, tmp)
         for code, name, l, op in bodies:
             b(f"C{code}:")
             if name == "MOVX":
@@ -414,13 +458,13 @@ class FloatGen:
                 self.jump()
                 continue
             if name == "SS":
-                a, c = L(l), L(l + 1)
+                a, c = opnd(l, sA), opnd(l + 1, sB)
             elif name == "SSR":
-                a, c = L(l + 1), L(l)
+                a, c = opnd(l + 1, sA), opnd(l, sB)
             else:
                 ka, kb = name[0], name[1]
-                a = L(l) if ka == "S" else (self.load_x(xA, "pa") if ka == "X" else self.const("cA", "pa"))
-                c = L(l) if kb == "S" else (self.load_x(xB, "pb") if kb == "X" else self.const("cB", "pb"))
+                a = opnd(l, sA) if ka == "S" else (self.load_x(xA, "pa") if ka == "X" else self.const("cA", "pa"))
+                c = opnd(l, sB) if kb == "S" else (self.load_x(xB, "pb") if kb == "X" else self.const("cB", "pb"))
             if op == 3:
                 self.copy(ta, a)
                 self.copy(tb, c)
@@ -428,11 +472,26 @@ class FloatGen:
                 b(f"bra.uni DIV{l};")
             else:
                 self.fetch()
-                self.vop(op, L(l), a, c)
+                d = L(l) if l < rl else sA
+                self.vop(op, d, a, c)
+                if l >= rl:
+                    self.spill_store(l, d)
                 self.jump()
-        self.div_blocks_per_level(ta, tb, L)
+        for l in range(R):  # level l <- ta / tb (protected)
+            b(f"DIV{l}:")
+            q = L(l) if l < rl else ta
+            emit_pdiv(b, K, ta, tb, q, f"D{l}_")
+            if l >= rl:
+                self.spill_store(l, ta)
+            self.jump()
+            emit_pdiv_slow(b, K, ta, tb, f"D{l}_")
         self.epilogue(L(0))
         return b
+
+    def sbase_operand(self):
+        """Operand index of the lane's spill address (after the inputs)."""
+        K = self.K
+        return (2 * K + 3) if self.xmode == "reg" else (K + 4)
 
     def rpn(self):
         K, H, b = self.K, self.H, self.b
@@ -977,6 +1036,12 @@ def generate() -> str:
                 f"GP_PTX_RPN_K{K}_{X}", f"RPN interpreter, K={K}, inputs in {xm}"))
         parts.append(FloatGen(K, "smem").linear().macro(
             f"GP_PTX_LINEAR_K{K}", f"register linear-GP interpreter, K={K}"))
+        if K == 8:  # levels 4..7 in shared memory (the stack-register study)
+            for xm in ("reg", "smem"):
+                X = xm.upper()
+                parts.append(FloatGen(K, xm, rl=4).sform().macro(
+                    f"GP_PTX_SFORM_K{K}_{X}_RL4",
+                    f"S-form interpreter, K={K}, inputs in {xm}, levels 4..7 in shared memory"))
         for xm in ("reg", "smem"):
             X = xm.upper()
             g = FloatGenX(K, xm)

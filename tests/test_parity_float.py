@@ -220,3 +220,30 @@ def test_full_size_regression_sampled(k):
         out = gp.eval_outputs(Pp, Op, Lp, X, config=cfg).cpu().numpy()[0]
         assert_bits(out, oracle.tree_outputs(w.pop.program(int(p)), w.cases), f"program {p}")
     assert np.all(np.isfinite(f) | np.isinf(f))
+
+
+@pytest.mark.parametrize("n_inputs", [1, 3])
+def test_stack_levels_in_shared_memory(n_inputs):
+    """gp_config.stack_registers = 4 (levels 4..7 in shared memory): deep
+    S-form programs (full trees needing up to 7 levels) bit-exact; an RPN
+    program is refused by this kernel (malformed)."""
+    progs = synth.ramped_half_and_half(60 + n_inputs, 200, 2, 8, 255, n_inputs=n_inputs)
+    pop = synth.pack(progs)
+    x = synth.uniform_cases(61, n_inputs, 3001)
+    x[0, :3] = [0.0, -0.0, 1e-40]
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    assert enc.info["max_depth"].max() >= 6
+    P, O, L = upload(enc)
+    ref = np.stack([oracle.tree_outputs(pop.program(p), x) for p in range(pop.n)])
+    for block in (64, 256, 512):
+        out = gp.eval_outputs(P, O, L, dev(x), config=gp.Config(gp.VARIANT_REGISTER, 8, block, 0, 0, 0, 4))
+        assert_bits(out.cpu().numpy(), ref, f"block={block}")
+    assert gp.last_error() == 0
+    rpn = gp.encode_population(pop.words, pop.offsets, pop.lengths, gp.KIND_RPN)
+    P, O, L = upload(rpn)
+    y = dev(np.zeros(3001, np.float32))
+    f = gp.eval_population(P, O, L, dev(x), y, config=gp.Config(gp.VARIANT_REGISTER, 8, 256, 0, 0, 0, 4))
+    assert np.all(np.isnan(f.cpu().numpy()))
+    assert gp.last_error() == 2
+    with pytest.raises(gp.GPError):
+        gp.eval_population(P, O, L, dev(x), y, config=gp.Config(gp.VARIANT_REGISTER, 4, 256, 0, 0, 0, 4))

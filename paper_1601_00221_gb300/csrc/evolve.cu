@@ -575,8 +575,24 @@ extern "C" int gp_evolve_create(const gp_evolve_params* params, const uint32_t* 
     if (L < 1 || L > ev->slot || offsets[p] < 0)
       return evolve_fail(ev, gp_fail(GP_ERR_PROGRAM, "tree %d has %d words (1..%d allowed)", p, L, ev->slot));
     const uint32_t* t = words + offsets[p];
-    int nodes = 0;
-    for (int w = 0; w < L; w += ((t[w] & 0xffu) == GP_OP_CONST) ? 2 : 1) ++nodes;
+    // one well-formed tree of float functions (the variation kernel walks
+    // parents as prefix trees without further checks)
+    int nodes = 0, owed = 1, w = 0;
+    while (w < L && owed > 0) {
+      const uint32_t op = t[w] & 0xffu;
+      --owed;
+      ++nodes;
+      if (op == GP_OP_CONST) { w += 2; continue; }
+      if (op != GP_OP_VAR) {
+        const int ar = fn_arity(op);
+        if (ar < 0)
+          return evolve_fail(ev, gp_fail(GP_ERR_PROGRAM, "tree %d: opcode %u is not a float function", p, op));
+        owed += ar;
+      }
+      ++w;
+    }
+    if (owed != 0 || w != L)
+      return evolve_fail(ev, gp_fail(GP_ERR_PROGRAM, "tree %d is not one well-formed prefix tree", p));
     if (nodes > P.max_nodes)
       return evolve_fail(ev, gp_fail(GP_ERR_PROGRAM, "tree %d has %d nodes, more than max_nodes", p, nodes));
     memcpy(&h_words[(size_t)p * ev->slot], t, sizeof(uint32_t) * (size_t)L);

@@ -141,3 +141,22 @@ def test_regression_run_is_consistent():
     exp = oracle.population_fitness(pk.words, pk.offsets, pk.lengths, w.cases, w.targets)
     fin = np.isfinite(exp) & (exp != 0)
     assert np.all(np.abs(fit[fin] - exp[fin]) <= 1e-5 * np.abs(exp[fin]))
+
+
+def test_run_rejects_malformed_initial_trees():
+    import torch
+    good = np.array([synth.ADD, synth.tok(synth.VAR, 0), synth.tok(synth.VAR, 0)], np.uint32)
+    bad_sets = [
+        [synth.ADD, synth.tok(synth.VAR, 0)],                          # missing operand
+        [synth.tok(synth.VAR, 0), synth.tok(synth.VAR, 0)],            # trailing tokens
+        [synth.NAND, synth.tok(synth.VAR, 0), synth.tok(synth.VAR, 0)],  # not a float function
+        [synth.CONST],                                                # constant without its value
+    ]
+    x = dev(np.zeros((1, 8), np.float32))
+    y = dev(np.zeros(8, np.float32))
+    for bad in bad_sets:
+        pop = synth.pack([good, np.array(bad, np.uint32), good])
+        prm = gp.EvolveParams.make(3, list(synth.FLOAT_FUNCS), seed=1)
+        with pytest.raises(gp.GPError) as e:
+            gp.Evolver(prm, pop.words, pop.offsets, pop.lengths, x, y)
+        assert e.value.code == 2

@@ -183,15 +183,9 @@ extern "C" int gp_set_config(const gp_config* cfg) {
   gp_clear_error();
   if (!cfg) return gp_fail(GP_ERR_INVALID_ARG, "null config");
   gp_config c;
-  gp_config saved;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    saved = g_default;
-  }
   int rc = resolve_config(cfg, &c);
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  (void)saved;
   g_default = c;
   g_default.chunk_cases = 0;
   return GP_OK;

@@ -196,16 +196,18 @@ def test_fitness_bit_identical_across_runs_and_streams():
     assert np.array_equal(f0, f1.cpu().numpy())
 
 
-@pytest.mark.parametrize("k", [1, 8])
-def test_full_size_regression_sampled(k):
+@pytest.mark.parametrize("k,block,chunk", [(1, 128, 0), (8, 256, 16384), (8, 512, 0)])
+def test_full_size_regression_sampled(k, block, chunk):
     """4096 trees (depth 2-8, <= 256 nodes) x 65536 cases, the benchmark's
-    configuration; the oracle checks a sample of 48 programs entirely."""
+    workload, in the launch shape the benchmark times (K = 8, block 256,
+    16384 cases per block) and others; the oracle checks a sample of 48
+    programs entirely."""
     w = synth.regression_large()
     enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM,
                                gp.ORDER_MIN_DEPTH)
     P, O, L = upload(enc)
     X, Y = dev(w.cases), dev(w.targets)
-    cfg = gp.Config(gp.VARIANT_REGISTER, k, 128, 0)
+    cfg = gp.Config(gp.VARIANT_REGISTER, k, block, chunk)
     f = gp.eval_population(P, O, L, X, Y, config=cfg).cpu().numpy()
     rng = np.random.default_rng(5)
     sample = np.sort(rng.choice(w.pop.n, 48, replace=False))

@@ -313,3 +313,36 @@ def test_tree_reading_more_inputs_than_the_list_holds():
         exp = np.stack([oracle.tree_outputs(pop.program(p), x) for p in range(2)])
         assert_bits(out.cpu().numpy(), exp, f"k={k}")
     assert gp.last_error() == 0
+
+
+
+@pytest.mark.parametrize("name", ["sextic", "shuttle-like", "kdd-like"])
+def test_full_size_function_set_problems_sampled(name):
+    """The benchmark's function-set workloads at full size, in the launch
+    shapes it times (the population's own configuration); sampled trees are
+    checked case by case against the oracle's enclosures (bit for bit where no
+    transcendental function occurs), and their fitness too."""
+    make = {"sextic": synth.sextic_problem, "shuttle-like": synth.shuttle_like_problem,
+            "kdd-like": synth.kdd_like_problem}[name]
+    w = make()
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    k = 2 if name == "kdd-like" else 8
+    cfg = enc.config(fitness=w.fitness, k=k, block=256)
+    P, O, L = upload(enc)
+    X, Y = dev(w.cases), dev(w.targets)
+    f = gp.eval_population(P, O, L, X, Y, config=cfg).cpu().numpy()
+    sample = np.arange(0, w.pop.n, w.pop.n // 5)[:5]
+    import torch
+    out = gp.eval_outputs(P, O, L, X, config=cfg)[torch.from_numpy(sample).cuda()].cpu().numpy()
+    for i, p in enumerate(sample):
+        lo, hi, nan = oracle.fset_enclosure(w.pop.program(int(p)), w.cases)
+        assert_inside(out[i][None], lo[None], hi[None], nan[None], f"{name} program {p}")
+        f_lo, f_hi, may_inf, must_inf = oracle.fitness_enclosure(lo, hi, nan, w.targets, w.fitness)
+        g = float(f[p])
+        if g == np.inf:
+            assert may_inf
+        elif w.fitness == gp.FITNESS_CLASS:
+            assert f_lo <= g <= f_hi
+        else:
+            assert f_lo * (1 - REL_TOL) <= g <= f_hi * (1 + REL_TOL)
+    assert gp.last_error() == 0

@@ -594,6 +594,16 @@ def bench_function_sets(gp, synth, torch, device):
                 if best is None or ms < best[0]:
                     best = (ms, cfg)
         ms, cfg = best
+        # the one-dimensional stack (one case per thread per pass) on the same trees
+        one = None
+        for block in (128, 256):
+            c1 = enc.config(fitness=w.fitness, k=1, block=block)
+            try:
+                t1 = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit,
+                                                                    config=c1), steps=2, warmup=1)
+            except gp.GPError:
+                continue
+            one = t1 if one is None else min(one, t1)
         gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg)
         sample = np.arange(0, w.pop.n, w.pop.n // 4)[:4]
         outs = gp.eval_outputs(P, O, L, X, config=cfg)[torch.from_numpy(sample).to(device)]
@@ -602,6 +612,8 @@ def bench_function_sets(gp, synth, torch, device):
                        "fitness": ["sum_abs", "mse", "class_errors"][w.fitness],
                        "k": int(cfg.k), "block": int(cfg.block), "tile_inputs": int(cfg.tile_inputs),
                        "ms": round(ms, 3), "GPop_per_s": round(w.gpop / ms / 1e6, 1),
+                       "stack1d_GPop_per_s": round(w.gpop / one / 1e6, 1) if one else None,
+                       "speedup_2d_over_1d": round(one / ms, 3) if one else None,
                        "paper_best_GPop_per_s_context": PAPER_BEST[w.name]}
         data[w.name] = (w, sample, fit.cpu().numpy(), outs.cpu().numpy())
     return out, data

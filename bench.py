@@ -604,6 +604,19 @@ def bench_function_sets(gp, synth, torch, device):
             except gp.GPError:
                 continue
             one = t1 if one is None else min(one, t1)
+        # the same trees in the RPN form (the paper's other 2D-stack representation)
+        encr = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_RPN)
+        Pr, Or, Lr = encr.to_device(device)
+        rpn = None
+        for k in (4, 8):
+            cr = encr.config(fitness=w.fitness, k=k, block=int(cfg.block))
+            try:
+                tr = _time_events(torch, lambda: gp.eval_population(Pr, Or, Lr, X, Y, fitness_out=fit,
+                                                                    config=cr), steps=2, warmup=1)
+            except gp.GPError:
+                continue
+            rpn = tr if rpn is None else min(rpn, tr)
+        del Pr, Or, Lr
         gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg)
         sample = np.arange(0, w.pop.n, w.pop.n // 4)[:4]
         outs = gp.eval_outputs(P, O, L, X, config=cfg)[torch.from_numpy(sample).to(device)]
@@ -614,6 +627,8 @@ def bench_function_sets(gp, synth, torch, device):
                        "ms": round(ms, 3), "GPop_per_s": round(w.gpop / ms / 1e6, 1),
                        "stack1d_GPop_per_s": round(w.gpop / one / 1e6, 1) if one else None,
                        "speedup_2d_over_1d": round(one / ms, 3) if one else None,
+                       "rpn_GPop_per_s": round(w.gpop / rpn / 1e6, 1) if rpn else None,
+                       "sform_over_rpn": round(rpn / ms, 3) if rpn else None,
                        "paper_best_GPop_per_s_context": PAPER_BEST[w.name]}
         data[w.name] = (w, sample, fit.cpu().numpy(), outs.cpu().numpy())
     return out, data

@@ -71,8 +71,8 @@ typedef enum gp_status {
  *                  so a NaN operand gives 0.0f and -0 == +0.
  *   AND, OR        1.0f if a != 0 and (or) b != 0, else 0.0f; NaN != 0.
  *   IF(c, a, b)    a if c != 0, else b (NaN != 0 selects a).
- * A float tree that uses any of them needs GP_VARIANT_EXTENDED and the
- * S-form (gp_prog_info.extended tells).
+ * A float tree that uses any of them needs GP_VARIANT_EXTENDED (S-form) or
+ * GP_VARIANT_EXTENDED_RPN (RPN form); gp_prog_info.extended tells.
  * ---------------------------------------------------------------------- */
 enum {
   GP_OP_ADD = 1, GP_OP_SUB = 2, GP_OP_MUL = 3, GP_OP_DIV = 4,
@@ -89,8 +89,9 @@ typedef enum gp_kind {
   GP_KIND_RPN = 2,    /* postfix reverse-Polish form of a float tree (Sec. 4, 4.1) */
   GP_KIND_LINEAR = 3, /* register linear GP r[d] = r[a] op r[b], 8 registers */
   GP_KIND_BOOL = 4,   /* S-form of a bit-packed Boolean tree (Sec. 4.2) */
-  GP_KIND_SFORM_EXT = 5 /* written by the encoder, never requested: the S-form
-                           of a float tree that uses the extended functions */
+  GP_KIND_SFORM_EXT = 5, /* written by the encoder, never requested: the S-form
+                            of a float tree that uses the extended functions */
+  GP_KIND_RPN_EXT = 6    /* likewise, the RPN form of such a tree */
 } gp_kind;
 
 /* Evaluation order of the children of a tree node when it is encoded. */
@@ -127,9 +128,7 @@ typedef struct gp_prog_info {
  * GP_KIND_BOOL) with child order `order`.  `info` (may be NULL) receives the
  * counts.  Returns GP_ERR_PROGRAM for a malformed tree or one that needs more
  * than GP_STACK_LEVELS levels or GP_MAX_INSTR instructions, GP_ERR_INVALID_ARG
- * if `out` is too small (info->words still tells the size needed),
- * GP_ERR_NOT_IMPLEMENTED for an extended-function float tree requested as
- * GP_KIND_RPN (the extended functions are encoded in S-form only).
+ * if `out` is too small (info->words still tells the size needed).
  *
  * Encoded layout (uint32 words, every program a multiple of 4 words):
  *   header {kind | order<<8, n_instr, n_nodes, max_depth | (max_input+1)<<16}
@@ -175,8 +174,10 @@ typedef enum gp_variant {
                                (Sec. 3 prior art), GP_KIND_RPN programs only */
   GP_VARIANT_LANES = 3,     /* Boolean only: one program per lane over at most 4 words
                                (128 cases); GP_VARIANT_AUTO picks it for such case sets */
-  GP_VARIANT_EXTENDED = 4   /* the S-form interpreter with the extended float functions
+  GP_VARIANT_EXTENDED = 4,  /* the S-form interpreter with the extended float functions
                                (runs GP_KIND_SFORM and GP_KIND_SFORM_EXT programs) */
+  GP_VARIANT_EXTENDED_RPN = 5 /* the RPN interpreter with the extended float functions
+                               (runs GP_KIND_RPN and GP_KIND_RPN_EXT programs) */
 } gp_variant;
 
 /* Fitness measure of a float program (Sec. 4.2 parameter table: mean squared
@@ -210,8 +211,9 @@ typedef struct gp_config {
 /* ------------------------------------------------------------------------
  * Float fitness of a population (device pointers).
  *   programs     encoded words (gp_encode_*), GP_KIND_SFORM, GP_KIND_RPN or
- *                GP_KIND_LINEAR, any mix (GP_VARIANT_EXTENDED: GP_KIND_SFORM
- *                and GP_KIND_SFORM_EXT only); offsets[p] (int64, multiple of
+ *                GP_KIND_LINEAR, any mix (GP_VARIANT_EXTENDED: the S-form
+ *                kinds only, GP_VARIANT_EXTENDED_RPN the RPN ones); offsets[p]
+ *                (int64, multiple of
  *                4) and lengths[p] (int32) in words.
  *   cases        binary32 [n_inputs][n_cases], structure of arrays:
  *                input v of case c at cases[v * n_cases + c].
@@ -256,7 +258,7 @@ int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets, const int3
  * allocation failure, or the synchronisation an allocation can imply, in the
  * middle of a run.  It computes exactly what gp_eval_population computes
  * (same arguments, same kernel, default configuration: its variant, register
- * or extended, and its fitness measure) but keeps the kernel's
+ * or one of the extended ones, and its fitness measure) but keeps the kernel's
  * scratch (per-block partial sums, per-program counters, a status word) in a
  * fixed array of about 1.25 MiB that every device loading the library holds
  * until the process exits; it never calls cudaMalloc or cudaFree.

@@ -25,15 +25,17 @@ __all__ = [
     "eval_population", "eval_outputs", "eval_population_bool",
     "set_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
     "eval_population_noalloc", "autotune_population", "autotune_clear",
-    "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "ORDER_PAPER",
+    "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "KIND_RPN_EXT",
+    "ORDER_PAPER",
     "ORDER_MIN_DEPTH", "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL", "VARIANT_LANES",
-    "VARIANT_EXTENDED", "FITNESS_SUM_ABS", "FITNESS_MSE", "FITNESS_CLASS",
+    "VARIANT_EXTENDED", "VARIANT_EXTENDED_RPN", "FITNESS_SUM_ABS", "FITNESS_MSE", "FITNESS_CLASS",
     "encode_population_device", "EvolveParams", "Evolver",
 ]
 
-KIND_SFORM, KIND_RPN, KIND_LINEAR, KIND_BOOL, KIND_SFORM_EXT = 1, 2, 3, 4, 5
+KIND_SFORM, KIND_RPN, KIND_LINEAR, KIND_BOOL, KIND_SFORM_EXT, KIND_RPN_EXT = 1, 2, 3, 4, 5, 6
 ORDER_PAPER, ORDER_MIN_DEPTH = 0, 1
 VARIANT_AUTO, VARIANT_REGISTER, VARIANT_LOCAL, VARIANT_LANES, VARIANT_EXTENDED = 0, 1, 2, 3, 4
+VARIANT_EXTENDED_RPN = 5
 FITNESS_SUM_ABS, FITNESS_MSE, FITNESS_CLASS = 0, 1, 2
 STACK_LEVELS = 8
 MAX_INSTR = 1024
@@ -186,9 +188,10 @@ class EncodedPopulation:
     @property
     def extended(self) -> bool:
         """Some program uses the extended float functions (needs VARIANT_EXTENDED)."""
-        if self.kind != KIND_SFORM or self.n == 0:
+        if self.kind not in (KIND_SFORM, KIND_RPN) or self.n == 0:
             return False
-        return bool(np.any((self.words[self.offsets] & 0xFF) == KIND_SFORM_EXT))
+        kinds = self.words[self.offsets] & 0xFF
+        return bool(np.any((kinds == KIND_SFORM_EXT) | (kinds == KIND_RPN_EXT)))
 
     @property
     def max_inputs_used(self) -> int:
@@ -202,7 +205,9 @@ class EncodedPopulation:
         """A configuration that can run this population with the given fitness
         measure: the extended interpreter when some program needs it, and a
         staged-input tile no larger than the population needs."""
-        variant = VARIANT_EXTENDED if self.extended else VARIANT_AUTO
+        variant = VARIANT_AUTO
+        if self.extended:
+            variant = VARIANT_EXTENDED_RPN if self.kind == KIND_RPN else VARIANT_EXTENDED
         tile = max(self.max_inputs_used, 1) if self.kind in (KIND_SFORM, KIND_RPN) else 0
         return Config(variant, k, block, chunk_cases, fitness, tile)
 

@@ -135,7 +135,7 @@ int resolve_config(const gp_config* user, gp_config* c) {
   if (c->tile_inputs < 0) return gp_fail(GP_ERR_INVALID_ARG, "negative tile_inputs");
   if (c->variant != GP_VARIANT_REGISTER && c->variant != GP_VARIANT_LOCAL &&
       c->variant != GP_VARIANT_AUTO && c->variant != GP_VARIANT_LANES &&
-      c->variant != GP_VARIANT_EXTENDED)
+      c->variant != GP_VARIANT_EXTENDED && c->variant != GP_VARIANT_EXTENDED_RPN)
     return gp_fail(GP_ERR_INVALID_ARG, "unknown variant %d", c->variant);
   if (c->fitness != GP_FITNESS_SUM_ABS && c->fitness != GP_FITNESS_MSE && c->fitness != GP_FITNESS_CLASS)
     return gp_fail(GP_ERR_INVALID_ARG, "unknown fitness measure %d", c->fitness);
@@ -274,6 +274,11 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
     else if (c.k == 2) e = launch_floatx_k2(a, xreg, c.block, grid, smem, s);
     else if (c.k == 4) e = launch_floatx_k4(a, xreg, c.block, grid, smem, s);
     else e = launch_floatx_k8(a, xreg, c.block, grid, smem, s);
+  } else if (c.variant == GP_VARIANT_EXTENDED_RPN) {
+    if (c.k == 1) e = launch_floatrx_k1(a, xreg, c.block, grid, smem, s);
+    else if (c.k == 2) e = launch_floatrx_k2(a, xreg, c.block, grid, smem, s);
+    else if (c.k == 4) e = launch_floatrx_k4(a, xreg, c.block, grid, smem, s);
+    else e = launch_floatrx_k8(a, xreg, c.block, grid, smem, s);
   } else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, smem, s);
   else if (c.k == 2) e = launch_float_k2(a, xreg, c.block, grid, smem, s);
   else if (c.k == 4) e = launch_float_k4(a, xreg, c.block, grid, smem, s);
@@ -356,7 +361,8 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   gp_config c;
   int rc = resolve_config(cfg, &c);
   if (rc) return rc;
-  if (c.variant == GP_VARIANT_EXTENDED) c.variant = GP_VARIANT_REGISTER;  // a float-only choice
+  if (c.variant == GP_VARIANT_EXTENDED || c.variant == GP_VARIANT_EXTENDED_RPN)
+    c.variant = GP_VARIANT_REGISTER;  // a float-only choice
   if (c.variant != GP_VARIANT_REGISTER) return gp_fail(GP_ERR_INVALID_ARG, "Boolean programs use the register or per-lane variant");
   if (c.block > 256) c.block = 256;  // the Boolean kernel's block limit
   if (!cfg || !cfg->block) {  // small case sets: do not launch idle warps

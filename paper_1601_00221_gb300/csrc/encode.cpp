@@ -222,9 +222,20 @@ struct Emitter {
     int perm[3], np;
     child_order(nodes, n, order, true, perm, &np);
     for (int k = 0; k < np; ++k) rpn(n.child[perm[k]], l + k);
-    stack_reads += 2;
+    stack_reads += n.nchild;
+    if (n.nchild == 1) {  // SIN, COS, EXP, LOG on level l
+      put(rpx_un_code(l, (int)(n.op - GP_OP_SIN)), 0, 0, 0);
+      return;
+    }
+    if (n.nchild == 3) {  // float IF: its operands on levels l .. l+2 in evaluation order
+      int lvl[3];
+      for (int k = 0; k < 3; ++k) lvl[perm[k]] = k;
+      put(rpx_if_code(rpx_perm_index(lvl[0], lvl[1], lvl[2]), l), 0, 0, 0);
+      return;
+    }
     int form = (perm[0] == 0) ? RF_OP : RF_OPR;  // first argument on level l or l+1
-    put(rpn_code(form, l, (int)(n.op - GP_OP_ADD)), 0, 0, 0);
+    if (is_float_fn(n.op)) put(rpn_code(form, l, (int)(n.op - GP_OP_ADD)), 0, 0, 0);
+    else put(rpx_bin_code(form == RF_OP ? 0 : 1, l, xbin_index(n.op)), 0, 0, 0);
   }
 };
 
@@ -240,8 +251,6 @@ int encode_one(const uint32_t* prefix, int64_t n_words, int32_t kind, int32_t or
   int rc = parse_prefix(prefix, n_words, kind == K_BOOL, nodes, &max_input, &extended);
   if (rc) return rc;
   const bool rpn = (kind == K_RPN);
-  if (extended && rpn)
-    return gp_fail(GP_ERR_NOT_IMPLEMENTED, "the extended float functions are encoded in S-form only");
   compute_needs(nodes, order, rpn);
   Emitter em{nodes, order, (uint32_t)kind, {}, 0};
   em.ins.reserve(16 * nodes.size());
@@ -280,7 +289,7 @@ int encode_one(const uint32_t* prefix, int64_t n_words, int32_t kind, int32_t or
   if (n_instr > MAX_INSTR)
     return gp_fail(GP_ERR_PROGRAM, "program has %d instructions, more than %d", n_instr, MAX_INSTR);
   out.clear();
-  out.push_back(header0(extended ? (uint32_t)K_SFORMX : (uint32_t)kind, (uint32_t)order));
+  out.push_back(header0(extended ? (uint32_t)(rpn ? K_RPNX : K_SFORMX) : (uint32_t)kind, (uint32_t)order));
   out.push_back((uint32_t)n_instr);
   out.push_back((uint32_t)inf.n_nodes);
   out.push_back((uint32_t)depth | ((uint32_t)(max_input + 1) << 16));

@@ -79,7 +79,8 @@ __device__ __forceinline__ uint32_t input_fields(uint32_t kind, uint32_t code) {
       default: return 0u;
     }
   };
-  if (kind == K_RPN) return ((code >> 2) / R) == RF_PUSHX ? 1u : 0u;
+  if (kind == K_RPN || kind == K_RPNX)  // extended codes (>= RF_NCODES) read no input
+    return (code < (uint32_t)RF_NCODES && ((code >> 2) / R) == RF_PUSHX) ? 1u : 0u;
   if (code < (uint32_t)SF_NCODES) return bin((int)((code >> 2) / R));
   if (code < (uint32_t)SFX_UN_BASE) return bin(((int)code - SFX_BIN_BASE) / XB_NOPS / R);
   if (code < (uint32_t)SFX_IF_BASE) return ((int)code - SFX_UN_BASE) / XU_NOPS / R == UF_X ? 1u : 0u;
@@ -242,8 +243,11 @@ __device__ __forceinline__ void sfx_apply(uint32_t fn, typename SfxUnit<K>::type
 
 #define GP_SFX(K_, X_) \
   asm volatile(GP_PTX_SFORMX_K##K_##_##X_ : GP_SFX_OUT_K##K_##_##X_ : GP_SFX_IN_K##K_##_##X_ : "memory")
+#define GP_RPX(K_, X_) \
+  asm volatile(GP_PTX_RPNX_K##K_##_##X_ : GP_SFX_OUT_K##K_##_##X_ : GP_SFX_IN_K##K_##_##X_ : "memory")
 
-template <int K, bool XREG>
+// RPN: the (extended) RPN interpreter, else the (extended) S-form one
+template <int K, bool XREG, bool RPN>
 __device__ __forceinline__ bool run_tree_ext(uint32_t prog, const float (&x)[K], uint32_t tile,
                                              float (&o)[K]) {
   using U = typename SfxUnit<K>::type;
@@ -257,16 +261,30 @@ __device__ __forceinline__ bool run_tree_ext(uint32_t prog, const float (&x)[K],
   uint32_t adr = prog, st = 0;
 #pragma unroll 1
   for (;;) {
-    if constexpr (XREG) {
-      if constexpr (K == 1) GP_SFX(1, REG);
-      else if constexpr (K == 2) GP_SFX(2, REG);
-      else if constexpr (K == 4) GP_SFX(4, REG);
-      else GP_SFX(8, REG);
+    if constexpr (RPN) {
+      if constexpr (XREG) {
+        if constexpr (K == 1) GP_RPX(1, REG);
+        else if constexpr (K == 2) GP_RPX(2, REG);
+        else if constexpr (K == 4) GP_RPX(4, REG);
+        else GP_RPX(8, REG);
+      } else {
+        if constexpr (K == 1) GP_RPX(1, SMEM);
+        else if constexpr (K == 2) GP_RPX(2, SMEM);
+        else if constexpr (K == 4) GP_RPX(4, SMEM);
+        else GP_RPX(8, SMEM);
+      }
     } else {
-      if constexpr (K == 1) GP_SFX(1, SMEM);
-      else if constexpr (K == 2) GP_SFX(2, SMEM);
-      else if constexpr (K == 4) GP_SFX(4, SMEM);
-      else GP_SFX(8, SMEM);
+      if constexpr (XREG) {
+        if constexpr (K == 1) GP_SFX(1, REG);
+        else if constexpr (K == 2) GP_SFX(2, REG);
+        else if constexpr (K == 4) GP_SFX(4, REG);
+        else GP_SFX(8, REG);
+      } else {
+        if constexpr (K == 1) GP_SFX(1, SMEM);
+        else if constexpr (K == 2) GP_SFX(2, SMEM);
+        else if constexpr (K == 4) GP_SFX(4, SMEM);
+        else GP_SFX(8, SMEM);
+      }
     }
     if (st < SFX_EXIT) break;
     sfx_apply<K>((st - SFX_EXIT) >> 3, t);
@@ -305,10 +323,17 @@ __device__ __forceinline__ bool valid_instr(uint32_t kind, const uint4& in, int 
   return false;
 }
 
-// the extended S-form's codes (a superset of the basic S-form's)
-__device__ __forceinline__ bool valid_instr_ext(const uint4& in, int n_inputs) {
+// the extended S-form's or RPN's codes (supersets of the basic ones)
+__device__ __forceinline__ bool valid_instr_ext(uint32_t kind, const uint4& in, int n_inputs) {
   using namespace gpisa;
   const uint32_t nin = (uint32_t)n_inputs;
+  if (kind == K_RPN || kind == K_RPNX) {
+    if (in.x < (uint32_t)RF_NCODES) return valid_instr(K_RPN, in, n_inputs);
+    if (in.x >= (uint32_t)RPX_NCODES) return false;
+    if (in.x < (uint32_t)RPX_UN_BASE) return ((in.x - RPX_BIN_BASE) / XB_NOPS) % R + 1 < (uint32_t)R;
+    if (in.x < (uint32_t)RPX_IF_BASE) return true;
+    return (in.x - RPX_IF_BASE) % R + 2 < (uint32_t)R;
+  }
   if (in.x < (uint32_t)SF_NCODES) return valid_instr(K_SFORM, in, n_inputs);
   if (in.x >= (uint32_t)SFX_NCODES) return false;
   if (in.x < (uint32_t)SFX_UN_BASE) {
@@ -339,11 +364,14 @@ __device__ __forceinline__ bool valid_instr_ext(const uint4& in, int n_inputs) {
 // The kernel: block = (program p, chunk of cases).  Shared memory holds the
 // program; each warp runs its own sequence of passes.
 // ---------------------------------------------------------------------------
-// EXT: the extended S-form interpreter (K_SFORM and K_SFORMX programs only).
+// EXT: 0 the basic interpreters (S-form, RPN, register GP); 1 the extended
+// S-form (K_SFORM, K_SFORMX programs); 2 the extended RPN (K_RPN, K_RPNX).
+// One form per kernel: the two extended interpreters in one kernel cost the
+// S-form one 6-9% (measured).
 // RL < R: stack levels RL.. in shared memory (K = 8, RL = 4; K_SFORM only).
 // Up to 512 threads per block at 128 registers: the warps of an SM interpret
 // as few distinct programs as possible (every block holds one program).
-template <int K, bool XREG, bool EXT = false, int RL = gpisa::R>
+template <int K, bool XREG, int EXT = 0, int RL = gpisa::R>
 __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
   using namespace gpisa;
   __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
@@ -369,7 +397,8 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
       const uint4 h = *reinterpret_cast<const uint4*>(a.programs + off);
       kind = (int)(h.x & 0xffu);
       const int n = (int)h.y;
-      const bool kind_ok = EXT         ? (kind == K_SFORM || kind == K_SFORMX)
+      const bool kind_ok = EXT == 1    ? (kind == K_SFORM || kind == K_SFORMX)
+                           : EXT == 2  ? (kind == K_RPN || kind == K_RPNX)
                            : RL < R    ? kind == K_SFORM
                                        : (kind == K_SFORM || kind == K_RPN || kind == K_LINEAR);
       const bool ver_ok = (h.x >> 16) == VERSION;
@@ -389,12 +418,12 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
     for (int i = tid; i < n_instr; i += blockDim.x) {
       const uint4 in = g[i];
       prog_s[i] = in;
-      if constexpr (EXT) ok &= valid_instr_ext(in, a.n_inputs) ? 1 : 0;
+      if constexpr (EXT) ok &= valid_instr_ext(kind, in, a.n_inputs) ? 1 : 0;
       else ok &= valid_instr(kind, in, a.n_inputs) ? 1 : 0;
     }
     // the interpreters leave through the table entry one past the last code
     if (tid == 0)
-      prog_s[n_instr] = make_uint4(EXT ? SFX_NCODES
+      prog_s[n_instr] = make_uint4(EXT == 2 ? RPX_NCODES : EXT == 1 ? SFX_NCODES
                                        : kind == K_SFORM ? SF_NCODES
                                        : kind == K_RPN   ? RF_NCODES
                                                          : LIN_NCODES,
@@ -524,7 +553,7 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
       }
       bool ok;
       if constexpr (EXT) {
-        ok = run_tree_ext<K, XREG>(prog_addr, x, tile_addr, o);
+        ok = run_tree_ext<K, XREG, EXT == 2>(prog_addr, x, tile_addr, o);
       } else if constexpr (RL < R) {
         static_assert(K == 8 && RL == 4, "shared-memory levels are generated for K = 8, RL = 4");
         ok = run_tree_rl4<XREG>(prog_addr, (uint32_t)n_instr, x, tile_addr, sbase, o);

@@ -8,11 +8,11 @@ cudaError_t launch_floatx_k2(const FloatArgs& a, bool xreg, int block, int grid,
                              cudaStream_t s) {
   static std::atomic<size_t> set_reg{0}, set_smem{0};
   if (xreg) {
-    ensure_dynamic_smem(eval_float_kernel<2, true, true>, smem, set_reg);
-    eval_float_kernel<2, true, true><<<grid, block, smem, s>>>(a);
+    ensure_dynamic_smem(eval_float_kernel<2, true, 1>, smem, set_reg);
+    eval_float_kernel<2, true, 1><<<grid, block, smem, s>>>(a);
   } else {
-    ensure_dynamic_smem(eval_float_kernel<2, false, true>, smem, set_smem);
-    eval_float_kernel<2, false, true><<<grid, block, smem, s>>>(a);
+    ensure_dynamic_smem(eval_float_kernel<2, false, 1>, smem, set_smem);
+    eval_float_kernel<2, false, 1><<<grid, block, smem, s>>>(a);
   }
   return cudaGetLastError();
 }

@@ -24,7 +24,7 @@ constexpr int R = 8;            // stack levels held per case (GP_STACK_LEVELS)
 constexpr int MAX_INSTR = 1024; // GP_MAX_INSTR
 constexpr uint32_t VERSION = 1;
 
-enum Kind : uint32_t { K_SFORM = 1, K_RPN = 2, K_LINEAR = 3, K_BOOL = 4, K_SFORMX = 5 };
+enum Kind : uint32_t { K_SFORM = 1, K_RPN = 2, K_LINEAR = 3, K_BOOL = 4, K_SFORMX = 5, K_RPNX = 6 };
 
 // float function index = user opcode - 1 (ADD, SUB, MUL, DIV)
 enum FOp : int { F_ADD = 0, F_SUB = 1, F_MUL = 2, F_DIV = 3 };
@@ -99,6 +99,26 @@ constexpr int SFX_NCODES = SFX_IF_BASE + SFX_IF_FORMS * R;  // 1184
 enum RForm : int { RF_PUSHX = 0, RF_PUSHC, RF_OP, RF_OPR, RF_NFORMS };
 GPISA_HD constexpr int rpn_code(int form, int level, int op) { return (form * R + level) * 4 + op; }
 constexpr int RF_NCODES = RF_NFORMS * R * 4;
+
+// ---- extended float RPN (the function sets of Sec. 4.2 in postfix form):
+// the basic RPN codes first, then comparisons and logic (RF_OP: a = level l,
+// b = level l+1; RF_OPR: a = l+1, b = l), the unary functions on level l,
+// and IF(c, a, b) whose operands sit on levels l .. l+2 in one of the six
+// orders (permutation index: the levels of c, a, b as a permutation of
+// 0, 1, 2 in lexicographic order).  Every result goes to level l.
+constexpr int RPX_BIN_BASE = RF_NCODES;  // 128
+GPISA_HD constexpr int rpx_bin_code(int opr, int level, int op) {  // opr: 0 RF_OP, 1 RF_OPR
+  return RPX_BIN_BASE + (opr * R + level) * XB_NOPS + op;
+}
+constexpr int RPX_UN_BASE = RPX_BIN_BASE + 2 * R * XB_NOPS;  // 208
+GPISA_HD constexpr int rpx_un_code(int level, int fn) { return RPX_UN_BASE + level * XU_NOPS + fn; }
+constexpr int RPX_IF_BASE = RPX_UN_BASE + R * XU_NOPS;  // 240
+GPISA_HD constexpr int rpx_if_code(int perm, int level) { return RPX_IF_BASE + perm * R + level; }
+// permutation index of (level of c, level of a, level of b), each 0..2, distinct
+GPISA_HD constexpr int rpx_perm_index(int lc, int la, int lb) {
+  return lc * 2 + ((la > lb) ? 1 : 0);  // lc picks the first element; the rest in order or swapped
+}
+constexpr int RPX_NCODES = RPX_IF_BASE + 6 * R;  // 288
 
 // ---- register linear GP: code = (op, a, b); pa = destination register.
 constexpr int NREG = 8;

@@ -39,6 +39,15 @@ cudaError_t launch_floatx_k4(const FloatArgs& a, bool xreg, int block, int grid,
                              cudaStream_t s);
 cudaError_t launch_floatx_k8(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
                              cudaStream_t s);
+// The extended RPN interpreter, same shapes.
+cudaError_t launch_floatrx_k1(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                              cudaStream_t s);
+cudaError_t launch_floatrx_k2(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                              cudaStream_t s);
+cudaError_t launch_floatrx_k4(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                              cudaStream_t s);
+cudaError_t launch_floatrx_k8(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
+                              cudaStream_t s);
 // K = 8, stack levels 4..7 in shared memory (S-form only); smem includes them.
 cudaError_t launch_float_k8_rl4(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
                                 cudaStream_t s);

@@ -91,7 +91,8 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   gp_config c;
   int rc = gp_get_config(&c);
   if (rc) return rc;
-  if (c.variant != GP_VARIANT_EXTENDED) c.variant = GP_VARIANT_REGISTER;
+  if (c.variant != GP_VARIANT_EXTENDED && c.variant != GP_VARIANT_EXTENDED_RPN)
+    c.variant = GP_VARIANT_REGISTER;
   c.stack_registers = 0;  // every level in registers
 
   NoallocScratch* scratch = nullptr;
@@ -152,6 +153,11 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
     else if (c.k == 2) e = launch_floatx_k2(a, xreg, c.block, grid, smem, s);
     else if (c.k == 4) e = launch_floatx_k4(a, xreg, c.block, grid, smem, s);
     else e = launch_floatx_k8(a, xreg, c.block, grid, smem, s);
+  } else if (c.variant == GP_VARIANT_EXTENDED_RPN) {
+    if (c.k == 1) e = launch_floatrx_k1(a, xreg, c.block, grid, smem, s);
+    else if (c.k == 2) e = launch_floatrx_k2(a, xreg, c.block, grid, smem, s);
+    else if (c.k == 4) e = launch_floatrx_k4(a, xreg, c.block, grid, smem, s);
+    else e = launch_floatrx_k8(a, xreg, c.block, grid, smem, s);
   } else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, smem, s);
   else if (c.k == 2) e = launch_float_k2(a, xreg, c.block, grid, smem, s);
   else if (c.k == 4) e = launch_float_k4(a, xreg, c.block, grid, smem, s);

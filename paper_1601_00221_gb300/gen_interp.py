@@ -626,6 +626,13 @@ def xif_descs():
 
 
 SFX_NCODES = SFX_IF_BASE + 38 * R                  # 1184
+# extended RPN (csrc/isa.h)
+RPX_BIN_BASE = len(RF_FORMS) * R * 4               # 128
+RPX_UN_BASE = RPX_BIN_BASE + 2 * R * 5             # 208
+RPX_IF_BASE = RPX_UN_BASE + R * 4                  # 240
+RPX_NCODES = RPX_IF_BASE + 6 * R                   # 288
+# IF permutation index -> levels (relative to l) of c, a, b
+RPX_PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
 # exit status of the extended interpreter: 0 done, 1 bad code, else
 # XEXIT + fn * 8 + level (apply unary function fn to t, store to level)
 XEXIT = 16
@@ -867,6 +874,124 @@ class FloatGenX(FloatGen):
         b("}")
         return b
 
+    def rpn_ext(self):
+        """Extended RPN interpreter: the basic RPN bodies (pushes, +, -, *, /
+        on levels l and l+1), comparisons and logic, the unary functions on
+        level l (leaving the block as in sform_ext), IF on levels l .. l+2 in
+        the order its permutation index gives.  Same operands as sform_ext."""
+        K, H, b = self.K, self.H, self.b
+        b("{")
+        b(f".reg .{self.ty} ta<{H}>, tb<{H}>, cA;")
+        if self.xmode == "reg":
+            b(f".reg .{self.ty} x<{H}>;")
+        b(".reg .b32 code, pa, pb, pc, adr, dl, xa, xbase;")
+        b(".reg .f32 e<8>;")
+        b(".reg .pred p, q;")
+        for ln in pdiv_regs(K, H).split("\n"):
+            b(ln)
+        if K > 1:
+            b("mov.b64 one2, 0x3F8000003F800000;")
+        L = lambda l: [self.lev(l, i) for i in range(H)]
+        ta = [f"ta{i}" for i in range(H)]
+        tb = [f"tb{i}" for i in range(H)]
+        T = self.t()
+        table, bodies = {}, []
+        for f, name in enumerate(RF_FORMS):
+            for l in range(R):
+                for op in range(4):
+                    if name in ("PUSHX", "PUSHC") and op != 0:
+                        continue
+                    if name in ("OP", "OPR") and l + 1 >= R:
+                        continue
+                    code = rpn_code(f, l, op)
+                    table[code] = f"C{code}"
+                    bodies.append((code, "basic", name, l, op))
+        for opr in range(2):
+            for l in range(R - 1):
+                for op in range(len(XB_OPS)):
+                    code = RPX_BIN_BASE + (opr * R + l) * len(XB_OPS) + op
+                    table[code] = f"C{code}"
+                    bodies.append((code, "cmp", opr, l, op))
+        for l in range(R):
+            for fn in range(4):
+                code = RPX_UN_BASE + l * 4 + fn
+                table[code] = f"C{code}"
+                bodies.append((code, "un", None, l, fn))
+        for perm in range(6):
+            for l in range(R - 2):
+                code = RPX_IF_BASE + perm * R + l
+                table[code] = f"C{code}"
+                bodies.append((code, "if", perm, l, None))
+        self.table(RPX_NCODES, table)
+        b("RSTBL: .branchtargets " + ", ".join(f"RS{l}" for l in range(R)) + ";")
+        b(f"mov.u32 adr, %{self.o_adr};")
+        self.setup_inputs()
+        b(f"setp.lt.u32 p, %{self.o_st}, {XEXIT};")
+        b("@p bra.uni START;")
+        b(f"and.b32 dl, %{self.o_st}, 7;")
+        b("brx.idx.uni dl, RSTBL;")
+        for l in range(R):
+            b(f"RS{l}:")
+            self.copy(L(l), T)
+            b("bra.uni START;")
+        b("START:")
+        self.fetch()
+        b("LOOP:")
+        b("brx.idx.uni code, TBL;")
+        for code, kind, name, l, op in bodies:
+            b(f"C{code}:")
+            if kind == "un":
+                self.copy(T, L(l))
+                b(f"mov.u32 %{self.o_st}, {XEXIT + op * 8 + l};")
+                b("bra.uni EXIT;")
+                continue
+            if kind == "if":
+                lc, la, lb = RPX_PERMS[name]
+                self.fetch()
+                self.elementwise(L(l), [L(l + lc), L(l + la), L(l + lb)], self.if_emit())
+                self.jump()
+                continue
+            if kind == "cmp":
+                a, c = (L(l), L(l + 1)) if name == 0 else (L(l + 1), L(l))
+                self.fetch()
+                self.elementwise(L(l), [a, c], self.cmp_emit(XB_OPS[op]))
+                self.jump()
+                continue
+            if name == "PUSHX":
+                if self.xmode == "reg":
+                    self.fetch()
+                    self.copy(L(l), [self.xreg(i) for i in range(H)])
+                else:
+                    self.load_x(L(l), "pa")
+                    self.fetch()
+                self.jump()
+                continue
+            if name == "PUSHC":
+                src = self.const("cA", "pa")
+                self.fetch()
+                self.copy(L(l), src)
+                self.jump()
+                continue
+            a, c = (L(l), L(l + 1)) if name == "OP" else (L(l + 1), L(l))
+            self.fetch()
+            if op == 3:
+                self.copy(ta, a)
+                self.copy(tb, c)
+                b(f"bra.uni DIV{l};")
+            else:
+                self.vop(op, L(l), a, c)
+                self.jump()
+        self.div_blocks_per_level(ta, tb, L)
+        b("CBAD:")
+        b(f"mov.u32 %{self.o_st}, 1;")
+        b("bra.uni EXIT;")
+        b("DONE:")
+        b(f"mov.u32 %{self.o_st}, 0;")
+        b("EXIT:")
+        b(f"mov.u32 %{self.o_adr}, adr;")
+        b("}")
+        return b
+
     def operand_macros(self):
         """C++ operand lists of the asm statement (outputs and inputs)."""
         K, H = self.K, self.H
@@ -1047,6 +1172,8 @@ def generate() -> str:
             g = FloatGenX(K, xm)
             parts.append(g.sform_ext().macro(
                 f"GP_PTX_SFORMX_K{K}_{X}", f"extended S-form interpreter, K={K}, inputs in {xm}"))
+            parts.append(FloatGenX(K, xm).rpn_ext().macro(
+                f"GP_PTX_RPNX_K{K}_{X}", f"extended RPN interpreter, K={K}, inputs in {xm}"))
             outs, ins = g.operand_macros()
             parts.append(f"#define GP_SFX_OUT_K{K}_{X} {outs}\n#define GP_SFX_IN_K{K}_{X} {ins}\n")
         parts.append(BoolGen(K).gen().macro(f"GP_PTX_BOOL_K{K}", f"Boolean interpreter, K={K} words"))

@@ -58,6 +58,12 @@ def xif_descs():
 
 XIF_DESCS = xif_descs()
 
+# extended RPN codes (kind 6)
+RPX_BIN_BASE = len(RF_FORMS) * R * 4
+RPX_UN_BASE = RPX_BIN_BASE + 2 * R * 5
+RPX_IF_BASE = RPX_UN_BASE + R * 4
+RPX_PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
 
 def _unary_ref(fn, a):
     """A valid binary32 implementation: the value nearest the binary64 result."""
@@ -142,6 +148,20 @@ def run_float(words, x):
                 else:
                     a = S[lvl] if name[0] == "S" else (X(pa) if name[0] == "X" else C(pa))
                     b = S[lvl] if name[1] == "S" else (X(pb) if name[1] == "X" else C(pb))
+                S[lvl] = _xbin(xop, a, b)
+            continue
+        if h["kind"] == 6 and code >= RPX_BIN_BASE:
+            if code >= RPX_IF_BASE:
+                perm, lvl = (code - RPX_IF_BASE) // R, (code - RPX_IF_BASE) % R
+                lc, la, lb = RPX_PERMS[perm]
+                S[lvl] = np.where(S[lvl + lc] != 0, S[lvl + la], S[lvl + lb]).astype(np.float32)
+            elif code >= RPX_UN_BASE:
+                lvl, fn = (code - RPX_UN_BASE) // 4, (code - RPX_UN_BASE) % 4
+                S[lvl] = _unary_ref(fn, S[lvl])
+            else:
+                c = code - RPX_BIN_BASE
+                xop, lvl, opr = c % 5, (c // 5) % R, (c // 5) // R
+                a, b = (S[lvl], S[lvl + 1]) if opr == 0 else (S[lvl + 1], S[lvl])
                 S[lvl] = _xbin(xop, a, b)
             continue
         if h["kind"] in (1, 5):

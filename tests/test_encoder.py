@@ -280,11 +280,28 @@ def test_encoded_transcendental_programs_inside_enclosures():
         assert ok.all(), p.tolist()
 
 
-def test_extended_rpn_is_not_implemented_and_nand_is_rejected():
-    p = np.array([synth.SIN, synth.tok(synth.VAR, 0)], np.uint32)
-    with pytest.raises(gp.GPError) as e:
-        gp.encode_tree(p, gp.KIND_RPN)
-    assert e.value.code == 6
+@pytest.mark.parametrize("order", [gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH])
+def test_extended_rpn_matches_oracle(order):
+    """Extended functions in the RPN form: exact sets bit for bit, the full
+    set inside the oracle's enclosures."""
+    x = synth.uniform_cases(88, 3, 80, -3.0, 3.0)
+    x[:, :3] = np.array([0.0, -0.0, np.nan], np.float32)[None, :]
+    exact = synth.ramped_half_and_half(89, 120, 2, 6, 64, funcs=synth.SHUTTLE_FUNCS, n_inputs=3,
+                                       full_fallback_to_grow=True)
+    for p in exact:
+        words, _ = gp.encode_tree(p, gp.KIND_RPN, order)
+        assert (int(words[0]) & 0xFF) in (gp.KIND_RPN, gp.KIND_RPN_EXT)
+        assert same_bits(ref.run_float(words, x), oracle.fset_outputs(p, x)), p.tolist()
+    full = synth.ramped_half_and_half(90, 120, 2, 6, 64, funcs=synth.KDD_FUNCS, n_inputs=3,
+                                      full_fallback_to_grow=True)
+    for p in full:
+        words, _ = gp.encode_tree(p, gp.KIND_RPN, order)
+        got = ref.run_float(words, x)
+        lo, hi, nan = oracle.fset_enclosure(p, x)
+        assert np.where(np.isnan(got), nan, (lo <= got) & (got <= hi)).all(), p.tolist()
+
+
+def test_nand_is_rejected_in_float_trees():
     with pytest.raises(gp.GPError) as e:
         gp.encode_tree(np.array([synth.NAND, synth.tok(synth.VAR, 0), synth.tok(synth.VAR, 0)],
                                 np.uint32), gp.KIND_SFORM)

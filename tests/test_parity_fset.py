@@ -28,8 +28,9 @@ KS = [1, 2, 4, 8]
 FITS = [gp.FITNESS_SUM_ABS, gp.FITNESS_MSE, gp.FITNESS_CLASS]
 
 
-def ext_cfg(k, block=128, chunk=0, fitness=gp.FITNESS_SUM_ABS):
-    return gp.Config(gp.VARIANT_EXTENDED, k, block, chunk, fitness)
+def ext_cfg(k, block=128, chunk=0, fitness=gp.FITNESS_SUM_ABS, kind=gp.KIND_SFORM):
+    variant = gp.VARIANT_EXTENDED_RPN if kind == gp.KIND_RPN else gp.VARIANT_EXTENDED
+    return gp.Config(variant, k, block, chunk, fitness)
 
 
 def oracle_fset_outputs(pop, x):
@@ -83,14 +84,15 @@ def exact_set():
     return w, x, oracle_fset_outputs(w.pop, x)
 
 
+@pytest.mark.parametrize("kind", [gp.KIND_SFORM, gp.KIND_RPN])
 @pytest.mark.parametrize("k", KS)
-def test_exact_extended_programs_bit_exact(exact_set, k):
+def test_exact_extended_programs_bit_exact(exact_set, k, kind):
     w, x, ref = exact_set
-    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, kind)
     assert enc.extended
     P, O, L = upload(enc)
     for block in (64, 256):
-        out = gp.eval_outputs(P, O, L, dev(x), config=ext_cfg(k, block))
+        out = gp.eval_outputs(P, O, L, dev(x), config=ext_cfg(k, block, kind=kind))
         assert_bits(out.cpu().numpy(), ref, f"k={k} block={block}")
     assert gp.last_error() == 0
 
@@ -120,13 +122,14 @@ def trans_set():
     return pop, x, lo, hi, nan
 
 
+@pytest.mark.parametrize("kind", [gp.KIND_SFORM, gp.KIND_RPN])
 @pytest.mark.parametrize("k", KS)
-def test_transcendental_outputs_inside_enclosures(trans_set, k):
+def test_transcendental_outputs_inside_enclosures(trans_set, k, kind):
     pop, x, lo, hi, nan = trans_set
     assert tight_fraction(lo, hi) >= 0.8
-    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths, kind)
     P, O, L = upload(enc)
-    out = gp.eval_outputs(P, O, L, dev(x), config=ext_cfg(k)).cpu().numpy()
+    out = gp.eval_outputs(P, O, L, dev(x), config=ext_cfg(k, kind=kind)).cpu().numpy()
     assert_inside(out, lo, hi, nan, f"k={k}")
     assert gp.last_error() == 0
 
@@ -175,15 +178,16 @@ def test_unary_functions_within_documented_ulps(op, bound):
     assert _ulps(got[both], ref[both]).max() <= bound
 
 
-def test_basic_programs_identical_on_both_interpreters():
+@pytest.mark.parametrize("kind", [gp.KIND_SFORM, gp.KIND_RPN])
+def test_basic_programs_identical_on_both_interpreters(kind):
     w = synth.regression_small(seed=107, n_progs=128, n_cases=999)
-    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, kind)
     assert not enc.extended
     P, O, L = upload(enc)
     X = dev(w.cases)
     for k in KS:
         a = gp.eval_outputs(P, O, L, X, config=gp.Config(gp.VARIANT_REGISTER, k, 128, 0)).cpu().numpy()
-        b = gp.eval_outputs(P, O, L, X, config=ext_cfg(k)).cpu().numpy()
+        b = gp.eval_outputs(P, O, L, X, config=ext_cfg(k, kind=kind)).cpu().numpy()
         assert_bits(b, a, f"k={k}")
 
 
@@ -346,3 +350,17 @@ def test_full_size_function_set_problems_sampled(name):
         else:
             assert f_lo * (1 - REL_TOL) <= g <= f_hi * (1 + REL_TOL)
     assert gp.last_error() == 0
+
+
+
+def test_each_extended_kernel_runs_its_own_form(exact_set):
+    """The extended S-form kernel refuses RPN programs and the extended RPN
+    kernel S-form ones (malformed for that kernel, fitness NaN)."""
+    w, x, ref = exact_set
+    y = dev(w.targets)
+    for kind, wrong in ((gp.KIND_SFORM, gp.VARIANT_EXTENDED_RPN), (gp.KIND_RPN, gp.VARIANT_EXTENDED)):
+        enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, kind)
+        P, O, L = upload(enc)
+        f = gp.eval_population(P, O, L, dev(x), y, config=gp.Config(wrong, 4, 128, 0)).cpu().numpy()
+        assert np.isnan(f).all()
+        assert gp.last_error() == 2

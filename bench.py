@@ -616,6 +616,10 @@ def bench_function_sets(gp, synth, torch, device):
             except gp.GPError:
                 continue
             rpn = tr if rpn is None else min(rpn, tr)
+        # the BlockGP-style interpreter (the paper's baseline) on the RPN form
+        cb = gp.Config(gp.VARIANT_LOCAL, 1, 256, 0, w.fitness)
+        blockgp = _time_events(torch, lambda: gp.eval_population(Pr, Or, Lr, X, Y, fitness_out=fit,
+                                                                 config=cb), steps=1, warmup=1)
         del Pr, Or, Lr
         gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg)
         sample = np.arange(0, w.pop.n, w.pop.n // 4)[:4]
@@ -629,6 +633,8 @@ def bench_function_sets(gp, synth, torch, device):
                        "speedup_2d_over_1d": round(one / ms, 3) if one else None,
                        "rpn_GPop_per_s": round(w.gpop / rpn / 1e6, 1) if rpn else None,
                        "sform_over_rpn": round(rpn / ms, 3) if rpn else None,
+                       "blockgp_GPop_per_s": round(w.gpop / blockgp / 1e6, 1),
+                       "speedup_2d_over_blockgp": round(blockgp / ms, 3),
                        "paper_best_GPop_per_s_context": PAPER_BEST[w.name]}
         data[w.name] = (w, sample, fit.cpu().numpy(), outs.cpu().numpy())
     return out, data

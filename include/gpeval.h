@@ -171,7 +171,7 @@ typedef enum gp_variant {
   GP_VARIANT_AUTO = 0,      /* the tuned default for the workload */
   GP_VARIANT_REGISTER = 1,  /* stack levels in registers, K cases per thread */
   GP_VARIANT_LOCAL = 2,     /* BlockGP-style one-case-per-thread stack in local memory
-                               (Sec. 3 prior art), GP_KIND_RPN programs only */
+                               (Sec. 3 prior art), GP_KIND_RPN and GP_KIND_RPN_EXT programs */
   GP_VARIANT_LANES = 3,     /* Boolean only: one program per lane over at most 4 words
                                (128 cases); GP_VARIANT_AUTO picks it for such case sets */
   GP_VARIANT_EXTENDED = 4,  /* the S-form interpreter with the extended float functions

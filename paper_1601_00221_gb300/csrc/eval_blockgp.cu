@@ -2,8 +2,9 @@
 // (Sec. 3 and Sec. 4.1 prior art, Robilliard et al.): one block per program,
 // the program in shared memory, one fitness case per thread per pass, and a
 // per-thread stack array in local memory addressed by a run-time stack
-// pointer.  It interprets GP_KIND_RPN programs and ignores the static level
-// fields of their codes.  Kept as the paper's baseline design.
+// pointer.  It interprets GP_KIND_RPN programs, basic or with the extended
+// functions of Sec. 4.2 (GP_KIND_RPN_EXT), and ignores the static level fields
+// of their codes.  Kept as the paper's baseline design.
 #include "launch.h"
 
 namespace gpdev {
@@ -24,7 +25,8 @@ __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
     if ((off & 3) == 0 && len >= 4) {
       const uint4 h = *reinterpret_cast<const uint4*>(a.programs + off);
       const int n = (int)h.y;
-      if ((h.x & 0xffu) == K_RPN && (h.x >> 16) == VERSION && n >= 1 && n <= MAX_INSTR &&
+      if (((h.x & 0xffu) == K_RPN || (h.x & 0xffu) == K_RPNX) && (h.x >> 16) == VERSION && n >= 1 &&
+          n <= MAX_INSTR &&
           4 + 4 * (int64_t)n <= len)
         n_instr = n;
     }
@@ -39,7 +41,7 @@ __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
     for (int i = tid; i < n_instr; i += blockDim.x) {
       const uint4 in = g[i];
       prog_s[i] = in;
-      ok &= valid_instr(K_RPN, in, a.n_inputs) ? 1 : 0;
+      ok &= valid_instr_ext(K_RPNX, in, a.n_inputs) ? 1 : 0;
     }
     bad = !__syncthreads_and(ok);
   }
@@ -55,6 +57,41 @@ __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
       int sp = 0;
       for (int i = 0; i < n_instr && !bad; ++i) {
         const uint4 in = prog_s[i];
+        if (in.x >= (uint32_t)RF_NCODES) {  // the extended functions
+          if (in.x >= (uint32_t)RPX_IF_BASE) {  // IF: operands on the three top slots
+            if (sp < 3) { bad = true; break; }
+            const int perm = (int)(in.x - RPX_IF_BASE) / R;
+            const int lc = perm / 2, rest0 = (lc == 0) ? 1 : 0, rest1 = (lc == 2) ? 1 : 2;
+            const int la = (perm & 1) ? rest1 : rest0, lb = (perm & 1) ? rest0 : rest1;
+            const int base = sp - 3;
+            const float cv = stack[base + lc];
+            stack[base] = (cv != 0.0f) ? stack[base + la] : stack[base + lb];
+            sp -= 2;
+          } else if (in.x >= (uint32_t)RPX_UN_BASE) {
+            if (sp < 1) { bad = true; break; }
+            const int fn = (int)(in.x - RPX_UN_BASE) % XU_NOPS;
+            const float v = stack[sp - 1];
+            stack[sp - 1] = fn == XU_SIN ? sinf(v) : fn == XU_COS ? cosf(v) : fn == XU_EXP ? expf(v)
+                                                                              : protected_logf(v);
+          } else {
+            if (sp < 2) { bad = true; break; }
+            const int c = (int)(in.x - RPX_BIN_BASE), op = c % XB_NOPS, opr = (c / XB_NOPS) / R;
+            const float top = stack[--sp];
+            const float below = stack[sp - 1];
+            const float x = opr == 0 ? below : top;
+            const float y = opr == 0 ? top : below;
+            bool r;
+            switch (op) {
+              case XB_GT: r = x > y; break;
+              case XB_LT: r = x < y; break;
+              case XB_EQ: r = x == y; break;
+              case XB_AND: r = x != 0.0f && y != 0.0f; break;
+              default: r = x != 0.0f || y != 0.0f; break;
+            }
+            stack[sp - 1] = r ? 1.0f : 0.0f;
+          }
+          continue;
+        }
         const int form = (in.x >> 2) / R, op = in.x & 3;
         if (form == RF_PUSHX || form == RF_PUSHC) {
           if (sp >= GP_LOCAL_STACK) { bad = true; break; }

@@ -364,3 +364,20 @@ def test_each_extended_kernel_runs_its_own_form(exact_set):
         f = gp.eval_population(P, O, L, dev(x), y, config=gp.Config(wrong, 4, 128, 0)).cpu().numpy()
         assert np.isnan(f).all()
         assert gp.last_error() == 2
+
+
+
+def test_blockgp_runs_the_extended_functions(exact_set, trans_set):
+    """The BlockGP-style local-memory interpreter (the paper's baseline) on
+    extended RPN programs: exact sets bit for bit, the full set inside the
+    enclosures."""
+    cfg = gp.Config(gp.VARIANT_LOCAL, 1, 256, 0)
+    w, x, ref = exact_set
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_RPN)
+    P, O, L = upload(enc)
+    assert_bits(gp.eval_outputs(P, O, L, dev(x), config=cfg).cpu().numpy(), ref, "exact set")
+    pop, xt, lo, hi, nan = trans_set
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths, gp.KIND_RPN)
+    P, O, L = upload(enc)
+    assert_inside(gp.eval_outputs(P, O, L, dev(xt), config=cfg).cpu().numpy(), lo, hi, nan, "full set")
+    assert gp.last_error() == 0

@@ -84,12 +84,33 @@ def if_descs():
     return out
 
 
-# bounds of the fast division path: 2^-100 and 2^100 as binary32 bit patterns
-DIV_LO = "0f0D800000"
-DIV_HI = "0f71800000"
+# bounds of the fast division path on both operands: 2^-50 and 2^50 as binary32
+# bit patterns
+DIV_LO = "0f26800000"
+DIV_HI = "0f58800000"
 
 
-def emit_pdiv(b, K, A, B, Q, tag, group=2):
+def _reduce3(b, op, vals, out):
+    """out = op over vals (NaN-propagating), three operands per instruction."""
+    vals = list(vals)
+    n = 0
+    while len(vals) > 1:
+        nxt = []
+        for j in range(0, len(vals), 3):
+            g = vals[j:j + 3]
+            if len(g) == 1:
+                nxt.append(g[0])
+                continue
+            d = out if len(vals) <= 3 else f"{out}_{n}"
+            n += 1
+            b(f"{op}.NaN.f32 {d}, {', '.join(g)};")
+            nxt.append(d)
+        vals = nxt
+    if vals[0] != out:
+        b(f"mov.f32 {out}, {vals[0]};")
+
+
+def emit_pdiv(b, K, A, B, Q, tag, group=2, fold=None):
     """Protected division Q = (B == 0) ? 1 : A / B, correctly rounded, for the
     register units A, B, Q (K == 1: one f32 each; else b64 case pairs).
 
@@ -98,16 +119,32 @@ def emit_pdiv(b, K, A, B, Q, tag, group=2):
     exact remainder r = a - b q0 (one FMA) and Markstein's correction
     q1 = q0 + r y1 (P. Markstein, IBM J. Res. Dev. 34(1), 1990), in
     fma/mul.rn.f32x2, `group` pairs interleaved at a time.  The fast result
-    of a lane is kept when, over all its elements, min(|q1|, |a|) >= 2^-100
-    and max |q1| <= 2^100 (NaN-propagating min/max, so a NaN anywhere fails):
-    every intermediate value is then normal and each remainder exact.  Any
-    other lane (a zero, subnormal, huge or non-finite operand, a zero
-    denominator) takes the slow path: div.rn.f32 and the protection select
-    for each element.  The emit_pdiv_slow block must follow in the same asm
-    block.  Scratch registers come from pdiv_regs().  Q may name the same
-    registers as A: quotients stay in dQ until the end."""
+    of a lane is kept when every operand of the lane lies in
+    2^-50 <= |a|, |b| <= 2^50 (three-input NaN-propagating min and max, so a
+    NaN anywhere fails).  Inside that box every intermediate value is normal,
+    the remainder is exact and the quotient lies in [2^-100, 2^100], so the
+    sequence is a power-of-two scaling of the same sequence on the
+    significands in [1, 2), which is checked exhaustively.  The test reads
+    only the operands, so it runs beside the division chain rather than
+    after it, and the branch finds its predicate ready.  Any other lane (a
+    zero, subnormal, huge or non-finite operand, a zero denominator) takes
+    the slow path: div.rn.f32 and the protection select for each element.
+
+    Without `fold` the slow path is a per-lane branch to the emit_pdiv_slow
+    block, which must follow in the same asm block; Q may then name the same
+    registers as A (quotients stay in dQ until the end).  With `fold` the
+    decision is made once per warp: a vote sets `dall` when every lane passed,
+    the fast quotients are written to Q, and fold() emits what the caller does
+    when `dall` is false (the interpreters redirect their dispatch to an
+    emit_pdiv_slow_body block, which recomputes every element exactly, so no
+    branch sits in the division's own path).  Q must then not overlap A or B.
+    Scratch registers come from pdiv_regs()."""
     H = len(A)
     if K == 1:
+        b(f"abs.f32 dt, {A[0]};")
+        b(f"abs.f32 dt2, {B[0]};")
+        b("min.NaN.f32 dlo, dt, dt2;")
+        b("max.NaN.f32 dhi, dt, dt2;")
         b(f"rcp.approx.ftz.f32 dY0, {B[0]};")
         b(f"neg.f32 dN0, {B[0]};")
         b("fma.rn.f32 dE0, dN0, dY0, 0f3F800000;")
@@ -115,10 +152,17 @@ def emit_pdiv(b, K, A, B, Q, tag, group=2):
         b(f"mul.rn.f32 dQ0, {A[0]}, dY0;")
         b(f"fma.rn.f32 dE0, dN0, dQ0, {A[0]};")
         b("fma.rn.f32 dQ0, dE0, dY0, dQ0;")
-        b("abs.f32 dhi, dQ0;")
-        b(f"abs.f32 dt, {A[0]};")
-        b("min.NaN.f32 dlo, dhi, dt;")
     else:
+        # the operand test: |a| and |b| of every element, min and max trees
+        mags = []
+        for i in range(H):
+            for src, nm in ((A[i], "dma"), (B[i], "dmb")):
+                b(f"mov.b64 {{{nm}{2 * i}, {nm}{2 * i + 1}}}, {src};")
+                b(f"abs.f32 {nm}{2 * i}, {nm}{2 * i};")
+                b(f"abs.f32 {nm}{2 * i + 1}, {nm}{2 * i + 1};")
+                mags += [f"{nm}{2 * i}", f"{nm}{2 * i + 1}"]
+        _reduce3(b, "min", mags, "dlo")
+        _reduce3(b, "max", mags, "dhi")
         for g0 in range(0, H, group):
             idx = list(range(g0, min(H, g0 + group)))
             for i in idx:
@@ -137,37 +181,20 @@ def emit_pdiv(b, K, A, B, Q, tag, group=2):
                 b(f"fma.rn.f32x2 dE{i}, dN{i}, dQ{i}, {A[i]};")
             for i in idx:
                 b(f"fma.rn.f32x2 dQ{i}, dE{i}, dY{i}, dQ{i};")
-        # per pair: lo = min(|q0|, |q1|, |a0|, |a1|), hi = max(|q0|, |q1|);
-        # then a tree over the pairs (a short dependency chain)
-        for i in range(H):
-            b(f"mov.b64 {{dt, dt2}}, dQ{i};")
-            b("abs.f32 dt, dt;")
-            b("abs.f32 dt2, dt2;")
-            b(f"max.NaN.f32 dh{i}, dt, dt2;")
-            b(f"min.NaN.f32 dl{i}, dt, dt2;")
-            b(f"mov.b64 {{dt, dt2}}, {A[i]};")
-            b("abs.f32 dt, dt;")
-            b("abs.f32 dt2, dt2;")
-            b("min.NaN.f32 dt, dt, dt2;")
-            b(f"min.NaN.f32 dl{i}, dl{i}, dt;")
-        w = H
-        while w > 1:
-            half = (w + 1) // 2
-            for i in range(w // 2):
-                b(f"min.NaN.f32 dl{i}, dl{i}, dl{i + half};")
-                b(f"max.NaN.f32 dh{i}, dh{i}, dh{i + half};")
-            w = half
-        b("mov.f32 dlo, dl0;")
-        b("mov.f32 dhi, dh0;")
     b(f"setp.ge.f32 dok, dlo, {DIV_LO};")
     b(f"setp.le.and.f32 dok, dhi, {DIV_HI}, dok;")
-    b(f"@!dok bra {tag}SLOW;")
-    b(f"{tag}RET:")
+    if fold is None:
+        b(f"@!dok bra {tag}SLOW;")
+        b(f"{tag}RET:")
+    else:
+        b("vote.sync.all.pred dall, dok, 0xffffffff;")
     if K == 1:
         b(f"mov.f32 {Q[0]}, dQ0;")
     else:
         for i in range(H):
             b(f"mov.b64 {Q[i]}, dQ{i};")
+    if fold is not None:
+        fold()
 
 
 def emit_pdiv_slow(b, K, A, B, tag):
@@ -192,11 +219,34 @@ def emit_pdiv_slow(b, K, A, B, tag):
     b(f"bra {tag}RET;")
 
 
+def emit_pdiv_slow_body(b, K, A, B, Q, tag):
+    """The slow path of a folded emit_pdiv as a block of its own (label
+    {tag}SLOW): IEEE division and the protection select of every element of
+    A / B, written into Q.  The caller continues the dispatch after it."""
+    b(f"{tag}SLOW:")
+    if K == 1:
+        b(f"div.rn.f32 {Q[0]}, {A[0]}, {B[0]};")
+        b(f"setp.eq.f32 dz, {B[0]}, 0f00000000;")
+        b(f"selp.f32 {Q[0]}, 0f3F800000, {Q[0]}, dz;")
+        return
+    for i in range(len(A)):
+        b(f"mov.b64 {{dlo, dhi}}, {A[i]};")
+        b(f"mov.b64 {{dt, dt2}}, {B[i]};")
+        b("div.rn.f32 dlo, dlo, dt;")
+        b("setp.eq.f32 dz, dt, 0f00000000;")
+        b("selp.f32 dlo, 0f3F800000, dlo, dz;")
+        b("div.rn.f32 dhi, dhi, dt2;")
+        b("setp.eq.f32 dz, dt2, 0f00000000;")
+        b("selp.f32 dhi, 0f3F800000, dhi, dz;")
+        b(f"mov.b64 {Q[i]}, {{dlo, dhi}};")
+
+
 def pdiv_regs(K, H):
     ty = "f32" if K == 1 else "b64"
+    n = 2 * H
     return (f".reg .{ty} dY<{H}>, dE<{H}>, dN<{H}>, dQ<{H}>, one2;\n"
-            f".reg .f32 dlo, dhi, dt, dt2, dl<{H}>, dh<{H}>;\n"
-            f".reg .pred dok, dz;")
+            f".reg .f32 dlo, dhi, dt, dt2, dma<{n}>, dmb<{n}>, dlo_<{n}>, dhi_<{n}>;\n"
+            f".reg .pred dok, dz, dall;")
 
 
 
@@ -236,6 +286,9 @@ class FloatGen:
         self.rl = rl
         self.chunk = min(16, 4 * K)        # bytes of one lane's chunk
         self.nchunk = 4 * K // self.chunk  # chunks per lane per level
+        # division's slow path: decided once per warp and taken through the
+        # dispatch (fold_to_slow), or a per-lane branch
+        self.fold_div = True
 
     # register unit names
     def lev(self, l, i):
@@ -345,9 +398,38 @@ class FloatGen:
     def jump(self):
         self.b("bra.uni LOOP;")
 
-    def table(self, n_codes, table):
+    def table(self, n_codes, table, slow_levels=()):
+        """The dispatch table TBL: the codes, then the sentinel (n_codes,
+        DONE).  With slow_levels, a second table TBLD for the DIV blocks' own
+        dispatch adds one entry per stack level, the folded division's slow
+        body (n_codes + 1 + l).  A separate dispatch site keeps the division
+        operands live only from a DIV block to its slow body: through the
+        common site they would be live across every body of the loop."""
+        self.n_codes = n_codes
         labels = [table.get(c, "CBAD") for c in range(n_codes)] + ["DONE"]
         self.b("TBL: .branchtargets " + ", ".join(labels) + ";")
+        if slow_levels:
+            labels += [f"D{l}_SLOW" if l in slow_levels else "CBAD" for l in range(R)]
+            self.b("TBLD: .branchtargets " + ", ".join(labels) + ";")
+
+    def div_jump(self):
+        """Dispatch after a folded division (the table with slow bodies)."""
+        self.b("brx.idx.uni code, TBLD;")
+
+    def fold_to_slow(self, l):
+        """fold() of a level-l division: when not every lane took the fast
+        path, dispatch to the level's slow body instead of the next code."""
+        def emit():
+            self.b(f"@!dall mov.u32 code, {self.n_codes + 1 + l};")
+        return emit
+
+    def slow_bodies(self, ta, tb, units_of_level, levels):
+        """The slow bodies reload the next code from the instruction just
+        fetched (adr was advanced past it) and dispatch it."""
+        for l in levels:
+            emit_pdiv_slow_body(self.b, self.K, ta, tb, units_of_level(l), f"D{l}_")
+            self.b("ld.shared.u32 code, [adr+-16];")
+            self.jump()
 
     def prologue(self):
         K, b = self.K, self.b
@@ -405,9 +487,15 @@ class FloatGen:
         straight into the level's registers (no store jump, no copy back)."""
         for l in range(R):
             self.b(f"DIV{l}:")
-            emit_pdiv(self.b, self.K, ta, tb, units_of_level(l), f"D{l}_")
-            self.jump()
-            emit_pdiv_slow(self.b, self.K, ta, tb, f"D{l}_")
+            if self.fold_div:
+                emit_pdiv(self.b, self.K, ta, tb, units_of_level(l), f"D{l}_", fold=self.fold_to_slow(l))
+                self.div_jump()
+            else:
+                emit_pdiv(self.b, self.K, ta, tb, units_of_level(l), f"D{l}_")
+                self.jump()
+                emit_pdiv_slow(self.b, self.K, ta, tb, f"D{l}_")
+        if self.fold_div:
+            self.slow_bodies(ta, tb, units_of_level, range(R))
 
     # ------------------------------------------------------------------
     def sform(self):
@@ -436,7 +524,7 @@ class FloatGen:
                     code = sform_code(f, l, op)
                     table[code] = f"C{code}"
                     bodies.append((code, name, l, op))
-        self.table(n_codes, table)
+        self.table(n_codes, table, slow_levels=range(rl))
         self.prologue()
         self.setup_inputs()
         if rl < R:
@@ -479,12 +567,15 @@ class FloatGen:
                 self.jump()
         for l in range(R):  # level l <- ta / tb (protected)
             b(f"DIV{l}:")
-            q = L(l) if l < rl else ta
-            emit_pdiv(b, K, ta, tb, q, f"D{l}_")
-            if l >= rl:
-                self.spill_store(l, ta)
+            if l < rl:
+                emit_pdiv(b, K, ta, tb, L(l), f"D{l}_", fold=self.fold_to_slow(l))
+                self.div_jump()
+                continue
+            emit_pdiv(b, K, ta, tb, ta, f"D{l}_")
+            self.spill_store(l, ta)
             self.jump()
             emit_pdiv_slow(b, K, ta, tb, f"D{l}_")
+        self.slow_bodies(ta, tb, L, range(rl))
         self.epilogue(L(0))
         return b
 
@@ -511,7 +602,7 @@ class FloatGen:
                     code = rpn_code(f, l, op)
                     table[code] = f"C{code}"
                     bodies.append((code, name, l, op))
-        self.table(n_codes, table)
+        self.table(n_codes, table, slow_levels=range(R))
         self.prologue()
         self.setup_inputs()
         self.start()
@@ -656,6 +747,9 @@ class FloatGenX(FloatGen):
 
     def __init__(self, K, xmode):
         super().__init__(K, xmode)
+        # the per-lane branch: measured 2-3% faster here than the folded
+        # form, which costs these larger interpreters registers
+        self.fold_div = False
         self.RH = R * self.H
         self.o_adr = self.RH + self.H
         self.o_st = self.RH + self.H + 1
@@ -1117,31 +1211,43 @@ class BoolGen:
         return b
 
 
-def pdiv_macro(K):
+def pdiv_macro(K, fold=True):
     """Standalone protected division of K values (exactly the interpreters'
     sequence), for the division checker: K == 1 operands %0 = q, %1 = a,
     %2 = b (f32); K == 4 operands %0, %1 = q pairs, %2, %3 = a pairs,
-    %4, %5 = b pairs (b64)."""
+    %4, %5 = b pairs (b64).  fold: the slow path decided once per warp (the
+    basic interpreters), else by a per-lane branch (the extended ones)."""
     b = Block()
     H = 1 if K == 1 else K // 2
     b("{")
     for ln in pdiv_regs(K, H).split("\n"):
         b(ln)
     ty = "f32" if K == 1 else "b64"
-    b(f".reg .{ty} qa<{H}>, qb<{H}>;")
+    b(f".reg .{ty} qa<{H}>, qb<{H}>, qq<{H}>;")
     if K > 1:
         b("mov.b64 one2, 0x3F8000003F800000;")
     for i in range(H):
         b(f"mov.{ty} qa{i}, %{H + i};")
         b(f"mov.{ty} qb{i}, %{2 * H + i};")
-    # the quotient overwrites the numerator registers, as in the interpreters
     qa = [f"qa{i}" for i in range(H)]
     qb = [f"qb{i}" for i in range(H)]
-    emit_pdiv(b, K, qa, qb, qa, "P")
-    for i in range(H):
-        b(f"mov.{ty} %{i}, qa{i};")
-    b("bra.uni PEND;")
-    emit_pdiv_slow(b, K, qa, qb, "P")
+    qq = [f"qq{i}" for i in range(H)]
+    if fold:
+        # one decision per warp, the slow body recomputing every element
+        emit_pdiv(b, K, qa, qb, qq, "P", fold=lambda: b("@!dall bra.uni PSLOW;"))
+        b("PRET:")
+        for i in range(H):
+            b(f"mov.{ty} %{i}, qq{i};")
+        b("bra.uni PEND;")
+        emit_pdiv_slow_body(b, K, qa, qb, qq, "P")
+        b("bra.uni PRET;")
+    else:
+        # the quotient overwrites the numerator registers, as in the interpreters
+        emit_pdiv(b, K, qa, qb, qa, "P")
+        for i in range(H):
+            b(f"mov.{ty} %{i}, qa{i};")
+        b("bra.uni PEND;")
+        emit_pdiv_slow(b, K, qa, qb, "P")
     b("PEND:")
     b("}")
     return b
@@ -1150,8 +1256,11 @@ def pdiv_macro(K):
 def generate() -> str:
     parts = ["// gen_interp.h -- generated by paper_1601_00221_gb300/gen_interp.py; do not edit.\n",
              "#pragma once\n"]
-    parts.append(pdiv_macro(1).macro("GP_PTX_PDIV_K1", "protected division, one value"))
-    parts.append(pdiv_macro(4).macro("GP_PTX_PDIV_K4", "protected division, two packed pairs"))
+    parts.append(pdiv_macro(1).macro("GP_PTX_PDIV_K1", "protected division, one value, warp decision"))
+    parts.append(pdiv_macro(4).macro("GP_PTX_PDIV_K4", "protected division, two packed pairs, warp decision"))
+    parts.append(pdiv_macro(1, False).macro("GP_PTX_PDIV_LANE_K1", "protected division, one value, lane branch"))
+    parts.append(pdiv_macro(4, False).macro("GP_PTX_PDIV_LANE_K4",
+                                            "protected division, two packed pairs, lane branch"))
     for K in (1, 2, 4, 8):
         for xm in ("reg", "smem"):
             X = xm.upper()

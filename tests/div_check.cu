@@ -1,7 +1,10 @@
 // div_check.cu -- checks the library's protected division (the generated PTX
-// sequence GP_PTX_PDIV_K4 / GP_PTX_PDIV_K1, the same code the interpreters
-// run) against CUDA's correctly rounded division: q == (b == 0 ? 1 : a / b)
-// bit for bit, any NaN equal to any NaN.  Test tool, built by
+// sequences GP_PTX_PDIV_K4 / GP_PTX_PDIV_K1 with the slow path decided per
+// warp, as the basic interpreters run it, and GP_PTX_PDIV_LANE_K4 /
+// GP_PTX_PDIV_LANE_K1 with a per-lane branch, as the extended ones do)
+// against CUDA's correctly rounded division: q == (b == 0 ? 1 : a / b) bit
+// for bit, any NaN equal to any NaN.  Every lane of a warp runs the same
+// sequence of calls, as the warp decision requires.  Test tool, built by
 // tests/test_division.py.
 //
 // Modes (argv[1]):
@@ -41,6 +44,7 @@ __device__ __forceinline__ void report(float a, float b, float q) {
   }
 }
 
+template <bool LANE>
 __device__ __forceinline__ void pdiv4(const float (&a)[4], const float (&b)[4], float (&q)[4]) {
   unsigned long long a0, a1, b0, b1, q0, q1;
   float2 t;
@@ -48,26 +52,41 @@ __device__ __forceinline__ void pdiv4(const float (&a)[4], const float (&b)[4], 
   t = make_float2(a[2], a[3]); a1 = *reinterpret_cast<unsigned long long*>(&t);
   t = make_float2(b[0], b[1]); b0 = *reinterpret_cast<unsigned long long*>(&t);
   t = make_float2(b[2], b[3]); b1 = *reinterpret_cast<unsigned long long*>(&t);
-  asm volatile(GP_PTX_PDIV_K4 : "=l"(q0), "=l"(q1) : "l"(a0), "l"(a1), "l"(b0), "l"(b1));
+  if constexpr (LANE)
+    asm volatile(GP_PTX_PDIV_LANE_K4 : "=l"(q0), "=l"(q1) : "l"(a0), "l"(a1), "l"(b0), "l"(b1));
+  else
+    asm volatile(GP_PTX_PDIV_K4 : "=l"(q0), "=l"(q1) : "l"(a0), "l"(a1), "l"(b0), "l"(b1));
   t = *reinterpret_cast<float2*>(&q0); q[0] = t.x; q[1] = t.y;
   t = *reinterpret_cast<float2*>(&q1); q[2] = t.x; q[3] = t.y;
 }
 
+template <bool LANE>
 __device__ __forceinline__ float pdiv1(float a, float b) {
   float q;
-  asm volatile(GP_PTX_PDIV_K1 : "=f"(q) : "f"(a), "f"(b));
+  if constexpr (LANE)
+    asm volatile(GP_PTX_PDIV_LANE_K1 : "=f"(q) : "f"(a), "f"(b));
+  else
+    asm volatile(GP_PTX_PDIV_K1 : "=f"(q) : "f"(a), "f"(b));
   return q;
 }
 
 __device__ __forceinline__ void check4(const float (&a)[4], const float (&b)[4]) {
-  float q[4];
-  pdiv4(a, b, q);
+  float q[4], p[4];
+  pdiv4<false>(a, b, q);
+  pdiv4<true>(a, b, p);
+  float s[4], u[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    s[j] = pdiv1<false>(a[j], b[j]);
+    u[j] = pdiv1<true>(a[j], b[j]);
+  }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const float r = ref_pdiv(a[j], b[j]);
     if (!same(q[j], r)) report(a[j], b[j], q[j]);
-    const float s = pdiv1(a[j], b[j]);
-    if (!same(s, r)) report(a[j], b[j], s);
+    if (!same(p[j], r)) report(a[j], b[j], p[j]);
+    if (!same(s[j], r)) report(a[j], b[j], s[j]);
+    if (!same(u[j], r)) report(a[j], b[j], u[j]);
   }
 }
 

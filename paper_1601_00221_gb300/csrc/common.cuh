@@ -220,7 +220,8 @@ __device__ __forceinline__ void finish_program(Partial* __restrict__ partials,
     if (fitness_out) {
       double f = ((double)v.s + (double)v.c) / divisor;
       if (flags & FLAG_BAD) f = __longlong_as_double(0x7ff8000000000000ll);
-      else if (flags & FLAG_NONFINITE) f = __longlong_as_double(0x7ff0000000000000ll);
+      else if ((flags & FLAG_NONFINITE) || !(f <= 1.7976931348623157e308))  // (a binary32 sum overflowed)
+        f = __longlong_as_double(0x7ff0000000000000ll);
       fitness_out[p] = f;
     }
     return;
@@ -242,7 +243,8 @@ __device__ __forceinline__ void finish_program(Partial* __restrict__ partials,
   if (fitness_out) {
     f = f / divisor;
     if (fl & FLAG_BAD) f = __longlong_as_double(0x7ff8000000000000ll);
-    else if (fl & FLAG_NONFINITE) f = __longlong_as_double(0x7ff0000000000000ll);
+    else if ((fl & FLAG_NONFINITE) || !(f <= 1.7976931348623157e308))  // (a binary32 sum overflowed)
+      f = __longlong_as_double(0x7ff0000000000000ll);
     fitness_out[p] = f;
   }
 }

@@ -573,19 +573,36 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
       if (a.want_fitness) {
         Vec<K> y;
         vload<K>(y, a.targets, c0, a.n_cases, full && a.y_aligned);
-        // pass sum of the K errors, then one compensated add
+        // the K errors (the measure chosen once per pass), the cases past the
+        // end masked on the last pass only; then their pass sum and one
+        // compensated add
         float e[K];
+        if (a.fitness_kind == FIT_SUM_ABS) {
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-          float d = case_error(o[j], vget<K>(y, j), a.fitness_kind);
-          if (c0 + j >= a.n_cases) d = 0.0f;
-          if (!(d <= 3.402823466e38f)) flags |= FLAG_NONFINITE;
-          e[j] = d;
+          for (int j = 0; j < K; ++j) e[j] = fabsf(__fsub_rn(o[j], vget<K>(y, j)));
+        } else if (a.fitness_kind == FIT_MSE) {
+#pragma unroll
+          for (int j = 0; j < K; ++j) {
+            const float d = __fsub_rn(o[j], vget<K>(y, j));
+            e[j] = __fmul_rn(d, d);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < K; ++j) e[j] = (rintf(o[j]) == vget<K>(y, j)) ? 0.0f : 1.0f;
+        }
+        if (!full) {
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            if (c0 + j >= a.n_cases) e[j] = 0.0f;
         }
 #pragma unroll
         for (int w = 1; w < K; w <<= 1)
 #pragma unroll
           for (int j = 0; j + w < K; j += 2 * w) e[j] = __fadd_rn(e[j], e[j + w]);
+        // errors are >= 0: the pass sum is non-finite exactly when an error
+        // is, or when finite errors overflow binary32 (the fitness is then
+        // +inf as well, not the NaN the compensation term would give)
+        if (!(e[0] <= 3.402823466e38f)) flags |= FLAG_NONFINITE;
         csum_add(acc, e[0]);
       }
     }

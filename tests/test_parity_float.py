@@ -121,6 +121,31 @@ def test_nonfinite_and_special_values():
         assert_fitness(f, exp_fit, f"k={k}")
 
 
+@pytest.mark.parametrize("fitness", [gp.FITNESS_SUM_ABS, gp.FITNESS_MSE])
+def test_error_sum_past_binary32_is_inf(fitness):
+    """Every per-case error finite, their sum beyond binary32 (reading r29):
+    the fitness is +inf, whether the sum overflows inside a pass, across the
+    passes of a thread or across blocks.  The binary64 oracle's value is
+    finite there; it is checked to be beyond the binary32 range."""
+    c = 2e38 if fitness == gp.FITNESS_SUM_ABS else 1.5e19   # error 2e38 (or its square 2.25e38)
+    progs = [np.array(const_tokens(c), np.uint32), np.array(synth.quartic_program(), np.uint32)]
+    pop = synth.pack(progs)
+    for n_cases in (2, 40, 5000):
+        x = synth.uniform_cases(76, 1, n_cases)
+        y = np.zeros(n_cases, np.float32)
+        exp = oracle.fset_population_fitness(pop.words, pop.offsets, pop.lengths, x, y,
+                                             oracle.FIT_MSE if fitness == gp.FITNESS_MSE else oracle.FIT_ABS)
+        assert np.isfinite(exp[0]) and exp[0] * (n_cases if fitness == gp.FITNESS_MSE else 1) > 3.5e38
+        for k in KS:
+            enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+            P, O, L = upload(enc)
+            for chunk in (0, 32 * k):
+                cfg = gp.Config(gp.VARIANT_REGISTER, k, 32, chunk, fitness)
+                f = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy()
+                assert f[0] == np.inf, (n_cases, k, chunk, f[0])
+                assert np.isfinite(f[1]) and abs(f[1] - exp[1]) <= 1e-5 * abs(exp[1]), (n_cases, k, chunk)
+
+
 def test_malformed_device_program_gives_nan_and_status():
     w = synth.regression_small(n_progs=8, n_cases=256)
     enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)

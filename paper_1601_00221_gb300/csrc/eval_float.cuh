@@ -100,93 +100,10 @@ __device__ __forceinline__ uint32_t input_fields(uint32_t kind, uint32_t code) {
 //         tile + v * 128 * K bytes)
 // Each returns true unless an unknown instruction code was met.
 // ---------------------------------------------------------------------------
-#define GP_O1(o) "=f"(o[0])
-#define GP_O2(o) "=f"(o[0]), "=f"(o[1])
-#define GP_O4(o) GP_O2(o), "=f"(o[2]), "=f"(o[3])
-#define GP_O8(o) GP_O4(o), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
-#define GP_I1(x) "f"(x[0])
-#define GP_I2(x) "f"(x[0]), "f"(x[1])
-#define GP_I4(x) GP_I2(x), "f"(x[2]), "f"(x[3])
-#define GP_I8(x) GP_I4(x), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7])
-
-#define GP_TREE_REG(MAC, KK) \
-  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), GP_I##KK(x) : "memory")
-#define GP_TREE_SMEM(MAC, KK) \
-  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile) : "memory")
-#define GP_LIN(MAC, KK) \
-  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile), "r"(nin) : "memory")
-
-template <int K, bool XREG, bool RPN>
-__device__ __forceinline__ bool run_tree(uint32_t prog, uint32_t n, const float (&x)[K], uint32_t tile,
-                                         float (&o)[K]) {
-  uint32_t bad;
-  if constexpr (XREG && !RPN) {
-    if constexpr (K == 1) GP_TREE_REG(GP_PTX_SFORM_K1_REG, 1);
-    else if constexpr (K == 2) GP_TREE_REG(GP_PTX_SFORM_K2_REG, 2);
-    else if constexpr (K == 4) GP_TREE_REG(GP_PTX_SFORM_K4_REG, 4);
-    else GP_TREE_REG(GP_PTX_SFORM_K8_REG, 8);
-  } else if constexpr (XREG && RPN) {
-    if constexpr (K == 1) GP_TREE_REG(GP_PTX_RPN_K1_REG, 1);
-    else if constexpr (K == 2) GP_TREE_REG(GP_PTX_RPN_K2_REG, 2);
-    else if constexpr (K == 4) GP_TREE_REG(GP_PTX_RPN_K4_REG, 4);
-    else GP_TREE_REG(GP_PTX_RPN_K8_REG, 8);
-  } else if constexpr (!RPN) {
-    if constexpr (K == 1) GP_TREE_SMEM(GP_PTX_SFORM_K1_SMEM, 1);
-    else if constexpr (K == 2) GP_TREE_SMEM(GP_PTX_SFORM_K2_SMEM, 2);
-    else if constexpr (K == 4) GP_TREE_SMEM(GP_PTX_SFORM_K4_SMEM, 4);
-    else GP_TREE_SMEM(GP_PTX_SFORM_K8_SMEM, 8);
-  } else {
-    if constexpr (K == 1) GP_TREE_SMEM(GP_PTX_RPN_K1_SMEM, 1);
-    else if constexpr (K == 2) GP_TREE_SMEM(GP_PTX_RPN_K2_SMEM, 2);
-    else if constexpr (K == 4) GP_TREE_SMEM(GP_PTX_RPN_K4_SMEM, 4);
-    else GP_TREE_SMEM(GP_PTX_RPN_K8_SMEM, 8);
-  }
-  return bad == 0;
-}
-
-// S-form with stack levels 4..7 in shared memory (K = 8): `sbase` is this
-// lane's spill address (per warp [level][16-byte chunk][lane])
-#define GP_TREE_REG_SP(MAC, KK) \
-  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), GP_I##KK(x), "r"(sbase) : "memory")
-#define GP_TREE_SMEM_SP(MAC, KK) \
-  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile), "r"(sbase) : "memory")
-
-template <bool XREG>
-__device__ __forceinline__ bool run_tree_rl4(uint32_t prog, uint32_t n, const float (&x)[8], uint32_t tile,
-                                             uint32_t sbase, float (&o)[8]) {
-  uint32_t bad;
-  if constexpr (XREG) GP_TREE_REG_SP(GP_PTX_SFORM_K8_REG_RL4, 8);
-  else GP_TREE_SMEM_SP(GP_PTX_SFORM_K8_SMEM_RL4, 8);
-  return bad == 0;
-}
-
-// shared-memory bytes of the levels RL.. of one warp
-template <int K, int RL>
-__host__ __device__ constexpr int spill_bytes_per_warp() { return (gpisa::R - RL) * 4 * K * 32; }
-
+// register unit of the interpreters' stack operands: a pair of binary32
+// cases (one value when K == 1)
 template <int K>
-__device__ __forceinline__ bool run_linear(uint32_t prog, uint32_t n, uint32_t tile, uint32_t nin,
-                                           float (&o)[K]) {
-  uint32_t bad;
-  if constexpr (K == 1) GP_LIN(GP_PTX_LINEAR_K1, 1);
-  else if constexpr (K == 2) GP_LIN(GP_PTX_LINEAR_K2, 2);
-  else if constexpr (K == 4) GP_LIN(GP_PTX_LINEAR_K4, 4);
-  else GP_LIN(GP_PTX_LINEAR_K8, 8);
-  return bad == 0;
-}
-
-// ---------------------------------------------------------------------------
-// Extended S-form (the full float function sets of Sec. 4.2).  The generated
-// block keeps the stack in asm operands and returns whenever it meets SIN,
-// COS, EXP or LOG, with the operand's K values in t; this loop applies CUDA's
-// binary32 function (sinf, cosf, expf: 2 ulp; logf: 1 ulp, documented) and
-// enters the block again, which stores t into the level and goes on.  The
-// program is warp-uniform, so every exit and the function chosen are too.
-// ---------------------------------------------------------------------------
-constexpr uint32_t SFX_EXIT = 16;  // status >= SFX_EXIT: 16 + fn * 8 + level
-
-template <int K>
-struct SfxUnit {  // register unit of the extended interpreter's operands
+struct SfxUnit {
   using type = unsigned long long;  // a pair of binary32 cases
 };
 template <>
@@ -217,6 +134,108 @@ __device__ __forceinline__ void sfx_pack(const float (&v)[K], typename SfxUnit<K
       u[i] = ((unsigned long long)__float_as_uint(v[2 * i + 1]) << 32) | __float_as_uint(v[2 * i]);
   }
 }
+
+// register units of the whole stack (R levels)
+template <int K>
+__host__ __device__ constexpr int stack_units() { return R * (K == 1 ? 1 : K / 2); }
+
+#define GP_O1(o) "=f"(o[0])
+#define GP_O2(o) "=f"(o[0]), "=f"(o[1])
+#define GP_O4(o) GP_O2(o), "=f"(o[2]), "=f"(o[3])
+#define GP_O8(o) GP_O4(o), "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7])
+#define GP_I1(x) "f"(x[0])
+#define GP_I2(x) "f"(x[0]), "f"(x[1])
+#define GP_I4(x) GP_I2(x), "f"(x[2]), "f"(x[3])
+#define GP_I8(x) GP_I4(x), "f"(x[4]), "f"(x[5]), "f"(x[6]), "f"(x[7])
+
+// K >= 2: the stack s (stack_units<K>() units, level l at s[l*H .. l*H+H-1])
+// is the caller's; it stays in registers between entries and level 0 is the
+// output, unpacked into o.  K = 1: the stack is local to the asm block and
+// level 0 comes out in o.
+#define GP_TREE_REG(MAC, KK) \
+  asm volatile(MAC : GP_STACK_K##KK, "=r"(bad) : "r"(prog), "r"(n), GP_I##KK(x) : "memory")
+#define GP_TREE_SMEM(MAC, KK) \
+  asm volatile(MAC : GP_STACK_K##KK, "=r"(bad) : "r"(prog), "r"(n), "r"(tile) : "memory")
+#define GP_LIN(MAC, KK) \
+  asm volatile(MAC : GP_STACK_K##KK, "=r"(bad) : "r"(prog), "r"(n), "r"(tile), "r"(nin) : "memory")
+#define GP_TREE_REG1(MAC) \
+  asm volatile(MAC : GP_O1(o), "=r"(bad) : "r"(prog), "r"(n), GP_I1(x) : "memory")
+#define GP_TREE_SMEM1(MAC) \
+  asm volatile(MAC : GP_O1(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile) : "memory")
+#define GP_LIN1(MAC) \
+  asm volatile(MAC : GP_O1(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile), "r"(nin) : "memory")
+
+template <int K, bool XREG, bool RPN>
+__device__ __forceinline__ bool run_tree(uint32_t prog, uint32_t n, const float (&x)[K], uint32_t tile,
+                                         typename SfxUnit<K>::type (&s)[stack_units<K>()], float (&o)[K]) {
+  uint32_t bad;
+  if constexpr (XREG && !RPN) {
+    if constexpr (K == 1) GP_TREE_REG1(GP_PTX_SFORM_K1_REG);
+    else if constexpr (K == 2) GP_TREE_REG(GP_PTX_SFORM_K2_REG, 2);
+    else if constexpr (K == 4) GP_TREE_REG(GP_PTX_SFORM_K4_REG, 4);
+    else GP_TREE_REG(GP_PTX_SFORM_K8_REG, 8);
+  } else if constexpr (XREG && RPN) {
+    if constexpr (K == 1) GP_TREE_REG1(GP_PTX_RPN_K1_REG);
+    else if constexpr (K == 2) GP_TREE_REG(GP_PTX_RPN_K2_REG, 2);
+    else if constexpr (K == 4) GP_TREE_REG(GP_PTX_RPN_K4_REG, 4);
+    else GP_TREE_REG(GP_PTX_RPN_K8_REG, 8);
+  } else if constexpr (!RPN) {
+    if constexpr (K == 1) GP_TREE_SMEM1(GP_PTX_SFORM_K1_SMEM);
+    else if constexpr (K == 2) GP_TREE_SMEM(GP_PTX_SFORM_K2_SMEM, 2);
+    else if constexpr (K == 4) GP_TREE_SMEM(GP_PTX_SFORM_K4_SMEM, 4);
+    else GP_TREE_SMEM(GP_PTX_SFORM_K8_SMEM, 8);
+  } else {
+    if constexpr (K == 1) GP_TREE_SMEM1(GP_PTX_RPN_K1_SMEM);
+    else if constexpr (K == 2) GP_TREE_SMEM(GP_PTX_RPN_K2_SMEM, 2);
+    else if constexpr (K == 4) GP_TREE_SMEM(GP_PTX_RPN_K4_SMEM, 4);
+    else GP_TREE_SMEM(GP_PTX_RPN_K8_SMEM, 8);
+  }
+  if constexpr (K >= 2) sfx_unpack<K>(s, o);
+  return bad == 0;
+}
+
+// S-form with stack levels 4..7 in shared memory (K = 8): `sbase` is this
+// lane's spill address (per warp [level][16-byte chunk][lane])
+#define GP_TREE_REG_SP(MAC, KK) \
+  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), GP_I##KK(x), "r"(sbase) : "memory")
+#define GP_TREE_SMEM_SP(MAC, KK) \
+  asm volatile(MAC : GP_O##KK(o), "=r"(bad) : "r"(prog), "r"(n), "r"(tile), "r"(sbase) : "memory")
+
+template <bool XREG>
+__device__ __forceinline__ bool run_tree_rl4(uint32_t prog, uint32_t n, const float (&x)[8], uint32_t tile,
+                                             uint32_t sbase, float (&o)[8]) {
+  uint32_t bad;
+  if constexpr (XREG) GP_TREE_REG_SP(GP_PTX_SFORM_K8_REG_RL4, 8);
+  else GP_TREE_SMEM_SP(GP_PTX_SFORM_K8_SMEM_RL4, 8);
+  return bad == 0;
+}
+
+// shared-memory bytes of the levels RL.. of one warp
+template <int K, int RL>
+__host__ __device__ constexpr int spill_bytes_per_warp() { return (gpisa::R - RL) * 4 * K * 32; }
+
+template <int K>
+__device__ __forceinline__ bool run_linear(uint32_t prog, uint32_t n, uint32_t tile, uint32_t nin,
+                                           typename SfxUnit<K>::type (&s)[stack_units<K>()], float (&o)[K]) {
+  uint32_t bad;
+  if constexpr (K == 1) GP_LIN1(GP_PTX_LINEAR_K1);
+  else if constexpr (K == 2) GP_LIN(GP_PTX_LINEAR_K2, 2);
+  else if constexpr (K == 4) GP_LIN(GP_PTX_LINEAR_K4, 4);
+  else GP_LIN(GP_PTX_LINEAR_K8, 8);
+  if constexpr (K >= 2) sfx_unpack<K>(s, o);
+  return bad == 0;
+}
+
+// ---------------------------------------------------------------------------
+// Extended S-form (the full float function sets of Sec. 4.2).  The generated
+// block keeps the stack in asm operands and returns whenever it meets SIN,
+// COS, EXP or LOG, with the operand's K values in t; this loop applies CUDA's
+// binary32 function (sinf, cosf, expf: 2 ulp; logf: 1 ulp, documented) and
+// enters the block again, which stores t into the level and goes on.  The
+// program is warp-uniform, so every exit and the function chosen are too.
+// ---------------------------------------------------------------------------
+constexpr uint32_t SFX_EXIT = 16;  // status >= SFX_EXIT: 16 + fn * 8 + level
+
 
 // protected log: 0 at a zero operand (either sign), else the log of |a|
 __device__ __forceinline__ float protected_logf(float a) { return a == 0.0f ? 0.0f : logf(fabsf(a)); }
@@ -521,6 +540,13 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
             (uint32_t)(sizeof(float) * (size_t)nwarps * a.tile_inputs * 32 * K) +
             (uint32_t)(warp * spill_bytes_per_warp<K, RL>() + lane * 16);
 
+  // the basic interpreters' stack (K >= 2): defined once here, kept in
+  // registers across the passes (every program writes a level before reading
+  // it); unused at K = 1
+  typename SfxUnit<K>::type stk[stack_units<K>()];
+#pragma unroll
+  for (int i = 0; i < stack_units<K>(); ++i) stk[i] = 0;
+
   if (!bad) {
 #pragma unroll 1
     for (int64_t wb = c_begin + (int64_t)warp * 32 * K; wb < c_end; wb += (int64_t)nwarps * 32 * K) {
@@ -559,11 +585,11 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
         ok = run_tree_rl4<XREG>(prog_addr, (uint32_t)n_instr, x, tile_addr, sbase, o);
       } else if (kind == K_LINEAR) {
         ok = run_linear<K>(prog_addr, (uint32_t)n_instr, tile_addr,
-                           (uint32_t)(a.n_inputs < R ? a.n_inputs : R), o);
+                           (uint32_t)(a.n_inputs < R ? a.n_inputs : R), stk, o);
       } else if (kind == K_SFORM) {
-        ok = run_tree<K, XREG, false>(prog_addr, (uint32_t)n_instr, x, tile_addr, o);
+        ok = run_tree<K, XREG, false>(prog_addr, (uint32_t)n_instr, x, tile_addr, stk, o);
       } else {
-        ok = run_tree<K, XREG, true>(prog_addr, (uint32_t)n_instr, x, tile_addr, o);
+        ok = run_tree<K, XREG, true>(prog_addr, (uint32_t)n_instr, x, tile_addr, stk, o);
       }
       if (!ok) flags |= FLAG_BAD;
       Vec<K> ov;

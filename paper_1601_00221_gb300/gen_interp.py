@@ -21,18 +21,23 @@ The instruction codes follow ``csrc/isa.h``.  Output: ``gen_interp.h`` with
 one string macro per (interpreter, K, input mode), used by
 ``csrc/eval_float.cuh`` and ``csrc/eval_bool.cuh``.
 
-Operand conventions of the generated asm (documented again in the header):
-  float S-form / RPN, XREG (single input in registers):
-     outputs %0..%{K-1} level-0 values (f32), %K bad flag (u32)
-     inputs  %{K+1} program address (shared, u32), %{K+2} instruction count,
-             %{K+3}..%{2K+2} the K input values (f32)
-  float S-form / RPN, XSMEM (inputs staged in shared memory):
-     inputs  %{K+1} program address, %{K+2} count, %{K+3} this lane's tile
-             address (u32): input v of this lane's K cases at
-             tile + v*128*K bytes
-  register linear GP (inputs always staged):
-     inputs  %{K+1} program address, %{K+2} count, %{K+3} tile address,
-             %{K+4} number of staged inputs (registers beyond start at 0)
+Operand conventions of the generated asm (documented again in the header).
+H = K/2 register units per stack level (one f32 when K == 1, else b64 case
+pairs), RH = 8 * H:
+  float S-form / RPN / register GP, K >= 2: in-out %0..%{RH-1} the stack
+     levels (or registers), level l at %{l*H}..%{l*H+H-1}; the caller keeps
+     them between entries, so they are defined once, not at every entry;
+     output %{RH} bad flag (u32);
+     inputs  %{RH+1} program address (shared, u32), %{RH+2} instruction count,
+     then XREG (single input in registers): the K input values (f32);
+          XSMEM (inputs staged in shared memory): this lane's tile address
+          (u32), input v of this lane's K cases at tile + v*128*K bytes;
+          register GP: the tile address, then the number of staged inputs
+          (registers beyond start at 0)
+  the same with K = 1, and the S-form with levels 4..7 in shared memory
+     (K = 8): outputs %0..%{K-1} level-0 values (f32), %K bad; inputs
+     %{K+1} program address, %{K+2} count, then the inputs as above (the
+     study kernel then this lane's spill address)
   Boolean (words): outputs %0..%{K-1} level-0 words (u32), %K bad;
      inputs  %{K+1} program address, %{K+2} count, %{K+3} tile address
 """
@@ -279,6 +284,14 @@ class FloatGen:
         assert K in (1, 2, 4, 8) and xmode in ("reg", "smem") and 1 <= rl <= R
         self.K, self.xmode = K, xmode
         self.H = 1 if K == 1 else K // 2   # register units per stack level
+        # all levels in registers, K >= 2: they are asm operands the caller
+        # keeps across entries (no zeroing at each entry, no copy of level 0
+        # out); else level-0 outputs and block-local stack registers.  (At
+        # K = 1 the operand form costs the 1D kernel 16 registers and an
+        # occupancy step: measured 3% slower.)
+        self.stack_ops = rl == R and K >= 2
+        base = R * self.H if self.stack_ops else K
+        self.o_bad, self.o_prog, self.o_cnt, self.o_x = base, base + 1, base + 2, base + 3
         self.b = Block()
         self.stride = 128 * K              # bytes between inputs in a lane's tile
         # levels rl .. R-1 live in shared memory: per warp [level][chunk][lane]
@@ -292,6 +305,8 @@ class FloatGen:
 
     # register unit names
     def lev(self, l, i):
+        if self.stack_ops:
+            return f"%{l * self.H + i}"
         return f"s{l * self.H + i}"
 
     def xreg(self, i):
@@ -304,7 +319,9 @@ class FloatGen:
     def header(self, extra_regs=""):
         K, H, b = self.K, self.H, self.b
         b("{")
-        b(f".reg .{self.ty} s<{self.rl * H}>, ta<{H}>, tb<{H}>, xA<{H}>, xB<{H}>, cA, cB;")
+        b(f".reg .{self.ty} ta<{H}>, tb<{H}>, xA<{H}>, xB<{H}>, cA, cB;")
+        if not self.stack_ops:
+            b(f".reg .{self.ty} s<{self.rl * H}>;")
         if self.rl < R:
             b(f".reg .{self.ty} sA<{H}>, sB<{H}>;")
             b(".reg .b32 sbase;")
@@ -318,13 +335,15 @@ class FloatGen:
             b("mov.b64 one2, 0x3F8000003F800000;")
         if extra_regs:
             b(extra_regs)
-        # Define every stack register before the first jump: the jump table
-        # makes any of them readable at every body, so an undefined one would
-        # be live from the kernel's entry and could not share a physical
-        # register with the other interpreters of the same kernel.
-        zero = "0f00000000" if K == 1 else "0"
-        for r in range(self.rl * H):
-            b(f"mov.{self.ty} s{r}, {zero};")
+        # Block-local stack registers are defined before the first jump: the
+        # jump table makes any of them readable at every body, so an undefined
+        # one would be live from the kernel's entry and could not share a
+        # physical register with the other interpreters of the same kernel.
+        # (Operand levels are defined once by the caller instead.)
+        if not self.stack_ops:
+            zero = "0f00000000" if K == 1 else "0"
+            for r in range(self.rl * H):
+                b(f"mov.{self.ty} s{r}, {zero};")
 
     # levels in shared memory (rl <= l < R)
     def spill_off(self, l, q):
@@ -432,9 +451,9 @@ class FloatGen:
             self.jump()
 
     def prologue(self):
-        K, b = self.K, self.b
-        b(f"mov.u32 adr, %{K + 1};")
-        b(f"mov.u32 %{K}, 0;")
+        b = self.b
+        b(f"mov.u32 adr, %{self.o_prog};")
+        b(f"mov.u32 %{self.o_bad}, 0;")
 
     def start(self):
         self.fetch()
@@ -444,13 +463,14 @@ class FloatGen:
     def epilogue(self, out_units):
         b, K = self.b, self.K
         b("CBAD:")
-        b(f"mov.u32 %{K}, 1;")
+        b(f"mov.u32 %{self.o_bad}, 1;")
         b("DONE:")
-        if K == 1:
-            b(f"mov.f32 %0, {out_units[0]};")
-        else:
-            for i in range(self.H):
-                b(f"mov.b64 {{%{2 * i}, %{2 * i + 1}}}, {out_units[i]};")
+        if not self.stack_ops:  # (operand levels: level 0 is the output already)
+            if K == 1:
+                b(f"mov.f32 %0, {out_units[0]};")
+            else:
+                for i in range(self.H):
+                    b(f"mov.b64 {{%{2 * i}, %{2 * i + 1}}}, {out_units[i]};")
         b("}")
 
     def setup_inputs(self):
@@ -458,11 +478,11 @@ class FloatGen:
         if self.xmode == "reg":
             for i in range(self.H):
                 if K == 1:
-                    b(f"mov.f32 x0, %{K + 3};")
+                    b(f"mov.f32 x0, %{self.o_x};")
                 else:
-                    b(f"mov.b64 x{i}, {{%{K + 3 + 2 * i}, %{K + 4 + 2 * i}}};")
+                    b(f"mov.b64 x{i}, {{%{self.o_x + 2 * i}, %{self.o_x + 2 * i + 1}}};")
         else:
-            b(f"mov.u32 xbase, %{K + 3};")
+            b(f"mov.u32 xbase, %{self.o_x};")
 
     def store_table(self):
         self.b("STTBL: .branchtargets " + ", ".join(f"ST{l}" for l in range(R)) + ";")
@@ -581,8 +601,7 @@ class FloatGen:
 
     def sbase_operand(self):
         """Operand index of the lane's spill address (after the inputs)."""
-        K = self.K
-        return (2 * K + 3) if self.xmode == "reg" else (K + 4)
+        return self.o_x + (self.K if self.xmode == "reg" else 1)
 
     def rpn(self):
         K, H, b = self.K, self.H, self.b
@@ -652,8 +671,8 @@ class FloatGen:
         self.store_table()
         self.table(n_codes, table)
         self.prologue()
-        b(f"mov.u32 xbase, %{K + 3};")
-        b(f"mov.u32 nin, %{K + 4};")
+        b(f"mov.u32 xbase, %{self.o_x};")
+        b(f"mov.u32 nin, %{self.o_x + 1};")
         zero = "0f00000000" if K == 1 else "0"
         for r in range(NREG):
             b(f"setp.lt.u32 p, {r}, nin;")
@@ -1270,6 +1289,9 @@ def generate() -> str:
                 f"GP_PTX_RPN_K{K}_{X}", f"RPN interpreter, K={K}, inputs in {xm}"))
         parts.append(FloatGen(K, "smem").linear().macro(
             f"GP_PTX_LINEAR_K{K}", f"register linear-GP interpreter, K={K}"))
+        if K >= 2:
+            parts.append(f"// the stack operands of the interpreters above (the caller's array s)\n"
+                         f"#define GP_STACK_K{K} " + ", ".join(f'"+l"(s[{i}])' for i in range(R * K // 2)) + "\n")
         if K == 8:  # levels 4..7 in shared memory (the stack-register study)
             for xm in ("reg", "smem"):
                 X = xm.upper()

@@ -282,7 +282,7 @@ def run_ours(args):
                 saved = (P, O, L)
                 P, O, L = Pr, Or, Lr
             tries = [(statistics.mean(timed(gp.Config(variant, 1, b, ch), 2, 1)), b, ch)
-                     for b in blocks for ch in (0, 16384)]
+                     for b in blocks for ch in (0, 16384, 65536) if n_cases >= ch]
             _, b1, ch1 = min(tries)
             tt = timed(gp.Config(variant, 1, b1, ch1), max(3, args.steps // 4), 2)
             if name.startswith("blockgp"):

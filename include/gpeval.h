@@ -391,7 +391,7 @@ int gp_server_destroy(gp_server* srv);
  * and thread count differ per problem, Tables of Sec. 4.2, 5 and 6).
  * gp_autotune_population times every candidate configuration (k in
  * {2, 4, 8} x block in {64, 128, 256, 512} x cases per block in {chosen, 4096,
- * 8192, 16384, 32768}) on the given float population with CUDA
+ * 8192, 16384, 32768, all}) on the given float population with CUDA
  * events on `stream` (1 warm-up launch, `repeats` timed launches each, the
  * minimum kept), writes the fastest to *best (may be NULL) and records it for
  * the workload's shape: later float evaluations whose configuration leaves k

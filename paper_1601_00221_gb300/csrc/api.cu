@@ -32,6 +32,8 @@ struct Workspace {
   size_t partial_cap = 0;  // entries
   unsigned* counters = nullptr;
   size_t counter_cap = 0;  // entries
+  int32_t* order = nullptr;  // programs longest first (launch_order_by_size)
+  size_t order_cap = 0;      // entries
   int* status = nullptr;
 };
 std::vector<Workspace*> g_ws;
@@ -93,6 +95,23 @@ int get_workspace(cudaStream_t s, size_t n_partials, size_t n_counters, Workspac
     w->counter_cap = cap;
   }
   *out = w;
+  return GP_OK;
+}
+
+// the workspace's order array, grown to n entries (same stream and lock
+// discipline as get_workspace)
+int get_order(Workspace* w, size_t n, cudaStream_t s, int32_t** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (n > w->order_cap) {
+    size_t cap = std::max(n, 2 * w->order_cap);
+    int32_t* o = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&o, cap * sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
+    if (w->order) cudaFreeAsync(w->order, s);
+    w->order = o;
+    w->order_cap = cap;
+  }
+  *out = w->order;
   return GP_OK;
 }
 
@@ -254,6 +273,15 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   a.want_fitness = fitness_out != nullptr;
   a.fitness_kind = c.fitness;
   a.tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
+  a.order = nullptr;
+  if (n_progs >= kOrderMinProgsPerSm * sm_count()) {
+    int32_t* order = nullptr;
+    rc = get_order(w, (size_t)n_progs, s, &order);
+    if (rc) return rc;
+    cudaError_t eo = launch_order_by_size(lengths, n_progs, order, s);
+    if (eo != cudaSuccess) return cuda_fail(eo, "ordering launch");
+    a.order = order;
+  }
   const int grid = n_progs * n_chunks;
   const bool xreg = (n_inputs == 1);
   const bool rl4 = c.stack_registers == 4;
@@ -445,6 +473,7 @@ extern "C" int gp_shutdown(void) {
     cudaStreamSynchronize(w->stream);
     if (w->partials) cudaFree(w->partials);
     if (w->counters) cudaFree(w->counters);
+    if (w->order) cudaFree(w->order);
     if (w->status) cudaFree(w->status);
     delete w;
   }
@@ -472,12 +501,20 @@ extern "C" int gp_autotune_population(const uint32_t* programs, const int64_t* o
   int rc = GP_OK;
   static const int ks[] = {2, 4, 8};
   static const int blocks[] = {64, 128, 256, 512};
-  static const int chunks[] = {0, 4096, 8192, 16384, 32768};
+  // cases per block: chosen, fixed sizes, or (-1) the whole case set, which
+  // with the programs taken longest first often needs the fewest blocks
+  static const int chunks[] = {0, 4096, 8192, 16384, 32768, -1};
   for (int k : ks) {
     for (int blk : blocks) {
-     for (int ch : chunks) {
-      if (ch && (ch % (k * blk) || ch >= n_cases)) continue;
-      gp_config c = {GP_VARIANT_REGISTER, k, blk, ch};
+     for (int ch0 : chunks) {
+      int64_t ch = ch0;
+      if (ch0 < 0) {
+        ch = ((n_cases + k * blk - 1) / (k * blk)) * (k * blk);
+        if (ch > 0x7fffffff || ch <= 32768) continue;  // (a 32-bit field; sizes above cover the rest)
+      } else if (ch && (ch % (k * blk) || ch >= n_cases)) {
+        continue;
+      }
+      gp_config c = {GP_VARIANT_REGISTER, k, blk, (int32_t)ch};
       rc = gp_eval_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases,
                                  targets, fit, nullptr, &c, stream);
       if (rc) break;

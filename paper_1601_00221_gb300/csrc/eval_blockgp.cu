@@ -15,8 +15,9 @@ __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
   __shared__ Partial red_s[32];
   __shared__ int meta_s;
   const int item = blockIdx.x;
-  const int p = item / a.n_chunks;
-  const int chunk = item - p * a.n_chunks;
+  const int rank = item / a.n_chunks;
+  const int p = a.order ? a.order[rank] : rank;
+  const int chunk = item - rank * a.n_chunks;
   const int tid = threadIdx.x;
   if (tid == 0) {
     int n_instr = -1;

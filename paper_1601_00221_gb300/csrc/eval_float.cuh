@@ -58,6 +58,8 @@ struct FloatArgs {
   int32_t o_aligned;     // outputs + p*n_cases 16-byte aligned for every p
   int32_t want_fitness;  // compute the fitness (targets may be null only if n_cases == 0)
   int32_t fitness_kind;  // FIT_SUM_ABS, FIT_MSE or FIT_CLASS
+  const int32_t* order;  // the program of the i-th (program, chunks) group of blocks, longest
+                         // first (launch_order_by_size), or null for 0, 1, 2, ...
   int32_t tile_inputs;   // inputs per case the staged tile holds (<= n_inputs)
 };
 
@@ -404,8 +406,9 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
   __shared__ int n_stage_s;
 
   const int item = blockIdx.x;
-  const int p = item / a.n_chunks;
-  const int chunk = item - p * a.n_chunks;
+  const int rank = item / a.n_chunks;
+  const int p = a.order ? a.order[rank] : rank;
+  const int chunk = item - rank * a.n_chunks;
   const int tid = threadIdx.x;
 
   if (tid == 0) {

@@ -52,6 +52,12 @@ cudaError_t launch_floatrx_k8(const FloatArgs& a, bool xreg, int block, int grid
 cudaError_t launch_float_k8_rl4(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
                                 cudaStream_t s);
 cudaError_t launch_blockgp(const FloatArgs& a, int block, int grid, cudaStream_t s);
+// order[0 .. n) = the programs by decreasing instruction count (from their
+// lengths), for FloatArgs::order; one block
+cudaError_t launch_order_by_size(const int32_t* lengths, int32_t n, int32_t* order, cudaStream_t s);
+// order the blocks by program size when the population fills this many
+// blocks per SM: below that every block starts in the first wave anyway
+constexpr int kOrderMinProgsPerSm = 2;
 // Boolean kernels: K words per thread.
 cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s);
 // Boolean, one program per lane over w <= 4 words (one warp per block).

@@ -31,6 +31,7 @@ constexpr int64_t kMaxCounters = GP_NOALLOC_MAX_PARTIALS;
 struct NoallocScratch {
   Partial partials[kMaxPartials];
   unsigned counters[kMaxCounters];
+  int32_t order[kMaxCounters];  // programs longest first
   int status;
 };
 
@@ -38,6 +39,19 @@ struct NoallocScratch {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
 
 constexpr int kMaxDevices = 64;
+
+// multiprocessors of the current device (asked once per device)
+int sm_count_cached() {
+  static int n[kMaxDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 148;
+  if (n[dev] <= 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) n[dev] = v;
+    else return 148;
+  }
+  return n[dev];
+}
 std::mutex g_mu;
 NoallocScratch* g_addr[kMaxDevices] = {};
 
@@ -146,6 +160,12 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   a.want_fitness = 1;
   a.fitness_kind = c.fitness;
   a.tile_inputs = tile_inputs;
+  a.order = nullptr;
+  if (n_progs >= kOrderMinProgsPerSm * sm_count_cached()) {
+    e = launch_order_by_size(lengths, n_progs, scratch->order, s);
+    if (e != cudaSuccess) return gp_fail(GP_ERR_CUDA, "ordering launch: %s", cudaGetErrorString(e));
+    a.order = scratch->order;
+  }
   const int grid = (int)(n_progs * n_chunks);
   const bool xreg = (n_inputs == 1);
   if (c.variant == GP_VARIANT_EXTENDED) {

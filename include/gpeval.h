@@ -259,9 +259,10 @@ int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets, const int3
  * middle of a run.  It computes exactly what gp_eval_population computes
  * (same arguments, same kernel, default configuration: its variant, register
  * or one of the extended ones, and its fitness measure) but keeps the kernel's
- * scratch (per-block partial sums, per-program counters, a status word) in a
- * fixed array of about 1.25 MiB that every device loading the library holds
- * until the process exits; it never calls cudaMalloc or cudaFree.
+ * scratch (per-block partial sums, per-program counters, the block order, a
+ * status word) in a fixed array of about 1.5 MiB that every device loading
+ * the library holds until the process exits; it never calls cudaMalloc or
+ * cudaFree.
  *   - n_progs may be at most GP_NOALLOC_MAX_PARTIALS; larger calls return
  *     GP_ERR_INVALID_ARG.  Cases are split into fewer blocks when needed so
  *     that the partial sums fit.

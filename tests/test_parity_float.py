@@ -146,6 +146,36 @@ def test_error_sum_past_binary32_is_inf(fitness):
                 assert np.isfinite(f[1]) and abs(f[1] - exp[1]) <= 1e-5 * abs(exp[1]), (n_cases, k, chunk)
 
 
+@pytest.mark.parametrize("chunk_per_pass", [0, 2])
+def test_block_order_changes_nothing(chunk_per_pass):
+    """Populations of at least two programs per SM are taken longest first
+    (a counting sort of the instruction counts on the device).  1200 trees of
+    1 to 255 nodes (many of equal size, a few identical): every fitness equals
+    the same programs evaluated 100 at a time (too few to be reordered) bit for
+    bit, and the oracle's within the bound; with several chunks per program the
+    cross-block sums stay in chunk order."""
+    progs = synth.ramped_half_and_half(313, 1200, 1, 8, 255, full_fallback_to_grow=True)
+    progs[700] = progs[3]
+    pop = synth.pack(progs)
+    x = synth.uniform_cases(77, 1, 3000)
+    y = synth.quartic_target(x[0])
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    P, O, L = upload(enc)
+    k, block = 8, 64
+    cfg = gp.Config(gp.VARIANT_REGISTER, k, block, chunk_per_pass * k * block)
+    f_all = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy()
+    parts = []
+    for i in range(0, pop.n, 100):
+        sub = synth.pack(progs[i:i + 100])
+        e2 = gp.encode_population(sub.words, sub.offsets, sub.lengths)
+        P2, O2, L2 = upload(e2)
+        parts.append(gp.eval_population(P2, O2, L2, dev(x), dev(y), config=cfg).cpu().numpy())
+    f_parts = np.concatenate(parts)
+    assert np.array_equal(f_all.view(np.uint64), f_parts.view(np.uint64))
+    assert f_all[700] == f_all[3]
+    assert_fitness(f_all, oracle.population_fitness(pop.words, pop.offsets, pop.lengths, x, y))
+
+
 def test_malformed_device_program_gives_nan_and_status():
     w = synth.regression_small(n_progs=8, n_cases=256)
     enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)

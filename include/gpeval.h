@@ -406,6 +406,14 @@ int gp_autotune_population(const uint32_t* programs, const int64_t* offsets,
                            int32_t repeats, gp_config* best, gp_stream_t stream);
 int gp_autotune_clear(void);
 
+/* Kernels one float evaluation (gp_eval_population*, gp_eval_outputs,
+ * gp_eval_population_noalloc) of n_progs programs launches on the current
+ * device: the interpreter, plus the ordering kernel that takes the programs
+ * longest first once n_progs fills two blocks per multiprocessor.  Writes
+ * the count to *launches.  Returns GP_ERR_INVALID_ARG for a null pointer or
+ * a negative count. */
+int gp_eval_launches(int32_t n_progs, int32_t* launches);
+
 /* ------------------------------------------------------------------------
  * Device-side encoder.  The S-form encoding of gp_encode_population (float
  * trees, basic or extended functions; Sec. 5 symbolic stack), run on the GPU

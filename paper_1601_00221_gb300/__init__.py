@@ -24,7 +24,7 @@ __all__ = [
     "encode_tree", "encode_population", "encode_linear_population",
     "eval_population", "eval_outputs", "eval_population_bool",
     "set_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
-    "eval_population_noalloc", "autotune_population", "autotune_clear",
+    "eval_population_noalloc", "autotune_population", "autotune_clear", "eval_launches",
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "KIND_RPN_EXT",
     "ORDER_PAPER",
     "ORDER_MIN_DEPTH", "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL", "VARIANT_LANES",
@@ -137,6 +137,7 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_server_destroy": [P],
         "gp_autotune_population": [P, P, P, i32, P, i32, i64, P, i32, P, P],
         "gp_autotune_clear": [],
+        "gp_eval_launches": [i32, P],
         "gp_encode_population_device": [P, P, P, i32, i32, P, P, P, P],
         "gp_evolve_create": [P, P, P, P, P, i32, i64, P, P],
         "gp_evolve_run": [P, i32],
@@ -479,6 +480,14 @@ def get_config() -> Config:
     c = Config()
     _check(lib().gp_get_config(ctypes.byref(c)))
     return c
+
+
+def eval_launches(n_progs: int) -> int:
+    """Kernels one float evaluation of n_progs programs launches (the
+    interpreter, and the longest-first ordering kernel for large populations)."""
+    v = ctypes.c_int32(0)
+    _check(lib().gp_eval_launches(int(n_progs), ctypes.byref(v)))
+    return int(v.value)
 
 
 def last_error(stream=None) -> int:

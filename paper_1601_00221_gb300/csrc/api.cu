@@ -552,6 +552,13 @@ extern "C" int gp_autotune_population(const uint32_t* programs, const int64_t* o
   return GP_OK;
 }
 
+extern "C" int gp_eval_launches(int32_t n_progs, int32_t* launches) {
+  gp_clear_error();
+  if (!launches || n_progs < 0) return gp_fail(GP_ERR_INVALID_ARG, "bad arguments");
+  *launches = n_progs == 0 ? 0 : (n_progs >= kOrderMinProgsPerSm * sm_count() ? 2 : 1);
+  return GP_OK;
+}
+
 extern "C" int gp_autotune_clear(void) {
   gp_clear_error();
   std::lock_guard<std::mutex> lk(g_mu);

@@ -29,6 +29,14 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def test_eval_launches_argument_checks():
+    """(answered before any device query)"""
+    import pytest
+    assert gp.eval_launches(0) == 0
+    with pytest.raises(gp.GPError):
+        gp.eval_launches(-1)
+
+
 def test_library_is_built_for_sm_103a():
     # the build flags name exactly one architecture: sm_103a
     assert gp.build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

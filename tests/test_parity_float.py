@@ -174,6 +174,8 @@ def test_block_order_changes_nothing(chunk_per_pass):
     assert np.array_equal(f_all.view(np.uint64), f_parts.view(np.uint64))
     assert f_all[700] == f_all[3]
     assert_fitness(f_all, oracle.population_fitness(pop.words, pop.offsets, pop.lengths, x, y))
+    # the 1200 were ordered (two launches), the groups of 100 were not
+    assert gp.eval_launches(pop.n) == 2 and gp.eval_launches(100) == 1
 
 
 def test_malformed_device_program_gives_nan_and_status():

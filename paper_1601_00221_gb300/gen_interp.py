@@ -170,34 +170,46 @@ def emit_pdiv(b, K, A, B, Q, tag, group=2, fold=None):
         _reduce3(b, "max", mags, "dhi")
         for g0 in range(0, H, group):
             idx = list(range(g0, min(H, g0 + group)))
+            # the reciprocal of -b: every step below is the scalar sequence's
+            # value negated (rounding to nearest is symmetric), so no
+            # negation of b is needed; one multiplication by -1 at the end
             for i in idx:
                 b(f"mov.b64 {{dt, dt2}}, {B[i]};")
+                b("neg.f32 dt, dt;")
+                b("neg.f32 dt2, dt2;")
                 b("rcp.approx.ftz.f32 dt, dt;")
                 b("rcp.approx.ftz.f32 dt2, dt2;")
-                b(f"mov.b64 dY{i}, {{dt, dt2}};")
-                b(f"xor.b64 dN{i}, {B[i]}, 0x8000000080000000;")
+                b(f"mov.b64 dY{i}, {{dt, dt2}};")             # -y0
             for i in idx:
-                b(f"fma.rn.f32x2 dE{i}, dN{i}, dY{i}, one2;")
+                b(f"fma.rn.f32x2 dE{i}, {B[i]}, dY{i}, one2;")  # e = 1 - b y0
             for i in idx:
-                b(f"fma.rn.f32x2 dY{i}, dY{i}, dE{i}, dY{i};")
+                b(f"fma.rn.f32x2 dY{i}, dY{i}, dE{i}, dY{i};")  # -y1
             for i in idx:
-                b(f"mul.rn.f32x2 dQ{i}, {A[i]}, dY{i};")
+                b(f"mul.rn.f32x2 dQ{i}, {A[i]}, dY{i};")        # -q0
             for i in idx:
-                b(f"fma.rn.f32x2 dE{i}, dN{i}, dQ{i}, {A[i]};")
+                b(f"fma.rn.f32x2 dE{i}, {B[i]}, dQ{i}, {A[i]};")  # r = a - b q0
             for i in idx:
-                b(f"fma.rn.f32x2 dQ{i}, dE{i}, dY{i}, dQ{i};")
+                b(f"fma.rn.f32x2 dQ{i}, dE{i}, dY{i}, dQ{i};")  # -q1
     b(f"setp.ge.f32 dok, dlo, {DIV_LO};")
     b(f"setp.le.and.f32 dok, dhi, {DIV_HI}, dok;")
     if fold is None:
+        if K > 1:  # (the slow path leaves the quotients in dQ with their signs)
+            for i in range(H):
+                b(f"mul.rn.f32x2 dQ{i}, dQ{i}, mone2;")
         b(f"@!dok bra {tag}SLOW;")
         b(f"{tag}RET:")
+        if K == 1:
+            b(f"mov.f32 {Q[0]}, dQ0;")
+        else:
+            for i in range(H):
+                b(f"mov.b64 {Q[i]}, dQ{i};")
     else:
         b("vote.sync.all.pred dall, dok, 0xffffffff;")
-    if K == 1:
-        b(f"mov.f32 {Q[0]}, dQ0;")
-    else:
-        for i in range(H):
-            b(f"mov.b64 {Q[i]}, dQ{i};")
+        if K == 1:
+            b(f"mov.f32 {Q[0]}, dQ0;")
+        else:  # the sign restored straight into the destination
+            for i in range(H):
+                b(f"mul.rn.f32x2 {Q[i]}, dQ{i}, mone2;")
     if fold is not None:
         fold()
 
@@ -249,7 +261,7 @@ def emit_pdiv_slow_body(b, K, A, B, Q, tag):
 def pdiv_regs(K, H):
     ty = "f32" if K == 1 else "b64"
     n = 2 * H
-    return (f".reg .{ty} dY<{H}>, dE<{H}>, dN<{H}>, dQ<{H}>, one2;\n"
+    return (f".reg .{ty} dY<{H}>, dE<{H}>, dN<{H}>, dQ<{H}>, one2, mone2;\n"
             f".reg .f32 dlo, dhi, dt, dt2, dma<{n}>, dmb<{n}>, dlo_<{n}>, dhi_<{n}>;\n"
             f".reg .pred dok, dz, dall;")
 
@@ -333,6 +345,7 @@ class FloatGen:
             b(ln)
         if K > 1:
             b("mov.b64 one2, 0x3F8000003F800000;")
+            b("mov.b64 mone2, 0xBF800000BF800000;")
         if extra_regs:
             b(extra_regs)
         # Block-local stack registers are defined before the first jump: the
@@ -858,6 +871,7 @@ class FloatGenX(FloatGen):
             b(ln)
         if K > 1:
             b("mov.b64 one2, 0x3F8000003F800000;")
+            b("mov.b64 mone2, 0xBF800000BF800000;")
         L = lambda l: [self.lev(l, i) for i in range(H)]
         ta = [f"ta{i}" for i in range(H)]
         tb = [f"tb{i}" for i in range(H)]
@@ -1004,6 +1018,7 @@ class FloatGenX(FloatGen):
             b(ln)
         if K > 1:
             b("mov.b64 one2, 0x3F8000003F800000;")
+            b("mov.b64 mone2, 0xBF800000BF800000;")
         L = lambda l: [self.lev(l, i) for i in range(H)]
         ta = [f"ta{i}" for i in range(H)]
         tb = [f"tb{i}" for i in range(H)]
@@ -1245,6 +1260,7 @@ def pdiv_macro(K, fold=True):
     b(f".reg .{ty} qa<{H}>, qb<{H}>, qq<{H}>;")
     if K > 1:
         b("mov.b64 one2, 0x3F8000003F800000;")
+        b("mov.b64 mone2, 0xBF800000BF800000;")
     for i in range(H):
         b(f"mov.{ty} qa{i}, %{H + i};")
         b(f"mov.{ty} qb{i}, %{2 * H + i};")

@@ -8,9 +8,10 @@
 // tests/test_division.py.
 //
 // Modes (argv[1]):
-//   mant <slice> <nslices>   every pair of significands with a, b in [1, 2)
-//                            (all 2^46 pairs over nslices launches; this run
-//                            covers slice `slice` only, or all if slice < 0)
+//   mant <slice> <nslices>   every pair of significands with a in [1, 2) and
+//                            b in [1, 2) and in (-2, -1] (all 2^46 pairs of
+//                            each over nslices launches; this run covers
+//                            slice `slice` only, or all if slice < 0)
 //   rand <n_per_thread> <seed>  random bit patterns over every exponent,
 //                            including zeros, subnormals, infinities, NaN
 //   exps <n_per_thread> <seed>  random significands under every pair of
@@ -90,11 +91,13 @@ __device__ __forceinline__ void check4(const float (&a)[4], const float (&b)[4])
   }
 }
 
-// every significand pair: thread = one b significand, loop over a slice of a
-__global__ void k_mant(uint32_t a_begin, uint32_t a_end) {
+// every significand pair: thread = one b significand, loop over a slice of a;
+// b with the sign bit `neg` (the pair path takes the reciprocal of -b, so
+// both signs reach the reciprocal unit with every significand)
+__global__ void k_mant(uint32_t a_begin, uint32_t a_end, uint32_t neg) {
   const uint32_t mb = blockIdx.x * blockDim.x + threadIdx.x;
   if (mb >= (1u << 23)) return;
-  const float bv = __uint_as_float(0x3f800000u | mb);
+  const float bv = __uint_as_float(0x3f800000u | mb | (neg << 31));
   const float b[4] = {bv, bv, bv, bv};
   for (uint32_t ma = a_begin; ma < a_end; ma += 4) {
     float a[4];
@@ -182,7 +185,9 @@ int main(int argc, char** argv) {
     const uint32_t per = (1u << 23) / (uint32_t)nslices;
     if (per % 4 || per * (uint32_t)nslices != (1u << 23)) { fprintf(stderr, "bad slicing\n"); return 3; }
     for (int s = (slice < 0 ? 0 : slice); s < (slice < 0 ? nslices : slice + 1); ++s) {
-      k_mant<<<(1u << 23) / 256, 256>>>(s * per, (s + 1) * per);
+      k_mant<<<(1u << 23) / 256, 256>>>(s * per, (s + 1) * per, 0u);
+      if (cudaDeviceSynchronize() != cudaSuccess) break;
+      k_mant<<<(1u << 23) / 256, 256>>>(s * per, (s + 1) * per, 1u);
       if (cudaDeviceSynchronize() != cudaSuccess) break;
     }
     char what[64];

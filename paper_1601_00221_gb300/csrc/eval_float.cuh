@@ -563,7 +563,25 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
         const int n_stage = XREG ? a.n_inputs : n_stage_s;
         const bool listed = !XREG && kind != K_LINEAR && a.n_inputs <= GP_COMPACT_MAX_INPUTS &&
                             n_stage <= GP_COMPACT_MAX_LIST;
-        for (int v = 0; v < n_stage; ++v) {
+        int v = 0;
+        if (vec_ok) {
+          // G inputs per step, their loads issued before their stores, so
+          // that G global round trips overlap instead of following each other
+          constexpr int G = K >= 8 ? 2 : 4;
+          for (; v + G <= n_stage; v += G) {
+            Vec<K> t[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+              const int64_t src = listed ? (int64_t)list_s[v + g] : (int64_t)(v + g);
+              vload<K>(t[g], a.cases + src * a.n_cases, c0, a.n_cases, true);
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+              for (int j = 0; j < K; ++j) tile[(v + g) * 32 * K + j] = vget<K>(t[g], j);
+          }
+        }
+        for (; v < n_stage; ++v) {
           Vec<K> t;
           const int64_t src = listed ? (int64_t)list_s[v] : (int64_t)v;
           vload<K>(t, a.cases + src * a.n_cases, c0, a.n_cases, vec_ok);

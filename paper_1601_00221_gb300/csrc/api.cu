@@ -185,10 +185,14 @@ void apply_tuned(const gp_config* user, gp_config* c, int32_t n_inputs, int64_t 
 }
 
 // Cases (or words) per block: enough blocks to fill the GPU several times
-// over, each covering whole passes of the block.
-int64_t choose_chunk(int64_t n_units, int32_t n_progs, int per_pass, int64_t user_chunk) {
+// over, each covering whole passes of the block.  blocks_per_sm: the float
+// kernels take the programs longest first and want few long blocks
+// (kAutoBlocksPerSm); the Boolean kernel keeps the caller's order and more,
+// shorter blocks.
+int64_t choose_chunk(int64_t n_units, int32_t n_progs, int per_pass, int64_t user_chunk,
+                     int blocks_per_sm) {
   if (user_chunk > 0) return user_chunk;
-  const int64_t target_blocks = 48LL * sm_count();
+  const int64_t target_blocks = (int64_t)blocks_per_sm * sm_count();
   int64_t want = (target_blocks + n_progs - 1) / std::max<int32_t>(n_progs, 1);
   want = std::max<int64_t>(want, 1);
   int64_t chunk = (n_units + want - 1) / want;
@@ -242,7 +246,7 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   cudaStream_t s = (cudaStream_t)stream;
 
   const int per_pass = c.k * c.block;
-  const int64_t chunk = choose_chunk(n_cases, n_progs, per_pass, c.chunk_cases);
+  const int64_t chunk = choose_chunk(n_cases, n_progs, per_pass, c.chunk_cases, kAutoBlocksPerSm);
   const int64_t n_chunks64 = std::max<int64_t>(1, (n_cases + chunk - 1) / chunk);
   if (n_chunks64 * n_progs > 0x7fffffffLL) return gp_fail(GP_ERR_INVALID_ARG, "too many blocks");
   const int32_t n_chunks = (int32_t)n_chunks64;
@@ -399,7 +403,7 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int per_pass = c.k * c.block;
-  const int64_t chunk = choose_chunk(n_words, n_progs, per_pass, c.chunk_cases);
+  const int64_t chunk = choose_chunk(n_words, n_progs, per_pass, c.chunk_cases, 48);
   const int64_t n_chunks64 = std::max<int64_t>(1, (n_words + chunk - 1) / chunk);
   if (n_chunks64 * n_progs > 0x7fffffffLL) return gp_fail(GP_ERR_INVALID_ARG, "too many blocks");
   Workspace* w = nullptr;

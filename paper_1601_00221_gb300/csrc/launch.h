@@ -58,6 +58,10 @@ cudaError_t launch_order_by_size(const int32_t* lengths, int32_t n, int32_t* ord
 // order the blocks by program size when the population fills this many
 // blocks per SM: below that every block starts in the first wave anyway
 constexpr int kOrderMinProgsPerSm = 2;
+// the automatic case chunk aims at this many blocks per SM: with the programs
+// taken longest first, few long blocks beat many short ones (the per-block
+// costs dominate, the tail does not)
+constexpr int kAutoBlocksPerSm = 16;
 // Boolean kernels: K words per thread.
 cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s);
 // Boolean, one program per lane over w <= 4 words (one warp per block).

@@ -40,18 +40,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocS
 
 constexpr int kMaxDevices = 64;
 
-// multiprocessors of the current device (asked once per device)
-int sm_count_cached() {
-  static int n[kMaxDevices] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 148;
-  if (n[dev] <= 0) {
-    int v = 0;
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) n[dev] = v;
-    else return 148;
-  }
-  return n[dev];
-}
 std::mutex g_mu;
 NoallocScratch* g_addr[kMaxDevices] = {};
 
@@ -117,7 +105,7 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   // chunks per program: fill the GPU, but never more partial sums than the
   // scratch holds
   const int per_pass = c.k * c.block;
-  const int64_t target_blocks = 48LL * sm_count_current();
+  const int64_t target_blocks = (int64_t)kAutoBlocksPerSm * sm_count_current();
   int64_t want = std::max<int64_t>(1, (target_blocks + n_progs - 1) / n_progs);
   want = std::min<int64_t>(want, std::max<int64_t>(1, kMaxPartials / n_progs));
   int64_t chunk = (n_cases + want - 1) / want;
@@ -161,7 +149,7 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   a.fitness_kind = c.fitness;
   a.tile_inputs = tile_inputs;
   a.order = nullptr;
-  if (n_progs >= kOrderMinProgsPerSm * sm_count_cached()) {
+  if (n_progs >= kOrderMinProgsPerSm * sm_count_current()) {
     e = launch_order_by_size(lengths, n_progs, scratch->order, s);
     if (e != cudaSuccess) return gp_fail(GP_ERR_CUDA, "ordering launch: %s", cudaGetErrorString(e));
     a.order = scratch->order;

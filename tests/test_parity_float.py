@@ -146,14 +146,15 @@ def test_error_sum_past_binary32_is_inf(fitness):
                 assert np.isfinite(f[1]) and abs(f[1] - exp[1]) <= 1e-5 * abs(exp[1]), (n_cases, k, chunk)
 
 
-@pytest.mark.parametrize("chunk_per_pass", [0, 2])
+@pytest.mark.parametrize("chunk_per_pass", [2, 6])
 def test_block_order_changes_nothing(chunk_per_pass):
     """Populations of at least two programs per SM are taken longest first
     (a counting sort of the instruction counts on the device).  1200 trees of
     1 to 255 nodes (many of equal size, a few identical): every fitness equals
     the same programs evaluated 100 at a time (too few to be reordered) bit for
     bit, and the oracle's within the bound; with several chunks per program the
-    cross-block sums stay in chunk order."""
+    cross-block sums stay in chunk order.  (The chunk is given: a chosen one
+    depends on the population's size, and with it the summation order.)"""
     progs = synth.ramped_half_and_half(313, 1200, 1, 8, 255, full_fallback_to_grow=True)
     progs[700] = progs[3]
     pop = synth.pack(progs)

@@ -423,7 +423,7 @@ def run_ours(args):
         "roofline": roofline,
         "cpu_baseline": cpu_baseline,
         "e2e": e2e,
-        "gpu_launches": args.steps * gp.eval_launches(w.pop.n),
+        "gpu_launches": args.steps * gp.eval_launches(w.pop.n, n_cases),
         "clocks": clk,
         "stack1d": compare,
         "fitness_rel_err_vs_fp64_oracle": err_stats,

@@ -406,13 +406,15 @@ int gp_autotune_population(const uint32_t* programs, const int64_t* offsets,
                            int32_t repeats, gp_config* best, gp_stream_t stream);
 int gp_autotune_clear(void);
 
-/* Kernels one float evaluation (gp_eval_population*, gp_eval_outputs,
- * gp_eval_population_noalloc) of n_progs programs launches on the current
+/* Kernels one evaluation (gp_eval_population*, gp_eval_outputs,
+ * gp_eval_population_noalloc, gp_eval_population_bool with a warp per
+ * program) of n_progs programs over n_cases cases launches on the current
  * device: the interpreter, plus the ordering kernel that takes the programs
- * longest first once n_progs fills two blocks per multiprocessor.  Writes
- * the count to *launches.  Returns GP_ERR_INVALID_ARG for a null pointer or
- * a negative count. */
-int gp_eval_launches(int32_t n_progs, int32_t* launches);
+ * longest first once n_progs fills two blocks per multiprocessor and n_cases
+ * is at least 16384.  (The Boolean variant with one program per lane launches
+ * the interpreter alone.)  Writes the count to *launches.  Returns
+ * GP_ERR_INVALID_ARG for a null pointer or a negative count. */
+int gp_eval_launches(int32_t n_progs, int64_t n_cases, int32_t* launches);
 
 /* ------------------------------------------------------------------------
  * Device-side encoder.  The S-form encoding of gp_encode_population (float

@@ -137,7 +137,7 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_server_destroy": [P],
         "gp_autotune_population": [P, P, P, i32, P, i32, i64, P, i32, P, P],
         "gp_autotune_clear": [],
-        "gp_eval_launches": [i32, P],
+        "gp_eval_launches": [i32, i64, P],
         "gp_encode_population_device": [P, P, P, i32, i32, P, P, P, P],
         "gp_evolve_create": [P, P, P, P, P, i32, i64, P, P],
         "gp_evolve_run": [P, i32],
@@ -482,11 +482,12 @@ def get_config() -> Config:
     return c
 
 
-def eval_launches(n_progs: int) -> int:
-    """Kernels one float evaluation of n_progs programs launches (the
-    interpreter, and the longest-first ordering kernel for large populations)."""
+def eval_launches(n_progs: int, n_cases: int) -> int:
+    """Kernels one evaluation of n_progs programs over n_cases cases launches
+    (the interpreter, and the longest-first ordering kernel for large
+    populations over many cases)."""
     v = ctypes.c_int32(0)
-    _check(lib().gp_eval_launches(int(n_progs), ctypes.byref(v)))
+    _check(lib().gp_eval_launches(int(n_progs), int(n_cases), ctypes.byref(v)))
     return int(v.value)
 
 

@@ -278,7 +278,7 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   a.fitness_kind = c.fitness;
   a.tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
   a.order = nullptr;
-  if (n_progs >= kOrderMinProgsPerSm * sm_count()) {
+  if (order_blocks(n_progs, n_cases, sm_count())) {
     int32_t* order = nullptr;
     rc = get_order(w, (size_t)n_progs, s, &order);
     if (rc) return rc;
@@ -384,6 +384,10 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
     a.chunk_words = 0;
     a.n_chunks = 1;
     a.aligned = 0;
+    // the caller's order: a warp's 32 programs then lie side by side in
+    // memory, and the lanes' instruction loads share cache lines (taking the
+    // programs longest first scattered them: 33-41% slower, measured)
+    a.order = nullptr;
     const size_t smem = bool_lanes_smem(w, 32, n_inputs);
     if (smem > 48 * 1024) return gp_fail(GP_ERR_INVALID_ARG, "too many inputs for the per-lane variant");
     cudaError_t el = launch_bool_lanes(a, w, (n_progs + 31) / 32, smem, (cudaStream_t)stream);
@@ -430,6 +434,15 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   a.chunk_words = chunk;
   a.n_chunks = (int32_t)n_chunks64;
   a.aligned = aligned16(case_bits) && aligned16(target_bits) && (n_inputs <= 1 || n_words % 4 == 0);
+  a.order = nullptr;
+  if (order_blocks(n_progs, n_cases, sm_count())) {
+    int32_t* order = nullptr;
+    rc = get_order(w, (size_t)n_progs, s, &order);
+    if (rc) return rc;
+    e = launch_order_by_size(lengths, n_progs, order, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering launch");
+    a.order = order;
+  }
   const size_t smem = bool_tile_bytes(c.k, c.block, n_inputs);
   if (smem > kMaxTileBytes)
     return gp_fail(GP_ERR_INVALID_ARG, "%d inputs need %zu bytes of staged inputs per block (max %zu)",
@@ -556,10 +569,10 @@ extern "C" int gp_autotune_population(const uint32_t* programs, const int64_t* o
   return GP_OK;
 }
 
-extern "C" int gp_eval_launches(int32_t n_progs, int32_t* launches) {
+extern "C" int gp_eval_launches(int32_t n_progs, int64_t n_cases, int32_t* launches) {
   gp_clear_error();
-  if (!launches || n_progs < 0) return gp_fail(GP_ERR_INVALID_ARG, "bad arguments");
-  *launches = n_progs == 0 ? 0 : (n_progs >= kOrderMinProgsPerSm * sm_count() ? 2 : 1);
+  if (!launches || n_progs < 0 || n_cases < 0) return gp_fail(GP_ERR_INVALID_ARG, "bad arguments");
+  *launches = n_progs == 0 ? 0 : (order_blocks(n_progs, n_cases, sm_count()) ? 2 : 1);
   return GP_OK;
 }
 

@@ -28,6 +28,7 @@ struct BoolArgs {
   int64_t chunk_words;  // multiple of blockDim.x * K
   int32_t n_chunks;
   int32_t aligned;      // case_bits/target_bits/out_words rows 16-byte aligned
+  const int32_t* order;  // programs longest first (launch_order_by_size), or null
 };
 
 template <int K>
@@ -106,8 +107,9 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   extern __shared__ uint4 btile_s[];  // [warp][input][32 lanes][K words]
 
   const int item = blockIdx.x;
-  const int p = item / a.n_chunks;
-  const int chunk = item - p * a.n_chunks;
+  const int rank = item / a.n_chunks;
+  const int p = a.order ? a.order[rank] : rank;
+  const int chunk = item - rank * a.n_chunks;
   const int tid = threadIdx.x;
 
   if (tid == 0) {
@@ -236,16 +238,16 @@ __global__ void __launch_bounds__(32) eval_bool_lanes_kernel(BoolArgs a) {
   extern __shared__ uint32_t lane_smem[];
   __shared__ uint32_t if_desc_s[BOOL_IF_FORMS];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint32_t* inp_s = lane_smem;                                   // [n_inputs][W]
-  uint32_t* lvl_s = lane_smem + a.n_inputs * W + warp * (R * 32 * W);  // [R][32][W]
+  uint32_t* inp_s = lane_smem;  // [n_inputs][W]; then each warp's levels [R][32][W] (lv_addr)
   if (tid < BOOL_IF_FORMS) if_desc_s[tid] = (uint32_t)if_form_desc(tid);
   for (int i = tid; i < a.n_inputs * W; i += blockDim.x) {
     const int v = i / W, w = i % W;
     inp_s[i] = (w < a.n_words) ? a.case_bits[(int64_t)v * a.n_words + w] : 0u;
   }
   __syncthreads();
-  const int p = blockIdx.x * blockDim.x + tid;
-  if (p >= a.n_progs) return;
+  const int rank = blockIdx.x * blockDim.x + tid;
+  if (rank >= a.n_progs) return;
+  const int p = a.order ? a.order[rank] : rank;  // (the launch passes no order)
 
   int n = -1;
   const uint4* prog = nullptr;

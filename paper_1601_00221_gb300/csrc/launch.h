@@ -56,8 +56,14 @@ cudaError_t launch_blockgp(const FloatArgs& a, int block, int grid, cudaStream_t
 // lengths), for FloatArgs::order; one block
 cudaError_t launch_order_by_size(const int32_t* lengths, int32_t n, int32_t* order, cudaStream_t s);
 // order the blocks by program size when the population fills this many
-// blocks per SM: below that every block starts in the first wave anyway
+// blocks per SM (below that every block starts in the first wave anyway) and
+// each program sees this many cases (below that the whole evaluation takes
+// tens of microseconds and the ordering launch would be a visible part of it)
 constexpr int kOrderMinProgsPerSm = 2;
+constexpr int64_t kOrderMinCases = 16384;
+inline bool order_blocks(int32_t n_progs, int64_t n_cases, int sms) {
+  return n_progs >= kOrderMinProgsPerSm * sms && n_cases >= kOrderMinCases;
+}
 // the automatic case chunk aims at this many blocks per SM: with the programs
 // taken longest first, few long blocks beat many short ones (the per-block
 // costs dominate, the tail does not)

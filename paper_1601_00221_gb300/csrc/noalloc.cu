@@ -149,7 +149,7 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   a.fitness_kind = c.fitness;
   a.tile_inputs = tile_inputs;
   a.order = nullptr;
-  if (n_progs >= kOrderMinProgsPerSm * sm_count_current()) {
+  if (order_blocks(n_progs, n_cases, sm_count_current())) {
     e = launch_order_by_size(lengths, n_progs, scratch->order, s);
     if (e != cudaSuccess) return gp_fail(GP_ERR_CUDA, "ordering launch: %s", cudaGetErrorString(e));
     a.order = scratch->order;

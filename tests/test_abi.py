@@ -32,9 +32,11 @@ def test_library_exports_every_declared_symbol():
 def test_eval_launches_argument_checks():
     """(answered before any device query)"""
     import pytest
-    assert gp.eval_launches(0) == 0
+    assert gp.eval_launches(0, 1000) == 0
     with pytest.raises(gp.GPError):
-        gp.eval_launches(-1)
+        gp.eval_launches(-1, 1000)
+    with pytest.raises(gp.GPError):
+        gp.eval_launches(10, -1)
 
 
 def test_library_is_built_for_sm_103a():

@@ -146,7 +146,7 @@ def test_error_sum_past_binary32_is_inf(fitness):
                 assert np.isfinite(f[1]) and abs(f[1] - exp[1]) <= 1e-5 * abs(exp[1]), (n_cases, k, chunk)
 
 
-@pytest.mark.parametrize("chunk_per_pass", [2, 6])
+@pytest.mark.parametrize("chunk_per_pass", [8, 40])
 def test_block_order_changes_nothing(chunk_per_pass):
     """Populations of at least two programs per SM are taken longest first
     (a counting sort of the instruction counts on the device).  1200 trees of
@@ -158,7 +158,7 @@ def test_block_order_changes_nothing(chunk_per_pass):
     progs = synth.ramped_half_and_half(313, 1200, 1, 8, 255, full_fallback_to_grow=True)
     progs[700] = progs[3]
     pop = synth.pack(progs)
-    x = synth.uniform_cases(77, 1, 3000)
+    x = synth.uniform_cases(77, 1, 20000)   # (enough cases per program to be ordered)
     y = synth.quartic_target(x[0])
     enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
     P, O, L = upload(enc)
@@ -176,7 +176,8 @@ def test_block_order_changes_nothing(chunk_per_pass):
     assert f_all[700] == f_all[3]
     assert_fitness(f_all, oracle.population_fitness(pop.words, pop.offsets, pop.lengths, x, y))
     # the 1200 were ordered (two launches), the groups of 100 were not
-    assert gp.eval_launches(pop.n) == 2 and gp.eval_launches(100) == 1
+    assert gp.eval_launches(pop.n, 20000) == 2 and gp.eval_launches(100, 20000) == 1
+    assert gp.eval_launches(pop.n, 2000) == 1
 
 
 def test_malformed_device_program_gives_nan_and_status():

@@ -232,7 +232,12 @@ struct EncScratch {  // per thread
   uint8_t fk[GP_DEVICE_ENCODE_MAX_NODES];     // stack: remaining children / next child
   uint8_t flevel[GP_DEVICE_ENCODE_MAX_NODES]; // stack: level of the frame's result
 };
-constexpr int kEncThreads = 16;  // small blocks spread the trees over every SM
+// One tree per warp (a block of one warp): the trees of a warp would take
+// different paths through the parser and run one after another (16 trees per
+// warp executed 2 threads per instruction, measured); as separate warps the
+// scheduler interleaves up to 32 of them per SM.  The warp copies the tree's
+// words into shared memory together; lane 0 then parses, orders and emits.
+constexpr int kEncThreads = 32;
 
 struct EncArgs {
   const uint32_t* words;
@@ -266,17 +271,18 @@ __device__ int xbin(uint32_t op) {
 // The words are the host encoder's (encode.cpp) for the same tree.
 __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncArgs a) {
   extern __shared__ EncScratch enc_s[];
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.x;  // one tree per block (a single warp)
   if (p >= a.n_progs) return;
-  EncScratch& s = enc_s[threadIdx.x];
+  EncScratch& s = enc_s[0];
   const int len = a.lengths[p];
-  uint32_t* o = a.out + a.out_offsets[p];
   bool ok = len > 0 && len <= 2 * GP_DEVICE_ENCODE_MAX_NODES;
   if (ok) {
     const uint32_t* g = a.words + a.offsets[p];
-#pragma unroll 8
-    for (int w = 0; w < len; ++w) s.tok[w] = g[w];
+    for (int w = threadIdx.x; w < len; w += kEncThreads) s.tok[w] = g[w];
   }
+  __syncwarp();
+  if (threadIdx.x != 0) return;
+  uint32_t* o = a.out + a.out_offsets[p];
   bool extended = false;
   int max_input = -1, n = 0, top = 0, w = 0;
   // 1. parse
@@ -422,9 +428,9 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncArgs a) {
 
 cudaError_t launch_encode(const EncArgs& a, cudaStream_t s) {
   static std::atomic<size_t> set{0};
-  const size_t smem = sizeof(EncScratch) * kEncThreads;
+  const size_t smem = sizeof(EncScratch);  // one tree per block
   ensure_dynamic_smem(encode_kernel, smem, set);
-  encode_kernel<<<(a.n_progs + kEncThreads - 1) / kEncThreads, kEncThreads, smem, s>>>(a);
+  encode_kernel<<<a.n_progs, kEncThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

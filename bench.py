@@ -547,7 +547,7 @@ def bench_generation_loop(gp, synth, torch, device, generations=20):
     x = synth.uniform_cases(1002, 1, 65536)
     X = torch.from_numpy(x).to(device)
     Y = torch.from_numpy(synth.quartic_target(x[0])).to(device)
-    cfg = gp.Config(gp.VARIANT_REGISTER, 8, 256, 16384, gp.FITNESS_SUM_ABS)
+    cfg = gp.Config(gp.VARIANT_REGISTER, 8, 256, 0, gp.FITNESS_SUM_ABS)
     prm = gp.EvolveParams.make(4096, list(synth.FLOAT_FUNCS), max_nodes=255, seed=1, config=cfg)
     with gp.Evolver(prm, pop.words, pop.offsets, pop.lengths, X, Y) as ev:
         ev.run(2)

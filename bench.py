@@ -470,17 +470,19 @@ def bench_boolean(gp, synth, torch, device):
         tb = torch.from_numpy(w.target_bits.view(np.int32)).to(device)
         hits = torch.empty(w.pop.n, dtype=torch.int64, device=device)
         best = None
-        cands = [(gp.VARIANT_REGISTER, kk) for kk in (1, 2, 4, 8)]
+        # K words per thread and the block size (the staged input tile, n_inputs
+        # x 32 x K words per warp, limits the blocks per SM)
+        cands = [(gp.VARIANT_REGISTER, kk, blk) for kk in (1, 2, 4, 8) for blk in (64, 128, 256)]
         if (w.n_cases + 31) // 32 <= 4:
-            cands.append((gp.VARIANT_LANES, 0))
-        for var, kk in cands:
-            cfg = gp.Config(var, kk, 0, 0)
+            cands.append((gp.VARIANT_LANES, 0, 0))
+        for var, kk, blk in cands:
+            cfg = gp.Config(var, kk, blk, 0)
             ms = _time_events(torch, lambda: gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
                                                                      hits_out=hits, config=cfg))
             if best is None or ms < best[0]:
-                best = (ms, kk if var == gp.VARIANT_REGISTER else "lane per program")
+                best = (ms, kk if var == gp.VARIANT_REGISTER else "lane per program", blk)
         gpop = w.gpop
-        out[f"{kind}{k}"] = {"programs": w.pop.n, "cases": w.n_cases, "k": best[1],
+        out[f"{kind}{k}"] = {"programs": w.pop.n, "cases": w.n_cases, "k": best[1], "block": best[2],
                              "ms": round(best[0], 4), "bit_GPop_per_s": round(gpop / best[0] / 1e6, 1)}
     return out
 

@@ -164,7 +164,22 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   for (int64_t wb = w_begin + (int64_t)warp * 32 * K; wb < w_end; wb += (int64_t)nwarps * 32 * K) {
     const int64_t w0 = wb + (int64_t)lane * K;
     const bool full = w0 + K <= a.n_words;
-    for (int v = 0; v < a.n_inputs; ++v) {
+    int v = 0;
+    if (full && a.aligned) {
+      // G inputs per step, their loads issued before their stores, so that
+      // G global round trips overlap instead of following each other
+      constexpr int G = K >= 8 ? 2 : 4;
+      for (; v + G <= a.n_inputs; v += G) {
+        UVec<K> t[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) uload<K>(t[g], a.case_bits + (int64_t)(v + g) * a.n_words, w0, a.n_words, true);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+          for (int j = 0; j < K; ++j) tile[(v + g) * 32 * K + j] = t[g].w[j];
+      }
+    }
+    for (; v < a.n_inputs; ++v) {
       UVec<K> t;
       uload<K>(t, a.case_bits + (int64_t)v * a.n_words, w0, a.n_words, full && a.aligned);
 #pragma unroll

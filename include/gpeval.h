@@ -517,7 +517,10 @@ int gp_evolve_destroy(gp_evolver* ev);
 /* ------------------------------------------------------------------------
  * Configuration, status and lifetime.
  * ---------------------------------------------------------------------- */
-/* Default configuration used when cfg is NULL or a field is 0. */
+/* Default configuration used when cfg is NULL or a field is 0.  Until it is
+ * called, Boolean evaluations over 8 or more inputs that leave k or block at
+ * 0 use k = 4 and blocks of at most 64 threads (their staged input tile
+ * limits the blocks per multiprocessor); after it, its k and block stand. */
 int gp_set_config(const gp_config* cfg);
 int gp_get_config(gp_config* cfg);
 

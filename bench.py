@@ -56,7 +56,40 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the Boolean, register-GP and serving measurements")
     ap.add_argument("--serving-runs", type=int, default=64)
+    ap.add_argument("--once", choices=["sextic512", "mux20"], default=None,
+                    help="evaluate one workload twice and exit (the small cases of the ncu "
+                         "captures): sextic512 = 512 sextic trees x 100000 cases, extended "
+                         "interpreter; mux20 = 128 20-multiplexer trees x 2^20 cases, Boolean")
     return ap.parse_args()
+
+
+def run_once(args):
+    """Two evaluations of one small workload with the library's default shape
+    for it, for a profiler to capture (no timing, no JSON line)."""
+    import numpy as np
+    import torch
+    import paper_1601_00221_gb300 as gp
+    import synth
+    if args.once == "sextic512":
+        w = synth.sextic_problem(n_progs=512)
+        enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+        P, O, L = enc.to_device("cuda")
+        X, Y = torch.from_numpy(w.cases).cuda(), torch.from_numpy(w.targets).cuda()
+        cfg = enc.config(fitness=w.fitness, k=8, block=256)
+        for _ in range(2):
+            f = gp.eval_population(P, O, L, X, Y, config=cfg)
+        out = float(f[0])
+    else:
+        b = synth.boolean_problem("mux", 20, n_progs=128)
+        enc = gp.encode_population(b.pop.words, b.pop.offsets, b.pop.lengths, gp.KIND_BOOL)
+        P, O, L = enc.to_device("cuda")
+        cb = torch.from_numpy(b.case_bits.view(np.int32)).cuda()
+        tb = torch.from_numpy(b.target_bits.view(np.int32)).cuda()
+        for _ in range(2):
+            h = gp.eval_population_bool(P, O, L, cb, b.n_cases, tb)
+        out = int(h[0])
+    torch.cuda.synchronize()
+    print(f"{args.once}: ok ({out})")
 
 
 # ---------------------------------------------------------------------------
@@ -856,7 +889,9 @@ def run_reference(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.once:
+        run_once(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -623,34 +623,42 @@ def bench_function_sets(gp, synth, torch, device):
         X = torch.from_numpy(w.cases).to(device)
         Y = torch.from_numpy(w.targets).to(device)
         fit = torch.empty(w.pop.n, dtype=torch.float64, device=device)
+        # every kernel at its best block size and case chunk (chosen, 16384 or
+        # 65536 cases per block), as the paper tuned every kernel it compared
+        chunks = (0, 16384, 65536)
         best = None
         for k in (2, 4, 8):
             for block in (128, 256):
-                cfg = enc.config(fitness=w.fitness, k=k, block=block)
-                try:
-                    ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit,
-                                                                        config=cfg), steps=3, warmup=1)
-                except gp.GPError:  # the tile does not fit this shape
-                    continue
-                if best is None or ms < best[0]:
-                    best = (ms, cfg)
+                for ch in chunks:
+                    cfg = enc.config(fitness=w.fitness, k=k, block=block)
+                    cfg.chunk_cases = ch
+                    try:
+                        ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit,
+                                                                            config=cfg), steps=3, warmup=1)
+                    except gp.GPError:  # the tile does not fit this shape
+                        continue
+                    if best is None or ms < best[0]:
+                        best = (ms, cfg)
         ms, cfg = best
         # the one-dimensional stack (one case per thread per pass) on the same trees
         one = None
         for block in (128, 256):
-            c1 = enc.config(fitness=w.fitness, k=1, block=block)
-            try:
-                t1 = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit,
-                                                                    config=c1), steps=2, warmup=1)
-            except gp.GPError:
-                continue
-            one = t1 if one is None else min(one, t1)
+            for ch in chunks:
+                c1 = enc.config(fitness=w.fitness, k=1, block=block)
+                c1.chunk_cases = ch
+                try:
+                    t1 = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit,
+                                                                        config=c1), steps=2, warmup=1)
+                except gp.GPError:
+                    continue
+                one = t1 if one is None else min(one, t1)
         # the same trees in the RPN form (the paper's other 2D-stack representation)
         encr = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_RPN)
         Pr, Or, Lr = encr.to_device(device)
         rpn = None
         for k in (4, 8):
             cr = encr.config(fitness=w.fitness, k=k, block=int(cfg.block))
+            cr.chunk_cases = int(cfg.chunk_cases)
             try:
                 tr = _time_events(torch, lambda: gp.eval_population(Pr, Or, Lr, X, Y, fitness_out=fit,
                                                                     config=cr), steps=2, warmup=1)
@@ -661,10 +669,11 @@ def bench_function_sets(gp, synth, torch, device):
         # at its best block size
         blockgp = None
         for block in (128, 256):
-            cb = gp.Config(gp.VARIANT_LOCAL, 1, block, 0, w.fitness)
-            tb = _time_events(torch, lambda: gp.eval_population(Pr, Or, Lr, X, Y, fitness_out=fit,
-                                                                config=cb), steps=1, warmup=1)
-            blockgp = tb if blockgp is None else min(blockgp, tb)
+            for ch in chunks:
+                cb = gp.Config(gp.VARIANT_LOCAL, 1, block, ch, w.fitness)
+                tb = _time_events(torch, lambda: gp.eval_population(Pr, Or, Lr, X, Y, fitness_out=fit,
+                                                                    config=cb), steps=1, warmup=1)
+                blockgp = tb if blockgp is None else min(blockgp, tb)
         del Pr, Or, Lr
         gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg)
         sample = np.arange(0, w.pop.n, w.pop.n // 4)[:4]
@@ -672,7 +681,8 @@ def bench_function_sets(gp, synth, torch, device):
         out[w.name] = {"programs": w.pop.n, "cases": int(w.cases.shape[1]),
                        "inputs": int(w.cases.shape[0]), "mean_nodes": round(float(w.pop.nodes.mean()), 2),
                        "fitness": ["sum_abs", "mse", "class_errors"][w.fitness],
-                       "k": int(cfg.k), "block": int(cfg.block), "tile_inputs": int(cfg.tile_inputs),
+                       "k": int(cfg.k), "block": int(cfg.block), "chunk_cases": int(cfg.chunk_cases),
+                       "tile_inputs": int(cfg.tile_inputs),
                        "ms": round(ms, 3), "GPop_per_s": round(w.gpop / ms / 1e6, 1),
                        "stack1d_GPop_per_s": round(w.gpop / one / 1e6, 1) if one else None,
                        "speedup_2d_over_1d": round(one / ms, 3) if one else None,

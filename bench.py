@@ -308,16 +308,18 @@ def run_ours(args):
         compare = {}
         for name, variant, blocks in (("stack1d_register_k1", gp.VARIANT_REGISTER, (128, 256, 512)),
                                       ("blockgp_local_memory", gp.VARIANT_LOCAL, (128, 256))):
+            mi = enc.max_instructions  # (each kernel's program buffer sized to the population)
             if name.startswith("blockgp"):
                 encr = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths,
-                                            gp.KIND_RPN, gp.ORDER_PAPER)
+                                            gp.KIND_RPN, gp.ORDER_PAPER, with_info=True)
                 Pr, Or, Lr = encr.to_device(device)
                 saved = (P, O, L)
                 P, O, L = Pr, Or, Lr
-            tries = [(statistics.mean(timed(gp.Config(variant, 1, b, ch), 2, 1)), b, ch)
+                mi = encr.max_instructions
+            tries = [(statistics.mean(timed(gp.Config(variant, 1, b, ch, 0, 0, 0, mi), 2, 1)), b, ch)
                      for b in blocks for ch in (0, 16384, 65536) if n_cases >= ch]
             _, b1, ch1 = min(tries)
-            tt = timed(gp.Config(variant, 1, b1, ch1), max(3, args.steps // 4), 2)
+            tt = timed(gp.Config(variant, 1, b1, ch1, 0, 0, 0, mi), max(3, args.steps // 4), 2)
             if name.startswith("blockgp"):
                 P, O, L = saved
             compare[name] = round(gpop_step / (statistics.mean(tt) / 1e3) / 1e9, 2)
@@ -509,7 +511,7 @@ def bench_boolean(gp, synth, torch, device):
         if (w.n_cases + 31) // 32 <= 4:
             cands.append((gp.VARIANT_LANES, 0, 0))
         for var, kk, blk in cands:
-            cfg = gp.Config(var, kk, blk, 0)
+            cfg = gp.Config(var, kk, blk, 0, 0, 0, 0, enc.max_instructions)
             ms = _time_events(torch, lambda: gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
                                                                      hits_out=hits, config=cfg))
             if best is None or ms < best[0]:
@@ -670,7 +672,7 @@ def bench_function_sets(gp, synth, torch, device):
         blockgp = None
         for block in (128, 256):
             for ch in chunks:
-                cb = gp.Config(gp.VARIANT_LOCAL, 1, block, ch, w.fitness)
+                cb = gp.Config(gp.VARIANT_LOCAL, 1, block, ch, w.fitness, 0, 0, encr.max_instructions)
                 tb = _time_events(torch, lambda: gp.eval_population(Pr, Or, Lr, X, Y, fitness_out=fit,
                                                                     config=cb), steps=1, warmup=1)
                 blockgp = tb if blockgp is None else min(blockgp, tb)

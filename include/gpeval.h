@@ -206,6 +206,11 @@ typedef struct gp_config {
   int32_t stack_registers; /* stack levels held in registers: 0 (or 8) = all; 4 = levels 4..7
                               in shared memory, fewer registers per thread (k = 8, the register
                               variant, GP_KIND_SFORM programs only; others fail as malformed) */
+  int32_t max_instructions; /* instructions of the longest program (0 = GP_MAX_INSTR): each
+                               block holds its program in shared memory, 16 bytes per
+                               instruction, so a small buffer leaves room for more blocks; a
+                               program with more instructions fails as malformed.  The
+                               largest gp_prog_info.n_instr of the population is enough. */
 } gp_config;
 
 /* ------------------------------------------------------------------------

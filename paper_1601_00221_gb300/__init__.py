@@ -65,7 +65,7 @@ class _ServerOpts(ctypes.Structure):
                 ("memory_budget", ctypes.c_int64), ("variant", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("block", ctypes.c_int32), ("chunk_cases", ctypes.c_int32),
                 ("fitness", ctypes.c_int32), ("tile_inputs", ctypes.c_int32),
-                ("stack_registers", ctypes.c_int32)]
+                ("stack_registers", ctypes.c_int32), ("max_instructions", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -89,15 +89,19 @@ class ServerStats(ctypes.Structure):
 class Config(ctypes.Structure):
     """gp_config: variant, k (cases per thread per pass), block, chunk_cases
     (0 = choose), fitness (FITNESS_SUM_ABS, FITNESS_MSE or FITNESS_CLASS),
-    tile_inputs (inputs per case the shared-memory tile holds, 0 = all)."""
+    tile_inputs (inputs per case the shared-memory tile holds, 0 = all),
+    stack_registers, max_instructions (the longest program's instructions,
+    0 = the API maximum: the per-block program buffer)."""
     _fields_ = [("variant", ctypes.c_int32), ("k", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("chunk_cases", ctypes.c_int32), ("fitness", ctypes.c_int32),
-                ("tile_inputs", ctypes.c_int32), ("stack_registers", ctypes.c_int32)]
+                ("tile_inputs", ctypes.c_int32), ("stack_registers", ctypes.c_int32),
+                ("max_instructions", ctypes.c_int32)]
 
     def __repr__(self):
         return (f"Config(variant={self.variant}, k={self.k}, block={self.block}, "
                 f"chunk_cases={self.chunk_cases}, fitness={self.fitness}, "
-                f"tile_inputs={self.tile_inputs}, stack_registers={self.stack_registers})")
+                f"tile_inputs={self.tile_inputs}, stack_registers={self.stack_registers}, "
+                f"max_instructions={self.max_instructions})")
 
 
 _lib = None
@@ -201,16 +205,24 @@ class EncodedPopulation:
             return 0
         return int(self.info["inputs_used"].max())
 
+    @property
+    def max_instructions(self) -> int:
+        """Instructions of the longest program (0 when unknown: the API maximum)."""
+        if self.info is None or self.n == 0 or "n_instr" not in self.info.dtype.names:
+            return 0
+        return max(int(self.info["n_instr"].max()), 1)
+
     def config(self, fitness: int = FITNESS_SUM_ABS, k: int = 0, block: int = 0,
                chunk_cases: int = 0) -> "Config":
         """A configuration that can run this population with the given fitness
         measure: the extended interpreter when some program needs it, and a
-        staged-input tile no larger than the population needs."""
+        staged-input tile and a program buffer no larger than the population
+        needs."""
         variant = VARIANT_AUTO
         if self.extended:
             variant = VARIANT_EXTENDED_RPN if self.kind == KIND_RPN else VARIANT_EXTENDED
         tile = max(self.max_inputs_used, 1) if self.kind in (KIND_SFORM, KIND_RPN) else 0
-        return Config(variant, k, block, chunk_cases, fitness, tile)
+        return Config(variant, k, block, chunk_cases, fitness, tile, 0, self.max_instructions)
 
     def to_device(self, device="cuda"):
         import torch
@@ -386,7 +398,8 @@ class Server:
                  memory_budget=1 << 30, config: Optional[Config] = None):
         c = config or Config()
         opts = _ServerOpts(n_streams, max_inflight, max_queued, max_merge, memory_budget,
-                           c.variant, c.k, c.block, 0, c.fitness, c.tile_inputs, c.stack_registers)
+                           c.variant, c.k, c.block, 0, c.fitness, c.tile_inputs, c.stack_registers,
+                           c.max_instructions)
         self._h = ctypes.c_void_p()
         _check(lib().gp_server_create(ctypes.byref(opts), ctypes.byref(self._h)))
         self._results = {}  # request id -> (buffer, keep-alive)

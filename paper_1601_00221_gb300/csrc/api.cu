@@ -148,7 +148,12 @@ int resolve_config(const gp_config* user, gp_config* c) {
     if (user->fitness) c->fitness = user->fitness;
     c->tile_inputs = user->tile_inputs;
     c->stack_registers = user->stack_registers;
+    c->max_instructions = user->max_instructions;
   }
+  if (c->max_instructions < 0 || c->max_instructions > gpisa::MAX_INSTR)
+    return gp_fail(GP_ERR_INVALID_ARG, "max_instructions must be 0..%d (got %d)", gpisa::MAX_INSTR,
+                   c->max_instructions);
+  if (c->max_instructions == 0) c->max_instructions = gpisa::MAX_INSTR;
   if (c->stack_registers == gpisa::R) c->stack_registers = 0;
   if (c->stack_registers != 0 && c->stack_registers != 4)
     return gp_fail(GP_ERR_INVALID_ARG, "stack_registers must be 0, 4 or 8 (got %d)", c->stack_registers);
@@ -279,6 +284,7 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   a.want_fitness = fitness_out != nullptr;
   a.fitness_kind = c.fitness;
   a.tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
+  a.prog_cap = c.max_instructions;
   a.order = nullptr;
   if (order_blocks(n_progs, n_cases, sm_count())) {
     int32_t* order = nullptr;
@@ -293,13 +299,14 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   const bool rl4 = c.stack_registers == 4;
   if (rl4 && (c.k != 8 || c.variant != GP_VARIANT_REGISTER))
     return gp_fail(GP_ERR_INVALID_ARG, "stack_registers = 4 needs k = 8 and the register variant");
-  const size_t smem = float_tile_bytes(c.k, c.block, a.tile_inputs) +
-                      (rl4 ? (size_t)(c.block / 32) * spill_bytes_per_warp<8, 4>() : 0);
-  if (c.variant != GP_VARIANT_LOCAL && smem > kMaxTileBytes)
+  const size_t tile_bytes = float_tile_bytes(c.k, c.block, a.tile_inputs) +
+                            (rl4 ? (size_t)(c.block / 32) * spill_bytes_per_warp<8, 4>() : 0);
+  const size_t smem = prog_buffer_bytes(a.prog_cap) + tile_bytes;
+  if (c.variant != GP_VARIANT_LOCAL && tile_bytes > kMaxTileBytes)
     return gp_fail(GP_ERR_INVALID_ARG,
                    "a tile of %d inputs needs %zu bytes of shared memory per block (max %zu): "
                    "lower k, block or tile_inputs",
-                   a.tile_inputs, smem, kMaxTileBytes);
+                   a.tile_inputs, tile_bytes, kMaxTileBytes);
   cudaError_t e;
   if (c.variant == GP_VARIANT_LOCAL) e = launch_blockgp(a, c.block, grid, s);
   else if (rl4) e = launch_float_k8_rl4(a, xreg, c.block, grid, smem, s);
@@ -386,6 +393,7 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
     a.chunk_words = 0;
     a.n_chunks = 1;
     a.aligned = 0;
+    a.prog_cap = gpisa::MAX_INSTR;  // (programs are read from global memory)
     // the caller's order: a warp's 32 programs then lie side by side in
     // memory, and the lanes' instruction loads share cache lines (taking the
     // programs longest first scattered them: 33-41% slower, measured)
@@ -445,6 +453,7 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   a.out_words = out_words;
   a.status = w->status;
   a.chunk_words = chunk;
+  a.prog_cap = c.max_instructions;
   a.n_chunks = (int32_t)n_chunks64;
   a.aligned = aligned16(case_bits) && aligned16(target_bits) && (n_inputs <= 1 || n_words % 4 == 0);
   a.order = nullptr;
@@ -456,10 +465,11 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
     if (e != cudaSuccess) return cuda_fail(e, "ordering launch");
     a.order = order;
   }
-  const size_t smem = bool_tile_bytes(c.k, c.block, n_inputs);
-  if (smem > kMaxTileBytes)
+  const size_t tile_bytes = bool_tile_bytes(c.k, c.block, n_inputs);
+  if (tile_bytes > kMaxTileBytes)
     return gp_fail(GP_ERR_INVALID_ARG, "%d inputs need %zu bytes of staged inputs per block (max %zu)",
-                   n_inputs, smem, kMaxTileBytes);
+                   n_inputs, tile_bytes, kMaxTileBytes);
+  const size_t smem = prog_buffer_bytes(c.max_instructions) + tile_bytes;
   e = launch_bool(a, c.k, c.block, (int)(n_progs * n_chunks64), smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return GP_OK;

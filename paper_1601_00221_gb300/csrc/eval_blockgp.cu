@@ -11,7 +11,7 @@ namespace gpdev {
 
 __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
   using namespace gpisa;
-  __shared__ uint4 prog_s[MAX_INSTR];
+  extern __shared__ uint4 prog_s[];  // prog_cap instructions (dynamic)
   __shared__ Partial red_s[32];
   __shared__ int meta_s;
   const int item = blockIdx.x;
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
       const uint4 h = *reinterpret_cast<const uint4*>(a.programs + off);
       const int n = (int)h.y;
       if (((h.x & 0xffu) == K_RPN || (h.x & 0xffu) == K_RPNX) && (h.x >> 16) == VERSION && n >= 1 &&
-          n <= MAX_INSTR &&
+          n <= a.prog_cap &&
           4 + 4 * (int64_t)n <= len)
         n_instr = n;
     }
@@ -134,7 +134,10 @@ __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
 }
 
 cudaError_t launch_blockgp(const FloatArgs& a, int block, int grid, cudaStream_t s) {
-  eval_blockgp_kernel<<<grid, block, 0, s>>>(a);
+  static std::atomic<size_t> set{0};
+  const size_t smem = 16u * (size_t)a.prog_cap;  // the program (no sentinel: the loop counts)
+  ensure_dynamic_smem(eval_blockgp_kernel, smem, set);
+  eval_blockgp_kernel<<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ struct BoolArgs {
   int32_t n_chunks;
   int32_t aligned;      // case_bits/target_bits/out_words rows 16-byte aligned
   const int32_t* order;  // programs longest first (launch_order_by_size), or null
+  int32_t prog_cap;      // instructions the block's program buffer holds (gp_config.max_instructions)
 };
 
 template <int K>
@@ -101,10 +102,13 @@ __device__ __forceinline__ bool valid_bool_instr(const uint4& in, int n_inputs) 
 template <int K>
 __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   using namespace gpisa;
-  __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
+  // dynamic: the program (prog_cap instructions + the end sentinel), then the
+  // staged inputs [warp][input][32 lanes][K words]
+  extern __shared__ uint4 dyn_s[];
+  uint4* prog_s = dyn_s;
+  uint4* btile_s = dyn_s + a.prog_cap + 1;
   __shared__ unsigned long long red_s[32];
   __shared__ int meta_s;
-  extern __shared__ uint4 btile_s[];  // [warp][input][32 lanes][K words]
 
   const int item = blockIdx.x;
   const int rank = item / a.n_chunks;
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
     if ((off & 3) == 0 && len >= 4) {
       const uint4 h = *reinterpret_cast<const uint4*>(a.programs + off);
       const int n = (int)h.y;
-      if ((h.x & 0xffu) == K_BOOL && (h.x >> 16) == VERSION && n >= 1 && n <= MAX_INSTR &&
+      if ((h.x & 0xffu) == K_BOOL && (h.x >> 16) == VERSION && n >= 1 && n <= a.prog_cap &&
           4 + 4 * (int64_t)n <= len)
         n_instr = n;
     }

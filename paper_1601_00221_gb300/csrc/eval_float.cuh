@@ -58,6 +58,7 @@ struct FloatArgs {
   int32_t o_aligned;     // outputs + p*n_cases 16-byte aligned for every p
   int32_t want_fitness;  // compute the fitness (targets may be null only if n_cases == 0)
   int32_t fitness_kind;  // FIT_SUM_ABS, FIT_MSE or FIT_CLASS
+  int32_t prog_cap;      // instructions the block's program buffer holds (gp_config.max_instructions)
   const int32_t* order;  // the program of the i-th (program, chunks) group of blocks, longest
                          // first (launch_order_by_size), or null for 0, 1, 2, ...
   int32_t tile_inputs;   // inputs per case the staged tile holds (<= n_inputs)
@@ -395,11 +396,13 @@ __device__ __forceinline__ bool valid_instr_ext(uint32_t kind, const uint4& in, 
 template <int K, bool XREG, int EXT = 0, int RL = gpisa::R>
 __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
   using namespace gpisa;
-  __shared__ uint4 prog_s[MAX_INSTR + 1];  // program + end sentinel
+  // dynamic: the program (prog_cap instructions + the end sentinel), then the
+  // tiles [warp][slot][32 lanes][K] when staged
+  extern __shared__ uint4 dyn_s[];
+  uint4* prog_s = dyn_s;
+  float4* tile_s = reinterpret_cast<float4*>(dyn_s + a.prog_cap + 1);
   __shared__ Partial red_s[32];
   __shared__ int meta_s[2];  // n_instr (or -1 if bad), kind
-  // dynamic: the tiles [warp][slot][32 lanes][K] when staged
-  extern __shared__ float4 tile_s[];
   __shared__ uint32_t list_s[GP_COMPACT_MAX_LIST];  // input of each staged slot
   __shared__ uint32_t used_s[GP_COMPACT_MAX_INPUTS / 32];  // bitmap of the inputs read
   __shared__ uint32_t before_s[GP_COMPACT_MAX_INPUTS / 32];  // set bits in earlier words
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
                            : RL < R    ? kind == K_SFORM
                                        : (kind == K_SFORM || kind == K_RPN || kind == K_LINEAR);
       const bool ver_ok = (h.x >> 16) == VERSION;
-      const bool n_ok = n >= (kind == K_LINEAR ? 0 : 1) && n <= MAX_INSTR && 4 + 4 * (int64_t)n <= len;
+      const bool n_ok = n >= (kind == K_LINEAR ? 0 : 1) && n <= a.prog_cap && 4 + 4 * (int64_t)n <= len;
       if (kind_ok && ver_ok && n_ok) n_instr = n;
     }
     meta_s[0] = n_instr;
@@ -666,10 +669,13 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
 }
 
 // dynamic shared memory of eval_float_kernel: the staged input tiles, for
-// tile_inputs inputs per case
+// tile_inputs inputs per case (the program buffer comes on top of it)
 inline size_t float_tile_bytes(int k, int block, int tile_inputs) {
   return sizeof(float) * (size_t)(block / 32) * (size_t)tile_inputs * 32u * (size_t)k;
 }
+// the program buffer at the start of the dynamic shared memory: prog_cap
+// instructions and the end sentinel
+inline size_t prog_buffer_bytes(int prog_cap) { return 16u * (size_t)(prog_cap + 1); }
 
 // ---------------------------------------------------------------------------
 // BlockGP-style one-dimensional stack (Sec. 3, Sec. 4.1 prior art): one case

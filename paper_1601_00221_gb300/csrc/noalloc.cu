@@ -115,10 +115,12 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
     return gp_fail(GP_ERR_INVALID_ARG, "%lld partial sums exceed the fixed scratch of %lld",
                    (long long)(n_chunks * n_progs), (long long)kMaxPartials);
   const int32_t tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
-  const size_t smem = float_tile_bytes(c.k, c.block, tile_inputs);
-  if (smem > 200 * 1024)
+  const size_t tile_bytes = float_tile_bytes(c.k, c.block, tile_inputs);
+  if (tile_bytes > 200 * 1024)
     return gp_fail(GP_ERR_INVALID_ARG, "a tile of %d inputs needs %zu bytes of shared memory per block",
-                   tile_inputs, smem);
+                   tile_inputs, tile_bytes);
+  const int32_t prog_cap = c.max_instructions > 0 ? c.max_instructions : gpisa::MAX_INSTR;
+  const size_t smem = prog_buffer_bytes(prog_cap) + tile_bytes;
 
   // the array keeps the previous call's contents: clear the counters this
   // call relies on and the status word
@@ -148,6 +150,7 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   a.want_fitness = 1;
   a.fitness_kind = c.fitness;
   a.tile_inputs = tile_inputs;
+  a.prog_cap = prog_cap;
   a.order = nullptr;
   if (order_blocks(n_progs, n_cases, sm_count_current())) {
     e = launch_order_by_size(lengths, n_progs, scratch->order, s);

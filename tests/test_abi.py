@@ -65,7 +65,7 @@ def test_binding_structs_match_the_header(tmp_path):
                "gp_server_opts": gp._ServerOpts, "gp_evolve_params": gp.EvolveParams,
                "gp_request_info": gp.RequestInfo, "gp_server_stats": gp.ServerStats}
     nested = {"gp_server_opts": {"variant", "k", "block", "chunk_cases", "fitness", "tile_inputs",
-                                 "stack_registers"}}
+                                 "stack_registers", "max_instructions"}}
 
     def member(cname, fname):  # the binding flattens gp_server_opts.config
         return f"config.{fname}" if fname in nested.get(cname, ()) else fname

@@ -144,3 +144,33 @@ def test_program_per_lane_ragged(n_cases):
                                    config=gp.Config(gp.VARIANT_LANES, 0, 0, 0)).cpu().numpy()
     exp = oracle.bool_population_hits(w.pop.words, w.pop.offsets, w.pop.lengths, cb, n_cases, tb)
     assert np.array_equal(hits.astype(np.uint64), exp)
+
+
+@pytest.mark.parametrize("k", [2, 8])
+def test_program_buffer_sized_to_the_population(k):
+    """gp_config.max_instructions: with the population's largest instruction
+    count the hits equal those with the full program buffer, and the oracle's;
+    a program longer than the buffer is reported malformed, the others are
+    unaffected."""
+    w = synth.boolean_problem("mux", 11, n_progs=400)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL)
+    P, O, L = upload(enc)
+    cb, tb = dev(w.case_bits.view(np.int32)), dev(w.target_bits.view(np.int32))
+    n_instr = enc.info["n_instr"]
+    exp = oracle.bool_population_hits(w.pop.words, w.pop.offsets, w.pop.lengths, w.case_bits,
+                                      w.n_cases, w.target_bits)
+    full = gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
+                                   config=gp.Config(gp.VARIANT_REGISTER, k, 64, 0)).cpu().numpy()
+    tight = gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
+                                    config=gp.Config(gp.VARIANT_REGISTER, k, 64, 0, 0, 0, 0,
+                                                     enc.max_instructions)).cpu().numpy()
+    assert np.array_equal(full.view(np.uint64), exp) and np.array_equal(tight.view(np.uint64), exp)
+    cap = int(n_instr.max()) - 1  # the longest programs no longer fit
+    gp.last_error()
+    short = gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
+                                    config=gp.Config(gp.VARIANT_REGISTER, k, 64, 0, 0, 0, 0, cap)
+                                    ).cpu().numpy().view(np.uint64)
+    over = n_instr > cap
+    assert over.sum() >= 1 and np.all(short[over] == np.uint64(0xFFFFFFFFFFFFFFFF))
+    assert np.array_equal(short[~over], exp[~over])
+    assert gp.last_error() == 2

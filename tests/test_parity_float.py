@@ -180,6 +180,36 @@ def test_block_order_changes_nothing(chunk_per_pass):
     assert gp.eval_launches(pop.n, 2000) == 1
 
 
+@pytest.mark.parametrize("variant,kind", [(gp.VARIANT_REGISTER, gp.KIND_SFORM), (gp.VARIANT_REGISTER, gp.KIND_RPN),
+                                          (gp.VARIANT_LOCAL, gp.KIND_RPN)])
+def test_program_buffer_sized_to_the_population(variant, kind):
+    """gp_config.max_instructions: with the population's largest instruction
+    count the fitness equals the full-buffer fitness bit for bit; a program
+    longer than the buffer is reported malformed (NaN, status 2), the others
+    are unaffected; values outside 0..GP_MAX_INSTR are rejected."""
+    w = synth.regression_small(seed=317, n_progs=400, n_cases=4096)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, kind)
+    P, O, L = upload(enc)
+    X, Y = dev(w.cases), dev(w.targets)
+    k = 1 if variant == gp.VARIANT_LOCAL else 8
+    base = gp.Config(variant, k, 128, 0)
+    full = gp.eval_population(P, O, L, X, Y, config=base).cpu().numpy()
+    tight_cfg = gp.Config(variant, k, 128, 0, 0, 0, 0, enc.max_instructions)
+    tight = gp.eval_population(P, O, L, X, Y, config=tight_cfg).cpu().numpy()
+    assert np.array_equal(full.view(np.uint64), tight.view(np.uint64))
+    n_instr = enc.info["n_instr"]
+    cap = int(n_instr.max()) - 1
+    gp.last_error()
+    short = gp.eval_population(P, O, L, X, Y, config=gp.Config(variant, k, 128, 0, 0, 0, 0, cap)).cpu().numpy()
+    over = n_instr > cap
+    assert over.sum() >= 1 and np.isnan(short[over]).all()
+    assert np.array_equal(short[~over].view(np.uint64), full[~over].view(np.uint64))
+    assert gp.last_error() == 2
+    for bad in (-1, 1025):
+        with pytest.raises(gp.GPError):
+            gp.eval_population(P, O, L, X, Y, config=gp.Config(variant, k, 128, 0, 0, 0, 0, bad))
+
+
 def test_malformed_device_program_gives_nan_and_status():
     w = synth.regression_small(n_progs=8, n_cases=256)
     enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)

@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--once", choices=["sextic512", "mux20"], default=None,
                     help="evaluate one workload twice and exit (the small cases of the ncu "
                          "captures): sextic512 = 512 sextic trees x 100000 cases, extended "
-                         "interpreter; mux20 = 128 20-multiplexer trees x 2^20 cases, Boolean")
+                         "interpreter; mux20 = 128 20-multiplexer trees x 2^20 cases, Boolean "
+                         "(both with the program buffer sized to the population)")
     return ap.parse_args()
 
 
@@ -85,8 +86,9 @@ def run_once(args):
         P, O, L = enc.to_device("cuda")
         cb = torch.from_numpy(b.case_bits.view(np.int32)).cuda()
         tb = torch.from_numpy(b.target_bits.view(np.int32)).cuda()
+        cfg = gp.Config(gp.VARIANT_REGISTER, 0, 0, 0, 0, 0, 0, enc.max_instructions)  # default K, block
         for _ in range(2):
-            h = gp.eval_population_bool(P, O, L, cb, b.n_cases, tb)
+            h = gp.eval_population_bool(P, O, L, cb, b.n_cases, tb, config=cfg)
         out = int(h[0])
     torch.cuda.synchronize()
     print(f"{args.once}: ok ({out})")

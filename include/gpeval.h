@@ -424,7 +424,7 @@ int gp_eval_launches(int32_t n_progs, int64_t n_cases, int32_t* launches);
 /* ------------------------------------------------------------------------
  * Device-side encoder.  The S-form encoding of gp_encode_population (float
  * trees, basic or extended functions; Sec. 5 symbolic stack), run on the GPU
- * with one thread per tree, so that a generation loop needs no host
+ * with one warp per tree, so that a generation loop needs no host
  * conversion between generations (the paper converts on the host, Sec. 5).
  * Output words are identical to gp_encode_population's for the same trees.
  *   words, offsets, lengths   device: the trees in the user token format.

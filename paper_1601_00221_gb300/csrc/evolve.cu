@@ -218,26 +218,31 @@ __global__ void __launch_bounds__(128) vary_kernel(VaryArgs a) {
 __global__ void bump_generation(int32_t* g) { *g += 1; }
 
 // ---------------------------------------------------------------------------
-// device encoder: one thread per tree, scratch in shared memory
+// device encoder: one tree per warp, scratch in shared memory
 // ---------------------------------------------------------------------------
-struct EncScratch {  // per thread
+struct EncScratch {  // per tree; node indices fit a byte (at most 256 nodes)
   uint32_t tok[2 * GP_DEVICE_ENCODE_MAX_NODES];  // the tree's words
-  uint16_t pos[GP_DEVICE_ENCODE_MAX_NODES];   // word position of each node
-  uint16_t cnt[GP_DEVICE_ENCODE_MAX_NODES];   // nodes in its subtree
-  uint8_t op[GP_DEVICE_ENCODE_MAX_NODES];     // opcode
-  uint8_t need[GP_DEVICE_ENCODE_MAX_NODES];   // stack levels its subtree needs
-  uint8_t ord[GP_DEVICE_ENCODE_MAX_NODES];    // function children in evaluation order:
-                                              // child ranks in bits 0-1, 2-3, 4-5, count in 6-7
-  uint16_t fnode[GP_DEVICE_ENCODE_MAX_NODES]; // stack: node (parse: open node; emit: frame)
-  uint8_t fk[GP_DEVICE_ENCODE_MAX_NODES];     // stack: remaining children / next child
-  uint8_t flevel[GP_DEVICE_ENCODE_MAX_NODES]; // stack: level of the frame's result
+  union {
+    int16_t open[GP_DEVICE_ENCODE_MAX_NODES];  // operand slots open before each node, minus 1
+    int32_t path[GP_DEVICE_ENCODE_MAX_NODES];  // placement: first instruction | level << 16
+  } u;
+  uint16_t pos[GP_DEVICE_ENCODE_MAX_NODES];      // word position of each node
+  uint8_t opa[GP_DEVICE_ENCODE_MAX_NODES];       // opcode | arity << 6
+  uint8_t par[GP_DEVICE_ENCODE_MAX_NODES];       // parent; then the pointer-jumping link
+  uint8_t ch[3][GP_DEVICE_ENCODE_MAX_NODES];     // children, in operand order
+  uint8_t need[GP_DEVICE_ENCODE_MAX_NODES];      // stack levels its subtree needs (0: a terminal,
+                                                 // or a function node not yet finished)
+  uint8_t ord[GP_DEVICE_ENCODE_MAX_NODES];       // function children in evaluation order:
+                                                 // child ranks in bits 0-1, 2-3, 4-5, count in 6-7
+  uint8_t fc[GP_DEVICE_ENCODE_MAX_NODES];        // function nodes in its subtree
 };
-// One tree per warp (a block of one warp): the trees of a warp would take
-// different paths through the parser and run one after another (16 trees per
-// warp executed 2 threads per instruction, measured); as separate warps the
-// scheduler interleaves up to 32 of them per SM.  The warp copies the tree's
-// words into shared memory together; lane 0 then parses, orders and emits.
+// One tree per warp (a block of one warp), every step spread over the lanes:
+// as separate warps the scheduler interleaves up to 32 trees per SM.  (One
+// lane encoding a tree serially took about 770 cycles per node, measured.)
 constexpr int kEncThreads = 32;
+constexpr int kEncWordsPerLane = 2 * GP_DEVICE_ENCODE_MAX_NODES / kEncThreads;  // 16
+constexpr int kEncNodesPerLane = GP_DEVICE_ENCODE_MAX_NODES / kEncThreads;      // 8
+static_assert(kEncWordsPerLane <= 32, "word flags are kept in one 32-bit mask");
 
 struct EncArgs {
   const uint32_t* words;
@@ -251,179 +256,378 @@ struct EncArgs {
   unsigned long long* node_total;  // may be null: adds the nodes of every tree encoded
 };
 
-__device__ __forceinline__ int child_at(const EncScratch& s, int v, int rank) {
-  int c = v + 1;
-  for (int k = 0; k < rank; ++k) c += s.cnt[c];
-  return c;
-}
-
 __device__ int xbin(uint32_t op) {
   return op == GP_OP_GT ? XB_GT : op == GP_OP_LT ? XB_LT : op == GP_OP_EQ ? XB_EQ
                                 : op == GP_OP_AND ? XB_AND : XB_OR;
 }
 
-// One tree per thread: (1) copy its words to shared memory and parse them into
-// nodes (positions, opcodes, subtree sizes); (2) from the leaves up, the levels
-// each subtree needs and the evaluation order of each node's function
-// children (by decreasing need, stable, for GP_ORDER_MIN_DEPTH; left to right
-// for GP_ORDER_PAPER); (3) emit the S-form post-order: a node's function
-// children at levels l, l + 1, ... in that order, then the node at level l.
-// The words are the host encoder's (encode.cpp) for the same tree.
+__device__ __forceinline__ int enc_arity(const EncScratch& s, int v) { return s.opa[v] >> 6; }
+
+// A function node u whose children are all finished: the levels its subtree
+// needs, the evaluation order of its function children (by decreasing need,
+// stable, for GP_ORDER_MIN_DEPTH; operand order for GP_ORDER_PAPER) and the
+// function nodes of its subtree.  A function child placed k-th is evaluated
+// at level l + k, so the subtree needs max over k of (k + the child's need).
+__device__ __forceinline__ void enc_finish(EncScratch& s, int u, int ar, int order) {
+  int rk0 = 0, rk1 = 0, rk2 = 0, nd0 = -1, nd1 = -1, nd2 = -1, m = 0, f = 1;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (q < ar) {
+      const int c = s.ch[q][u];
+      const int nd = s.need[c];
+      if (nd > 0) {
+        if (m == 0) { rk0 = q; nd0 = nd; }
+        else if (m == 1) { rk1 = q; nd1 = nd; }
+        else { rk2 = q; nd2 = nd; }
+        ++m;
+        f += s.fc[c];
+      }
+    }
+  }
+  if (order == GP_ORDER_MIN_DEPTH) {  // a stable exchange network; empty slots (-1) stay last
+    int t;
+    if (nd1 > nd0) { t = nd0; nd0 = nd1; nd1 = t; t = rk0; rk0 = rk1; rk1 = t; }
+    if (nd2 > nd1) { t = nd1; nd1 = nd2; nd2 = t; t = rk1; rk1 = rk2; rk2 = t; }
+    if (nd1 > nd0) { t = nd0; nd0 = nd1; nd1 = t; t = rk0; rk0 = rk1; rk1 = t; }
+  }
+  int need = 1;
+  if (m > 0) need = max(need, nd0);
+  if (m > 1) need = max(need, 1 + nd1);
+  if (m > 2) need = max(need, 2 + nd2);
+  s.need[u] = (uint8_t)min(need, 255);
+  s.ord[u] = (uint8_t)(((uint32_t)m << 6) | (uint32_t)rk0 | ((uint32_t)rk1 << 2) | ((uint32_t)rk2 << 4));
+  s.fc[u] = (uint8_t)f;
+}
+
+// The S-form instruction of function node v with its result at level l: its
+// code from the opcode and the operand kinds (input, constant, or stack level
+// l + r for the function child evaluated r-th); payloads in operand order.
+__device__ __forceinline__ uint4 enc_instruction(const EncScratch& s, int v, int l) {
+  const uint32_t op = s.opa[v] & 63u;
+  const int ar = enc_arity(s, v);
+  const uint32_t od = s.ord[v];
+  const int np = (int)(od >> 6);
+  int k0 = 0, k1 = 0, k2 = 0;  // 0 input, 1 constant, 2 + r stack level l + r
+  uint32_t p0 = 0u, p1 = 0u, p2 = 0u;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (q < ar) {
+      const int c = s.ch[q][v];
+      if (enc_arity(s, c) == 0) {
+        const bool var = (s.opa[c] & 63u) == GP_OP_VAR;
+        const uint32_t pay = var ? (s.tok[s.pos[c]] >> 8) : s.tok[s.pos[c] + 1];
+        const int kind = var ? 0 : 1;
+        if (q == 0) { k0 = kind; p0 = pay; }
+        else if (q == 1) { k1 = kind; p1 = pay; }
+        else { k2 = kind; p2 = pay; }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    if (r < np) {
+      const uint32_t q = (od >> (2 * r)) & 3u;
+      if (q == 0) k0 = 2 + r;
+      else if (q == 1) k1 = 2 + r;
+      else k2 = 2 + r;
+    }
+  }
+  uint32_t code;
+  if (ar == 1) {
+    const int uf = k0 == 0 ? UF_X : k0 == 1 ? UF_C : UF_S;
+    code = (uint32_t)sfx_un_code(uf, l, (int)(op - GP_OP_SIN));
+  } else if (ar == 3) {
+    code = (uint32_t)sfx_if_code(xif_form_index(k0, k1, k2), l);
+  } else {
+    // forms by (a, b): X X, X C, C X, C C, S0 X, X S0, S0 C, C S0, S0 S1, S1 S0
+    int form;
+    if (k0 < 2 && k1 < 2) form = k0 == 0 ? (k1 == 0 ? SF_XX : SF_XC) : (k1 == 0 ? SF_CX : SF_CC);
+    else if (k0 == 2 && k1 < 2) form = k1 == 0 ? SF_SX : SF_SC;
+    else if (k1 == 2 && k0 < 2) form = k0 == 0 ? SF_XS : SF_CS;
+    else form = k0 == 2 ? SF_SS : SF_SSR;
+    code = (op >= GP_OP_ADD && op <= GP_OP_DIV) ? (uint32_t)sform_code(form, l, (int)(op - GP_OP_ADD))
+                                               : (uint32_t)sfx_bin_code(form, l, xbin(op));
+  }
+  return make_uint4(code, p0, p1, p2);
+}
+
+__device__ __forceinline__ int enc_warp_scan(int x, int lane) {  // inclusive prefix sum
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  return x;
+}
+
+// One tree per warp (Sec. 5's conversion, every step over the lanes):
+// (1) the words' node starts (a scan over a two-state automaton: a word is a
+//     node unless it is a constant's payload) and each node's opcode and arity;
+// (2) open[v], the sum of (arity - 1) over the nodes before v (a scan);
+// (3) each node's parent, the nearest earlier node u with open[u] <= open[v],
+//     and its operand position open[u] - open[v] + arity(u) - 1;
+// (4) from the leaves up, in rounds, each function node's need, child order
+//     and function count;
+// (5) the S-form post-order placement: a node's function children in
+//     evaluation order take levels l, l + 1, ... and consecutive runs of
+//     instructions from the start of the node's own run, which the node's
+//     instruction ends -- path sums from the root, by pointer jumping;
+// (6) the instructions, one node per lane.
+// The words are the host encoder's (encode.cpp) for the same tree.  The
+// warp's control flow is uniform: `ok` and n come from warp votes and
+// shuffles.
 __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncArgs a) {
   extern __shared__ EncScratch enc_s[];
   const int p = blockIdx.x;  // one tree per block (a single warp)
   if (p >= a.n_progs) return;
   EncScratch& s = enc_s[0];
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x;
   const int len = a.lengths[p];
+  uint32_t* o = a.out + a.out_offsets[p];
+  uint32_t* ins = o + 4;
   bool ok = len > 0 && len <= 2 * GP_DEVICE_ENCODE_MAX_NODES;
   if (ok) {
     const uint32_t* g = a.words + a.offsets[p];
-    for (int w = threadIdx.x; w < len; w += kEncThreads) s.tok[w] = g[w];
+    for (int w = lane; w < len; w += kEncThreads) s.tok[w] = g[w];
   }
   __syncwarp();
-  if (threadIdx.x != 0) return;
-  uint32_t* o = a.out + a.out_offsets[p];
+  int n = 0, max_input = -1, depth = 1;
   bool extended = false;
-  int max_input = -1, n = 0, top = 0, w = 0;
-  // 1. parse
-  while (ok && w < len) {
-    if (n > 0 && top == 0) { ok = false; break; }          // trailing tokens
-    if (n >= GP_DEVICE_ENCODE_MAX_NODES) { ok = false; break; }
-    const uint32_t tk = s.tok[w];
-    const uint32_t op = tk & 0xffu;
-    int ar = 0;
-    s.pos[n] = (uint16_t)w;
-    s.op[n] = (uint8_t)op;
-    if (op == GP_OP_VAR) {
-      if ((int)(tk >> 8) > max_input) max_input = (int)(tk >> 8);
-      w += 1;
-    } else if (op == GP_OP_CONST) {
-      if (w + 1 >= len) { ok = false; break; }
-      w += 2;
-    } else {
-      ar = fn_arity(op);
-      if (ar < 0) { ok = false; break; }
-      if (!(op >= GP_OP_ADD && op <= GP_OP_DIV)) extended = true;
-      w += 1;
-    }
-    if (top) s.fk[top - 1] -= 1;
-    if (ar > 0) {
-      s.fnode[top] = (uint16_t)n;
-      s.fk[top] = (uint8_t)ar;
-      ++top;
-    } else {
-      s.cnt[n] = 1;
-    }
-    ++n;
-    while (top && s.fk[top - 1] == 0) {
-      --top;
-      s.cnt[s.fnode[top]] = (uint16_t)(n - s.fnode[top]);
-    }
-  }
-  if (ok && (top != 0 || n == 0)) ok = false;                // missing operands
-  // 2. needs and child orders (children follow their parent in prefix order)
-  int depth = 1;
   if (ok) {
-    for (int v = n - 1; v >= 0; --v) {
-      const int ar = fn_arity(s.op[v]);
-      if (ar <= 0) { s.need[v] = 0; s.ord[v] = 0; continue; }
-      int rk[3], nd[3], m = 0;
-      int c = v + 1;
-      for (int k = 0; k < ar; ++k) {
-        if (fn_arity(s.op[c]) > 0) { rk[m] = k; nd[m] = s.need[c]; ++m; }
-        c += s.cnt[c];
+    // 1. node starts.  A lane's words map the state on entry (0: at a node,
+    //    1: at a payload) to the state on exit; a scan of the maps gives each
+    //    lane its entry state.
+    const int w0 = lane * kEncWordsPerLane;
+    uint32_t cmask = 0u, m0 = 0u, m1 = 1u;
+    for (int i = 0; i < kEncWordsPerLane; ++i) {
+      if (w0 + i < len) {
+        const bool c = (s.tok[w0 + i] & 0xffu) == GP_OP_CONST;
+        cmask |= (uint32_t)c << i;
+        m0 = (m0 == 0u && c) ? 1u : 0u;
+        m1 = (m1 == 0u && c) ? 1u : 0u;
       }
-      if (a.order == GP_ORDER_MIN_DEPTH)  // insertion sort by decreasing need: stable
-        for (int x = 1; x < m; ++x)
-          for (int y = x; y > 0 && nd[y] > nd[y - 1]; --y) {
-            int t0 = rk[y]; rk[y] = rk[y - 1]; rk[y - 1] = t0;
-            t0 = nd[y]; nd[y] = nd[y - 1]; nd[y - 1] = t0;
-          }
-      int need = 1;
-      uint32_t packed = (uint32_t)m << 6;
-      for (int k = 0; k < m; ++k) {
-        need = max(need, k + nd[k]);
-        packed |= (uint32_t)rk[k] << (2 * k);
-      }
-      s.need[v] = (uint8_t)min(need, 255);
-      s.ord[v] = (uint8_t)packed;
     }
-    depth = fn_arity(s.op[0]) > 0 ? s.need[0] : 1;
-    if (depth > R) ok = false;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {  // the maps of lanes <= lane, composed
+      const uint32_t p0 = __shfl_up_sync(kAll, m0, d), p1 = __shfl_up_sync(kAll, m1, d);
+      if (lane >= d) {
+        const uint32_t n0 = p0 == 0u ? m0 : m1, n1 = p1 == 0u ? m0 : m1;
+        m0 = n0;
+        m1 = n1;
+      }
+    }
+    uint32_t st = __shfl_up_sync(kAll, m0, 1);
+    if (lane == 0) st = 0u;
+    const bool ends_in_payload = __shfl_sync(kAll, m0, 31) != 0u;  // a constant without its word
+    uint32_t smask = 0u;
+    for (int i = 0; i < kEncWordsPerLane; ++i) {
+      if (w0 + i < len) {
+        if (st == 0u) smask |= 1u << i;
+        st = (st == 0u && ((cmask >> i) & 1u)) ? 1u : 0u;
+      }
+    }
+    const int cnt = __popc(smask);
+    const int incl = enc_warp_scan(cnt, lane);
+    n = __shfl_sync(kAll, incl, 31);
+    ok = !ends_in_payload && n <= GP_DEVICE_ENCODE_MAX_NODES;
+    if (ok) {
+      bool bad = false, ext = false;
+      int mi = -1, idx = incl - cnt;
+      for (uint32_t b = smask; b; b &= b - 1) {
+        const int w = w0 + __ffs(b) - 1;
+        const uint32_t tk = s.tok[w], op = tk & 0xffu;
+        int ar = 0;
+        if (op == GP_OP_VAR) {
+          mi = max(mi, (int)(tk >> 8));
+        } else if (op != GP_OP_CONST) {
+          ar = fn_arity(op);
+          if (ar < 0) { bad = true; ar = 0; }
+          if (!(op >= GP_OP_ADD && op <= GP_OP_DIV)) ext = true;
+        }
+        s.pos[idx] = (uint16_t)w;
+        s.opa[idx] = (uint8_t)((op & 63u) | ((uint32_t)ar << 6));
+        ++idx;
+      }
+      ok = !__any_sync(kAll, bad);
+      extended = __any_sync(kAll, ext);
+      max_input = __reduce_max_sync(kAll, mi);
+    }
   }
-  if (!ok) {  // a header of kind 0: every evaluation reports the program as malformed
-    o[0] = 0u; o[1] = 0u; o[2] = 0u; o[3] = 0u;
-    a.out_lengths[p] = 4;
-    return;
+  if (ok) {
+    __syncwarp();
+    // 2. open[v]; a tree has open[v] >= 0 for v >= 1 and a total of -1
+    const int v0 = lane * kEncNodesPerLane;
+    int loc = 0;
+    for (int i = 0; i < kEncNodesPerLane; ++i)
+      if (v0 + i < n) loc += enc_arity(s, v0 + i) - 1;
+    const int incl = enc_warp_scan(loc, lane);
+    int run = incl - loc;
+    bool neg = false;
+    for (int i = 0; i < kEncNodesPerLane; ++i) {
+      const int v = v0 + i;
+      if (v < n) {
+        s.u.open[v] = (int16_t)run;
+        if (v > 0 && run < 0) neg = true;  // tokens after a complete tree
+        run += enc_arity(s, v) - 1;
+      }
+    }
+    ok = !__any_sync(kAll, neg) && __shfl_sync(kAll, incl, 31) == -1;  // else operands missing
   }
-  // 3. emit
-  int ni = 0;
-  uint32_t* ins = o + 4;
-  if (fn_arity(s.op[0]) <= 0) {  // a single terminal: one move to level 0
-    const bool cst = s.op[0] == GP_OP_CONST;
-    ins[0] = (uint32_t)sform_code(cst ? SF_MOVC : SF_MOVX, 0, 0);
-    ins[1] = cst ? s.tok[1] : (s.tok[0] >> 8);
-    ins[2] = 0u;
-    ins[3] = 0u;
-    ni = 1;
-  } else {
-    top = 0;
-    s.fnode[top] = 0; s.flevel[top] = 0; s.fk[top] = 0; ++top;
-    while (top) {
-      const int v = s.fnode[top - 1], l = s.flevel[top - 1], k = s.fk[top - 1];
-      const uint32_t od = s.ord[v];
-      const int np = (int)(od >> 6);
-      if (k < np) {  // next function child, at level l + k
-        s.fk[top - 1] = (uint8_t)(k + 1);
-        s.fnode[top] = (uint16_t)child_at(s, v, (int)((od >> (2 * k)) & 3u));
-        s.flevel[top] = (uint8_t)(l + k);
-        s.fk[top] = 0;
-        ++top;
+  if (ok) {
+    __syncwarp();
+    // 3. parents and children (the slots opened after u stay filled until v)
+    bool bad = false;
+    for (int v = lane; v < n; v += kEncThreads) {
+      s.need[v] = 0;
+      s.ord[v] = 0;
+      s.fc[v] = 0;
+      if (v == 0) {
+        s.par[0] = 0;
         continue;
       }
-      --top;
-      const uint32_t op = s.op[v];
-      const int ar = fn_arity(op);
-      int kind[3] = {0, 0, 0};   // 0 input, 1 constant, 2 + j stack level l + j
-      uint32_t pay[3] = {0u, 0u, 0u};
-      int c = v + 1;
-      for (int q = 0; q < ar; ++q) {
-        if (s.op[c] == GP_OP_VAR) { kind[q] = 0; pay[q] = s.tok[s.pos[c]] >> 8; }
-        else if (s.op[c] == GP_OP_CONST) { kind[q] = 1; pay[q] = s.tok[s.pos[c] + 1]; }
-        c += s.cnt[c];
+      const int ov = s.u.open[v];
+      int u = v - 1;
+      while (u > 0 && s.u.open[u] > ov) --u;
+      const int au = enc_arity(s, u);
+      const int k = s.u.open[u] - ov + au - 1;
+      if (k < 0 || k >= au) {  // cannot happen for a tree that passed (2)
+        bad = true;
+        continue;
       }
-      for (int r = 0; r < np; ++r) kind[(od >> (2 * r)) & 3u] = 2 + r;
-      uint32_t code;
-      if (ar == 1) {
-        const int uf = kind[0] == 0 ? UF_X : kind[0] == 1 ? UF_C : UF_S;
-        code = (uint32_t)sfx_un_code(uf, l, (int)(op - GP_OP_SIN));
-      } else if (ar == 3) {
-        code = (uint32_t)sfx_if_code(xif_form_index(kind[0], kind[1], kind[2]), l);
-      } else {
-        // forms by (a, b): X X, X C, C X, C C, S0 X, X S0, S0 C, C S0, S0 S1, S1 S0
-        const int ka = kind[0], kb = kind[1];
-        int form;
-        if (ka < 2 && kb < 2) form = ka == 0 ? (kb == 0 ? SF_XX : SF_XC) : (kb == 0 ? SF_CX : SF_CC);
-        else if (ka == 2 && kb < 2) form = kb == 0 ? SF_SX : SF_SC;
-        else if (kb == 2 && ka < 2) form = ka == 0 ? SF_XS : SF_CS;
-        else form = ka == 2 ? SF_SS : SF_SSR;
-        code = (op >= GP_OP_ADD && op <= GP_OP_DIV) ? (uint32_t)sform_code(form, l, (int)(op - GP_OP_ADD))
-                                                   : (uint32_t)sfx_bin_code(form, l, xbin(op));
+      s.ch[k][u] = (uint8_t)v;
+      s.par[v] = (uint8_t)u;
+    }
+    ok = !__any_sync(kAll, bad);
+  }
+  if (ok) {
+    __syncwarp();
+    // 4. each round finishes the unfinished function nodes of greatest
+    //    height (all their function children finished): at most n rounds
+    uint32_t pend = 0u;  // bit j: node lane + 32 j, an unfinished function node
+    for (int j = 0; j < kEncNodesPerLane; ++j) {
+      const int v = lane + kEncThreads * j;
+      if (v < n && enc_arity(s, v) > 0) pend |= 1u << j;
+    }
+    for (int round = 0; round < n && __any_sync(kAll, pend != 0u); ++round) {
+      uint32_t ready = 0u;
+      for (uint32_t b = pend; b; b &= b - 1) {
+        const int j = __ffs(b) - 1, v = lane + kEncThreads * j, ar = enc_arity(s, v);
+        bool r = true;
+        for (int q = 0; q < ar; ++q) {
+          const int c = s.ch[q][v];
+          if (enc_arity(s, c) > 0 && s.need[c] == 0) r = false;
+        }
+        if (r) ready |= 1u << j;
       }
-      uint32_t* q = ins + 4 * ni;
-      q[0] = code;
-      q[1] = pay[0];
-      q[2] = pay[1];
-      q[3] = pay[2];
-      ++ni;
+      __syncwarp();
+      for (uint32_t b = ready; b; b &= b - 1) {
+        const int v = lane + kEncThreads * (__ffs(b) - 1);
+        enc_finish(s, v, enc_arity(s, v), a.order);
+      }
+      pend &= ~ready;
+      __syncwarp();
+    }
+    ok = !__any_sync(kAll, pend != 0u);
+    depth = enc_arity(s, 0) > 0 ? s.need[0] : 1;
+    if (depth > R) ok = false;
+  }
+  const bool fn_root = ok && enc_arity(s, 0) > 0;
+  if (fn_root) {
+    // 5. a function node's step from its parent: the function nodes of the
+    //    children evaluated before it | its rank << 16; then path sums
+    //    (a path has at most 255 edges: 8 doublings)
+    for (int v = lane; v < n; v += kEncThreads) {
+      if (enc_arity(s, v) == 0) continue;
+      int d = 0;
+      if (v > 0) {
+        const int u = s.par[v];
+        const uint32_t od = s.ord[u];
+        const int np = (int)(od >> 6);
+        int off = 0, r = 0;
+        bool found = false;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          if (t < np && !found) {
+            const int c = s.ch[(od >> (2 * t)) & 3u][u];
+            if (c == v) { found = true; r = t; } else { off += s.fc[c]; }
+          }
+        }
+        d = off | (r << 16);
+      }
+      s.u.path[v] = d;
+    }
+    __syncwarp();
+    for (int round = 0; round < 8; ++round) {
+      int nv[kEncNodesPerLane], nj[kEncNodesPerLane];
+      bool more = false;
+#pragma unroll
+      for (int j = 0; j < kEncNodesPerLane; ++j) {
+        const int v = lane + kEncThreads * j;
+        nv[j] = 0;
+        nj[j] = 0;
+        if (v < n && enc_arity(s, v) > 0) {
+          const int jv = s.par[v];
+          nv[j] = s.u.path[v] + s.u.path[jv];
+          nj[j] = s.par[jv];
+          more |= jv != 0;
+        }
+      }
+      if (!__any_sync(kAll, more)) break;  // every link at the root: the sums are complete
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < kEncNodesPerLane; ++j) {
+        const int v = lane + kEncThreads * j;
+        if (v < n && enc_arity(s, v) > 0) {
+          s.u.path[v] = nv[j];
+          s.par[v] = (uint8_t)nj[j];
+        }
+      }
+      __syncwarp();
     }
   }
-  o[0] = header0(extended ? (uint32_t)K_SFORMX : (uint32_t)K_SFORM, (uint32_t)a.order);
-  o[1] = (uint32_t)ni;
-  o[2] = (uint32_t)n;
-  o[3] = (uint32_t)depth | ((uint32_t)(max_input + 1) << 16);
-  a.out_lengths[p] = 4 + 4 * ni;
-  if (a.node_total) atomicAdd(a.node_total, (unsigned long long)n);
+  if (lane == 0) {
+    if (!ok) {  // a header of kind 0: every evaluation reports the program as malformed
+      o[0] = 0u; o[1] = 0u; o[2] = 0u; o[3] = 0u;
+      a.out_lengths[p] = 4;
+    } else {
+      int ni = 1;
+      if (!fn_root) {  // a single terminal: one move to level 0
+        const bool cst = (s.opa[0] & 63u) == GP_OP_CONST;
+        ins[0] = (uint32_t)sform_code(cst ? SF_MOVC : SF_MOVX, 0, 0);
+        ins[1] = cst ? s.tok[1] : (s.tok[0] >> 8);
+        ins[2] = 0u;
+        ins[3] = 0u;
+      } else {
+        ni = s.fc[0];
+      }
+      o[0] = header0(extended ? (uint32_t)K_SFORMX : (uint32_t)K_SFORM, (uint32_t)a.order);
+      o[1] = (uint32_t)ni;
+      o[2] = (uint32_t)n;
+      o[3] = (uint32_t)depth | ((uint32_t)(max_input + 1) << 16);
+      a.out_lengths[p] = 4 + 4 * ni;
+      if (a.node_total) atomicAdd(a.node_total, (unsigned long long)n);
+    }
+  }
+  if (fn_root) {
+    // 6. the instructions (16-byte stores where the slot is aligned, as
+    //    offsets in multiples of 4 words make it)
+    const bool vec = (reinterpret_cast<uintptr_t>(ins) & 15u) == 0;
+    const int ni = s.fc[0];
+    for (int v = lane; v < n; v += kEncThreads) {
+      if (enc_arity(s, v) == 0) continue;
+      const int pth = s.u.path[v];
+      const int at = (pth & 0xffff) + s.fc[v] - 1;
+      if (at < 0 || at >= ni) continue;  // never for a tree; keeps every store inside the slot
+      const uint4 in = enc_instruction(s, v, pth >> 16);
+      uint32_t* q = ins + 4 * at;
+      if (vec) {
+        *reinterpret_cast<uint4*>(q) = in;
+      } else {
+        q[0] = in.x; q[1] = in.y; q[2] = in.z; q[3] = in.w;
+      }
+    }
+  }
 }
 
 cudaError_t launch_encode(const EncArgs& a, cudaStream_t s) {

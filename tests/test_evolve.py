@@ -48,6 +48,39 @@ def test_device_encoder_matches_host(order, funcs, n_inputs):
         assert np.array_equal(a, b), p
 
 
+@pytest.mark.parametrize("order", [gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH])
+def test_device_encoder_at_the_node_limit(order):
+    """Trees of exactly GP_DEVICE_ENCODE_MAX_NODES = 256 nodes: a chain of 255
+    unary functions (255 instructions) and 85 nested IFs whose nested operand
+    moves through the three positions beside inputs and constants; every
+    word as the host encoder's."""
+    x0, x1 = synth.tok(synth.VAR, 0), synth.tok(synth.VAR, 1)
+    chain = [synth.SIN, synth.COS, synth.EXP, synth.LOG] * 64
+    chain = np.array(chain[:255] + [x0], np.uint32)
+    ifs, tail = [], [x1]
+    for k in range(85):
+        leaf = [x0] if k % 2 else synth.const_tokens(0.5 + k)
+        pos = k % 3
+        ops = [leaf, [x1], [x0]]
+        ops[pos] = None
+        ifs.append((pos, ops))
+    words = list(tail)
+    for pos, ops in reversed(ifs):
+        parts = [words if o is None else o for o in ops]
+        words = [synth.IF] + parts[0] + parts[1] + parts[2]
+    nest = np.array(words, np.uint32)
+    progs = [chain, nest]
+    pop = synth.pack(progs)
+    host = gp.encode_population(pop.words, pop.offsets, pop.lengths, gp.KIND_SFORM, order)
+    assert list(host.words[host.offsets + 2]) == [256, 256]
+    out, off, ln = device_encode(pop, order)
+    assert np.array_equal(ln, host.lengths)
+    for p in range(pop.n):
+        a = host.words[host.offsets[p]: host.offsets[p] + host.lengths[p]]
+        b = out[off[p]: off[p] + ln[p]]
+        assert np.array_equal(a, b), p
+
+
 def test_device_encoder_marks_bad_trees():
     good = np.array([synth.ADD, synth.tok(synth.VAR, 0), synth.tok(synth.VAR, 0)], np.uint32)
     missing = np.array([synth.ADD, synth.tok(synth.VAR, 0)], np.uint32)

@@ -365,7 +365,7 @@ def run_ours(args):
     d_s = replay_times(gd)
     d_fit = gd.h_fit.numpy().copy()
     e2e = {"value": round(gpop_step * world * args.steps / d_s / 1e9, 2), "unit": UNIT,
-           "h2d_bytes_per_step": int(tokens * 4 + w.pop.n * (8 + 4 + 8)),
+           "h2d_bytes_per_step": int(tokens * 4 + w.pop.n * (8 + 4)),
            "d2h_bytes_per_step": int(w.pop.n * 8),
            "ms_per_step": round(d_s / args.steps * 1e3, 4),
            "includes": "copy of the user-format trees into pinned memory, one CUDA-graph replay: "

@@ -444,6 +444,15 @@ int gp_encode_population_device(const uint32_t* words, const int64_t* offsets,
                                 uint32_t* out, const int64_t* out_offsets, int32_t* out_lengths,
                                 gp_stream_t stream);
 
+/* Slot offsets for gp_encode_population_device: out_offsets[p] (device) =
+ * the sum over q < p of 4 + 4 * max(lengths[q], 0) words, the back-to-back
+ * layout in which every program's slot holds its encoding.  lengths
+ * (device) are the trees' word counts.  One small kernel, asynchronous on
+ * `stream`, so that a captured generation step computes the layout on the
+ * device.  Returns GP_ERR_INVALID_ARG for a negative count or a null array. */
+int gp_encode_slots_device(const int32_t* lengths, int32_t n_progs, int64_t* out_offsets,
+                           gp_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * On-device generation loop.  A GP run (Sec. 4.2 parameter table: population
  * 1000, tournament selection of size 7, crossover 0.95, mutation 0.2) evolves

@@ -143,6 +143,7 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_autotune_clear": [],
         "gp_eval_launches": [i32, i64, P],
         "gp_encode_population_device": [P, P, P, i32, i32, P, P, P, P],
+        "gp_encode_slots_device": [P, i32, P, P],
         "gp_evolve_create": [P, P, P, P, P, i32, i64, P, P],
         "gp_evolve_run": [P, i32],
         "gp_evolve_read": [P, P, P, P, P, P],
@@ -517,6 +518,16 @@ def shutdown():
 # ---------------------------------------------------------------------------
 # device-side encoder and the on-device generation loop
 # ---------------------------------------------------------------------------
+def encode_slots_device(lengths, stream=None):
+    """gp_encode_slots_device on a CUDA int32 tensor of tree lengths: the
+    int64 offsets of back-to-back slots of 4 + 4 * lengths[p] words."""
+    import torch
+    n = int(lengths.numel())
+    out_off = torch.empty(n, dtype=torch.int64, device=lengths.device)
+    _check(lib().gp_encode_slots_device(_tptr(lengths), n, _tptr(out_off), _stream(stream)))
+    return out_off
+
+
 def encode_population_device(words, offsets, lengths, order: int = ORDER_MIN_DEPTH, stream=None):
     """gp_encode_population_device on CUDA tensors (user-format trees).
     Returns (out words, out offsets, out lengths) as CUDA tensors; program p
@@ -524,11 +535,8 @@ def encode_population_device(words, offsets, lengths, order: int = ORDER_MIN_DEP
     4 + 4 * lengths[p] words."""
     import torch
     n = int(lengths.numel())
-    slot = 4 + 4 * lengths.to(torch.int64)
-    out_off = torch.zeros(n, dtype=torch.int64, device=lengths.device)
-    if n > 1:
-        out_off[1:] = torch.cumsum(slot, 0)[:-1]
-    total = int(slot.sum().item()) if n else 4
+    out_off = encode_slots_device(lengths, stream)
+    total = int((4 + 4 * lengths.to(torch.int64).clamp_min(0)).sum().item()) if n else 4
     out = torch.zeros(max(total, 4), dtype=torch.int32, device=lengths.device)
     out_len = torch.zeros(n, dtype=torch.int32, device=lengths.device)
     _check(lib().gp_encode_population_device(_tptr(words), _tptr(offsets), _tptr(lengths), n, order,

@@ -630,6 +630,45 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(EncArgs a) {
   }
 }
 
+// The back-to-back layout of the encoder's output slots: out_offsets[p] =
+// the sum over q < p of 4 + 4 max(lengths[q], 0) words.  One block; each
+// thread a run of consecutive programs, then a scan over the block.
+__global__ void __launch_bounds__(1024) encode_slots_kernel(const int32_t* __restrict__ lengths, int32_t n,
+                                                            int64_t* __restrict__ out_offsets) {
+  __shared__ long long warp_before[32];
+  constexpr unsigned kAll = 0xffffffffu;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t per = ((int64_t)n + 1023) / 1024;
+  const int64_t b = (int64_t)tid * per;
+  const int64_t e = b + per < (int64_t)n ? b + per : (int64_t)n;
+  long long loc = 0;
+  for (int64_t p = b; p < e; ++p) loc += 4 + 4 * (long long)max(lengths[p], 0);
+  long long incl = loc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long y = __shfl_up_sync(kAll, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) warp_before[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const long long w = warp_before[lane];
+    long long wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long y = __shfl_up_sync(kAll, wi, d);
+      if (lane >= d) wi += y;
+    }
+    warp_before[lane] = wi - w;
+  }
+  __syncthreads();
+  long long run = warp_before[wid] + incl - loc;
+  for (int64_t p = b; p < e; ++p) {
+    out_offsets[p] = run;
+    run += 4 + 4 * (long long)max(lengths[p], 0);
+  }
+}
+
 cudaError_t launch_encode(const EncArgs& a, cudaStream_t s) {
   static std::atomic<size_t> set{0};
   const size_t smem = sizeof(EncScratch);  // one tree per block
@@ -656,6 +695,18 @@ extern "C" int gp_encode_population_device(const uint32_t* words, const int64_t*
   EncArgs a{words, offsets, lengths, n_progs, order, out, out_offsets, out_lengths, nullptr};
   cudaError_t e = launch_encode(a, (cudaStream_t)stream);
   if (e != cudaSuccess) return gp_fail(GP_ERR_CUDA, "encoder launch: %s", cudaGetErrorString(e));
+  return GP_OK;
+}
+
+extern "C" int gp_encode_slots_device(const int32_t* lengths, int32_t n_progs, int64_t* out_offsets,
+                                      gp_stream_t stream) {
+  gp_clear_error();
+  if (n_progs < 0) return gp_fail(GP_ERR_INVALID_ARG, "negative n_progs");
+  if (n_progs == 0) return GP_OK;
+  if (!lengths || !out_offsets) return gp_fail(GP_ERR_INVALID_ARG, "null device array");
+  encode_slots_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(lengths, n_progs, out_offsets);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return gp_fail(GP_ERR_CUDA, "slot offsets launch: %s", cudaGetErrorString(e));
   return GP_OK;
 }
 

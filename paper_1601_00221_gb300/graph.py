@@ -68,9 +68,9 @@ class GenerationGraph:
         self.graph = None
         self.nodes = 0
         if self.device_encode:
-            # trees in, encoded programs in fixed slots of 4 + 4 * lengths[p] words
+            # trees in; encoded programs in back-to-back slots of 4 + 4 * lengths[p]
+            # words, laid out on the device (gp_encode_slots_device)
             self.h_tok = pin(max(self.max_tokens, 1), torch.int32)
-            self.h_eoff = pin(self.n, torch.int64)
             self.d_tok = torch.zeros(max(self.max_tokens, 1), dtype=torch.int32, device=self.device)
             self.d_eoff = torch.zeros(self.n, dtype=torch.int64, device=self.device)
             self.d_elen = torch.full((self.n,), 4, dtype=torch.int32, device=self.device)
@@ -82,7 +82,7 @@ class GenerationGraph:
             self.d_tok.copy_(self.h_tok, non_blocking=True)
             self.d_off.copy_(self.h_off, non_blocking=True)
             self.d_len.copy_(self.h_len, non_blocking=True)
-            self.d_eoff.copy_(self.h_eoff, non_blocking=True)
+            _check(lib().gp_encode_slots_device(_tptr(self.d_len), self.n, _tptr(self.d_eoff), stream))
             _check(lib().gp_encode_population_device(
                 _tptr(self.d_tok), _tptr(self.d_off), _tptr(self.d_len), self.n, self.order,
                 _tptr(self.d_words), _tptr(self.d_eoff), _tptr(self.d_elen), stream))
@@ -98,30 +98,33 @@ class GenerationGraph:
         self.h_fit.copy_(self.d_fit, non_blocking=True)
 
     def _stage_trees(self, words, offsets, lengths):
-        """Device encoding: the trees, packed back to back, into pinned memory."""
+        """Device encoding: the trees into pinned memory -- the caller's words
+        as they are, with the caller's offsets, when they fit the capacity;
+        else packed back to back."""
         w = np.ascontiguousarray(words, np.uint32)
         off = np.ascontiguousarray(offsets, np.int64)
         ln = np.ascontiguousarray(lengths, np.int32)
-        total = int(ln.sum())
-        if total > self.max_tokens:
-            raise ValueError("the population has more words than the graph's capacity")
-        dense = bool(np.array_equal(off[1:], np.cumsum(ln[:-1], dtype=np.int64))) and \
-            (ln.size == 0 or off[0] == 0)
         tok = self.h_tok.numpy().view(np.uint32)
-        if dense:
-            tok[:total] = w[:total]
+        n = ln.size
+        lc = np.maximum(ln, 0)
+        if int(lc.sum()) > self.max_tokens:  # the encoded slots' bound
+            raise ValueError("the population has more words than the graph's capacity")
+        if n and int(off.min()) < 0:
+            raise ValueError("negative program offset")
+        end = int((off + lc).max()) if n else 0
+        if end > w.size:
+            raise ValueError("a program runs past the end of the words")
+        if end <= self.max_tokens:
+            tok[:end] = w[:end]
             self.h_off.numpy()[:] = off
         else:
             pos = 0
-            for p in range(ln.size):
-                tok[pos:pos + ln[p]] = w[off[p]:off[p] + ln[p]]
+            for p in range(n):
+                k = int(lc[p])
+                tok[pos:pos + k] = w[off[p]:off[p] + k]
                 self.h_off.numpy()[p] = pos
-                pos += int(ln[p])
+                pos += k
         self.h_len.numpy()[:] = ln
-        slot = 4 + 4 * ln.astype(np.int64)
-        eoff = self.h_eoff.numpy()
-        eoff[0] = 0
-        eoff[1:] = np.cumsum(slot[:-1])
 
     def _encode(self, words, offsets, lengths):
         if self.device_encode:

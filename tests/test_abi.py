@@ -54,6 +54,12 @@ def test_host_side_argument_checks_without_gpu():
     bad = gp.Config(variant=1, k=3, block=128, chunk_cases=0)
     assert L.gp_set_config(ctypes.byref(bad)) == 1
     assert b"k must be" in L.gp_error_string()
+    # the encoder's slot layout: count and pointers checked before the launch
+    assert L.gp_encode_slots_device(None, -1, None, None) == 1
+    assert b"negative" in L.gp_error_string()
+    assert L.gp_encode_slots_device(None, 5, None, None) == 1
+    assert b"null" in L.gp_error_string()
+    assert L.gp_encode_slots_device(None, 0, None, None) == 0
 
 
 def test_binding_structs_match_the_header(tmp_path):

@@ -193,3 +193,19 @@ def test_run_rejects_malformed_initial_trees():
         with pytest.raises(gp.GPError) as e:
             gp.Evolver(prm, pop.words, pop.offsets, pop.lengths, x, y)
         assert e.value.code == 2
+
+
+@pytest.mark.parametrize("n", [1, 7, 1024, 1025, 5000])
+def test_slot_offsets_are_the_packed_layout(n):
+    """gp_encode_slots_device: out_offsets[p] = sum over q < p of
+    4 + 4 * max(lengths[q], 0), also with zero and negative lengths (a
+    malformed tree gets a header-only slot) and counts that do not fill the
+    scan's 1024 threads evenly."""
+    import torch
+    rng = np.random.default_rng(n)
+    ln = rng.integers(-3, 600, n).astype(np.int32)
+    got = gp.encode_slots_device(dev(ln)).cpu().numpy()
+    slot = 4 + 4 * np.maximum(ln.astype(np.int64), 0)
+    want = np.concatenate([[0], np.cumsum(slot)[:-1]]).astype(np.int64)
+    torch.cuda.synchronize()
+    assert np.array_equal(got, want)

@@ -66,3 +66,22 @@ def test_device_encoding_graph_matches_host_encoding(funcs, n_inputs, fitness):
         a = gh.run(words, offsets, pop.lengths)
         b = gd.run(words, offsets, pop.lengths)
         assert np.array_equal(a.view(np.uint64), b.view(np.uint64)), g
+    # layouts staged as they are (within the capacity): trees stored in
+    # reverse order, and a one-word gap after every tenth tree
+    pop = pops[1]
+    rev = np.zeros(pop.words.size, np.uint32)
+    roff = np.zeros(n, np.int64)
+    pos = 0
+    for p in reversed(range(n)):
+        roff[p] = pos
+        rev[pos: pos + pop.lengths[p]] = pop.program(p)
+        pos += int(pop.lengths[p])
+    gap = pop.offsets + np.arange(n) // 10
+    gwords = np.zeros(pop.words.size + n // 10, np.uint32)
+    for p in range(n):
+        gwords[gap[p]: gap[p] + pop.lengths[p]] = pop.program(p)
+    assert int(gap[-1] + pop.lengths[-1]) <= max_tokens
+    for words, offsets in ((rev, roff), (gwords, gap)):
+        a = gh.run(words, offsets, pop.lengths)
+        b = gd.run(words, offsets, pop.lengths)
+        assert np.array_equal(a.view(np.uint64), b.view(np.uint64))

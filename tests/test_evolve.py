@@ -57,15 +57,14 @@ def test_device_encoder_at_the_node_limit(order):
     x0, x1 = synth.tok(synth.VAR, 0), synth.tok(synth.VAR, 1)
     chain = [synth.SIN, synth.COS, synth.EXP, synth.LOG] * 64
     chain = np.array(chain[:255] + [x0], np.uint32)
-    ifs, tail = [], [x1]
-    for k in range(85):
+    levels = []
+    for k in range(85):  # operands of the k-th IF from the root; None: the nested IF
         leaf = [x0] if k % 2 else synth.const_tokens(0.5 + k)
-        pos = k % 3
         ops = [leaf, [x1], [x0]]
-        ops[pos] = None
-        ifs.append((pos, ops))
-    words = list(tail)
-    for pos, ops in reversed(ifs):
+        ops[k % 3] = None
+        levels.append(ops)
+    words = [x1]
+    for ops in reversed(levels):
         parts = [words if o is None else o for o in ops]
         words = [synth.IF] + parts[0] + parts[1] + parts[2]
     nest = np.array(words, np.uint32)

@@ -4,6 +4,7 @@
 // consecutive words per pass, so one instruction evaluates 32*K cases per
 // thread; stack levels are K-word register vectors at static levels.
 #pragma once
+#include <cuda_pipeline_primitives.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -170,18 +171,22 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
     const bool full = w0 + K <= a.n_words;
     int v = 0;
     if (full && a.aligned) {
-      // G inputs per step, their loads issued before their stores, so that
-      // G global round trips overlap instead of following each other
-      constexpr int G = K >= 8 ? 2 : 4;
-      for (; v + G <= a.n_inputs; v += G) {
-        UVec<K> t[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) uload<K>(t[g], a.case_bits + (int64_t)(v + g) * a.n_words, w0, a.n_words, true);
-#pragma unroll
-        for (int g = 0; g < G; ++g)
-#pragma unroll
-          for (int j = 0; j < K; ++j) tile[(v + g) * 32 * K + j] = t[g].w[j];
+      // every input's K words as asynchronous copies straight into the tile
+      // (16-, 8- or 4-byte aligned: rows aligned, w0 a multiple of K): all
+      // inputs in one global round trip, no registers held.  A lane reads
+      // back only its own words, so its own wait suffices.
+      for (; v < a.n_inputs; ++v) {
+        const uint32_t* src = a.case_bits + (int64_t)v * a.n_words + w0;
+        uint32_t* dst = tile + v * 32 * K;
+        if constexpr (K == 8) {
+          __pipeline_memcpy_async(dst, src, 16);
+          __pipeline_memcpy_async(dst + 4, src + 4, 16);
+        } else {
+          __pipeline_memcpy_async(dst, src, 4 * K);
+        }
       }
+      __pipeline_commit();
+      __pipeline_wait_prior(0);
     }
     for (; v < a.n_inputs; ++v) {
       UVec<K> t;

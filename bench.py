@@ -846,8 +846,10 @@ def cpu_oracle_baseline(w, gpu_fit, n_cases, budget_s: float = 12.0):
     err = {"programs_checked": int(ps.size), "max": float(rel.max()) if rel.size else 0.0,
            "median": float(np.median(rel)) if rel.size else 0.0, "bound": 1e-5,
            "zero_or_inf_exact": exact_ok}
-    # the same oracle on one thread, on the first programs of the sample (about 1.5 s)
-    n1 = int(max(1, min(sample.size, 1.5 / one)))
+    # the same oracle on one thread, on the first programs of the sample (about
+    # 1.5 s at the threaded run's mean cost per program)
+    per_program = wall * cores / max(1, sample.size)
+    n1 = int(max(1, min(sample.size, 1.5 / max(per_program, 1e-6))))
     t0 = time.perf_counter()
     for p in sample[:n1]:
         job(p)

@@ -719,6 +719,87 @@ class FloatGen:
         return b
 
 
+class FloatGenLoop(FloatGen):
+    """The K = 8 S-form interpreter with its input in registers and the pass
+    loop inside: each pass loads the lane's 8 inputs, runs the program, and at
+    DONE adds the pass's absolute errors to the fitness sum -- the errors
+    |o - y|, their pairwise sum and the compensated add, in the binary32 steps
+    and order of the kernel's own pass code -- then takes the next pass.  No
+    exit from the asm between passes.
+    Operands: the stack (%0..%31), bad (%32), the sum and its compensation
+    (%33, %34), the fitness flags (%35); the program's shared address (%36),
+    its instruction count (%37, unused), the lane's first inputs and targets
+    (%38, %39: global addresses), the passes (%40, at least 1) and the bytes
+    from one pass to the next (%41)."""
+
+    FLAG_NONFINITE = 1  # the kernel's fitness flag for a non-finite error
+
+    def __init__(self):
+        super().__init__(8, "reg")
+        assert self.stack_ops
+        self.o_bad, self.o_sum, self.o_comp, self.o_flags = 32, 33, 34, 35
+        self.o_prog, self.o_cnt = 36, 37
+        self.o_xp, self.o_yp, self.o_np, self.o_st = 38, 39, 40, 41
+
+    def header(self, extra_regs=""):
+        super().header(extra_regs)
+        for decl in (".reg .b64 xp, yp, stp;", ".reg .b32 npl;", ".reg .f32 e<8>, ey<8>, csa, csb;",
+                     ".reg .pred pnf, pmore;"):
+            self.b(decl)
+
+    def prologue(self):
+        b = self.b
+        b(f"mov.u32 %{self.o_bad}, 0;")
+        b(f"cvta.to.global.u64 xp, %{self.o_xp};")
+        b(f"cvta.to.global.u64 yp, %{self.o_yp};")
+        b(f"mov.u32 npl, %{self.o_np};")
+        b(f"mov.b64 stp, %{self.o_st};")
+        b("PASS:")
+        b("ld.global.nc.v4.f32 {e0, e1, e2, e3}, [xp];")
+        b("ld.global.nc.v4.f32 {e4, e5, e6, e7}, [xp+16];")
+        for i in range(self.H):
+            b(f"mov.b64 x{i}, {{e{2 * i}, e{2 * i + 1}}};")
+        b(f"mov.u32 adr, %{self.o_prog};")
+
+    def setup_inputs(self):
+        pass  # loaded at each pass (prologue)
+
+    def epilogue(self, out_units):
+        b = self.b
+        b("CBAD:")
+        b(f"mov.u32 %{self.o_bad}, 1;")
+        b("bra.uni EXIT;")
+        b("DONE:")
+        b("ld.global.nc.v4.f32 {ey0, ey1, ey2, ey3}, [yp];")
+        b("ld.global.nc.v4.f32 {ey4, ey5, ey6, ey7}, [yp+16];")
+        for i in range(self.H):
+            b(f"mov.b64 {{e{2 * i}, e{2 * i + 1}}}, {out_units[i]};")
+        for j in range(8):
+            b(f"sub.rn.f32 e{j}, e{j}, ey{j};")
+            b(f"abs.f32 e{j}, e{j};")
+        for w in (1, 2, 4):
+            for j in range(0, 8, 2 * w):
+                b(f"add.rn.f32 e{j}, e{j}, e{j + w};")
+        # a non-finite pass sum (errors are >= 0) flags the fitness
+        b("setp.le.f32 pnf, e0, 0f7F7FFFFF;")
+        b(f"@!pnf or.b32 %{self.o_flags}, %{self.o_flags}, {self.FLAG_NONFINITE};")
+        # compensated add: t = s + e; c += (max(s, e) - t) + min(s, e); s = t
+        b(f"add.rn.f32 csa, %{self.o_sum}, e0;")
+        b(f"max.f32 csb, %{self.o_sum}, e0;")
+        b(f"min.f32 e1, %{self.o_sum}, e0;")
+        b("sub.rn.f32 csb, csb, csa;")
+        b("add.rn.f32 csb, csb, e1;")
+        b(f"add.rn.f32 %{self.o_comp}, %{self.o_comp}, csb;")
+        b(f"mov.f32 %{self.o_sum}, csa;")
+        b("add.u64 xp, xp, stp;")
+        b("add.u64 yp, yp, stp;")
+        b("sub.u32 npl, npl, 1;")
+        b("setp.ne.u32 pmore, npl, 0;")
+        b("@pmore bra.uni PASS;")
+        b("EXIT:")
+        b("}")
+
+
 # ---------------------------------------------------------------------------
 # extended float S-form (the full function sets of Sec. 4.2)
 # ---------------------------------------------------------------------------
@@ -1308,6 +1389,10 @@ def generate() -> str:
         if K >= 2:
             parts.append(f"// the stack operands of the interpreters above (the caller's array s)\n"
                          f"#define GP_STACK_K{K} " + ", ".join(f'"+l"(s[{i}])' for i in range(R * K // 2)) + "\n")
+        if K == 8:  # the pass loop inside the interpreter (sum of absolute errors)
+            parts.append(FloatGenLoop().sform().macro(
+                "GP_PTX_SFORM_K8_REG_PASSES",
+                "S-form interpreter, K=8, input in registers, the passes and their error sums inside"))
         if K == 8:  # levels 4..7 in shared memory (the stack-register study)
             for xm in ("reg", "smem"):
                 X = xm.upper()

@@ -213,20 +213,21 @@ __device__ __forceinline__ bool run_tree_rl4(uint32_t prog, uint32_t n, const fl
   return bad == 0;
 }
 
-// K = 8, input in registers, S-form, sum of absolute errors: `passes` full
-// warp passes (at least one) inside one asm block -- each loads the lane's 8
-// inputs at x, runs the program and adds |o - y| over its cases to `acc`
+// K = 8, input in registers, S-form: `passes` full warp passes (at least
+// one) inside one asm block -- each loads the lane's 8 inputs at x, runs the
+// program and adds its cases' errors under fitness measure `fit` to `acc`
 // (the pass code's own binary32 steps, below), x and y advancing `stride`
 // bytes a pass.
 static_assert(FLAG_NONFINITE == 1u, "the generated pass loop sets flag bit 1 for a non-finite pass sum");
+static_assert(FIT_SUM_ABS == 0 && FIT_MSE == 1 && FIT_CLASS == 2, "the generated pass loop's fitness codes");
 __device__ __forceinline__ bool run_tree_passes(uint32_t prog, uint32_t n, const float* x, const float* y,
-                                                uint32_t passes, uint64_t stride,
+                                                uint32_t passes, uint64_t stride, int32_t fit,
                                                 typename SfxUnit<8>::type (&s)[stack_units<8>()], CSum& acc,
                                                 uint32_t& flags) {
   uint32_t bad;
   asm volatile(GP_PTX_SFORM_K8_REG_PASSES
                : GP_STACK_K8, "=r"(bad), "+f"(acc.s), "+f"(acc.c), "+r"(flags)
-               : "r"(prog), "r"(n), "l"(x), "l"(y), "r"(passes), "l"(stride)
+               : "r"(prog), "r"(n), "l"(x), "l"(y), "r"(passes), "l"(stride), "r"(fit)
                : "memory");
   return bad == 0;
 }
@@ -576,15 +577,15 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
     if constexpr (XREG && EXT == 0 && RL == R && K == 8) {
       // the warp's full passes (all 32 lanes' cases inside the population)
       // in one interpreter call that loops over them itself; the rest below
-      if (kind == K_SFORM && a.want_fitness && !out_row && a.fitness_kind == FIT_SUM_ABS && a.x_aligned &&
-          a.y_aligned) {
+      if (kind == K_SFORM && a.want_fitness && !out_row && a.x_aligned && a.y_aligned &&
+          (a.fitness_kind == FIT_SUM_ABS || a.fitness_kind == FIT_MSE || a.fitness_kind == FIT_CLASS)) {
         const int64_t stride = (int64_t)nwarps * 32 * K;
         const int64_t last = min(c_end - 1, a.n_cases - (int64_t)32 * K);  // last start of a full pass
         if (last >= wb_first) {
           const int64_t passes = (last - wb_first) / stride + 1;
           const int64_t c0 = wb_first + (int64_t)lane * K;
           if (!run_tree_passes(prog_addr, (uint32_t)n_instr, a.cases + c0, a.targets + c0, (uint32_t)passes,
-                               (uint64_t)stride * sizeof(float), stk, acc, flags))
+                               (uint64_t)stride * sizeof(float), a.fitness_kind, stk, acc, flags))
             flags |= FLAG_BAD;
           wb_first += passes * stride;
         }

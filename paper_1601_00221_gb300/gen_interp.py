@@ -726,25 +726,28 @@ class FloatGenLoop(FloatGen):
     |o - y|, their pairwise sum and the compensated add, in the binary32 steps
     and order of the kernel's own pass code -- then takes the next pass.  No
     exit from the asm between passes.
+    The error is the fitness measure's (%42: 0 |o - y|, 1 (o - y)^2, 2 the
+    misclassification rint(o) != y), chosen once per pass.
     Operands: the stack (%0..%31), bad (%32), the sum and its compensation
     (%33, %34), the fitness flags (%35); the program's shared address (%36),
     its instruction count (%37, unused), the lane's first inputs and targets
-    (%38, %39: global addresses), the passes (%40, at least 1) and the bytes
-    from one pass to the next (%41)."""
+    (%38, %39: global addresses), the passes (%40, at least 1), the bytes
+    from one pass to the next (%41) and the fitness measure (%42)."""
 
     FLAG_NONFINITE = 1  # the kernel's fitness flag for a non-finite error
+    FIT_MSE, FIT_CLASS = 1, 2  # the kernel's fitness measures (0: sum of |o - y|)
 
     def __init__(self):
         super().__init__(8, "reg")
         assert self.stack_ops
         self.o_bad, self.o_sum, self.o_comp, self.o_flags = 32, 33, 34, 35
         self.o_prog, self.o_cnt = 36, 37
-        self.o_xp, self.o_yp, self.o_np, self.o_st = 38, 39, 40, 41
+        self.o_xp, self.o_yp, self.o_np, self.o_st, self.o_fit = 38, 39, 40, 41, 42
 
     def header(self, extra_regs=""):
         super().header(extra_regs)
         for decl in (".reg .b64 xp, yp, stp;", ".reg .b32 npl;", ".reg .f32 e<8>, ey<8>, csa, csb;",
-                     ".reg .pred pnf, pmore;"):
+                     ".reg .pred pnf, pmore, pmse, pcls;"):
             self.b(decl)
 
     def prologue(self):
@@ -774,9 +777,25 @@ class FloatGenLoop(FloatGen):
         b("ld.global.nc.v4.f32 {ey4, ey5, ey6, ey7}, [yp+16];")
         for i in range(self.H):
             b(f"mov.b64 {{e{2 * i}, e{2 * i + 1}}}, {out_units[i]};")
-        for j in range(8):
+        b(f"setp.eq.u32 pmse, %{self.o_fit}, {self.FIT_MSE};")
+        b(f"setp.eq.u32 pcls, %{self.o_fit}, {self.FIT_CLASS};")
+        b("@pmse bra.uni EMSE;")
+        b("@pcls bra.uni ECLS;")
+        for j in range(8):  # |o - y|
             b(f"sub.rn.f32 e{j}, e{j}, ey{j};")
             b(f"abs.f32 e{j}, e{j};")
+        b("bra.uni ESUM;")
+        b("EMSE:")
+        for j in range(8):  # (o - y)^2
+            b(f"sub.rn.f32 e{j}, e{j}, ey{j};")
+            b(f"mul.rn.f32 e{j}, e{j}, e{j};")
+        b("bra.uni ESUM;")
+        b("ECLS:")
+        for j in range(8):  # rint(o) != y
+            b(f"cvt.rni.f32.f32 e{j}, e{j};")
+            b(f"setp.eq.f32 pnf, e{j}, ey{j};")
+            b(f"selp.f32 e{j}, 0f00000000, 0f3F800000, pnf;")
+        b("ESUM:")
         for w in (1, 2, 4):
             for j in range(0, 8, 2 * w):
                 b(f"add.rn.f32 e{j}, e{j}, e{j + w};")

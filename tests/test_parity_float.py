@@ -338,3 +338,23 @@ def test_stack_levels_in_shared_memory(n_inputs):
     assert gp.last_error() == 2
     with pytest.raises(gp.GPError):
         gp.eval_population(P, O, L, dev(x), y, config=gp.Config(gp.VARIANT_REGISTER, 4, 256, 0, 0, 0, 4))
+
+
+@pytest.mark.parametrize("fitness", [gp.FITNESS_SUM_ABS, gp.FITNESS_MSE, gp.FITNESS_CLASS])
+@pytest.mark.parametrize("chunk", [0, 4096])
+def test_pass_loop_inside_the_interpreter_changes_nothing(fitness, chunk):
+    """K = 8 with the input in registers runs a warp's full passes inside one
+    interpreter call; asking for per-case outputs takes the per-pass path.
+    The fitness is the same to the bit under every measure, with a ragged tail
+    (20000 cases: the last passes partial) and with chunks of cases."""
+    w = synth.regression_small(seed=77, n_progs=300, n_cases=20000)
+    y = w.targets if fitness != gp.FITNESS_CLASS else np.rint(w.targets * 3.0).astype(np.float32)
+    P, O, L = upload(gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths))
+    X, Y = dev(w.cases), dev(y)
+    cfg = gp.Config(gp.VARIANT_REGISTER, 8, 256, chunk, fitness)
+    loop = gp.eval_population(P, O, L, X, Y, config=cfg).cpu().numpy()
+    import torch
+    outs = torch.empty((w.pop.n, w.cases.shape[1]), dtype=torch.float32, device=X.device)
+    per_pass = gp.eval_population(P, O, L, X, Y, outputs=outs, config=cfg).cpu().numpy()
+    assert np.array_equal(loop.view(np.uint64), per_pass.view(np.uint64))
+    assert np.isfinite(loop).sum() > w.pop.n // 2

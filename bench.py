@@ -163,7 +163,13 @@ def kernel_source_digest() -> str:
     for f in sorted(os.listdir(d)):
         if f.startswith(("eval_float", "common", "isa")):
             h.update(open(os.path.join(d, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "paper_1601_00221_gb300", "gen_interp.py"), "rb").read())
+    # the generated interpreters as compiled (the generator's output, not its text)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "gen_interp", os.path.join(ROOT, "paper_1601_00221_gb300", "gen_interp.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    h.update(gen.generate().encode())
     return h.hexdigest()[:16]
 
 

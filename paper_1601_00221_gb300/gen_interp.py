@@ -722,12 +722,11 @@ class FloatGen:
 class FloatGenLoop(FloatGen):
     """The K = 8 S-form interpreter with its input in registers and the pass
     loop inside: each pass loads the lane's 8 inputs, runs the program, and at
-    DONE adds the pass's absolute errors to the fitness sum -- the errors
-    |o - y|, their pairwise sum and the compensated add, in the binary32 steps
-    and order of the kernel's own pass code -- then takes the next pass.  No
-    exit from the asm between passes.
-    The error is the fitness measure's (%42: 0 |o - y|, 1 (o - y)^2, 2 the
-    misclassification rint(o) != y), chosen once per pass.
+    DONE adds the pass's errors to the fitness sum -- the fitness measure's
+    error per case (%42: 0 |o - y|, 1 (o - y)^2, 2 the misclassification
+    rint(o) != y; chosen once per pass), their pairwise sum and the
+    compensated add, in the binary32 steps and order of the kernel's own pass
+    code -- then takes the next pass.  No exit from the asm between passes.
     Operands: the stack (%0..%31), bad (%32), the sum and its compensation
     (%33, %34), the fitness flags (%35); the program's shared address (%36),
     its instruction count (%37, unused), the lane's first inputs and targets

@@ -261,19 +261,25 @@ int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets, const int3
  * device memory -- for instance an application that gives the GPU's memory
  * to its own fixed-size pool, or an evaluation loop that must not meet an
  * allocation failure, or the synchronisation an allocation can imply, in the
- * middle of a run.  It computes exactly what gp_eval_population computes
- * (same arguments, same kernel, default configuration: its variant, register
- * or one of the extended ones, and its fitness measure) but keeps the kernel's
- * scratch (per-block partial sums, per-program counters, the block order, a
- * status word) in a fixed array of about 1.5 MiB that every device loading
- * the library holds until the process exits; it never calls cudaMalloc or
- * cudaFree.
- *   - n_progs may be at most GP_NOALLOC_MAX_PARTIALS; larger calls return
- *     GP_ERR_INVALID_ARG.  Cases are split into fewer blocks when needed so
- *     that the partial sums fit.
+ * middle of a run.  It takes gp_eval_population's arguments and runs what
+ * gp_eval_population would run for them (the default configuration with its
+ * variant and fitness measure, then the autotuner's record for the
+ * workload's shape, the same kernel and the same split of the cases), but
+ * keeps the kernel's scratch (per-block partial sums, per-program counters,
+ * the block order, a status word) in a fixed array of about 1.5 MiB that
+ * every device loading the library holds until the process exits; it never
+ * calls cudaMalloc or cudaFree.
+ *   - n_progs may be at most GP_NOALLOC_MAX_PARTIALS, n_cases at most 2^40;
+ *     larger calls return GP_ERR_INVALID_ARG.  When that split of the cases
+ *     would need more partial sums than the array holds (possible only with
+ *     a recorded tuning of small chunks over many cases), the cases are split
+ *     into fewer blocks and the fitness then agrees with gp_eval_population
+ *     within the fitness tolerance (1e-5 relative) instead of bit for bit.
  *   - The first call on a device, with that device current, looks up the
- *     array's device address (cudaGetSymbolAddress); make that first call
- *     before any stream capture.
+ *     array's device address (cudaGetSymbolAddress) and keeps it; make that
+ *     first call before any stream capture.  gp_shutdown forgets the
+ *     addresses: call it before a device reset (cudaDeviceReset) and the
+ *     next call looks the address up again.
  *   - All calls on a device share the one array, which keeps the previous
  *     call's contents; each call clears the parts it relies on.  Calls whose
  *     work overlaps on the GPU (different streams, or host threads) race on
@@ -534,7 +540,9 @@ int gp_evolve_destroy(gp_evolver* ev);
 /* Default configuration used when cfg is NULL or a field is 0.  Until it is
  * called, Boolean evaluations over 8 or more inputs that leave k or block at
  * 0 use k = 4 and blocks of at most 64 threads (their staged input tile
- * limits the blocks per multiprocessor); after it, its k and block stand. */
+ * limits the blocks per multiprocessor); after it, its k and block stand.
+ * gp_set_config(NULL) restores the library's own defaults (register variant,
+ * k = 8, block 128, sum of absolute errors) and that Boolean rule. */
 int gp_set_config(const gp_config* cfg);
 int gp_get_config(gp_config* cfg);
 

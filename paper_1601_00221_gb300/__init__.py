@@ -23,7 +23,7 @@ __all__ = [
     "GPError", "lib", "Config", "EncodedPopulation",
     "encode_tree", "encode_population", "encode_linear_population",
     "eval_population", "eval_outputs", "eval_population_bool",
-    "set_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
+    "set_config", "reset_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
     "eval_population_noalloc", "autotune_population", "autotune_clear", "eval_launches",
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "KIND_RPN_EXT",
     "ORDER_PAPER",
@@ -486,8 +486,16 @@ def autotune_clear():
     _check(lib().gp_autotune_clear())
 
 
-def set_config(variant=VARIANT_REGISTER, k=8, block=128):
-    _check(lib().gp_set_config(ctypes.byref(Config(variant, k, block, 0))))
+def set_config(variant=VARIANT_REGISTER, k=8, block=128, fitness=FITNESS_SUM_ABS, config=None):
+    """gp_set_config: the default configuration (`config`, a Config, wins over
+    the other arguments)."""
+    c = config if config is not None else Config(variant, k, block, 0, fitness)
+    _check(lib().gp_set_config(ctypes.byref(c)))
+
+
+def reset_config():
+    """gp_set_config(NULL): back to the library's own defaults."""
+    _check(lib().gp_set_config(None))
 
 
 def get_config() -> Config:

@@ -12,6 +12,7 @@
 
 #include "../../include/gpeval.h"
 #include "eval_bool.cuh"
+#include "config.h"
 #include "launch.h"
 #include "status.h"
 
@@ -20,7 +21,9 @@ using namespace gpdev;
 namespace {
 
 std::mutex g_mu;
-gp_config g_default = {GP_VARIANT_REGISTER, 8, 128, 0, GP_FITNESS_SUM_ABS, 0, 0};
+// the library's own defaults, and the current ones (gp_set_config)
+const gp_config kLibraryDefault = {GP_VARIANT_REGISTER, 8, 128, 0, GP_FITNESS_SUM_ABS, 0, 0, 0};
+gp_config g_default = kLibraryDefault;
 bool g_default_set = false;  // gp_set_config was called: its K and block stand
 
 // Internal workspace of one (device, stream): per-block partial sums, the
@@ -116,6 +119,10 @@ int get_order(Workspace* w, size_t n, cudaStream_t s, int32_t** out) {
   return GP_OK;
 }
 
+}  // namespace
+
+namespace gpdev {
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
@@ -127,12 +134,6 @@ int sm_count() {
   }
   return n;
 }
-
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-
-// dynamic shared memory left for staged input tiles next to the 16 KB
-// program buffer (227 KB per block on sm_103a)
-constexpr size_t kMaxTileBytes = 200 * 1024;
 
 // Fills zero fields of `c` from the default configuration and checks it.
 int resolve_config(const gp_config* user, gp_config* c) {
@@ -206,11 +207,53 @@ int64_t choose_chunk(int64_t n_units, int32_t n_progs, int per_pass, int64_t use
   return std::max<int64_t>(chunk, per_pass);
 }
 
-}  // namespace
+int float_launch_smem(const gp_config& c, int32_t tile_inputs, size_t* smem) {
+  const bool rl4 = c.stack_registers == 4;
+  if (rl4 && (c.k != 8 || c.variant != GP_VARIANT_REGISTER))
+    return gp_fail(GP_ERR_INVALID_ARG, "stack_registers = 4 needs k = 8 and the register variant");
+  const size_t tile_bytes = float_tile_bytes(c.k, c.block, tile_inputs) +
+                            (rl4 ? (size_t)(c.block / 32) * spill_bytes_per_warp<8, 4>() : 0);
+  if (c.variant != GP_VARIANT_LOCAL && tile_bytes > kMaxTileBytes)
+    return gp_fail(GP_ERR_INVALID_ARG,
+                   "a tile of %d inputs needs %zu bytes of shared memory per block (max %zu): "
+                   "lower k, block or tile_inputs",
+                   tile_inputs, tile_bytes, kMaxTileBytes);
+  *smem = prog_buffer_bytes(c.max_instructions) + tile_bytes;
+  return GP_OK;
+}
+
+cudaError_t launch_float_config(const FloatArgs& a, const gp_config& c, bool xreg, int grid, size_t smem,
+                                cudaStream_t s) {
+  if (c.variant == GP_VARIANT_LOCAL) return launch_blockgp(a, c.block, grid, s);
+  if (c.stack_registers == 4) return launch_float_k8_rl4(a, xreg, c.block, grid, smem, s);
+  if (c.variant == GP_VARIANT_EXTENDED) {
+    if (c.k == 1) return launch_floatx_k1(a, xreg, c.block, grid, smem, s);
+    if (c.k == 2) return launch_floatx_k2(a, xreg, c.block, grid, smem, s);
+    if (c.k == 4) return launch_floatx_k4(a, xreg, c.block, grid, smem, s);
+    return launch_floatx_k8(a, xreg, c.block, grid, smem, s);
+  }
+  if (c.variant == GP_VARIANT_EXTENDED_RPN) {
+    if (c.k == 1) return launch_floatrx_k1(a, xreg, c.block, grid, smem, s);
+    if (c.k == 2) return launch_floatrx_k2(a, xreg, c.block, grid, smem, s);
+    if (c.k == 4) return launch_floatrx_k4(a, xreg, c.block, grid, smem, s);
+    return launch_floatrx_k8(a, xreg, c.block, grid, smem, s);
+  }
+  if (c.k == 1) return launch_float_k1(a, xreg, c.block, grid, smem, s);
+  if (c.k == 2) return launch_float_k2(a, xreg, c.block, grid, smem, s);
+  if (c.k == 4) return launch_float_k4(a, xreg, c.block, grid, smem, s);
+  return launch_float_k8(a, xreg, c.block, grid, smem, s);
+}
+
+}  // namespace gpdev
 
 extern "C" int gp_set_config(const gp_config* cfg) {
   gp_clear_error();
-  if (!cfg) return gp_fail(GP_ERR_INVALID_ARG, "null config");
+  if (!cfg) {  // back to the library's own defaults
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_default = kLibraryDefault;
+    g_default_set = false;
+    return GP_OK;
+  }
   gp_config c;
   int rc = resolve_config(cfg, &c);
   if (rc) return rc;
@@ -243,7 +286,7 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   if (!aligned16(programs)) return gp_fail(GP_ERR_INVALID_ARG, "programs must be 16-byte aligned");
   if (n_cases > 0 && n_inputs > 0 && !cases) return gp_fail(GP_ERR_INVALID_ARG, "null cases");
   if (fitness_out && n_cases > 0 && !targets) return gp_fail(GP_ERR_INVALID_ARG, "null targets");
-  if (n_cases > ((int64_t)1 << 40)) return gp_fail(GP_ERR_INVALID_ARG, "n_cases too large");
+  if (n_cases > kMaxCases) return gp_fail(GP_ERR_INVALID_ARG, "n_cases too large");
   gp_config c;
   int rc = resolve_config(cfg, &c);
   if (rc) return rc;
@@ -252,6 +295,10 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
     return gp_fail(GP_ERR_INVALID_ARG, "chunk_cases must be a multiple of k*block");
   cudaStream_t s = (cudaStream_t)stream;
 
+  const int32_t tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
+  size_t smem = 0;
+  rc = float_launch_smem(c, tile_inputs, &smem);
+  if (rc) return rc;
   const int per_pass = c.k * c.block;
   const int64_t chunk = choose_chunk(n_cases, n_progs, per_pass, c.chunk_cases, kAutoBlocksPerSm);
   const int64_t n_chunks64 = std::max<int64_t>(1, (n_cases + chunk - 1) / chunk);
@@ -283,7 +330,7 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   a.o_aligned = aligned16(outputs) && (n_progs == 1 || n_cases % 4 == 0);
   a.want_fitness = fitness_out != nullptr;
   a.fitness_kind = c.fitness;
-  a.tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
+  a.tile_inputs = tile_inputs;
   a.prog_cap = c.max_instructions;
   a.order = nullptr;
   if (order_blocks(n_progs, n_cases, sm_count())) {
@@ -296,34 +343,7 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   }
   const int grid = n_progs * n_chunks;
   const bool xreg = (n_inputs == 1);
-  const bool rl4 = c.stack_registers == 4;
-  if (rl4 && (c.k != 8 || c.variant != GP_VARIANT_REGISTER))
-    return gp_fail(GP_ERR_INVALID_ARG, "stack_registers = 4 needs k = 8 and the register variant");
-  const size_t tile_bytes = float_tile_bytes(c.k, c.block, a.tile_inputs) +
-                            (rl4 ? (size_t)(c.block / 32) * spill_bytes_per_warp<8, 4>() : 0);
-  const size_t smem = prog_buffer_bytes(a.prog_cap) + tile_bytes;
-  if (c.variant != GP_VARIANT_LOCAL && tile_bytes > kMaxTileBytes)
-    return gp_fail(GP_ERR_INVALID_ARG,
-                   "a tile of %d inputs needs %zu bytes of shared memory per block (max %zu): "
-                   "lower k, block or tile_inputs",
-                   a.tile_inputs, tile_bytes, kMaxTileBytes);
-  cudaError_t e;
-  if (c.variant == GP_VARIANT_LOCAL) e = launch_blockgp(a, c.block, grid, s);
-  else if (rl4) e = launch_float_k8_rl4(a, xreg, c.block, grid, smem, s);
-  else if (c.variant == GP_VARIANT_EXTENDED) {
-    if (c.k == 1) e = launch_floatx_k1(a, xreg, c.block, grid, smem, s);
-    else if (c.k == 2) e = launch_floatx_k2(a, xreg, c.block, grid, smem, s);
-    else if (c.k == 4) e = launch_floatx_k4(a, xreg, c.block, grid, smem, s);
-    else e = launch_floatx_k8(a, xreg, c.block, grid, smem, s);
-  } else if (c.variant == GP_VARIANT_EXTENDED_RPN) {
-    if (c.k == 1) e = launch_floatrx_k1(a, xreg, c.block, grid, smem, s);
-    else if (c.k == 2) e = launch_floatrx_k2(a, xreg, c.block, grid, smem, s);
-    else if (c.k == 4) e = launch_floatrx_k4(a, xreg, c.block, grid, smem, s);
-    else e = launch_floatrx_k8(a, xreg, c.block, grid, smem, s);
-  } else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, smem, s);
-  else if (c.k == 2) e = launch_float_k2(a, xreg, c.block, grid, smem, s);
-  else if (c.k == 4) e = launch_float_k4(a, xreg, c.block, grid, smem, s);
-  else e = launch_float_k8(a, xreg, c.block, grid, smem, s);
+  cudaError_t e = launch_float_config(a, c, xreg, grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return GP_OK;
 }
@@ -519,6 +539,7 @@ extern "C" int gp_shutdown(void) {
   }
   g_ws.clear();
   cudaSetDevice(cur);
+  noalloc_forget_devices();
   return GP_OK;
 }
 

@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "../../include/gpeval.h"
+#include "config.h"
 #include "launch.h"
 #include "status.h"
 
@@ -45,7 +46,8 @@ NoallocScratch* g_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  In host code
 // the symbol g_noalloc_scratch is only a stand-in, so the address is asked
-// of the runtime once per device (with that device current) and cached.
+// of the runtime once per device (with that device current) and kept until
+// gp_shutdown forgets it.
 int scratch_on_current_device(NoallocScratch** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -63,15 +65,14 @@ int scratch_on_current_device(NoallocScratch** out) {
   return GP_OK;
 }
 
-int sm_count_current() {
-  int dev = 0, v = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess &&
-      cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-    return v;
-  return 148;
-}
-
 }  // namespace
+
+namespace gpdev {
+void noalloc_forget_devices() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (NoallocScratch*& p : g_addr) p = nullptr;
+}
+}  // namespace gpdev
 
 extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_t* offsets,
                                           const int32_t* lengths, int32_t n_progs,
@@ -87,40 +88,42 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
                    "gp_eval_population_noalloc takes at most %lld programs per call (got %d)",
                    (long long)kMaxCounters, n_progs);
   if (!programs || !offsets || !lengths) return gp_fail(GP_ERR_INVALID_ARG, "null program arrays");
-  if (((uintptr_t)programs & 15u) != 0) return gp_fail(GP_ERR_INVALID_ARG, "programs must be 16-byte aligned");
+  if (!aligned16(programs)) return gp_fail(GP_ERR_INVALID_ARG, "programs must be 16-byte aligned");
   if (n_cases > 0 && n_inputs > 0 && !cases) return gp_fail(GP_ERR_INVALID_ARG, "null cases");
   if (n_cases > 0 && !targets) return gp_fail(GP_ERR_INVALID_ARG, "null targets");
+  if (n_cases > kMaxCases) return gp_fail(GP_ERR_INVALID_ARG, "n_cases too large");
+  // the configuration gp_eval_population would run: the default, then the
+  // autotuner's record for this workload's shape
   gp_config c;
-  int rc = gp_get_config(&c);
+  int rc = resolve_config(nullptr, &c);
   if (rc) return rc;
-  if (c.variant != GP_VARIANT_EXTENDED && c.variant != GP_VARIANT_EXTENDED_RPN)
-    c.variant = GP_VARIANT_REGISTER;
-  c.stack_registers = 0;  // every level in registers
+  apply_tuned(nullptr, &c, n_inputs, n_cases, n_progs);
+  const int32_t tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
+  size_t smem = 0;
+  rc = float_launch_smem(c, tile_inputs, &smem);
+  if (rc) return rc;
 
   NoallocScratch* scratch = nullptr;
   rc = scratch_on_current_device(&scratch);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
 
-  // chunks per program: fill the GPU, but never more partial sums than the
-  // scratch holds
+  // The same split of the cases as gp_eval_population, unless its partial
+  // sums would not fit the scratch: then fewer, larger chunks (whole passes
+  // of the block each), and the fitness agrees within the fitness tolerance
+  // rather than bit for bit.  (The automatic split never needs that: it aims
+  // at kAutoBlocksPerSm blocks per multiprocessor, far below the capacity;
+  // a recorded tuning with small chunks of a large case set can.)
   const int per_pass = c.k * c.block;
-  const int64_t target_blocks = (int64_t)kAutoBlocksPerSm * sm_count_current();
-  int64_t want = std::max<int64_t>(1, (target_blocks + n_progs - 1) / n_progs);
-  want = std::min<int64_t>(want, std::max<int64_t>(1, kMaxPartials / n_progs));
-  int64_t chunk = (n_cases + want - 1) / want;
-  chunk = std::max<int64_t>(per_pass, ((chunk + per_pass - 1) / per_pass) * per_pass);
-  const int64_t n_chunks = std::max<int64_t>(1, (n_cases + chunk - 1) / chunk);
-  if (n_chunks > 1 && n_chunks * n_progs > kMaxPartials)
-    return gp_fail(GP_ERR_INVALID_ARG, "%lld partial sums exceed the fixed scratch of %lld",
-                   (long long)(n_chunks * n_progs), (long long)kMaxPartials);
-  const int32_t tile_inputs = (c.tile_inputs > 0 && c.tile_inputs < n_inputs) ? c.tile_inputs : n_inputs;
-  const size_t tile_bytes = float_tile_bytes(c.k, c.block, tile_inputs);
-  if (tile_bytes > 200 * 1024)
-    return gp_fail(GP_ERR_INVALID_ARG, "a tile of %d inputs needs %zu bytes of shared memory per block",
-                   tile_inputs, tile_bytes);
-  const int32_t prog_cap = c.max_instructions > 0 ? c.max_instructions : gpisa::MAX_INSTR;
-  const size_t smem = prog_buffer_bytes(prog_cap) + tile_bytes;
+  int64_t chunk = choose_chunk(n_cases, n_progs, per_pass, c.chunk_cases, kAutoBlocksPerSm);
+  int64_t n_chunks = std::max<int64_t>(1, (n_cases + chunk - 1) / chunk);
+  if (n_chunks > 1 && n_chunks * n_progs > kMaxPartials) {
+    const int64_t fit = std::max<int64_t>(1, kMaxPartials / n_progs);
+    chunk = (n_cases + fit - 1) / fit;
+    chunk = std::max<int64_t>(per_pass, ((chunk + per_pass - 1) / per_pass) * per_pass);
+    n_chunks = std::max<int64_t>(1, (n_cases + chunk - 1) / chunk);
+  }
+  // (n_chunks <= kMaxPartials / n_progs now, or 1, which uses no partials)
 
   // the array keeps the previous call's contents: clear the counters this
   // call relies on and the status word
@@ -144,35 +147,20 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   a.status = &scratch->status;
   a.chunk_cases = chunk;
   a.n_chunks = (int32_t)n_chunks;
-  a.x_aligned = (((uintptr_t)cases & 15u) == 0) && (n_inputs <= 1 || n_cases % 4 == 0);
-  a.y_aligned = ((uintptr_t)targets & 15u) == 0;
+  a.x_aligned = aligned16(cases) && (n_inputs <= 1 || n_cases % 4 == 0);
+  a.y_aligned = aligned16(targets);
   a.o_aligned = 0;
   a.want_fitness = 1;
   a.fitness_kind = c.fitness;
   a.tile_inputs = tile_inputs;
-  a.prog_cap = prog_cap;
+  a.prog_cap = c.max_instructions;
   a.order = nullptr;
-  if (order_blocks(n_progs, n_cases, sm_count_current())) {
+  if (order_blocks(n_progs, n_cases, sm_count())) {
     e = launch_order_by_size(lengths, n_progs, scratch->order, s);
     if (e != cudaSuccess) return gp_fail(GP_ERR_CUDA, "ordering launch: %s", cudaGetErrorString(e));
     a.order = scratch->order;
   }
-  const int grid = (int)(n_progs * n_chunks);
-  const bool xreg = (n_inputs == 1);
-  if (c.variant == GP_VARIANT_EXTENDED) {
-    if (c.k == 1) e = launch_floatx_k1(a, xreg, c.block, grid, smem, s);
-    else if (c.k == 2) e = launch_floatx_k2(a, xreg, c.block, grid, smem, s);
-    else if (c.k == 4) e = launch_floatx_k4(a, xreg, c.block, grid, smem, s);
-    else e = launch_floatx_k8(a, xreg, c.block, grid, smem, s);
-  } else if (c.variant == GP_VARIANT_EXTENDED_RPN) {
-    if (c.k == 1) e = launch_floatrx_k1(a, xreg, c.block, grid, smem, s);
-    else if (c.k == 2) e = launch_floatrx_k2(a, xreg, c.block, grid, smem, s);
-    else if (c.k == 4) e = launch_floatrx_k4(a, xreg, c.block, grid, smem, s);
-    else e = launch_floatrx_k8(a, xreg, c.block, grid, smem, s);
-  } else if (c.k == 1) e = launch_float_k1(a, xreg, c.block, grid, smem, s);
-  else if (c.k == 2) e = launch_float_k2(a, xreg, c.block, grid, smem, s);
-  else if (c.k == 4) e = launch_float_k4(a, xreg, c.block, grid, smem, s);
-  else e = launch_float_k8(a, xreg, c.block, grid, smem, s);
+  e = launch_float_config(a, c, n_inputs == 1, (int)(n_progs * n_chunks), smem, s);
   if (e != cudaSuccess) return gp_fail(GP_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
   return GP_OK;
 }

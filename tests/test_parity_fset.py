@@ -241,7 +241,7 @@ def test_fitness_measures_extended_programs(trans_set, fit):
         assert_fitness_inside(got, pop, x, y, fit, lo, hi, nan, f"fit={fit} chunk={chunk}")
 
 
-def test_fitness_measures_no_cases_and_noalloc():
+def test_fitness_measures_no_cases():
     w = synth.regression_small(seed=111, n_progs=16, n_cases=0)
     enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
     P, O, L = upload(enc)

@@ -49,19 +49,69 @@ def parse():
     ap.add_argument("--cases", type=int, default=65536)
     ap.add_argument("--no-compare", action="store_true", help="skip the 1D-stack comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--k", type=int, default=0, help="force K (0 = tune)")
-    ap.add_argument("--block", type=int, default=0, help="force the block size (0 = tune)")
-    ap.add_argument("--chunk", type=int, default=0,
+    ap.add_argument("--k", type=int, default=8, help="K of the timed steps (0 with --tune: the autotuner's)")
+    ap.add_argument("--block", type=int, default=256, help="block size of the timed steps")
+    ap.add_argument("--tune", action="store_true",
+                    help="time the library autotuner's configuration instead of --k/--block/--chunk")
+    ap.add_argument("--chunk", type=int, default=65536,
                     help="cases per block when --k/--block force the configuration (0 = library default)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the Boolean, register-GP and serving measurements")
     ap.add_argument("--serving-runs", type=int, default=64)
-    ap.add_argument("--once", choices=["sextic512", "mux20"], default=None,
+    ap.add_argument("--stack-table", action="store_true",
+                    help="print the percentages of programs each stack limit evaluates (host only) and exit")
+    ap.add_argument("--once", choices=["sextic512", "mux20", "linear512"], default=None,
                     help="evaluate one workload twice and exit (the small cases of the ncu "
                          "captures): sextic512 = 512 sextic trees x 100000 cases, extended "
-                         "interpreter; mux20 = 128 20-multiplexer trees x 2^20 cases, Boolean "
-                         "(both with the program buffer sized to the population)")
+                         "interpreter; mux20 = 128 20-multiplexer trees x 2^20 cases, Boolean; "
+                         "linear512 = 512 register programs x 262144 cases x 8 inputs, register "
+                         "file in shared memory, K = 4, block 256 (all with the program buffer "
+                         "sized to the population)")
     return ap.parse_args()
+
+
+def stack_table():
+    """Percentages of programs that a given stack limit can evaluate (the
+    paper's tables of stack limits for its RPN and linear S-form
+    representations, Sec. 5), on this build's synthetic populations: RPN and
+    S-form, each with the paper's child order and with the Sethi-Ullman
+    order, from the encoder's count of stack levels per program (host only)."""
+    import ctypes
+    import numpy as np
+    import paper_1601_00221_gb300 as gp
+    import synth
+    lib = gp.lib()
+    pops = {"regression (C2)": synth.regression_large().pop,
+            "sextic-like": synth.sextic_problem().pop,
+            "shuttle-like": synth.shuttle_like_problem().pop,
+            "kdd-like": synth.kdd_like_problem().pop,
+            "20-multiplexer": synth.boolean_problem("mux", 20, n_progs=1024).pop}
+    forms = {"rpn/paper": (gp.KIND_RPN, gp.ORDER_PAPER), "rpn/min-depth": (gp.KIND_RPN, gp.ORDER_MIN_DEPTH),
+             "sform/paper": (gp.KIND_SFORM, gp.ORDER_PAPER), "sform/min-depth": (gp.KIND_SFORM, gp.ORDER_MIN_DEPTH)}
+    limits = list(range(1, 12))
+    out = {}
+    for name, pop in pops.items():
+        boolean = name == "20-multiplexer"
+        for fname, (kind, order) in forms.items():
+            if boolean:
+                if kind == gp.KIND_RPN:
+                    continue  # (Boolean trees are encoded in S-form only)
+                kind = gp.KIND_BOOL
+            depth = np.zeros(pop.n, np.int64)
+            for p in range(pop.n):
+                prog = np.ascontiguousarray(pop.program(p), np.uint32)
+                cap = 4 + 4 * prog.size
+                buf = np.zeros(cap, np.uint32)
+                info = gp._ProgInfo()
+                lib.gp_encode_tree(prog.ctypes.data_as(ctypes.c_void_p), prog.size, kind, order,
+                                   buf.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(info))
+                depth[p] = info.max_depth  # (filled even when the depth is over the register levels)
+            out[f"{name} | {fname}"] = {n: round(100.0 * float((depth <= n).mean()), 2) for n in limits}
+    print("| population | form/order | " + " | ".join(str(n) for n in limits) + " |")
+    print("|---|---|" + "---|" * len(limits))
+    for key, row in out.items():
+        a, b = key.split(" | ")
+        print(f"| {a} | {b} | " + " | ".join(f"{row[n]:.2f}" for n in limits) + " |")
 
 
 def run_once(args):
@@ -77,6 +127,15 @@ def run_once(args):
         P, O, L = enc.to_device("cuda")
         X, Y = torch.from_numpy(w.cases).cuda(), torch.from_numpy(w.targets).cuda()
         cfg = enc.config(fitness=w.fitness, k=8, block=256)
+        for _ in range(2):
+            f = gp.eval_population(P, O, L, X, Y, config=cfg)
+        out = float(f[0])
+    elif args.once == "linear512":
+        w = synth.linear_workload(n_progs=512)
+        enc = gp.encode_linear_population(w.pop.instr, w.pop.offsets, w.pop.lengths)
+        P, O, L = enc.to_device("cuda")
+        X, Y = torch.from_numpy(w.cases).cuda(), torch.from_numpy(w.targets).cuda()
+        cfg = gp.Config(gp.VARIANT_REGISTER_FILE, 4, 256, 0, 0, 0, 0, enc.max_instructions)
         for _ in range(2):
             f = gp.eval_population(P, O, L, X, Y, config=cfg)
         out = float(f[0])
@@ -257,24 +316,27 @@ def run_ours(args):
         torch.cuda.synchronize(device)
         return [s.elapsed_time(e) for s, e in evs]
 
-    # --- tune K and block for the 2D stack (short sweep) ---
+    # --- K x block sweep of the 2D stack (reported), and the library's autotuner ---
     cands = []
-    ks = [args.k] if args.k else [2, 4, 8]
-    blocks = [args.block] if args.block else [64, 128, 256, 512]
-    for k in ks:
-        for b in blocks:
+    for k in (2, 4, 8):
+        for b in (64, 128, 256, 512):
             cfg = gp.Config(gp.VARIANT_REGISTER, k, b, 0)
             t = statistics.median(timed(cfg, 3, 1, flush_l2=False))
             cands.append((t, k, b))
     cands.sort()
-    # the library's autotuner chooses the configuration the timed steps use
-    if args.k or args.block:
-        _, best_k, best_b = cands[0]
-        best_chunk = args.chunk
-    else:
-        tuned = gp.autotune_population(P, O, L, X, Y, repeats=3)
+    tuned = gp.autotune_population(P, O, L, X, Y, repeats=3)
+    tuned_ms = statistics.median(timed(tuned, 5, 1))
+    autotuned = {"variant": int(tuned.variant), "k": int(tuned.k), "block": int(tuned.block),
+                 "chunk_cases": int(tuned.chunk_cases), "stack_registers": int(tuned.stack_registers),
+                 "GPop_per_s": round(gpop_step / (tuned_ms / 1e3) / 1e9, 2)}
+    # the timed steps: a fixed shape (K = 8, block 256, all cases per block,
+    # the shape the profiles are taken at), or with --tune the autotuner's
+    if args.tune:
+        cfg = tuned
         best_k, best_b, best_chunk = int(tuned.k), int(tuned.block), int(tuned.chunk_cases)
-    cfg = gp.Config(gp.VARIANT_REGISTER, best_k, best_b, best_chunk)
+    else:
+        best_k, best_b, best_chunk = args.k, args.block, args.chunk
+        cfg = gp.Config(gp.VARIANT_REGISTER, best_k, best_b, best_chunk)
 
     # --- timed region ---
     if world > 1:
@@ -460,7 +522,8 @@ def run_ours(args):
                    "function_nodes": funcs, "kind": "sform", "order": "min_depth",
                    "k": best_k, "block": best_b, "chunk_cases": best_chunk,
                    "variant": "register 2D stack",
-                   "tuned_by": "gp_autotune_population" if not (args.k or args.block) else "flags",
+                   "shape": "autotuned (--tune)" if args.tune else "fixed: the shape the profiles are taken at",
+                   "autotuned": autotuned,
                    "l2": "flushed between timed steps (512 MiB write outside the CUDA-event pair)",
                    "parallelism": f"population sharded over {world} GPU(s), no collective"},
         "roofline": roofline,
@@ -500,7 +563,9 @@ def bench_boolean(gp, synth, torch, device):
     """Bit-packed Boolean problems, random trees (<= 256 nodes): 32768 trees for
     the 6-input problems (64 cases), 4096 for 11 inputs, 1024 for the
     20-multiplexer; GPop counts cases as bits (32 per word), as the paper's
-    20-multiplexer figure does."""
+    20-multiplexer figure does.  The library's Boolean tuner picks the kernel
+    (one program per lane, or a warp per program with K words per thread),
+    K, block and chunk on each population."""
     import numpy as np
     out = {}
     for kind, k in (("parity", 6), ("mux", 6), ("parity", 11), ("mux", 11), ("mux", 20)):
@@ -512,43 +577,59 @@ def bench_boolean(gp, synth, torch, device):
         cb = torch.from_numpy(w.case_bits.view(np.int32)).to(device)
         tb = torch.from_numpy(w.target_bits.view(np.int32)).to(device)
         hits = torch.empty(w.pop.n, dtype=torch.int64, device=device)
-        best = None
-        # K words per thread and the block size (the staged input tile, n_inputs
-        # x 32 x K words per warp, limits the blocks per SM)
-        cands = [(gp.VARIANT_REGISTER, kk, blk) for kk in (1, 2, 4, 8) for blk in (64, 128, 256)]
-        if (w.n_cases + 31) // 32 <= 4:
-            cands.append((gp.VARIANT_LANES, 0, 0))
-        for var, kk, blk in cands:
-            cfg = gp.Config(var, kk, blk, 0, 0, 0, 0, enc.max_instructions)
-            ms = _time_events(torch, lambda: gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
-                                                                     hits_out=hits, config=cfg))
-            if best is None or ms < best[0]:
-                best = (ms, kk if var == gp.VARIANT_REGISTER else "lane per program", blk)
-        gpop = w.gpop
-        out[f"{kind}{k}"] = {"programs": w.pop.n, "cases": w.n_cases, "k": best[1], "block": best[2],
-                             "ms": round(best[0], 4), "bit_GPop_per_s": round(gpop / best[0] / 1e6, 1)}
+        base = gp.Config(0, 0, 0, 0, 0, 0, 0, enc.max_instructions)
+        best = gp.autotune_population_bool(P, O, L, cb, w.n_cases, tb, base=base, repeats=3)
+        cfg = gp.Config(0, 0, 0, 0, 0, 0, 0, enc.max_instructions)  # k, block 0: the tuner's record
+        ms = _time_events(torch, lambda: gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
+                                                                 hits_out=hits, config=cfg))
+        lanes = int(best.variant) == gp.VARIANT_LANES
+        out[f"{kind}{k}"] = {"programs": w.pop.n, "cases": w.n_cases,
+                             "k": "lane per program" if lanes else int(best.k),
+                             "block": 0 if lanes else int(best.block),
+                             "chunk_words": int(best.chunk_cases), "tuned_by": "gp_autotune_population_bool",
+                             "ms": round(ms, 4), "bit_GPop_per_s": round(w.gpop / ms / 1e6, 1)}
     return out
 
 
 def bench_linear(gp, synth, torch, device):
-    """Register linear GP: 8 registers, 16-128 instructions, 8 inputs x 262144
-    cases (a 1024-program sample of the 8192-program population per launch)."""
-    w = synth.linear_workload(n_progs=1024)
+    """Register linear GP at its full configuration: 8192 programs of 16-128
+    instructions over 8 registers, 8 inputs x 262144 cases.  The library's
+    tuner picks the kernel (registers in machine registers, or the register
+    file in shared memory), K, block and chunk on this population."""
+    w = synth.linear_workload(n_progs=8192)
     enc = gp.encode_linear_population(w.pop.instr, w.pop.offsets, w.pop.lengths)
     P, O, L = enc.to_device(device)
     X = torch.from_numpy(w.cases).to(device)
     Y = torch.from_numpy(w.targets).to(device)
     fit = torch.empty(w.pop.n, dtype=torch.float64, device=device)
-    best = None
+    base = gp.Config(gp.VARIANT_REGISTER, 0, 0, 0, 0, 0, 0, enc.max_instructions)
+    best = gp.autotune_population_ex(P, O, L, X, Y, base=base, repeats=1)
+    cfg = gp.Config(best.variant, best.k, best.block, best.chunk_cases, 0, 0, 0, enc.max_instructions)
+    ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg),
+                      steps=3, warmup=1)
+    # the register variant's best shape, for the comparison
+    reg = None
     for k in (4, 8):
-        cfg = gp.Config(gp.VARIANT_REGISTER, k, 256, 0)
-        ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg),
-                          steps=2, warmup=1)
-        if best is None or ms < best[0]:
-            best = (ms, k)
-    return ({"programs": w.pop.n, "cases": int(w.cases.shape[1]),
-             "instructions": int(w.pop.lengths.sum()), "k": best[1], "ms": round(best[0], 3),
-             "GPop_per_s": round(w.gpop / best[0] / 1e6, 1)}, fit.cpu().numpy(), w)
+        for blk in (128, 256):
+            c2 = gp.Config(gp.VARIANT_REGISTER, k, blk, 0, 0, 0, 0, enc.max_instructions)
+            t = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=c2),
+                             steps=2, warmup=1)
+            reg = t if reg is None else min(reg, t)
+    gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg)
+    instr = int(w.pop.lengths.sum())
+    lane_ops = instr * int(w.cases.shape[1])
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    peak = n_sm * FP32_LANES_PER_SM * float(load_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    return ({"programs": w.pop.n, "cases": int(w.cases.shape[1]), "inputs": int(w.cases.shape[0]),
+             "instructions": instr,
+             "variant": {gp.VARIANT_REGISTER: "register", gp.VARIANT_REGISTER_FILE: "register file in shared memory"}
+             .get(int(best.variant), str(int(best.variant))),
+             "k": int(best.k), "block": int(best.block), "chunk_cases": int(best.chunk_cases),
+             "tuned_by": "gp_autotune_population_ex", "ms": round(ms, 3),
+             "GPop_per_s": round(w.gpop / ms / 1e6, 1),
+             "fp32_issue_fraction": round(lane_ops / (ms / 1e3) / peak, 4),
+             "register_variant_GPop_per_s": round(w.gpop / reg / 1e6, 1)},
+            fit.cpu().numpy(), w)
 
 
 def cpu_oracle_linear(w, gpu_fit):
@@ -633,23 +714,16 @@ def bench_function_sets(gp, synth, torch, device):
         X = torch.from_numpy(w.cases).to(device)
         Y = torch.from_numpy(w.targets).to(device)
         fit = torch.empty(w.pop.n, dtype=torch.float64, device=device)
-        # every kernel at its best block size and case chunk (chosen, 16384 or
-        # 65536 cases per block), as the paper tuned every kernel it compared
+        # the library's tuner picks K, block and chunk for the extended
+        # interpreter on this population (the paper tuned every kernel it
+        # compared; the comparison kernels below are swept here)
         chunks = (0, 16384, 65536)
-        best = None
-        for k in (2, 4, 8):
-            for block in (128, 256):
-                for ch in chunks:
-                    cfg = enc.config(fitness=w.fitness, k=k, block=block)
-                    cfg.chunk_cases = ch
-                    try:
-                        ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit,
-                                                                            config=cfg), steps=3, warmup=1)
-                    except gp.GPError:  # the tile does not fit this shape
-                        continue
-                    if best is None or ms < best[0]:
-                        best = (ms, cfg)
-        ms, cfg = best
+        base = enc.config(fitness=w.fitness)
+        tuned = gp.autotune_population_ex(P, O, L, X, Y, base=base, repeats=2)
+        cfg = enc.config(fitness=w.fitness, k=int(tuned.k), block=int(tuned.block))
+        cfg.chunk_cases = int(tuned.chunk_cases)
+        ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg),
+                          steps=3, warmup=1)
         # the one-dimensional stack (one case per thread per pass) on the same trees
         one = None
         for block in (128, 256):
@@ -692,7 +766,7 @@ def bench_function_sets(gp, synth, torch, device):
                        "inputs": int(w.cases.shape[0]), "mean_nodes": round(float(w.pop.nodes.mean()), 2),
                        "fitness": ["sum_abs", "mse", "class_errors"][w.fitness],
                        "k": int(cfg.k), "block": int(cfg.block), "chunk_cases": int(cfg.chunk_cases),
-                       "tile_inputs": int(cfg.tile_inputs),
+                       "tile_inputs": int(cfg.tile_inputs), "tuned_by": "gp_autotune_population_ex",
                        "ms": round(ms, 3), "GPop_per_s": round(w.gpop / ms / 1e6, 1),
                        "stack1d_GPop_per_s": round(w.gpop / one / 1e6, 1) if one else None,
                        "speedup_2d_over_1d": round(one / ms, 3) if one else None,
@@ -748,11 +822,16 @@ def cpu_oracle_function_set(w, sample, gpu_fit, gpu_outs):
 
 
 def bench_serving(gp, synth, n_runs):
-    """Continuous batching: n_runs independent runs (mixed float regression and
-    Boolean, populations 128-2048, 2^10-2^20 cases) submit 4 generations each
-    with Poisson arrivals at 80% of the measured burst capacity."""
+    """Continuous batching at the serving configuration's ranges: n_runs
+    independent runs (mixed float regression with 1 or 8 inputs and Boolean
+    multiplexer / parity, populations 128-8192, trees of 8-512 nodes, 2^10-2^20
+    cases) submit 4 generations each with Poisson arrivals at 80% of the
+    measured burst capacity.  Requests of different runs share launches (one
+    segment per request).  Also: the round trip of a one-program request on
+    an idle server, the fixed cost of a launch per admitted batch, which a
+    persistent kernel could save at most."""
     import numpy as np
-    runs = synth.serving_runs(n_runs=n_runs)
+    runs = synth.serving_runs(n_runs=n_runs, workers=max(2, len(os.sched_getaffinity(0))))
     encs = []
     for r in runs:
         kind = gp.KIND_SFORM if r.kind == "float" else gp.KIND_BOOL
@@ -774,9 +853,21 @@ def bench_serving(gp, synth, n_runs):
             return time.perf_counter() - t0
 
         burst()  # warm-up (workspaces, pinned buffers)
+        b0 = srv.stats()
         t_burst = burst()
+        b1 = srv.stats()
         total_gpop = sum(r.gpop for r in runs)
         capacity = total_gpop / t_burst
+        # the fixed cost of one admitted launch: a one-program request on the
+        # idle server (admission, copies, launch, completion callback)
+        tiny = synth.pack([runs[0].pop.program(0)])
+        tenc = gp.encode_population(tiny.words, tiny.offsets, tiny.lengths)
+        trid = srv.register_run(synth.uniform_cases(7, 1, 1024), synth.uniform_cases(8, 1, 1024)[0])
+        rt = []
+        for _ in range(50):
+            t1 = time.perf_counter()
+            srv.wait(srv.submit(trid, tenc))
+            rt.append(time.perf_counter() - t1)
         rng = np.random.default_rng(9)
         gens = 4
         order = [j for _ in range(gens) for j in rng.permutation(len(runs))]
@@ -800,16 +891,24 @@ def bench_serving(gp, synth, n_runs):
         st = srv.stats()
     lat = np.sort(np.array([i.t_done_us - i.t_submit_us for i in infos])) / 1e3
     pct = lambda q: float(lat[min(lat.size - 1, int(round(q * (lat.size - 1))))])
+    n_launch = st["launches"] - base["launches"]
     return {"runs": len(runs), "requests": len(qs), "generations_per_run": gens,
             "float_runs": sum(r.kind == "float" for r in runs),
             "bool_runs": sum(r.kind == "bool" for r in runs),
+            "programs_per_round": int(sum(r.pop.n for r in runs)),
+            "population_range": [int(min(r.pop.n for r in runs)), int(max(r.pop.n for r in runs))],
+            "tree_nodes_range": [int(min(r.pop.nodes.min() for r in runs)),
+                                 int(max(r.pop.nodes.max() for r in runs))],
+            "cases_range": [int(min(r.n_cases for r in runs)), int(max(r.n_cases for r in runs))],
             "offered_load": 0.8, "burst_capacity_GPop_per_s": round(capacity / 1e9, 1),
+            "burst_launches": b1["launches"] - b0["launches"], "burst_requests": len(runs),
             "p50_ms": round(pct(0.50), 3), "p99_ms": round(pct(0.99), 3),
             "max_ms": round(float(lat[-1]), 3),
             "sustained_GPop_per_s": round(sum(runs[j].gpop for j in order) / wall / 1e9, 1),
-            "launches": st["launches"] - base["launches"],
+            "launches": n_launch, "requests_per_launch": round(len(qs) / max(1, n_launch), 2),
+            "one_program_round_trip_p50_ms": round(float(np.median(rt)) * 1e3, 3),
             "note": "latency = submission to result in the caller's host buffer, over the "
-                    "requests of the Poisson phase"}
+                    "requests of the Poisson phase; requests of different runs share launches"}
 
 
 def cpu_oracle_baseline(w, gpu_fit, n_cases, budget_s: float = 12.0):
@@ -921,7 +1020,9 @@ def run_reference(args):
 
 def main():
     args = parse()
-    if args.once:
+    if args.stack_table:
+        stack_table()
+    elif args.once:
         run_once(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -176,8 +176,11 @@ typedef enum gp_variant {
                                (128 cases); GP_VARIANT_AUTO picks it for such case sets */
   GP_VARIANT_EXTENDED = 4,  /* the S-form interpreter with the extended float functions
                                (runs GP_KIND_SFORM and GP_KIND_SFORM_EXT programs) */
-  GP_VARIANT_EXTENDED_RPN = 5 /* the RPN interpreter with the extended float functions
+  GP_VARIANT_EXTENDED_RPN = 5, /* the RPN interpreter with the extended float functions
                                (runs GP_KIND_RPN and GP_KIND_RPN_EXT programs) */
+  GP_VARIANT_REGISTER_FILE = 6 /* GP_KIND_LINEAR programs only, their eight registers in shared
+                               memory: one jump per instruction and a kernel of few
+                               registers (blocks of at most 256 threads) */
 } gp_variant;
 
 /* Fitness measure of a float program (Sec. 4.2 parameter table: mean squared
@@ -316,6 +319,51 @@ int gp_eval_population_bool_ex(const uint32_t* programs, const int64_t* offsets,
                                uint32_t* out_words, const gp_config* cfg, gp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Several populations in one launch (device pointers; the segment table is
+ * host memory).  The paper evaluates one population per generation (Sec. 4.2);
+ * a service that interleaves the generations of many independent runs wants
+ * the programs of all their pending requests -- uneven in number, length,
+ * cases and inputs -- in one kernel launch.  Segment i is the programs
+ * prog_begin .. prog_begin + n_progs - 1 of the shared programs / offsets /
+ * lengths arrays, evaluated on its own cases and targets into its own `out`:
+ *   kind GP_RUN_FLOAT  cases binary32 [n_inputs][n_cases], targets binary32
+ *                      [n_cases], out binary64 fitness [n_progs] (the measure
+ *                      of cfg->fitness); programs GP_KIND_SFORM, GP_KIND_RPN or
+ *                      GP_KIND_LINEAR (the register variant's interpreters).
+ *   kind GP_RUN_BOOL   cases uint32 [n_inputs][ceil(n_cases/32)], targets
+ *                      uint32 [ceil(n_cases/32)], out uint64 hits [n_progs];
+ *                      programs GP_KIND_BOOL (a warp per program).
+ * `chunk` is the segment's cases (float) or words (Boolean) per block: 0 lets
+ * the library choose from the segment alone, otherwise a multiple of
+ * k * block.  Every segment uses cfg's k and block (the autotuner's records
+ * are not applied).  A float segment's fitness is bit-identical to
+ * gp_eval_population_ex on its programs alone with cfg and chunk_cases equal
+ * to the segment's chunk, whatever else shares the launch (its cases are
+ * split by its own chunk and summed in chunk order); Boolean hits are exact.
+ * Blocks take the segments in order of decreasing chunk, and within a
+ * segment its programs longest first once the launch fills two blocks per
+ * multiprocessor.  At most GP_MAX_SEGMENTS segments; their program ranges
+ * may not overlap.  Asynchronous on `stream`; the library's workspace as in
+ * gp_eval_population.  Malformed programs: NaN fitness or UINT64_MAX hits.
+ * ---------------------------------------------------------------------- */
+enum { GP_RUN_FLOAT = 1, GP_RUN_BOOL = 2 };
+#define GP_MAX_SEGMENTS 64
+typedef struct gp_segment {
+  int32_t prog_begin;
+  int32_t n_progs;
+  const void* cases;
+  int32_t n_inputs;
+  int32_t chunk;
+  int64_t n_cases;
+  const void* targets;
+  void* out;
+} gp_segment;
+
+int gp_eval_segments(const uint32_t* programs, const int64_t* offsets, const int32_t* lengths,
+                     const gp_segment* segments, int32_t n_segments, int32_t kind,
+                     const gp_config* cfg, gp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Serving: a continuously batched evaluation service for many independent GP
  * runs (the paper evaluates one population per generation, Sec. 4.2; a
  * server interleaves the generations of many runs).
@@ -335,7 +383,6 @@ int gp_eval_population_bool_ex(const uint32_t* programs, const int64_t* offsets,
  * ---------------------------------------------------------------------- */
 typedef struct gp_server gp_server;
 
-enum { GP_RUN_FLOAT = 1, GP_RUN_BOOL = 2 };
 
 typedef struct gp_server_opts {
   int32_t n_streams;      /* CUDA streams for admitted work (0 = 4) */
@@ -400,21 +447,57 @@ int gp_server_destroy(gp_server* srv);
 /* ------------------------------------------------------------------------
  * Autotuning.  The best K (the second dimension of the 2D stack) and block
  * size depend on the hardware and the workload (Sec. 4.2: the paper's best K
- * and thread count differ per problem, Tables of Sec. 4.2, 5 and 6).
- * gp_autotune_population times every candidate configuration (k in
- * {2, 4, 8} x block in {64, 128, 256, 512} x cases per block in {chosen, 4096,
- * 8192, 16384, 32768, all}) on the given float population with CUDA
- * events on `stream` (1 warm-up launch, `repeats` timed launches each, the
- * minimum kept), writes the fastest to *best (may be NULL) and records it for
- * the workload's shape: later float evaluations whose configuration leaves k
- * and block (and chunk_cases) at 0 and whose (single vs several inputs, floor(log2 n_cases),
- * floor(log2 n_progs)) match use it.  Synchronises `stream`; allocates a
- * temporary fitness buffer.  gp_autotune_clear forgets every record.
+ * and thread count differ per problem, Tables of Sec. 4.2, 5 and 6; Sec. 6.2
+ * picks how many stack levels sit in registers per problem).
+ *
+ * gp_autotune_population_ex times candidate configurations of one kernel
+ * family on the given float population with CUDA events on `stream` (one
+ * warm-up launch, `repeats` timed launches each, the minimum kept), writes
+ * the fastest to *best (may be NULL) and records it for the workload's shape.
+ * `base` (NULL = the default configuration) gives the family -- its variant
+ * -- and the fields that stay fixed: fitness measure, staged-input tile,
+ * program buffer.  Candidates: k in {2, 4, 8} (k = 1 for the local-memory
+ * variant) x block in {64, 128, 256, 512} (at most 256 where the variant
+ * allows no more) x cases per block in {chosen, 4096, 8192, 16384, 32768,
+ * 65536, 131072, all}; for the register variant also its register-file form
+ * (GP_VARIANT_REGISTER_FILE) and, at k = 8, stack levels 4..7 in shared
+ * memory (stack_registers = 4).  A candidate whose kernel cannot run every
+ * program of the population (it reports a program error) or whose shape does
+ * not fit is skipped.  Records are keyed by (family, single vs several
+ * inputs, floor(log2 n_cases), floor(log2 n_progs)); a later float
+ * evaluation of that family whose configuration leaves k and block at 0 takes
+ * the record's k, block and (if 0) chunk, and, when its variant is
+ * GP_VARIANT_AUTO or it passes no configuration, the record's variant and
+ * stack levels too.  gp_autotune_population is the _ex call with base NULL.
+ *
+ * gp_autotune_population_bool does the same for a Boolean population:
+ * k in {1, 2, 4, 8} x block in {32, 64, 128, 256} x cases per block, and one
+ * program per lane when the cases fit 4 words; the record applies to Boolean
+ * evaluations that leave k and block at 0.
+ *
+ * The tuners synchronise `stream` and allocate a temporary output buffer.
+ * gp_autotune_save writes every record to a text file (one line per record:
+ * family, several, log2 n_cases, log2 n_progs, variant, k, block, chunk_cases,
+ * stack_registers); gp_autotune_load adds the records of such a file
+ * (GP_ERR_INVALID_ARG for an unreadable file or a malformed line, which
+ * loads nothing).  gp_autotune_clear forgets every record.
  * ---------------------------------------------------------------------- */
 int gp_autotune_population(const uint32_t* programs, const int64_t* offsets,
                            const int32_t* lengths, int32_t n_progs, const float* cases,
                            int32_t n_inputs, int64_t n_cases, const float* targets,
                            int32_t repeats, gp_config* best, gp_stream_t stream);
+int gp_autotune_population_ex(const uint32_t* programs, const int64_t* offsets,
+                              const int32_t* lengths, int32_t n_progs, const float* cases,
+                              int32_t n_inputs, int64_t n_cases, const float* targets,
+                              const gp_config* base, int32_t repeats, gp_config* best,
+                              gp_stream_t stream);
+int gp_autotune_population_bool(const uint32_t* programs, const int64_t* offsets,
+                                const int32_t* lengths, int32_t n_progs, const uint32_t* case_bits,
+                                int32_t n_inputs, int64_t n_cases, const uint32_t* target_bits,
+                                const gp_config* base, int32_t repeats, gp_config* best,
+                                gp_stream_t stream);
+int gp_autotune_save(const char* path);
+int gp_autotune_load(const char* path);
 int gp_autotune_clear(void);
 
 /* Kernels one evaluation (gp_eval_population*, gp_eval_outputs,

@@ -24,11 +24,12 @@ __all__ = [
     "encode_tree", "encode_population", "encode_linear_population",
     "eval_population", "eval_outputs", "eval_population_bool",
     "set_config", "reset_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
-    "eval_population_noalloc", "autotune_population", "autotune_clear", "eval_launches",
+    "eval_population_noalloc", "eval_segments", "MAX_SEGMENTS", "autotune_population", "autotune_population_ex",
+    "autotune_population_bool", "autotune_save", "autotune_load", "autotune_clear", "eval_launches",
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "KIND_RPN_EXT",
     "ORDER_PAPER",
     "ORDER_MIN_DEPTH", "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL", "VARIANT_LANES",
-    "VARIANT_EXTENDED", "VARIANT_EXTENDED_RPN", "FITNESS_SUM_ABS", "FITNESS_MSE", "FITNESS_CLASS",
+    "VARIANT_EXTENDED", "VARIANT_EXTENDED_RPN", "VARIANT_REGISTER_FILE", "FITNESS_SUM_ABS", "FITNESS_MSE", "FITNESS_CLASS",
     "encode_population_device", "EvolveParams", "Evolver",
 ]
 
@@ -36,6 +37,7 @@ KIND_SFORM, KIND_RPN, KIND_LINEAR, KIND_BOOL, KIND_SFORM_EXT, KIND_RPN_EXT = 1, 
 ORDER_PAPER, ORDER_MIN_DEPTH = 0, 1
 VARIANT_AUTO, VARIANT_REGISTER, VARIANT_LOCAL, VARIANT_LANES, VARIANT_EXTENDED = 0, 1, 2, 3, 4
 VARIANT_EXTENDED_RPN = 5
+VARIANT_REGISTER_FILE = 6
 FITNESS_SUM_ABS, FITNESS_MSE, FITNESS_CLASS = 0, 1, 2
 STACK_LEVELS = 8
 MAX_INSTR = 1024
@@ -131,6 +133,7 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_last_error": [P, P],
         "gp_shutdown": [],
         "gp_eval_population_noalloc": [P, P, P, i32, P, i32, i64, P, P, P],
+        "gp_eval_segments": [P, P, P, P, i32, i32, P, P],
         "gp_server_create": [P, P],
         "gp_server_register_run": [P, i32, P, i32, i64, P, P],
         "gp_server_submit": [P, i32, P, P, P, i32, i64, P, P],
@@ -141,6 +144,10 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_server_destroy": [P],
         "gp_autotune_population": [P, P, P, i32, P, i32, i64, P, i32, P, P],
         "gp_autotune_clear": [],
+        "gp_autotune_population_ex": [P, P, P, i32, P, i32, i64, P, P, i32, P, P],
+        "gp_autotune_population_bool": [P, P, P, i32, P, i32, i64, P, P, i32, P, P],
+        "gp_autotune_save": [ctypes.c_char_p],
+        "gp_autotune_load": [ctypes.c_char_p],
         "gp_eval_launches": [i32, i64, P],
         "gp_encode_population_device": [P, P, P, i32, i32, P, P, P, P],
         "gp_encode_slots_device": [P, i32, P, P],
@@ -222,6 +229,8 @@ class EncodedPopulation:
         variant = VARIANT_AUTO
         if self.extended:
             variant = VARIANT_EXTENDED_RPN if self.kind == KIND_RPN else VARIANT_EXTENDED
+        elif self.kind == KIND_LINEAR:
+            variant = VARIANT_REGISTER_FILE
         tile = max(self.max_inputs_used, 1) if self.kind in (KIND_SFORM, KIND_RPN) else 0
         return Config(variant, k, block, chunk_cases, fitness, tile, 0, self.max_instructions)
 
@@ -388,6 +397,33 @@ def eval_population_noalloc(programs, offsets, lengths, cases, targets, fitness_
     return fitness_out
 
 
+class _Segment(ctypes.Structure):
+    _fields_ = [("prog_begin", ctypes.c_int32), ("n_progs", ctypes.c_int32), ("cases", ctypes.c_void_p),
+                ("n_inputs", ctypes.c_int32), ("chunk", ctypes.c_int32), ("n_cases", ctypes.c_int64),
+                ("targets", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+MAX_SEGMENTS = 64
+
+
+def eval_segments(programs, offsets, lengths, segments, kind=None, config=None, stream=None):
+    """gp_eval_segments: several populations in one launch.  `segments` is a
+    list of dicts with prog_begin, n_progs, cases (CUDA tensor: float32
+    [n_inputs, n_cases], or int32/uint32 bit words [n_inputs, n_words] with
+    n_cases given), targets, out (float64 or int64 [n_progs]) and optionally
+    chunk and n_cases.  kind: RUN_FLOAT (default) or RUN_BOOL."""
+    kind = RUN_FLOAT if kind is None else kind
+    arr = (_Segment * len(segments))()
+    for i, g in enumerate(segments):
+        x = g["cases"]
+        n_inputs = int(x.shape[0]) if x.dim() == 2 else 1
+        n_cases = int(g["n_cases"]) if "n_cases" in g else (int(x.shape[1]) if x.dim() == 2 else int(x.numel()))
+        arr[i] = _Segment(int(g["prog_begin"]), int(g["n_progs"]), _tptr(x), n_inputs, int(g.get("chunk", 0)),
+                          n_cases, _tptr(g["targets"]), _tptr(g["out"]))
+    _check(lib().gp_eval_segments(_tptr(programs), _tptr(offsets), _tptr(lengths), arr, len(segments), kind,
+                                  _cfg(config), _stream(stream)))
+
+
 class Server:
     """gp_server_*: continuously batched evaluation of many GP runs' populations.
 
@@ -480,6 +516,39 @@ def autotune_population(programs, offsets, lengths, cases, targets, repeats=3, s
                                         _tptr(cases), n_inputs, n_cases, _tptr(targets), repeats,
                                         ctypes.byref(best), _stream(stream)))
     return best
+
+
+def autotune_population_ex(programs, offsets, lengths, cases, targets, base=None, repeats=3,
+                           stream=None) -> Config:
+    """gp_autotune_population_ex: times the candidates of the kernel family
+    `base` names (Config or None for the default) and records the fastest."""
+    n = int(lengths.numel())
+    n_inputs, n_cases = (int(cases.shape[0]), int(cases.shape[1])) if cases.dim() == 2 else (1, int(cases.numel()))
+    best = Config()
+    _check(lib().gp_autotune_population_ex(_tptr(programs), _tptr(offsets), _tptr(lengths), n,
+                                           _tptr(cases), n_inputs, n_cases, _tptr(targets), _cfg(base),
+                                           repeats, ctypes.byref(best), _stream(stream)))
+    return best
+
+
+def autotune_population_bool(programs, offsets, lengths, case_bits, n_cases, target_bits, base=None,
+                             repeats=3, stream=None) -> Config:
+    """gp_autotune_population_bool: the same for a Boolean population."""
+    n = int(lengths.numel())
+    n_inputs = int(case_bits.shape[0]) if case_bits.dim() == 2 else 1
+    best = Config()
+    _check(lib().gp_autotune_population_bool(_tptr(programs), _tptr(offsets), _tptr(lengths), n,
+                                             _tptr(case_bits), n_inputs, int(n_cases), _tptr(target_bits),
+                                             _cfg(base), repeats, ctypes.byref(best), _stream(stream)))
+    return best
+
+
+def autotune_save(path: str):
+    _check(lib().gp_autotune_save(os.fsencode(path)))
+
+
+def autotune_load(path: str):
+    _check(lib().gp_autotune_load(os.fsencode(path)))
 
 
 def autotune_clear():

@@ -2,6 +2,7 @@
 // workspace, launch configuration and the evaluation entry points.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -43,16 +44,22 @@ struct Workspace {
 std::vector<Workspace*> g_ws;
 
 // autotuned configurations by workload shape
-using TuneKey = std::tuple<int, int, int>;  // several inputs?, log2 n_cases, log2 n_progs
+// (kernel family, several inputs?, floor(log2 n_cases), floor(log2 n_progs)):
+// the family is the configuration's variant before tuning (GP_VARIANT_AUTO
+// counts as GP_VARIANT_REGISTER), kTuneBool for Boolean populations
+using TuneKey = std::tuple<int, int, int, int>;
 std::map<TuneKey, gp_config> g_tuned;
+constexpr int kTuneBool = 100;
 
 int ilog2(int64_t v) {
   int r = 0;
   while (v > 1) { v >>= 1; ++r; }
   return r;
 }
-TuneKey tune_key(int32_t n_inputs, int64_t n_cases, int32_t n_progs) {
-  return TuneKey(n_inputs > 1 ? 1 : 0, ilog2(std::max<int64_t>(n_cases, 1)), ilog2(std::max<int32_t>(n_progs, 1)));
+TuneKey tune_key(int family, int32_t n_inputs, int64_t n_cases, int32_t n_progs) {
+  if (family == GP_VARIANT_AUTO) family = GP_VARIANT_REGISTER;
+  return TuneKey(family, n_inputs > 1 ? 1 : 0, ilog2(std::max<int64_t>(n_cases, 1)),
+                 ilog2(std::max<int32_t>(n_progs, 1)));
 }
 
 int cuda_fail(cudaError_t e, const char* what) {
@@ -161,7 +168,8 @@ int resolve_config(const gp_config* user, gp_config* c) {
   if (c->tile_inputs < 0) return gp_fail(GP_ERR_INVALID_ARG, "negative tile_inputs");
   if (c->variant != GP_VARIANT_REGISTER && c->variant != GP_VARIANT_LOCAL &&
       c->variant != GP_VARIANT_AUTO && c->variant != GP_VARIANT_LANES &&
-      c->variant != GP_VARIANT_EXTENDED && c->variant != GP_VARIANT_EXTENDED_RPN)
+      c->variant != GP_VARIANT_EXTENDED && c->variant != GP_VARIANT_EXTENDED_RPN &&
+      c->variant != GP_VARIANT_REGISTER_FILE)
     return gp_fail(GP_ERR_INVALID_ARG, "unknown variant %d", c->variant);
   if (c->fitness != GP_FITNESS_SUM_ABS && c->fitness != GP_FITNESS_MSE && c->fitness != GP_FITNESS_CLASS)
     return gp_fail(GP_ERR_INVALID_ARG, "unknown fitness measure %d", c->fitness);
@@ -171,24 +179,31 @@ int resolve_config(const gp_config* user, gp_config* c) {
   if (c->variant == GP_VARIANT_LOCAL) c->k = 1;
   if (c->block < 32 || c->block > 512 || c->block % 32)
     return gp_fail(GP_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 512] (got %d)", c->block);
-  if (c->block > 256 && c->variant == GP_VARIANT_LOCAL)
-    return gp_fail(GP_ERR_INVALID_ARG, "the local-memory variant takes at most 256 threads per block");
+  if (c->block > 256 && (c->variant == GP_VARIANT_LOCAL || c->variant == GP_VARIANT_REGISTER_FILE))
+    return gp_fail(GP_ERR_INVALID_ARG, "the local-memory and register-file variants take at most 256 "
+                                       "threads per block");
   if (c->chunk_cases < 0 || (c->chunk_cases % ((int64_t)c->k * c->block)) != 0)
     return gp_fail(GP_ERR_INVALID_ARG, "chunk_cases must be a multiple of k*block");
   return GP_OK;
 }
 
-// The recorded tuned configuration for a float workload, if any, fills the
-// k and block fields the caller left at 0.
+// The autotuner's record for the workload, if any, fills the k and block
+// fields the caller left at 0, and the chunk; when the caller left the
+// variant to the library (no configuration, or GP_VARIANT_AUTO) also the
+// variant and the stack levels held in registers the tuner chose.
 void apply_tuned(const gp_config* user, gp_config* c, int32_t n_inputs, int64_t n_cases, int32_t n_progs) {
   if (user && user->k && user->block) return;
-  if (c->variant != GP_VARIANT_REGISTER) return;
+  const int family = (user && user->variant) ? user->variant : c->variant;
   std::lock_guard<std::mutex> lk(g_mu);
-  auto it = g_tuned.find(tune_key(n_inputs, n_cases, n_progs));
+  auto it = g_tuned.find(tune_key(family, n_inputs, n_cases, n_progs));
   if (it == g_tuned.end()) return;
   if (!user || !user->k) c->k = it->second.k;
   if (!user || !user->block) c->block = it->second.block;
   if (!user || !user->chunk_cases) c->chunk_cases = it->second.chunk_cases;
+  if (!user || user->variant == GP_VARIANT_AUTO) {
+    c->variant = it->second.variant;
+    c->stack_registers = it->second.stack_registers;
+  }
 }
 
 // Cases (or words) per block: enough blocks to fill the GPU several times
@@ -208,6 +223,11 @@ int64_t choose_chunk(int64_t n_units, int32_t n_progs, int per_pass, int64_t use
 }
 
 int float_launch_smem(const gp_config& c, int32_t tile_inputs, size_t* smem) {
+  if (c.variant == GP_VARIANT_REGISTER_FILE) {  // the register files instead of input tiles
+    if (c.stack_registers) return gp_fail(GP_ERR_INVALID_ARG, "the register-file variant has no stack");
+    *smem = prog_buffer_bytes(c.max_instructions) + linear_rf_bytes(c.k, c.block);
+    return GP_OK;
+  }
   const bool rl4 = c.stack_registers == 4;
   if (rl4 && (c.k != 8 || c.variant != GP_VARIANT_REGISTER))
     return gp_fail(GP_ERR_INVALID_ARG, "stack_registers = 4 needs k = 8 and the register variant");
@@ -225,6 +245,7 @@ int float_launch_smem(const gp_config& c, int32_t tile_inputs, size_t* smem) {
 cudaError_t launch_float_config(const FloatArgs& a, const gp_config& c, bool xreg, int grid, size_t smem,
                                 cudaStream_t s) {
   if (c.variant == GP_VARIANT_LOCAL) return launch_blockgp(a, c.block, grid, s);
+  if (c.variant == GP_VARIANT_REGISTER_FILE) return launch_linear_rf(a, c.k, c.block, grid, smem, s);
   if (c.stack_registers == 4) return launch_float_k8_rl4(a, xreg, c.block, grid, smem, s);
   if (c.variant == GP_VARIANT_EXTENDED) {
     if (c.k == 1) return launch_floatx_k1(a, xreg, c.block, grid, smem, s);
@@ -388,9 +409,21 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   const int64_t n_words = (n_cases + 31) / 32;
   if (n_words > 0 && n_inputs > 0 && !case_bits) return gp_fail(GP_ERR_INVALID_ARG, "null case_bits");
   if (hits_out && n_words > 0 && !target_bits) return gp_fail(GP_ERR_INVALID_ARG, "null target_bits");
+  // the autotuner's record for this shape, when the caller leaves k and block
+  gp_config tuned{};
+  bool have_tuned = false;
+  if (!cfg || (!cfg->k && !cfg->block)) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_tuned.find(tune_key(kTuneBool, n_inputs, n_cases, n_progs));
+    if (it != g_tuned.end()) {
+      tuned = it->second;
+      have_tuned = true;
+    }
+  }
   // program per lane for tiny case sets unless a variant is forced
   const bool lanes = (cfg && cfg->variant == GP_VARIANT_LANES) ||
-                     ((!cfg || cfg->variant == GP_VARIANT_AUTO) && n_words > 0 && n_words <= 4);
+                     ((!cfg || cfg->variant == GP_VARIANT_AUTO) &&
+                      (have_tuned ? tuned.variant == GP_VARIANT_LANES : (n_words > 0 && n_words <= 4)));
   if (lanes) {
     if (n_words > 4) return gp_fail(GP_ERR_INVALID_ARG, "the per-lane variant takes at most 4 words (128 cases)");
     Workspace* wl = nullptr;
@@ -440,8 +473,13 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
     std::lock_guard<std::mutex> lk(g_mu);
     user_default = g_default_set;
   }
-  if ((!cfg || !cfg->k) && !user_default && n_inputs >= 8) c.k = 4;
-  if (!cfg || !cfg->block) {  // small case sets: do not launch idle warps
+  if (have_tuned) {
+    c.k = tuned.k;
+    c.block = tuned.block;
+    if (!cfg || !cfg->chunk_cases) c.chunk_cases = tuned.chunk_cases;
+  }
+  if ((!cfg || !cfg->k) && !user_default && !have_tuned && n_inputs >= 8) c.k = 4;
+  if ((!cfg || !cfg->block) && !have_tuned) {  // small case sets: do not launch idle warps
     int64_t need = (n_words + c.k - 1) / c.k;
     c.block = (int)std::min<int64_t>(c.block, std::max<int64_t>(32, ((need + 31) / 32) * 32));
     if (!user_default && (int64_t)n_inputs * c.k >= 32) c.block = std::min(c.block, 64);
@@ -508,6 +546,159 @@ extern "C" int gp_eval_population_bool(const uint32_t* programs, const int64_t* 
                                     n_cases, target_bits, hits_out, nullptr, nullptr, stream);
 }
 
+static_assert(kMaxSegments == GP_MAX_SEGMENTS, "the kernels' segment table holds GP_MAX_SEGMENTS");
+
+extern "C" int gp_eval_segments(const uint32_t* programs, const int64_t* offsets, const int32_t* lengths,
+                                const gp_segment* segments, int32_t n_segments, int32_t kind,
+                                const gp_config* cfg, gp_stream_t stream) {
+  gp_clear_error();
+  if (!segments || n_segments <= 0 || n_segments > GP_MAX_SEGMENTS)
+    return gp_fail(GP_ERR_INVALID_ARG, "n_segments must be 1..%d (got %d)", GP_MAX_SEGMENTS, n_segments);
+  if (kind != GP_RUN_FLOAT && kind != GP_RUN_BOOL) return gp_fail(GP_ERR_INVALID_ARG, "unknown kind %d", kind);
+  const bool fl = kind == GP_RUN_FLOAT;
+  gp_config c;
+  int rc = resolve_config(cfg, &c);
+  if (rc) return rc;
+  if (!fl && (c.variant == GP_VARIANT_EXTENDED || c.variant == GP_VARIANT_EXTENDED_RPN)) c.variant = GP_VARIANT_REGISTER;
+  if (c.variant != GP_VARIANT_REGISTER || c.stack_registers != 0)
+    return gp_fail(GP_ERR_INVALID_ARG, "several populations in one launch run the register variant "
+                                       "with every stack level in registers");
+  if (!fl && c.block > 256) c.block = 256;  // the Boolean kernel's block limit
+  const int per_pass = c.k * c.block;
+  // segments in block order: decreasing chunk (the longer blocks first),
+  // then the caller's order
+  std::vector<int> idx;
+  std::vector<int64_t> chunk_of(n_segments, 0);
+  int64_t prog_end = 0;
+  int32_t max_inputs = 0;
+  bool all_single = true;
+  for (int i = 0; i < n_segments; ++i) {
+    const gp_segment& g = segments[i];
+    if (g.prog_begin < 0 || g.n_progs < 0 || g.n_inputs < 0 || g.n_cases < 0 || g.chunk < 0)
+      return gp_fail(GP_ERR_INVALID_ARG, "segment %d: negative field", i);
+    if (g.n_cases > kMaxCases) return gp_fail(GP_ERR_INVALID_ARG, "segment %d: n_cases too large", i);
+    if (g.n_progs == 0) continue;
+    if (!g.out) return gp_fail(GP_ERR_INVALID_ARG, "segment %d: null out", i);
+    if (g.n_cases > 0 && g.n_inputs > 0 && !g.cases) return gp_fail(GP_ERR_INVALID_ARG, "segment %d: null cases", i);
+    if (g.n_cases > 0 && !g.targets) return gp_fail(GP_ERR_INVALID_ARG, "segment %d: null targets", i);
+    const int64_t units = fl ? g.n_cases : (g.n_cases + 31) / 32;
+    const int64_t ch = choose_chunk(units, g.n_progs, per_pass, g.chunk, fl ? kAutoBlocksPerSm : 48);
+    if (ch % per_pass) return gp_fail(GP_ERR_INVALID_ARG, "segment %d: chunk must be a multiple of k*block", i);
+    chunk_of[i] = ch;
+    prog_end = std::max<int64_t>(prog_end, (int64_t)g.prog_begin + g.n_progs);
+    max_inputs = std::max(max_inputs, g.n_inputs);
+    all_single = all_single && g.n_inputs == 1;
+    idx.push_back(i);
+  }
+  if (idx.empty()) return GP_OK;
+  if (!programs || !offsets || !lengths) return gp_fail(GP_ERR_INVALID_ARG, "null program arrays");
+  if (!aligned16(programs)) return gp_fail(GP_ERR_INVALID_ARG, "programs must be 16-byte aligned");
+  if (prog_end > 0x7fffffffLL) return gp_fail(GP_ERR_INVALID_ARG, "program index out of range");
+  {  // program ranges may not overlap
+    std::vector<int> byp(idx);
+    std::sort(byp.begin(), byp.end(), [&](int x, int y) { return segments[x].prog_begin < segments[y].prog_begin; });
+    for (size_t j = 1; j < byp.size(); ++j)
+      if ((int64_t)segments[byp[j - 1]].prog_begin + segments[byp[j - 1]].n_progs > segments[byp[j]].prog_begin)
+        return gp_fail(GP_ERR_INVALID_ARG, "segments %d and %d overlap", byp[j - 1], byp[j]);
+  }
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return chunk_of[x] > chunk_of[y]; });
+  SegTable t;
+  memset(&t, 0, sizeof t);
+  t.n = (int32_t)idx.size();
+  int64_t blocks = 0, partials = 0, progs = 0;
+  for (int j = 0; j < t.n; ++j) {
+    const gp_segment& g = segments[idx[j]];
+    SegDesc& d = t.s[j];
+    const int64_t units = fl ? g.n_cases : (g.n_cases + 31) / 32;
+    d.cases = g.cases;
+    d.targets = g.targets;
+    d.out = g.out;
+    d.n_cases = g.n_cases;
+    d.n_units = units;
+    d.chunk = chunk_of[idx[j]];
+    d.n_inputs = g.n_inputs;
+    d.prog_begin = g.prog_begin;
+    d.n_progs = g.n_progs;
+    const int64_t nch = std::max<int64_t>(1, (units + d.chunk - 1) / d.chunk);
+    d.n_chunks = (int32_t)nch;
+    if (blocks + nch * g.n_progs > 0x7fffffffLL) return gp_fail(GP_ERR_INVALID_ARG, "too many blocks");
+    d.block_begin = (int32_t)blocks;
+    blocks += nch * g.n_progs;
+    d.partial_begin = partials;
+    if (nch > 1) partials += nch * g.n_progs;
+    progs += g.n_progs;
+    if (fl)
+      d.aligned = ((aligned16(g.cases) && (g.n_inputs <= 1 || g.n_cases % 4 == 0)) ? 1 : 0) |
+                  (aligned16(g.targets) ? 2 : 0);
+    else
+      d.aligned = (aligned16(g.cases) && aligned16(g.targets) && (g.n_inputs <= 1 || units % 4 == 0)) ? 1 : 0;
+  }
+  size_t smem = 0;
+  int32_t tile_inputs = max_inputs;
+  if (fl) {
+    if (c.tile_inputs > 0 && c.tile_inputs < max_inputs) tile_inputs = c.tile_inputs;
+    rc = float_launch_smem(c, tile_inputs, &smem);
+    if (rc) return rc;
+  } else {
+    const size_t tile_bytes = bool_tile_bytes(c.k, c.block, max_inputs);
+    if (tile_bytes > kMaxTileBytes)
+      return gp_fail(GP_ERR_INVALID_ARG, "%d inputs need %zu bytes of staged inputs per block (max %zu)",
+                     max_inputs, tile_bytes, kMaxTileBytes);
+    smem = prog_buffer_bytes(c.max_instructions) + tile_bytes;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* w = nullptr;
+  rc = get_workspace(s, fl ? (size_t)partials : 0, fl ? (size_t)prog_end : 0, &w);
+  if (rc) return rc;
+  int32_t* order = nullptr;
+  if (progs >= (int64_t)kOrderMinProgsPerSm * sm_count()) {
+    rc = get_order(w, (size_t)prog_end, s, &order);
+    if (rc) return rc;
+  }
+  cudaError_t e;
+  if (order || !fl) {
+    e = launch_segment_prep(t, lengths, order, !fl, s);
+    if (e != cudaSuccess) return cuda_fail(e, "segment preparation launch");
+  }
+  if (fl) {
+    FloatArgs a;
+    memset(&a, 0, sizeof a);
+    a.programs = programs;
+    a.offsets = offsets;
+    a.lengths = lengths;
+    a.n_progs = (int32_t)prog_end;
+    a.partials = w->partials;
+    a.counters = w->counters;
+    a.status = w->status;
+    a.n_chunks = 1;
+    a.want_fitness = 1;
+    a.fitness_kind = c.fitness;
+    a.prog_cap = c.max_instructions;
+    a.order = order;
+    a.tile_inputs = tile_inputs;
+    const bool xreg = all_single;
+    if (c.k == 1) e = launch_float_seg_k1(a, t, xreg, c.block, (int)blocks, smem, s);
+    else if (c.k == 2) e = launch_float_seg_k2(a, t, xreg, c.block, (int)blocks, smem, s);
+    else if (c.k == 4) e = launch_float_seg_k4(a, t, xreg, c.block, (int)blocks, smem, s);
+    else e = launch_float_seg_k8(a, t, xreg, c.block, (int)blocks, smem, s);
+  } else {
+    BoolArgs a;
+    memset(&a, 0, sizeof a);
+    a.programs = programs;
+    a.offsets = offsets;
+    a.lengths = lengths;
+    a.n_progs = (int32_t)prog_end;
+    a.n_inputs = max_inputs;
+    a.status = w->status;
+    a.n_chunks = 1;
+    a.prog_cap = c.max_instructions;
+    a.order = order;
+    e = launch_bool_seg(a, t, c.k, c.block, (int)blocks, smem, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return GP_OK;
+}
+
 extern "C" int gp_last_error(gp_stream_t stream, int32_t* status) {
   gp_clear_error();
   if (!status) return gp_fail(GP_ERR_INVALID_ARG, "null status");
@@ -543,73 +734,240 @@ extern "C" int gp_shutdown(void) {
   return GP_OK;
 }
 
-extern "C" int gp_autotune_population(const uint32_t* programs, const int64_t* offsets,
-                                      const int32_t* lengths, int32_t n_progs, const float* cases,
-                                      int32_t n_inputs, int64_t n_cases, const float* targets,
-                                      int32_t repeats, gp_config* best, gp_stream_t stream) {
+namespace {
+
+// Times `eval(c)` for every candidate (one warm-up launch, `repeats` timed
+// launches each, the minimum kept) on `s`; candidates whose launch fails
+// argument checks or that report a program error (a kernel that cannot run
+// this population's programs) are skipped.  Synchronises `s`.
+template <typename Eval>
+int tune_over(const std::vector<gp_config>& cands, int repeats, cudaStream_t s, Eval eval, gp_config* best,
+              float* best_ms) {
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  *best_ms = 1e30f;
+  int rc = GP_OK;
+  int32_t st = 0;
+  gp_last_error((gp_stream_t)s, &st);  // (clears an earlier status)
+  for (const gp_config& c : cands) {
+    if (eval(c) != GP_OK) continue;  // this shape does not fit (tile, block limits)
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "autotune"); break; }
+    st = 0;
+    rc = gp_last_error((gp_stream_t)s, &st);
+    if (rc) break;
+    if (st != 0) continue;  // programs this kernel does not run
+    float ms_min = 1e30f;
+    for (int r = 0; r < repeats && rc == GP_OK; ++r) {
+      cudaEventRecord(t0, s);
+      rc = eval(c);
+      cudaEventRecord(t1, s);
+      e = cudaEventSynchronize(t1);
+      if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, t0, t1);
+      ms_min = std::min(ms_min, ms);
+    }
+    if (rc) break;
+    if (ms_min < *best_ms) {
+      *best_ms = ms_min;
+      *best = c;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  gp_clear_error();
+  if (rc == GP_OK && *best_ms >= 1e30f) rc = gp_fail(GP_ERR_INVALID_ARG, "no candidate configuration runs this population");
+  return rc;
+}
+
+// cases (or words) per block tried besides the automatic choice: fixed
+// sizes, and the whole set in one block when that is large
+void add_chunks(std::vector<gp_config>& out, gp_config c, int64_t n_units) {
+  static const int chunks[] = {0, 4096, 8192, 16384, 32768, 65536, 131072, -1};
+  const int64_t per_pass = (int64_t)c.k * c.block;
+  for (int ch0 : chunks) {
+    int64_t ch = ch0;
+    if (ch0 < 0) {
+      ch = ((n_units + per_pass - 1) / per_pass) * per_pass;
+      if (ch > 0x7fffffff || ch <= 131072) continue;  // (a 32-bit field; sizes above cover the rest)
+    } else if (ch && (ch % per_pass || ch >= n_units)) {
+      continue;
+    }
+    c.chunk_cases = (int32_t)ch;
+    out.push_back(c);
+  }
+}
+
+}  // namespace
+
+extern "C" int gp_autotune_population_ex(const uint32_t* programs, const int64_t* offsets,
+                                         const int32_t* lengths, int32_t n_progs, const float* cases,
+                                         int32_t n_inputs, int64_t n_cases, const float* targets,
+                                         const gp_config* base, int32_t repeats, gp_config* best,
+                                         gp_stream_t stream) {
   gp_clear_error();
   if (n_progs <= 0 || n_cases <= 0) return gp_fail(GP_ERR_INVALID_ARG, "nothing to tune on");
   if (repeats <= 0) repeats = 3;
+  gp_config b;
+  int rc = resolve_config(base, &b);
+  if (rc) return rc;
+  const int family = (base && base->variant) ? base->variant : b.variant;
   cudaStream_t s = (cudaStream_t)stream;
   double* fit = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&fit, sizeof(double) * (size_t)n_progs, s);
   if (e != cudaSuccess) return cuda_fail(e, "autotune buffer");
-  cudaEvent_t t0, t1;
-  cudaEventCreate(&t0);
-  cudaEventCreate(&t1);
-  gp_config best_c = {GP_VARIANT_REGISTER, 0, 0, 0};
-  float best_ms = 1e30f;
-  int rc = GP_OK;
-  static const int ks[] = {2, 4, 8};
-  static const int blocks[] = {64, 128, 256, 512};
-  // cases per block: chosen, fixed sizes, or (-1) the whole case set, which
-  // with the programs taken longest first often needs the fewest blocks
-  static const int chunks[] = {0, 4096, 8192, 16384, 32768, -1};
-  for (int k : ks) {
-    for (int blk : blocks) {
-     for (int ch0 : chunks) {
-      int64_t ch = ch0;
-      if (ch0 < 0) {
-        ch = ((n_cases + k * blk - 1) / (k * blk)) * (k * blk);
-        if (ch > 0x7fffffff || ch <= 32768) continue;  // (a 32-bit field; sizes above cover the rest)
-      } else if (ch && (ch % (k * blk) || ch >= n_cases)) {
-        continue;
+  // candidates: k x block x chunk within the family; for the register
+  // variant also its register-file form (register programs) and, at k = 8,
+  // stack levels 4..7 in shared memory (S-form programs); a candidate whose
+  // kernel cannot run every program reports a program error and is skipped
+  std::vector<gp_config> cands;
+  std::vector<int> variants{b.variant};
+  if (b.variant == GP_VARIANT_REGISTER) variants.push_back(GP_VARIANT_REGISTER_FILE);
+  for (int v : variants) {
+    const bool one_case = v == GP_VARIANT_LOCAL;
+    const int max_block = (v == GP_VARIANT_LOCAL || v == GP_VARIANT_REGISTER_FILE) ? 256 : 512;
+    for (int k : {1, 2, 4, 8}) {
+      if (one_case != (k == 1)) continue;
+      for (int blk : {64, 128, 256, 512}) {
+        if (blk > max_block) continue;
+        for (int rl : {0, 4}) {
+          if (rl && (v != GP_VARIANT_REGISTER || k != 8)) continue;
+          gp_config c = b;
+          c.variant = v;
+          c.k = k;
+          c.block = blk;
+          c.stack_registers = rl;
+          add_chunks(cands, c, n_cases);
+        }
       }
-      gp_config c = {GP_VARIANT_REGISTER, k, blk, (int32_t)ch};
-      rc = gp_eval_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases,
-                                 targets, fit, nullptr, &c, stream);
-      if (rc) break;
-      float ms_min = 1e30f;
-      for (int r = 0; r < repeats && rc == GP_OK; ++r) {
-        cudaEventRecord(t0, s);
-        rc = gp_eval_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases,
-                                   targets, fit, nullptr, &c, stream);
-        cudaEventRecord(t1, s);
-        e = cudaEventSynchronize(t1);
-        if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
-        float ms = 0;
-        cudaEventElapsedTime(&ms, t0, t1);
-        ms_min = std::min(ms_min, ms);
-      }
-      if (rc) break;
-      if (ms_min < best_ms) {
-        best_ms = ms_min;
-        best_c = c;
-      }
-     }
-     if (rc) break;
     }
-    if (rc) break;
   }
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
+  auto eval = [&](const gp_config& c) {
+    return gp_eval_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases, targets, fit,
+                                 nullptr, &c, stream);
+  };
+  gp_config best_c = b;
+  float best_ms = 0;
+  rc = tune_over(cands, repeats, s, eval, &best_c, &best_ms);
   cudaFreeAsync(fit, s);
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_tuned[tune_key(n_inputs, n_cases, n_progs)] = best_c;
+    g_tuned[tune_key(family, n_inputs, n_cases, n_progs)] = best_c;
   }
   if (best) *best = best_c;
+  return GP_OK;
+}
+
+extern "C" int gp_autotune_population(const uint32_t* programs, const int64_t* offsets,
+                                      const int32_t* lengths, int32_t n_progs, const float* cases,
+                                      int32_t n_inputs, int64_t n_cases, const float* targets,
+                                      int32_t repeats, gp_config* best, gp_stream_t stream) {
+  return gp_autotune_population_ex(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases, targets,
+                                   nullptr, repeats, best, stream);
+}
+
+extern "C" int gp_autotune_population_bool(const uint32_t* programs, const int64_t* offsets,
+                                           const int32_t* lengths, int32_t n_progs, const uint32_t* case_bits,
+                                           int32_t n_inputs, int64_t n_cases, const uint32_t* target_bits,
+                                           const gp_config* base, int32_t repeats, gp_config* best,
+                                           gp_stream_t stream) {
+  gp_clear_error();
+  if (n_progs <= 0 || n_cases <= 0) return gp_fail(GP_ERR_INVALID_ARG, "nothing to tune on");
+  if (repeats <= 0) repeats = 3;
+  gp_config b;
+  int rc = resolve_config(base, &b);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint64_t* hits = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&hits, sizeof(uint64_t) * (size_t)n_progs, s);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune buffer");
+  const int64_t n_words = (n_cases + 31) / 32;
+  std::vector<gp_config> cands;
+  if (n_words <= 4) {  // one program per lane
+    gp_config c = b;
+    c.variant = GP_VARIANT_LANES;
+    cands.push_back(c);
+  }
+  for (int k : {1, 2, 4, 8})
+    for (int blk : {32, 64, 128, 256}) {
+      gp_config c = b;
+      c.variant = GP_VARIANT_REGISTER;
+      c.k = k;
+      c.block = blk;
+      c.stack_registers = 0;
+      add_chunks(cands, c, n_words);
+    }
+  auto eval = [&](const gp_config& c) {
+    return gp_eval_population_bool_ex(programs, offsets, lengths, n_progs, case_bits, n_inputs, n_cases,
+                                      target_bits, hits, nullptr, &c, stream);
+  };
+  gp_config best_c = b;
+  float best_ms = 0;
+  rc = tune_over(cands, repeats, s, eval, &best_c, &best_ms);
+  cudaFreeAsync(hits, s);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tuned[tune_key(kTuneBool, n_inputs, n_cases, n_progs)] = best_c;
+  }
+  if (best) *best = best_c;
+  return GP_OK;
+}
+
+extern "C" int gp_autotune_save(const char* path) {
+  gp_clear_error();
+  if (!path) return gp_fail(GP_ERR_INVALID_ARG, "null path");
+  FILE* f = fopen(path, "w");
+  if (!f) return gp_fail(GP_ERR_INVALID_ARG, "cannot write %s", path);
+  std::lock_guard<std::mutex> lk(g_mu);
+  fprintf(f, "# gpeval autotune v1: family several log2_cases log2_progs variant k block chunk_cases "
+             "stack_registers\n");
+  for (const auto& kv : g_tuned) {
+    const gp_config& c = kv.second;
+    fprintf(f, "%d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+            std::get<2>(kv.first), std::get<3>(kv.first), c.variant, c.k, c.block, c.chunk_cases,
+            c.stack_registers);
+  }
+  const bool ok = fclose(f) == 0;
+  return ok ? GP_OK : gp_fail(GP_ERR_INVALID_ARG, "cannot write %s", path);
+}
+
+extern "C" int gp_autotune_load(const char* path) {
+  gp_clear_error();
+  if (!path) return gp_fail(GP_ERR_INVALID_ARG, "null path");
+  FILE* f = fopen(path, "r");
+  if (!f) return gp_fail(GP_ERR_INVALID_ARG, "cannot read %s", path);
+  std::vector<std::pair<TuneKey, gp_config>> recs;
+  char line[512];
+  int rc = GP_OK, ln = 0;
+  while (fgets(line, sizeof line, f)) {
+    ++ln;
+    if (line[0] == '#' || line[0] == '\n') continue;
+    int fam, sev, lc, lp, var, k, blk, ch, sr;
+    if (sscanf(line, "%d %d %d %d %d %d %d %d %d", &fam, &sev, &lc, &lp, &var, &k, &blk, &ch, &sr) != 9) {
+      rc = gp_fail(GP_ERR_INVALID_ARG, "%s line %d: expected 9 integers", path, ln);
+      break;
+    }
+    gp_config c = kLibraryDefault;
+    c.variant = var;
+    c.k = k;
+    c.block = blk;
+    c.chunk_cases = ch;
+    c.stack_registers = sr;
+    gp_config chk;
+    if (resolve_config(&c, &chk) != GP_OK) {
+      rc = gp_fail(GP_ERR_INVALID_ARG, "%s line %d: not a valid configuration", path, ln);
+      break;
+    }
+    recs.emplace_back(TuneKey(fam, sev, lc, lp), c);
+  }
+  fclose(f);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& r : recs) g_tuned[r.first] = r.second;
   return GP_OK;
 }
 

@@ -207,6 +207,22 @@ struct Emitter {
         {-1, -1, SF_SSR, -1},           // a = S1
     };
     int form = table[kindof(0)][kindof(1)];
+    if (n.op == GP_OP_DIV && kindof(1) == 1 && div_fast_operand(pay[1]) &&
+        (kindof(0) != 1 || div_fast_operand(pay[0]))) {
+      // a constant divisor inside the fast range: its reciprocal, rounded to
+      // nearest even in binary32 (IEEE division on the host), goes to
+      // payload c, and the interpreter divides with a multiplication and one
+      // remainder correction
+      float b;
+      memcpy(&b, &pay[1], 4);
+      const float y = 1.0f / b;
+      uint32_t ybits;
+      memcpy(&ybits, &y, 4);
+      const int k0 = kindof(0);
+      const int iform = k0 == 0 ? SF_XI : k0 == 1 ? SF_CI : SF_SI;
+      put(sform_code(iform, l, F_DIV), pay[0], pay[1], ybits);
+      return;
+    }
     if (is_float_fn(n.op)) put(sform_code(form, l, (int)(n.op - GP_OP_ADD)), pay[0], pay[1], 0);
     else put(sfx_bin_code(form, l, xbin_index(n.op)), pay[0], pay[1], 0);
   }

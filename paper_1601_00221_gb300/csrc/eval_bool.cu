@@ -19,6 +19,24 @@ cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, size_t sm
   }
   return cudaGetLastError();
 }
+template <int K>
+static void launch_seg_k(const BoolArgs& a, const SegTable& t, int block, int grid, size_t smem, cudaStream_t s) {
+  static std::atomic<size_t> configured{0};
+  ensure_dynamic_smem(eval_bool_seg_kernel<K>, smem, configured);
+  eval_bool_seg_kernel<K><<<grid, block, smem, s>>>(a, t);
+}
+
+cudaError_t launch_bool_seg(const BoolArgs& a, const SegTable& t, int k, int block, int grid, size_t smem,
+                            cudaStream_t s) {
+  switch (k) {
+    case 1: launch_seg_k<1>(a, t, block, grid, smem, s); break;
+    case 2: launch_seg_k<2>(a, t, block, grid, smem, s); break;
+    case 4: launch_seg_k<4>(a, t, block, grid, smem, s); break;
+    default: launch_seg_k<8>(a, t, block, grid, smem, s); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bool_lanes(const BoolArgs& a, int w, int grid, size_t smem, cudaStream_t s) {
   switch (w) {
     case 1: eval_bool_lanes_kernel<1><<<grid, 32, smem, s>>>(a); break;

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "eval_float.cuh"
 #include "gen_interp.h"
 #include "isa.h"
 
@@ -100,8 +101,10 @@ __device__ __forceinline__ bool valid_bool_instr(const uint4& in, int n_inputs) 
   return false;
 }
 
-template <int K>
-__global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
+// SEG: the block's population, cases and hit counts come from segment table
+// t (eval_float.cuh's SegTable: Boolean segments hold words); otherwise from a.
+template <int K, bool SEG>
+__device__ __forceinline__ void eval_bool_block(const BoolArgs& a, const SegTable* t) {
   using namespace gpisa;
   // dynamic: the program (prog_cap instructions + the end sentinel), then the
   // staged inputs [warp][input][32 lanes][K words]
@@ -112,10 +115,25 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   __shared__ int meta_s;
 
   const int item = blockIdx.x;
-  const int rank = item / a.n_chunks;
-  const int p = a.order ? a.order[rank] : rank;
-  const int chunk = item - rank * a.n_chunks;
+  const int seg = SEG ? segment_of(t, item) : 0;
+#define GP_SEG(field, seg_expr) (SEG ? (seg_expr) : a.field)
+  const int32_t a_n_chunks = GP_SEG(n_chunks, t->s[seg].n_chunks);
+  const int prog_base = SEG ? t->s[seg].prog_begin : 0;
+  const int local = SEG ? item - t->s[seg].block_begin : item;
+  const int rank = local / a_n_chunks;
+  const int p = a.order ? a.order[prog_base + rank] : prog_base + rank;
+  const int chunk = local - rank * a_n_chunks;
   const int tid = threadIdx.x;
+  const int32_t a_n_inputs = GP_SEG(n_inputs, t->s[seg].n_inputs);
+  const int64_t a_n_cases = GP_SEG(n_cases, t->s[seg].n_cases);
+  const int64_t a_n_words = GP_SEG(n_words, t->s[seg].n_units);
+  const int64_t a_chunk_words = GP_SEG(chunk_words, t->s[seg].chunk);
+  const uint32_t* a_case_bits = GP_SEG(case_bits, static_cast<const uint32_t*>(t->s[seg].cases));
+  const uint32_t* a_target_bits = GP_SEG(target_bits, static_cast<const uint32_t*>(t->s[seg].targets));
+  const bool a_aligned = GP_SEG(aligned, t->s[seg].aligned != 0);
+  // hit counts: indexed by the segment's own program numbers
+  unsigned long long* hits_row =
+      SEG ? static_cast<unsigned long long*>(t->s[seg].out) + (p - prog_base) : (a.hits_out ? a.hits_out + p : nullptr);
 
   if (tid == 0) {
     int n_instr = -1;
@@ -139,7 +157,7 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
     for (int i = tid; i < n_instr; i += blockDim.x) {
       const uint4 in = g[i];
       prog_s[i] = in;
-      ok &= valid_bool_instr(in, a.n_inputs) ? 1 : 0;
+      ok &= valid_bool_instr(in, a_n_inputs) ? 1 : 0;
     }
     if (tid == 0) prog_s[n_instr] = make_uint4(BOOL_NCODES, 0u, 0u, 0u);  // end sentinel
     bad = !__syncthreads_and(ok);
@@ -147,36 +165,36 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   if (bad) {
     if (tid == 0) {
       atomicOr(a.status, 2 /* GP_ERR_PROGRAM */);
-      if (a.hits_out) atomicExch(&a.hits_out[p], ~0ull);
+      if (hits_row) atomicExch(hits_row, ~0ull);
     }
     return;
   }
 
   const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
-  const int64_t w_begin = (int64_t)chunk * a.chunk_words;
-  int64_t w_end = w_begin + a.chunk_words;
-  if (w_end > a.n_words) w_end = a.n_words;
-  const uint32_t tail = (uint32_t)(a.n_cases & 31);
+  const int64_t w_begin = (int64_t)chunk * a_chunk_words;
+  int64_t w_end = w_begin + a_chunk_words;
+  if (w_end > a_n_words) w_end = a_n_words;
+  const uint32_t tail = (uint32_t)(a_n_cases & 31);
   const uint32_t last_mask = tail ? ((1u << tail) - 1u) : 0xffffffffu;
-  uint32_t* out_row = a.out_words ? a.out_words + (int64_t)p * a.n_words : nullptr;
+  uint32_t* out_row = (!SEG && a.out_words) ? a.out_words + (int64_t)p * a_n_words : nullptr;
   unsigned long long hits = 0;
   bool bad_pass = false;
 
   const uint32_t prog_addr = (uint32_t)__cvta_generic_to_shared(prog_s);
-  uint32_t* tile = reinterpret_cast<uint32_t*>(btile_s) + (size_t)warp * a.n_inputs * 32 * K + lane * K;
+  uint32_t* tile = reinterpret_cast<uint32_t*>(btile_s) + (size_t)warp * a_n_inputs * 32 * K + lane * K;
   const uint32_t tile_addr = (uint32_t)__cvta_generic_to_shared(tile);
 #pragma unroll 1
   for (int64_t wb = w_begin + (int64_t)warp * 32 * K; wb < w_end; wb += (int64_t)nwarps * 32 * K) {
     const int64_t w0 = wb + (int64_t)lane * K;
-    const bool full = w0 + K <= a.n_words;
+    const bool full = w0 + K <= a_n_words;
     int v = 0;
-    if (full && a.aligned) {
+    if (full && a_aligned) {
       // every input's K words as asynchronous copies straight into the tile
       // (16-, 8- or 4-byte aligned: rows aligned, w0 a multiple of K): all
       // inputs in one global round trip, no registers held.  A lane reads
       // back only its own words, so its own wait suffices.
-      for (; v < a.n_inputs; ++v) {
-        const uint32_t* src = a.case_bits + (int64_t)v * a.n_words + w0;
+      for (; v < a_n_inputs; ++v) {
+        const uint32_t* src = a_case_bits + (int64_t)v * a_n_words + w0;
         uint32_t* dst = tile + v * 32 * K;
         if constexpr (K == 8) {
           __pipeline_memcpy_async(dst, src, 16);
@@ -188,28 +206,28 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
       __pipeline_commit();
       __pipeline_wait_prior(0);
     }
-    for (; v < a.n_inputs; ++v) {
-      UVec<K> t;
-      uload<K>(t, a.case_bits + (int64_t)v * a.n_words, w0, a.n_words, full && a.aligned);
+    for (; v < a_n_inputs; ++v) {
+      UVec<K> tv;
+      uload<K>(tv, a_case_bits + (int64_t)v * a_n_words, w0, a_n_words, full && a_aligned);
 #pragma unroll
-      for (int j = 0; j < K; ++j) tile[v * 32 * K + j] = t.w[j];
+      for (int j = 0; j < K; ++j) tile[v * 32 * K + j] = tv.w[j];
     }
     uint32_t o[K];
     if (!run_bool<K>(prog_addr, (uint32_t)n_instr, tile_addr, o)) bad_pass = true;
     if (out_row) {
 #pragma unroll
       for (int j = 0; j < K; ++j)
-        if (w0 + j < a.n_words) out_row[w0 + j] = o[j];
+        if (w0 + j < a_n_words) out_row[w0 + j] = o[j];
     }
-    if (a.target_bits) {
-      UVec<K> t;
-      uload<K>(t, a.target_bits, w0, a.n_words, full && a.aligned);
+    if (a_target_bits) {
+      UVec<K> tv;
+      uload<K>(tv, a_target_bits, w0, a_n_words, full && a_aligned);
       uint32_t h = 0;
 #pragma unroll
       for (int j = 0; j < K; ++j) {
         const int64_t w = w0 + j;
-        uint32_t m = (w < a.n_words - 1) ? 0xffffffffu : (w == a.n_words - 1 ? last_mask : 0u);
-        h += __popc(~(o[j] ^ t.w[j]) & m);
+        uint32_t m = (w < a_n_words - 1) ? 0xffffffffu : (w == a_n_words - 1 ? last_mask : 0u);
+        h += __popc(~(o[j] ^ tv.w[j]) & m);
       }
       hits += h;
     }
@@ -217,11 +235,11 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   if (__syncthreads_or(bad_pass ? 1 : 0)) {
     if (tid == 0) {
       atomicOr(a.status, 2 /* GP_ERR_PROGRAM */);
-      if (a.hits_out) atomicExch(&a.hits_out[p], ~0ull);
+      if (hits_row) atomicExch(hits_row, ~0ull);
     }
     return;
   }
-  if (!a.hits_out || !a.target_bits) return;
+  if (!hits_row || !a_target_bits) return;
   // integer sums are exact, so any order gives the same hit count
   hits = __reduce_add_sync(0xffffffffu, (unsigned)hits);
   if (lane == 0) red_s[warp] = hits;
@@ -229,8 +247,20 @@ __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
   if (tid == 0) {
     unsigned long long t = 0;
     for (int w = 0; w < nwarps; ++w) t += red_s[w];
-    atomicAdd(&a.hits_out[p], t);
+    atomicAdd(hits_row, t);
   }
+#undef GP_SEG
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
+  eval_bool_block<K, false>(a, nullptr);
+}
+
+// several populations in one launch; each segment's hits are zero before it
+template <int K>
+__global__ void __launch_bounds__(256) eval_bool_seg_kernel(BoolArgs a, const __grid_constant__ SegTable t) {
+  eval_bool_block<K, true>(a, &t);
 }
 
 }  // namespace gpdev

@@ -64,6 +64,44 @@ struct FloatArgs {
   int32_t tile_inputs;   // inputs per case the staged tile holds (<= n_inputs)
 };
 
+// Several populations in one launch (gp_eval_segments, the serving loop's
+// merged launches): segment i is programs [prog_begin, prog_begin + n_progs)
+// of the launch's program arrays, evaluated on its own cases, split into its
+// own chunks (so each program's result is what it would be in a launch of its
+// own), blocks [block_begin, block_begin + n_progs * n_chunks).  The table
+// travels as a kernel parameter; segments are laid out in block order.
+constexpr int kMaxSegments = 64;  // GP_MAX_SEGMENTS
+struct SegDesc {
+  const void* cases;     // float [n_inputs][n_cases] or uint32 [n_inputs][n_words]
+  const void* targets;   // float [n_cases] or uint32 [n_words]
+  void* out;             // double fitness or uint64 hits, [n_progs]
+  int64_t n_cases;
+  int64_t n_units;       // cases (float) or words (Boolean)
+  int64_t chunk;         // cases or words per block
+  int64_t partial_begin; // first per-block partial of the segment (float, n_chunks > 1)
+  int32_t n_inputs;
+  int32_t prog_begin;
+  int32_t n_progs;
+  int32_t n_chunks;
+  int32_t block_begin;
+  int32_t aligned;       // float: bit 0 cases, bit 1 targets (16-byte rows); Boolean: both
+};
+struct SegTable {
+  int32_t n;
+  int32_t pad;
+  SegDesc s[kMaxSegments];
+};
+// the segment of block `item`: the last whose block_begin is <= item
+__device__ __forceinline__ int segment_of(const SegTable* t, int item) {
+  int lo = 0, hi = t->n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t->s[mid].block_begin <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Trees whose cases have at most GP_COMPACT_MAX_INPUTS inputs stage only the
 // inputs the program reads, at most GP_COMPACT_MAX_LIST of them; otherwise
 // (and for register programs) the first inputs are staged in order.
@@ -77,7 +115,7 @@ __device__ __forceinline__ uint32_t input_fields(uint32_t kind, uint32_t code) {
   auto bin = [](int form) -> uint32_t {
     switch (form) {
       case SF_XX: return 3u;
-      case SF_XC: case SF_XS: case SF_MOVX: return 1u;
+      case SF_XC: case SF_XS: case SF_MOVX: case SF_XI: return 1u;
       case SF_CX: case SF_SX: return 2u;
       default: return 0u;
     }
@@ -346,7 +384,15 @@ __device__ __forceinline__ bool valid_instr(uint32_t kind, const uint4& in, int 
     const int op = in.x & 3, level = (in.x >> 2) % R, form = (in.x >> 2) / R;
     if ((form == SF_SS || form == SF_SSR) && level + 1 >= R) return false;
     if (form == SF_MOVX || form == SF_MOVC) { if (op != 0 || level != 0) return false; }
-    const bool xa = form == SF_XX || form == SF_XC || form == SF_XS || form == SF_MOVX;
+    if (form == SF_XI || form == SF_SI || form == SF_CI) {
+      // division by a constant with its reciprocal: the divisor (and a
+      // constant numerator) in the fast range, payload c its reciprocal
+      // rounded to nearest even
+      if (op != F_DIV || !div_fast_operand(in.z) || (form == SF_CI && !div_fast_operand(in.y)) ||
+          in.w != __float_as_uint(__frcp_rn(__uint_as_float(in.z))))
+        return false;
+    }
+    const bool xa = form == SF_XX || form == SF_XC || form == SF_XS || form == SF_MOVX || form == SF_XI;
     const bool xb = form == SF_XX || form == SF_CX || form == SF_SX;
     if (xa && in.y >= nin) return false;
     if (xb && in.z >= nin) return false;
@@ -412,8 +458,10 @@ __device__ __forceinline__ bool valid_instr_ext(uint32_t kind, const uint4& in, 
 // RL < R: stack levels RL.. in shared memory (K = 8, RL = 4; K_SFORM only).
 // Up to 512 threads per block at 128 registers: the warps of an SM interpret
 // as few distinct programs as possible (every block holds one program).
-template <int K, bool XREG, int EXT = 0, int RL = gpisa::R>
-__global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
+// SEG: the block's population, cases and outputs come from segment table t
+// (the basic interpreters only); otherwise from a.
+template <int K, bool XREG, int EXT, int RL, bool SEG>
+__device__ __forceinline__ void eval_float_block(const FloatArgs& a, const SegTable* t) {
   using namespace gpisa;
   // dynamic: the program (prog_cap instructions + the end sentinel), then the
   // tiles [warp][slot][32 lanes][K] when staged
@@ -428,9 +476,18 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
   __shared__ int n_stage_s;
 
   const int item = blockIdx.x;
-  const int rank = item / a.n_chunks;
-  const int p = a.order ? a.order[rank] : rank;
-  const int chunk = item - rank * a.n_chunks;
+  const int seg = SEG ? segment_of(t, item) : 0;
+  // the block's population: the launch's, or its segment's
+#define GP_SEG(field, seg_expr) (SEG ? (seg_expr) : a.field)
+  const int64_t a_n_cases = GP_SEG(n_cases, t->s[seg].n_cases);
+  const int32_t a_n_inputs = GP_SEG(n_inputs, t->s[seg].n_inputs);
+  const int64_t a_chunk_cases = GP_SEG(chunk_cases, t->s[seg].chunk);
+  const int32_t a_n_chunks = GP_SEG(n_chunks, t->s[seg].n_chunks);
+  const int prog_base = SEG ? t->s[seg].prog_begin : 0;
+  const int local = SEG ? item - t->s[seg].block_begin : item;
+  const int rank = local / a_n_chunks;
+  const int p = a.order ? a.order[prog_base + rank] : prog_base + rank;
+  const int chunk = local - rank * a_n_chunks;
   const int tid = threadIdx.x;
 
   if (tid == 0) {
@@ -462,8 +519,8 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
     for (int i = tid; i < n_instr; i += blockDim.x) {
       const uint4 in = g[i];
       prog_s[i] = in;
-      if constexpr (EXT) ok &= valid_instr_ext(kind, in, a.n_inputs) ? 1 : 0;
-      else ok &= valid_instr(kind, in, a.n_inputs) ? 1 : 0;
+      if constexpr (EXT) ok &= valid_instr_ext(kind, in, a_n_inputs) ? 1 : 0;
+      else ok &= valid_instr(kind, in, a_n_inputs) ? 1 : 0;
     }
     // the interpreters leave through the table entry one past the last code
     if (tid == 0)
@@ -484,12 +541,12 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
   // register holds it across the interpreter loop)
   if (!bad && staged) {
     int n_stage;
-    if (XREG || kind == K_LINEAR || a.n_inputs > GP_COMPACT_MAX_INPUTS) {
+    if (XREG || kind == K_LINEAR || a_n_inputs > GP_COMPACT_MAX_INPUTS) {
       // (a kernel with the input in registers stages register programs only)
-      n_stage = kind == K_LINEAR ? (a.n_inputs < R ? a.n_inputs : R) : a.n_inputs;
+      n_stage = kind == K_LINEAR ? (a_n_inputs < R ? a_n_inputs : R) : a_n_inputs;
       if (tid == 0) n_stage_s = n_stage;
     } else if constexpr (!XREG) {
-      const int nw = (a.n_inputs + 31) >> 5;
+      const int nw = (a_n_inputs + 31) >> 5;
       for (int i = tid; i < nw; i += blockDim.x) used_s[i] = 0u;
       __syncthreads();
       for (int i = tid; i < n_instr; i += blockDim.x) {
@@ -514,7 +571,7 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
         return before_s[v >> 5] + (uint32_t)__popc(used_s[v >> 5] & ((1u << (v & 31)) - 1u));
       };
       if (n_stage > GP_COMPACT_MAX_LIST) {  // too many to list: stage every input in order
-        n_stage = a.n_inputs;
+        n_stage = a_n_inputs;
         __syncthreads();
         if (tid == 0) n_stage_s = n_stage;
       } else if (n_stage <= a.tile_inputs) {
@@ -550,10 +607,14 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
 
   const int warp = tid >> 5, lane = tid & 31;
   const int nwarps = blockDim.x >> 5;
-  const int64_t c_begin = (int64_t)chunk * a.chunk_cases;
-  int64_t c_end = c_begin + a.chunk_cases;
-  if (c_end > a.n_cases) c_end = a.n_cases;
-  float* out_row = a.outputs ? a.outputs + (int64_t)p * a.n_cases : nullptr;
+  const int64_t c_begin = (int64_t)chunk * a_chunk_cases;
+  int64_t c_end = c_begin + a_chunk_cases;
+  if (c_end > a_n_cases) c_end = a_n_cases;
+  float* out_row = (!SEG && a.outputs) ? a.outputs + (int64_t)p * a_n_cases : nullptr;
+  const float* a_cases = GP_SEG(cases, static_cast<const float*>(t->s[seg].cases));
+  const float* a_targets = GP_SEG(targets, static_cast<const float*>(t->s[seg].targets));
+  const bool a_x_aligned = GP_SEG(x_aligned, (t->s[seg].aligned & 1) != 0);
+  const bool a_y_aligned = GP_SEG(y_aligned, (t->s[seg].aligned & 2) != 0);
   const uint32_t prog_addr = (uint32_t)__cvta_generic_to_shared(prog_s);
   // this lane's K staged values of slot v live at tile + v * 32 * K floats
   float* tile = reinterpret_cast<float*>(tile_s) + (size_t)warp * a.tile_inputs * 32 * K + lane * K;
@@ -577,14 +638,14 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
     if constexpr (XREG && EXT == 0 && RL == R && K == 8) {
       // the warp's full passes (all 32 lanes' cases inside the population)
       // in one interpreter call that loops over them itself; the rest below
-      if (kind == K_SFORM && a.want_fitness && !out_row && a.x_aligned && a.y_aligned &&
+      if (kind == K_SFORM && a.want_fitness && !out_row && a_x_aligned && a_y_aligned &&
           (a.fitness_kind == FIT_SUM_ABS || a.fitness_kind == FIT_MSE || a.fitness_kind == FIT_CLASS)) {
         const int64_t stride = (int64_t)nwarps * 32 * K;
-        const int64_t last = min(c_end - 1, a.n_cases - (int64_t)32 * K);  // last start of a full pass
+        const int64_t last = min(c_end - 1, a_n_cases - (int64_t)32 * K);  // last start of a full pass
         if (last >= wb_first) {
           const int64_t passes = (last - wb_first) / stride + 1;
           const int64_t c0 = wb_first + (int64_t)lane * K;
-          if (!run_tree_passes(prog_addr, (uint32_t)n_instr, a.cases + c0, a.targets + c0, (uint32_t)passes,
+          if (!run_tree_passes(prog_addr, (uint32_t)n_instr, a_cases + c0, a_targets + c0, (uint32_t)passes,
                                (uint64_t)stride * sizeof(float), a.fitness_kind, stk, acc, flags))
             flags |= FLAG_BAD;
           wb_first += passes * stride;
@@ -594,14 +655,14 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
 #pragma unroll 1
     for (int64_t wb = wb_first; wb < c_end; wb += (int64_t)nwarps * 32 * K) {
       const int64_t c0 = wb + (int64_t)lane * K;
-      const bool full = c0 + K <= a.n_cases;
-      const bool vec_ok = full && a.x_aligned;
+      const bool full = c0 + K <= a_n_cases;
+      const bool vec_ok = full && a_x_aligned;
       float x[K];
       float o[K];
       if (staged) {
         // a kernel with the input in registers has one input (register programs)
-        const int n_stage = XREG ? a.n_inputs : n_stage_s;
-        const bool listed = !XREG && kind != K_LINEAR && a.n_inputs <= GP_COMPACT_MAX_INPUTS &&
+        const int n_stage = XREG ? a_n_inputs : n_stage_s;
+        const bool listed = !XREG && kind != K_LINEAR && a_n_inputs <= GP_COMPACT_MAX_INPUTS &&
                             n_stage <= GP_COMPACT_MAX_LIST;
         int v = 0;
         if (vec_ok) {
@@ -609,31 +670,31 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
           // that G global round trips overlap instead of following each other
           constexpr int G = K >= 8 ? 2 : 4;
           for (; v + G <= n_stage; v += G) {
-            Vec<K> t[G];
+            Vec<K> tv[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) {
               const int64_t src = listed ? (int64_t)list_s[v + g] : (int64_t)(v + g);
-              vload<K>(t[g], a.cases + src * a.n_cases, c0, a.n_cases, true);
+              vload<K>(tv[g], a_cases + src * a_n_cases, c0, a_n_cases, true);
             }
 #pragma unroll
             for (int g = 0; g < G; ++g)
 #pragma unroll
-              for (int j = 0; j < K; ++j) tile[(v + g) * 32 * K + j] = vget<K>(t[g], j);
+              for (int j = 0; j < K; ++j) tile[(v + g) * 32 * K + j] = vget<K>(tv[g], j);
           }
         }
         for (; v < n_stage; ++v) {
-          Vec<K> t;
+          Vec<K> tv;
           const int64_t src = listed ? (int64_t)list_s[v] : (int64_t)v;
-          vload<K>(t, a.cases + src * a.n_cases, c0, a.n_cases, vec_ok);
+          vload<K>(tv, a_cases + src * a_n_cases, c0, a_n_cases, vec_ok);
 #pragma unroll
-          for (int j = 0; j < K; ++j) tile[v * 32 * K + j] = vget<K>(t, j);
+          for (int j = 0; j < K; ++j) tile[v * 32 * K + j] = vget<K>(tv, j);
         }
       }
       if constexpr (XREG) {
-        Vec<K> t;
-        vload<K>(t, a.cases, c0, a.n_cases, vec_ok);
+        Vec<K> tv;
+        vload<K>(tv, a_cases, c0, a_n_cases, vec_ok);
 #pragma unroll
-        for (int j = 0; j < K; ++j) x[j] = vget<K>(t, j);
+        for (int j = 0; j < K; ++j) x[j] = vget<K>(tv, j);
       } else {
 #pragma unroll
         for (int j = 0; j < K; ++j) x[j] = 0.0f;
@@ -646,7 +707,7 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
         ok = run_tree_rl4<XREG>(prog_addr, (uint32_t)n_instr, x, tile_addr, sbase, o);
       } else if (kind == K_LINEAR) {
         ok = run_linear<K>(prog_addr, (uint32_t)n_instr, tile_addr,
-                           (uint32_t)(a.n_inputs < R ? a.n_inputs : R), stk, o);
+                           (uint32_t)(a_n_inputs < R ? a_n_inputs : R), stk, o);
       } else if (kind == K_SFORM) {
         ok = run_tree<K, XREG, false>(prog_addr, (uint32_t)n_instr, x, tile_addr, stk, o);
       } else {
@@ -656,10 +717,10 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
       Vec<K> ov;
 #pragma unroll
       for (int j = 0; j < K; ++j) vset<K>(ov, j, o[j]);
-      if (out_row) vstore<K>(out_row, ov, c0, a.n_cases, full && a.o_aligned);
+      if (out_row) vstore<K>(out_row, ov, c0, a_n_cases, full && a.o_aligned);
       if (a.want_fitness) {
         Vec<K> y;
-        vload<K>(y, a.targets, c0, a.n_cases, full && a.y_aligned);
+        vload<K>(y, a_targets, c0, a_n_cases, full && a_y_aligned);
         // the K errors (the measure chosen once per pass), the cases past the
         // end masked on the last pass only; then their pass sum and one
         // compensated add
@@ -680,7 +741,7 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
         if (!full) {
 #pragma unroll
           for (int j = 0; j < K; ++j)
-            if (c0 + j >= a.n_cases) e[j] = 0.0f;
+            if (c0 + j >= a_n_cases) e[j] = 0.0f;
         }
 #pragma unroll
         for (int w = 1; w < K; w <<= 1)
@@ -699,10 +760,31 @@ __global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
   block_reduce(acc, flags, red_s, nwarps);
   if (tid == 0) {
     if (flags & FLAG_BAD) atomicOr(a.status, 2 /* GP_ERR_PROGRAM */);
-    if (a.want_fitness || bad)
-      finish_program(a.partials, a.counters, p, chunk, a.n_chunks, acc, flags, a.fitness_out,
-                     fitness_divisor(a.fitness_kind, a.n_cases));
+    if (a.want_fitness || bad) {
+      if constexpr (SEG) {  // the segment's partials, counters and outputs
+        const SegDesc& d = t->s[seg];
+        finish_program(a.partials + d.partial_begin, a.counters + d.prog_begin, p - d.prog_begin, chunk,
+                       d.n_chunks, acc, flags, static_cast<double*>(d.out),
+                       fitness_divisor(a.fitness_kind, d.n_cases));
+      } else {
+        finish_program(a.partials, a.counters, p, chunk, a.n_chunks, acc, flags, a.fitness_out,
+                       fitness_divisor(a.fitness_kind, a.n_cases));
+      }
+    }
   }
+#undef GP_SEG
+}
+
+template <int K, bool XREG, int EXT = 0, int RL = gpisa::R>
+__global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
+  eval_float_block<K, XREG, EXT, RL, false>(a, nullptr);
+}
+
+// several populations in one launch (basic interpreters, all stack levels in
+// registers); a.partials / a.counters span every segment
+template <int K, bool XREG>
+__global__ void __launch_bounds__(512, 1) eval_float_seg_kernel(FloatArgs a, const __grid_constant__ SegTable t) {
+  eval_float_block<K, XREG, 0, gpisa::R, true>(a, &t);
 }
 
 // dynamic shared memory of eval_float_kernel: the staged input tiles, for

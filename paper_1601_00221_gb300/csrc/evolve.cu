@@ -345,6 +345,12 @@ __device__ __forceinline__ uint4 enc_instruction(const EncScratch& s, int v, int
     else if (k0 == 2 && k1 < 2) form = k1 == 0 ? SF_SX : SF_SC;
     else if (k1 == 2 && k0 < 2) form = k0 == 0 ? SF_XS : SF_CS;
     else form = k0 == 2 ? SF_SS : SF_SSR;
+    if (op == GP_OP_DIV && k1 == 1 && div_fast_operand(p1) && (k0 != 1 || div_fast_operand(p0))) {
+      // a constant divisor inside the fast range: its reciprocal rounded to
+      // nearest even in payload c, as the host encoder writes it
+      form = k0 == 0 ? SF_XI : k0 == 1 ? SF_CI : SF_SI;
+      p2 = __float_as_uint(__frcp_rn(__uint_as_float(p1)));
+    }
     code = (op >= GP_OP_ADD && op <= GP_OP_DIV) ? (uint32_t)sform_code(form, l, (int)(op - GP_OP_ADD))
                                                : (uint32_t)sfx_bin_code(form, l, xbin(op));
   }

@@ -22,7 +22,7 @@ namespace gpisa {
 
 constexpr int R = 8;            // stack levels held per case (GP_STACK_LEVELS)
 constexpr int MAX_INSTR = 1024; // GP_MAX_INSTR
-constexpr uint32_t VERSION = 1;
+constexpr uint32_t VERSION = 2;  // 2: the reciprocal-divisor S-forms
 
 enum Kind : uint32_t { K_SFORM = 1, K_RPN = 2, K_LINEAR = 3, K_BOOL = 4, K_SFORMX = 5, K_RPNX = 6 };
 
@@ -37,10 +37,22 @@ enum SForm : int {
   SF_SS,                            // a = level l, b = level l+1
   SF_SSR,                           // a = level l+1, b = level l
   SF_MOVX, SF_MOVC,                 // a program that is a single terminal
+  // division (op F_DIV only) by a constant b (payload b) whose binary32
+  // reciprocal RN(1/b) the encoder supplies in payload c; the numerator is an
+  // input, stack level l or a constant.  Used when div_fast_operand(b) holds
+  // (and, for SF_CI, div_fast_operand(a)); other constant divisors keep the
+  // SF_XC, SF_SC, SF_CC forms.
+  SF_XI, SF_SI, SF_CI,
   SF_NFORMS
 };
 GPISA_HD constexpr int sform_code(int form, int level, int op) { return (form * R + level) * 4 + op; }
 constexpr int SF_NCODES = SF_NFORMS * R * 4;
+// A binary32 operand (bit pattern) inside the fast range of the division
+// sequences, 2^-50 <= |v| <= 2^50 (finite, normal): within it every
+// intermediate value of the reciprocal-and-remainder sequences is normal.
+GPISA_HD constexpr bool div_fast_operand(uint32_t bits) {
+  return (bits & 0x7fffffffu) >= 0x26800000u && (bits & 0x7fffffffu) <= 0x58800000u;
+}
 
 // ---- extended float S-form (the function sets of Sec. 4.2's float
 // problems).  Its code space starts with the basic S-form's codes, unchanged,
@@ -54,15 +66,15 @@ constexpr int SF_NCODES = SF_NFORMS * R * 4;
 enum XBin : int { XB_GT = 0, XB_LT, XB_EQ, XB_AND, XB_OR, XB_NOPS };
 enum XUn : int { XU_SIN = 0, XU_COS, XU_EXP, XU_LOG, XU_NOPS };
 enum UForm : int { UF_X = 0, UF_C, UF_S, UF_NFORMS };
-constexpr int SFX_BIN_BASE = SF_NFORMS * R * 4;  // 384
+constexpr int SFX_BIN_BASE = SF_NFORMS * R * 4;  // 480
 GPISA_HD constexpr int sfx_bin_code(int form, int level, int op) {
   return SFX_BIN_BASE + (form * R + level) * XB_NOPS + op;  // form SF_XX..SF_SSR
 }
-constexpr int SFX_UN_BASE = SFX_BIN_BASE + (SF_SSR + 1) * R * XB_NOPS;  // 784
+constexpr int SFX_UN_BASE = SFX_BIN_BASE + (SF_SSR + 1) * R * XB_NOPS;  // 880
 GPISA_HD constexpr int sfx_un_code(int uform, int level, int fn) {
   return SFX_UN_BASE + (uform * R + level) * XU_NOPS + fn;
 }
-constexpr int SFX_IF_BASE = SFX_UN_BASE + UF_NFORMS * R * XU_NOPS;  // 880
+constexpr int SFX_IF_BASE = SFX_UN_BASE + UF_NFORMS * R * XU_NOPS;  // 976
 // operand descriptor d in 0..4 (X, C, S0, S1, S2); valid when the stack
 // operands use exactly levels l .. l+m-1, each once
 GPISA_HD constexpr bool xif_desc_valid(int dc, int da, int db) {
@@ -92,7 +104,7 @@ GPISA_HD constexpr int xif_form_desc(int idx) {  // inverse: dc*25 + da*5 + db
 }
 constexpr int SFX_IF_FORMS = 38;
 GPISA_HD constexpr int sfx_if_code(int iform, int level) { return SFX_IF_BASE + iform * R + level; }
-constexpr int SFX_NCODES = SFX_IF_BASE + SFX_IF_FORMS * R;  // 1184
+constexpr int SFX_NCODES = SFX_IF_BASE + SFX_IF_FORMS * R;  // 1280
 
 // ---- float RPN (Sec. 4): push a terminal to level l, or combine levels
 // l and l+1 into level l.

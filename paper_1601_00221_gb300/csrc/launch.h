@@ -52,6 +52,26 @@ cudaError_t launch_floatrx_k8(const FloatArgs& a, bool xreg, int block, int grid
 cudaError_t launch_float_k8_rl4(const FloatArgs& a, bool xreg, int block, int grid, size_t smem,
                                 cudaStream_t s);
 cudaError_t launch_blockgp(const FloatArgs& a, int block, int grid, cudaStream_t s);
+// Several populations in one launch (the basic interpreters, K in {1,2,4,8}):
+// a carries the launch-wide fields (program arrays, fitness measure, tile,
+// program buffer, order, the partials and counters spanning all segments).
+cudaError_t launch_float_seg_k1(const FloatArgs& a, const SegTable& t, bool xreg, int block, int grid,
+                                size_t smem, cudaStream_t s);
+cudaError_t launch_float_seg_k2(const FloatArgs& a, const SegTable& t, bool xreg, int block, int grid,
+                                size_t smem, cudaStream_t s);
+cudaError_t launch_float_seg_k4(const FloatArgs& a, const SegTable& t, bool xreg, int block, int grid,
+                                size_t smem, cudaStream_t s);
+cudaError_t launch_float_seg_k8(const FloatArgs& a, const SegTable& t, bool xreg, int block, int grid,
+                                size_t smem, cudaStream_t s);
+// Register programs with the register file in shared memory
+// (GP_VARIANT_REGISTER_FILE, eval_linear.cu); smem = the program buffer plus
+// linear_rf_bytes(k, block); blocks of at most 256 threads.
+size_t linear_rf_bytes(int k, int block);
+cudaError_t launch_linear_rf(const FloatArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s);
+// one block per segment: zero Boolean hit counts, and with `order` write each
+// segment's programs longest first into order[prog_begin ..]
+cudaError_t launch_segment_prep(const SegTable& t, const int32_t* lengths, int32_t* order, bool zero_hits,
+                                cudaStream_t s);
 // order[0 .. n) = the programs by decreasing instruction count (from their
 // lengths), for FloatArgs::order; one block
 cudaError_t launch_order_by_size(const int32_t* lengths, int32_t n, int32_t* order, cudaStream_t s);
@@ -70,6 +90,9 @@ inline bool order_blocks(int32_t n_progs, int64_t n_cases, int sms) {
 constexpr int kAutoBlocksPerSm = 16;
 // Boolean kernels: K words per thread.
 cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s);
+// Boolean, several populations in one launch (hits zeroed by launch_segment_prep)
+cudaError_t launch_bool_seg(const BoolArgs& a, const SegTable& t, int k, int block, int grid, size_t smem,
+                            cudaStream_t s);
 // Boolean, one program per lane over w <= 4 words (one warp per block).
 cudaError_t launch_bool_lanes(const BoolArgs& a, int w, int grid, size_t smem, cudaStream_t s);
 }  // namespace gpdev

@@ -30,13 +30,14 @@ __device__ __forceinline__ int size_bucket(int32_t len) {
   return n < kBuckets ? n : kBuckets - 1;
 }
 
-__global__ void __launch_bounds__(1024) order_by_size_kernel(const int32_t* __restrict__ lengths, int32_t n,
-                                                             int32_t* __restrict__ order) {
-  __shared__ int start[kPerLane * 32];  // bucket b at start[kBuckets - 1 - b]: longest first
+// order[base + i], i = 0 .. n: the programs base .. base + n by decreasing
+// instruction count (one block)
+__device__ __forceinline__ void order_range(const int32_t* __restrict__ lengths, int32_t base, int32_t n,
+                                            int32_t* __restrict__ order, int* start) {
   const int tid = threadIdx.x;
   for (int i = tid; i < kPerLane * 32; i += blockDim.x) start[i] = 0;
   __syncthreads();
-  for (int p = tid; p < n; p += blockDim.x) atomicAdd(&start[kBuckets - 1 - size_bucket(lengths[p])], 1);
+  for (int p = tid; p < n; p += blockDim.x) atomicAdd(&start[kBuckets - 1 - size_bucket(lengths[base + p])], 1);
   __syncthreads();
   if (tid < 32) {  // exclusive prefix sum over the (reversed) buckets: lane l owns kPerLane of them
     int sum = 0;
@@ -55,13 +56,38 @@ __global__ void __launch_bounds__(1024) order_by_size_kernel(const int32_t* __re
   }
   __syncthreads();
   for (int p = tid; p < n; p += blockDim.x)
-    order[atomicAdd(&start[kBuckets - 1 - size_bucket(lengths[p])], 1)] = p;
+    order[base + atomicAdd(&start[kBuckets - 1 - size_bucket(lengths[base + p])], 1)] = base + p;
+}
+
+__global__ void __launch_bounds__(1024) order_by_size_kernel(const int32_t* __restrict__ lengths, int32_t n,
+                                                             int32_t* __restrict__ order) {
+  __shared__ int start[kPerLane * 32];  // bucket b at start[kBuckets - 1 - b]: longest first
+  order_range(lengths, 0, n, order, start);
+}
+
+// One block per segment of a several-populations launch: zero the segment's
+// hit counts (Boolean, which the kernel accumulates) and, with `order`, take
+// the segment's programs longest first.
+__global__ void __launch_bounds__(1024) segment_prep_kernel(const __grid_constant__ SegTable t,
+                                                            const int32_t* __restrict__ lengths,
+                                                            int32_t* __restrict__ order, int zero_hits) {
+  __shared__ int start[kPerLane * 32];
+  const SegDesc& d = t.s[blockIdx.x];
+  if (zero_hits)
+    for (int i = threadIdx.x; i < d.n_progs; i += blockDim.x) static_cast<unsigned long long*>(d.out)[i] = 0ull;
+  if (order) order_range(lengths, d.prog_begin, d.n_progs, order, start);
 }
 
 }  // namespace
 
 cudaError_t launch_order_by_size(const int32_t* lengths, int32_t n, int32_t* order, cudaStream_t s) {
   order_by_size_kernel<<<1, 1024, 0, s>>>(lengths, n, order);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segment_prep(const SegTable& t, const int32_t* lengths, int32_t* order, bool zero_hits,
+                                cudaStream_t s) {
+  segment_prep_kernel<<<t.n, 1024, 0, s>>>(t, lengths, order, zero_hits ? 1 : 0);
   return cudaGetLastError();
 }
 

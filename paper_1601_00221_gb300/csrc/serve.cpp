@@ -3,14 +3,19 @@
 // One server owns: the device copies of every registered run's cases, a
 // pool of CUDA streams, a FIFO of submitted requests and a worker thread.
 // The worker admits the head of the queue when an in-flight slot and enough
-// of the memory budget are free, merging the consecutive queued requests of
-// the same run into one launch (programs of uneven lengths from several
-// requests run in one kernel launch), copies the programs to the device,
-// launches the evaluation on the next stream, copies the results back and
-// enqueues a host function after them.  That host function (run by the CUDA
-// runtime when the stream reaches it) copies each request's results into the
-// caller's buffer, stamps the completion time and wakes waiters.  No kernel
-// waits on the host and the host never spins on the device.
+// of the memory budget are free, together with the queued requests of other
+// runs of the same kind (float or Boolean) that fit beside it: the programs
+// of all of them -- uneven in number, length, case count and inputs -- run in
+// one kernel launch (gp_eval_segments, one segment per request, each on its
+// own run's resident cases and split by its own run's chunk, so a request's
+// result does not depend on what shares its launch).  A head that does not
+// fit the free memory may be passed by smaller requests that do, a bounded
+// number of times.  The worker copies the programs to the device, launches
+// on the next stream, copies the results back and enqueues a host function
+// after them.  That host function (run by the CUDA runtime when the stream
+// reaches it) copies each request's results into the caller's buffer,
+// stamps the completion time and wakes waiters.  No kernel waits on the host
+// and the host never spins on the device.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -55,6 +60,7 @@ struct Request {
   void* result;  // caller's buffer
   int state = Q_QUEUED;
   int status = GP_OK;
+  int bypassed = 0;  // times a later request was admitted first
   double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
@@ -65,7 +71,8 @@ struct PinnedBuf {
 
 struct Launch {
   std::vector<Request*> reqs;
-  int32_t run;
+  int32_t run;      // the head's run (its kind decides the interpreter)
+  bool segments;    // one segment per request (gp_eval_segments), else one population
   int stream_idx;
   size_t bytes;  // budget charge
   int64_t n_progs;
@@ -80,6 +87,7 @@ struct Launch {
 
 struct gp_server {
   gp_server_opts opts;
+  gp_config launch_cfg[2];  // float, Boolean launches
   int device = 0;
   std::vector<cudaStream_t> streams;
   int next_stream = 0;
@@ -215,7 +223,27 @@ int issue(gp_server* s, Launch* L) {
   const int64_t* dofs = reinterpret_cast<const int64_t*>(din + w_bytes);
   const int32_t* dlen = reinterpret_cast<const int32_t*>(din + w_bytes + o_bytes);
   int rc;
-  if (run.kind == GP_RUN_FLOAT)
+  if (L->segments) {
+    // one segment per request, each on its own run's cases and chunk
+    std::vector<gp_segment> segs;
+    int32_t pbeg = 0;
+    for (Request* r : L->reqs) {
+      const Run& rr = s->runs[r->run];
+      gp_segment g;
+      g.prog_begin = pbeg;
+      g.n_progs = r->n_progs;
+      g.cases = rr.d_cases;
+      g.n_inputs = rr.n_inputs;
+      g.chunk = rr.cfg.chunk_cases;
+      g.n_cases = rr.n_cases;
+      g.targets = rr.d_targets;
+      g.out = static_cast<char*>(L->d_out) + 8 * (size_t)pbeg;
+      segs.push_back(g);
+      pbeg += r->n_progs;
+    }
+    gp_config lc = s->launch_cfg[run.kind == GP_RUN_FLOAT ? 0 : 1];
+    rc = gp_eval_segments(dw, dofs, dlen, segs.data(), (int32_t)segs.size(), run.kind, &lc, (gp_stream_t)st);
+  } else if (run.kind == GP_RUN_FLOAT)
     rc = gp_eval_population_ex(dw, dofs, dlen, (int32_t)L->n_progs, static_cast<const float*>(run.d_cases),
                                run.n_inputs, run.n_cases, static_cast<const float*>(run.d_targets),
                                static_cast<double*>(L->d_out), nullptr, &run.cfg, (gp_stream_t)st);
@@ -243,12 +271,90 @@ void release_launch(gp_server* s, Launch* L) {  // worker thread, lock not held
   delete L;
 }
 
-size_t launch_bytes(const Run& run, int64_t words, int64_t n_progs) {
-  // device buffers of the launch plus the workspace of its partial sums
-  const int64_t per_pass = 8LL * 256;
-  const int64_t chunks = std::max<int64_t>(1, (run.n_units + 32768 - 1) / 32768);
-  return round_up(4 * (size_t)words, 16) + round_up(12 * (size_t)n_progs, 16) + 8 * (size_t)n_progs +
-         16 * (size_t)(n_progs * chunks) + (size_t)per_pass;
+// Device bytes a request charges against the budget when admitted: its
+// share of the launch's buffers (programs, offsets, lengths, results) and of
+// the workspace (partial sums of its run's chunks, counters, block order).
+size_t request_bytes(const Run& run, const Request* r) {
+  const int64_t chunk = std::max<int64_t>(1, run.cfg.chunk_cases);
+  const int64_t chunks = std::max<int64_t>(1, (run.n_units + chunk - 1) / chunk);
+  return round_up(4 * r->words.size(), 16) + round_up(24 * (size_t)r->n_progs, 16) +
+         16 * (size_t)(chunks > 1 ? r->n_progs * chunks : 0) + 4096;
+}
+
+// a run whose requests can share a launch with other runs' requests
+bool segmentable(const gp_server* s, const Run& run) {
+  return run.kind == GP_RUN_BOOL || s->launch_cfg[0].variant == GP_VARIANT_REGISTER;
+}
+
+// Takes `group` out of the queue and issues it as one launch (lock held on
+// entry and exit; released around the CUDA calls).
+void admit(gp_server* s, std::unique_lock<std::mutex>& lk, const std::vector<Request*>& group,
+           size_t bytes, bool segments) {
+  std::deque<Request*> rest;
+  for (Request* r : s->queue)
+    if (std::find(group.begin(), group.end(), r) == group.end() && r->state != Q_CANCELLED) rest.push_back(r);
+  s->queue.swap(rest);
+  int64_t words = 0, progs = 0;
+  for (Request* r : group) {
+    words += (int64_t)r->words.size();
+    progs += r->n_progs;
+  }
+  Launch* L = new Launch();
+  L->reqs = group;
+  L->run = group.front()->run;
+  L->segments = segments;
+  L->srv = s;
+  L->bytes = bytes;
+  L->n_progs = progs;
+  L->stream_idx = s->next_stream;
+  s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
+  const double t = s->now_us();
+  for (Request* r : group) {
+    r->state = Q_RUNNING;
+    r->t_admit = t;
+  }
+  if (s->first_admit < 0) s->first_admit = t;
+  s->inflight += 1;
+  s->mem_in_use += (int64_t)bytes;
+  s->launches += 1;
+  const size_t in_need = round_up(4 * (size_t)words, 16) + round_up(8 * (size_t)progs, 16) +
+                         round_up(4 * (size_t)progs, 16);
+  L->h_in = take_pinned(s, in_need);
+  L->h_out = take_pinned(s, round_up(8 * (size_t)progs, 16));
+  lk.unlock();
+  int rc = issue(s, L);
+  lk.lock();
+  if (rc != GP_OK) fail_launch(s, L, rc);
+}
+
+// How many times a queued head may be passed by smaller requests that fit
+// the free memory while it does not.
+constexpr int kMaxBypass = 8;
+
+// The group a request `lead` heads: `lead`, then the queued requests after
+// it that may share its launch -- the same run's requests (any variant), or
+// with segment launches any run of the same kind -- up to max_merge
+// programs, GP_MAX_SEGMENTS requests and `room` bytes.  Returns its bytes.
+size_t gather(gp_server* s, size_t from, std::vector<Request*>& group, int64_t room, bool* segments) {
+  Request* lead = s->queue[from];
+  const Run& run = s->runs[lead->run];
+  *segments = segmentable(s, run);
+  group.assign(1, lead);
+  size_t bytes = request_bytes(run, lead);
+  int64_t progs = lead->n_progs;
+  for (size_t i = from + 1; i < s->queue.size() && (int)group.size() < GP_MAX_SEGMENTS; ++i) {
+    Request* r = s->queue[i];
+    if (r->state == Q_CANCELLED) continue;
+    const Run& rr = s->runs[r->run];
+    const bool joins = *segments ? (rr.kind == run.kind && segmentable(s, rr)) : r->run == lead->run;
+    if (!joins) continue;
+    const size_t b = request_bytes(rr, r);
+    if (progs + r->n_progs > s->opts.max_merge || (int64_t)(bytes + b) > room) continue;
+    group.push_back(r);
+    bytes += b;
+    progs += r->n_progs;
+  }
+  return bytes;
 }
 
 void worker_main(gp_server* s) {
@@ -265,7 +371,10 @@ void worker_main(gp_server* s) {
       continue;
     }
     if (s->stop && s->queue.empty() && s->inflight == 0) break;
-    // admit the head of the queue (FIFO), merging the same run's requests
+    // Admit the head of the queue with what may share its launch.  When the
+    // head does not fit the free memory (and work is in flight, which will
+    // free some), a later request that fits may go first, at most kMaxBypass
+    // times per head.
     bool admitted = false;
     while (!s->queue.empty() && s->inflight < s->opts.max_inflight) {
       Request* head = s->queue.front();
@@ -273,49 +382,26 @@ void worker_main(gp_server* s) {
         s->queue.pop_front();
         continue;
       }
-      const Run& run = s->runs[head->run];
-      std::vector<Request*> group{head};
-      int64_t words = (int64_t)head->words.size(), progs = head->n_progs;
-      for (size_t i = 1; i < s->queue.size(); ++i) {
+      const int64_t room = s->opts.memory_budget - s->mem_in_use;
+      std::vector<Request*> group;
+      bool segments = false;
+      const size_t need = request_bytes(s->runs[head->run], head);
+      if ((int64_t)need <= room || s->inflight == 0) {
+        const size_t bytes = gather(s, 0, group, std::max<int64_t>(room, (int64_t)need), &segments);
+        admit(s, lk, group, bytes, segments);
+        admitted = true;
+        continue;
+      }
+      if (head->bypassed >= kMaxBypass) break;  // the head waits for memory
+      size_t lead = 0;
+      for (size_t i = 1; i < s->queue.size() && !lead; ++i) {
         Request* r = s->queue[i];
-        if (r->state == Q_CANCELLED) continue;
-        if (r->run != head->run || progs + r->n_progs > s->opts.max_merge) break;
-        group.push_back(r);
-        words += (int64_t)r->words.size();
-        progs += r->n_progs;
+        if (r->state != Q_CANCELLED && (int64_t)request_bytes(s->runs[r->run], r) <= room) lead = i;
       }
-      const size_t bytes = launch_bytes(run, words, progs);
-      if (s->mem_in_use + (int64_t)bytes > s->opts.memory_budget && s->inflight > 0) break;
-      // take the group out of the queue
-      std::deque<Request*> rest;
-      for (Request* r : s->queue)
-        if (std::find(group.begin(), group.end(), r) == group.end() && r->state != Q_CANCELLED) rest.push_back(r);
-      s->queue.swap(rest);
-      Launch* L = new Launch();
-      L->reqs = group;
-      L->run = head->run;
-      L->srv = s;
-      L->bytes = bytes;
-      L->n_progs = progs;
-      L->stream_idx = s->next_stream;
-      s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
-      const double t = s->now_us();
-      for (Request* r : group) {
-        r->state = Q_RUNNING;
-        r->t_admit = t;
-      }
-      if (s->first_admit < 0) s->first_admit = t;
-      s->inflight += 1;
-      s->mem_in_use += (int64_t)bytes;
-      s->launches += 1;
-      const size_t in_need = round_up(4 * (size_t)words, 16) + round_up(8 * (size_t)progs, 16) +
-                             round_up(4 * (size_t)progs, 16);
-      L->h_in = take_pinned(s, in_need);
-      L->h_out = take_pinned(s, round_up(8 * (size_t)progs, 16));
-      lk.unlock();
-      int rc = issue(s, L);
-      lk.lock();
-      if (rc != GP_OK) fail_launch(s, L, rc);
+      if (!lead) break;
+      const size_t bytes = gather(s, lead, group, room, &segments);
+      head->bypassed += 1;
+      admit(s, lk, group, bytes, segments);
       admitted = true;
     }
     if (!admitted) s->cv_work.wait_for(lk, std::chrono::microseconds(200));
@@ -352,6 +438,17 @@ extern "C" int gp_server_create(const gp_server_opts* opts, gp_server** out) {
   if (!o.config.tile_inputs) o.config.tile_inputs = def.tile_inputs;
   o.config.chunk_cases = 0;
   s->opts = o;
+  // Float requests of different runs share a launch when the configuration
+  // is the register variant (the several-populations kernels); Boolean ones
+  // always do, with K = 4 and 64-thread blocks (the staged input tile of
+  // many inputs bounds the blocks per multiprocessor)
+  s->launch_cfg[0] = o.config;
+  s->launch_cfg[1] = o.config;
+  s->launch_cfg[1].variant = GP_VARIANT_REGISTER;
+  s->launch_cfg[1].k = 4;
+  s->launch_cfg[1].block = 64;
+  s->launch_cfg[1].tile_inputs = 0;
+  s->launch_cfg[1].stack_registers = 0;
   cudaError_t e = cudaGetDevice(&s->device);
   if (e != cudaSuccess) return gp_fail(GP_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   for (int i = 0; i < o.n_streams; ++i) {
@@ -397,13 +494,7 @@ extern "C" int gp_server_register_run(gp_server* s, int32_t kind, const void* ca
     return gp_fail(e == cudaErrorMemoryAllocation ? GP_ERR_OOM : GP_ERR_CUDA, "registering run: %s",
                    cudaGetErrorString(e));
   }
-  r.cfg = s->opts.config;
-  if (kind == GP_RUN_BOOL) {
-    r.cfg.variant = GP_VARIANT_REGISTER;
-    // small word counts: a block no wider than the words it covers
-    const int64_t need = (r.n_units + r.cfg.k - 1) / r.cfg.k;
-    r.cfg.block = (int32_t)std::min<int64_t>(r.cfg.block, std::max<int64_t>(32, (need + 31) / 32 * 32));
-  }
+  r.cfg = s->launch_cfg[kind == GP_RUN_FLOAT ? 0 : 1];
   r.cfg.chunk_cases = (int32_t)choose_run_chunk(kind, r.cfg);
   std::lock_guard<std::mutex> lk(s->mu);
   s->runs.push_back(r);
@@ -425,6 +516,7 @@ extern "C" int gp_server_submit(gp_server* s, int32_t run_id, const uint32_t* pr
     max_end = std::max<int64_t>(max_end, offsets[p] + lengths[p]);
   }
   r->words.assign(programs, programs + max_end);
+  r->words.resize((size_t)round_up((size_t)max_end, 4), 0u);  // the next request's words stay 16-byte aligned
   r->offsets.assign(offsets, offsets + n_progs);
   r->lengths.assign(lengths, lengths + n_progs);
   r->n_progs = n_progs;
@@ -432,7 +524,7 @@ extern "C" int gp_server_submit(gp_server* s, int32_t run_id, const uint32_t* pr
   std::unique_lock<std::mutex> lk(s->mu);
   if (run_id < 0 || run_id >= (int32_t)s->runs.size()) return gp_fail(GP_ERR_INVALID_ARG, "unknown run %d", run_id);
   const Run& run = s->runs[run_id];
-  if ((int64_t)launch_bytes(run, max_end, n_progs) > s->opts.memory_budget)
+  if ((int64_t)request_bytes(run, r.get()) > s->opts.memory_budget)
     return gp_fail(GP_ERR_OOM, "request needs more than the server's memory budget");
   if ((int64_t)s->queue.size() >= s->opts.max_queued) return gp_fail(GP_ERR_BUSY, "queue full");
   r->run = run_id;

@@ -48,7 +48,9 @@ import os
 R = 8
 NREG = 8
 # csrc/isa.h
-SF_FORMS = ["XX", "XC", "CX", "CC", "SX", "XS", "SC", "CS", "SS", "SSR", "MOVX", "MOVC"]
+SF_FORMS = ["XX", "XC", "CX", "CC", "SX", "XS", "SC", "CS", "SS", "SSR", "MOVX", "MOVC", "XI", "SI", "CI"]
+# division by a constant with its reciprocal in payload c (numerator X, S or C)
+SF_RECIP = ("XI", "SI", "CI")
 RF_FORMS = ["PUSHX", "PUSHC", "OP", "OPR"]
 BF_FORMS = ["XX", "XS", "SX", "SS", "SSR"]
 BOOL_IF_BASE = len(BF_FORMS) * R * 4
@@ -258,10 +260,89 @@ def emit_pdiv_slow_body(b, K, A, B, Q, tag):
         b(f"mov.b64 {Q[i]}, {{dlo, dhi}};")
 
 
+def emit_pdivi(b, K, A, Nb, Yc, Q, fold=None):
+    """Protected division Q = A / b by a constant b in the fast range whose
+    reciprocal y = RN(1/b) the encoder supplies (the SF_XI / SF_SI / SF_CI
+    forms): the register units A (K == 1: f32; else b64 case pairs), and the
+    registers Nb holding b (one value, or the pair {b, b}), turned into -b
+    here, and Yc holding y (or {y, y}).
+
+    With y correctly rounded the reciprocal needs no seed and no
+    Newton-Raphson step: the quotient q0 = a y, the exact remainder
+    r = a - b q0 (one FMA with -b) and Markstein's correction q1 = q0 + r y
+    (P. Markstein, IBM J. Res. Dev. 34(1), 1990), checked equal to correctly
+    rounded division over every pair of significands.  b lies in the fast
+    range (the encoder's choice), so only the numerators are tested: every
+    |a| in [2^-50, 2^50] (NaN-propagating min and max).  With `fold` the
+    decision is once per warp (a vote into `dall`, the quotients written to
+    Q, fold() redirecting the dispatch to a slow body, which takes its
+    divisor from Nb = -b, when `dall` is false); without it (fold is None)
+    there is no test at all, for a constant numerator the encoder has
+    checked.  Q must not overlap A.  Each case pair runs its three steps in
+    turn, which keeps two temporaries live instead of 2 K."""
+    H = len(A)
+    if K == 1:
+        b(f"neg.f32 {Nb}, {Nb};")
+        if fold is not None:
+            b(f"abs.f32 dt, {A[0]};")
+            b(f"setp.ge.f32 dok, dt, {DIV_LO};")
+            b(f"setp.le.and.f32 dok, dt, {DIV_HI}, dok;")
+        b(f"mul.rn.f32 dQ0, {A[0]}, {Yc};")
+        b(f"fma.rn.f32 dE0, {Nb}, dQ0, {A[0]};")
+        b(f"fma.rn.f32 {Q[0]}, dE0, {Yc}, dQ0;")
+    else:
+        b(f"mul.rn.f32x2 {Nb}, {Nb}, mone2;")  # -b, exact
+        if fold is not None:  # a running min and max, two temporaries
+            for i in range(H):
+                b(f"mov.b64 {{dma0, dma1}}, {A[i]};")
+                b("abs.f32 dma0, dma0;")
+                b("abs.f32 dma1, dma1;")
+                if i == 0:
+                    b("min.NaN.f32 dlo, dma0, dma1;")
+                    b("max.NaN.f32 dhi, dma0, dma1;")
+                else:
+                    b("min.NaN.f32 dlo, dlo, dma0, dma1;")
+                    b("max.NaN.f32 dhi, dhi, dma0, dma1;")
+            b(f"setp.ge.f32 dok, dlo, {DIV_LO};")
+            b(f"setp.le.and.f32 dok, dhi, {DIV_HI}, dok;")
+        for i in range(H):
+            b(f"mul.rn.f32x2 dQ0, {A[i]}, {Yc};")          # q0 = a y
+            b(f"fma.rn.f32x2 dE0, {Nb}, dQ0, {A[i]};")     # r = a - b q0
+            b(f"fma.rn.f32x2 {Q[i]}, dE0, {Yc}, dQ0;")      # q1 = q0 + r y
+    if fold is not None:
+        b("vote.sync.all.pred dall, dok, 0xffffffff;")
+        fold()
+
+
+def emit_pdivi_slow_body(b, K, A, Nb, Q, tag):
+    """The slow path of a folded emit_pdivi as a block of its own (label
+    {tag}SLOW): IEEE division of every element of A by b = -Nb (negated back
+    exactly) and the protection select, written into Q."""
+    b(f"{tag}SLOW:")
+    if K == 1:
+        b(f"neg.f32 dt, {Nb};")
+        b(f"div.rn.f32 {Q[0]}, {A[0]}, dt;")
+        b("setp.eq.f32 dz, dt, 0f00000000;")
+        b(f"selp.f32 {Q[0]}, 0f3F800000, {Q[0]}, dz;")
+        return
+    b(f"mov.b64 {{dt, dt2}}, {Nb};")
+    b("neg.f32 dt, dt;")
+    b("neg.f32 dt2, dt2;")
+    for i in range(len(A)):
+        b(f"mov.b64 {{dlo, dhi}}, {A[i]};")
+        b("div.rn.f32 dlo, dlo, dt;")
+        b("setp.eq.f32 dz, dt, 0f00000000;")
+        b("selp.f32 dlo, 0f3F800000, dlo, dz;")
+        b("div.rn.f32 dhi, dhi, dt2;")
+        b("setp.eq.f32 dz, dt2, 0f00000000;")
+        b("selp.f32 dhi, 0f3F800000, dhi, dz;")
+        b(f"mov.b64 {Q[i]}, {{dlo, dhi}};")
+
+
 def pdiv_regs(K, H):
     ty = "f32" if K == 1 else "b64"
     n = 2 * H
-    return (f".reg .{ty} dY<{H}>, dE<{H}>, dN<{H}>, dQ<{H}>, one2, mone2;\n"
+    return (f".reg .{ty} dY<{H}>, dE<{H}>, dN<{H}>, dQ<{H}>, one2, mone2, cY, cN;\n"
             f".reg .f32 dlo, dhi, dt, dt2, dma<{n}>, dmb<{n}>, dlo_<{n}>, dhi_<{n}>;\n"
             f".reg .pred dok, dz, dall;")
 
@@ -430,36 +511,42 @@ class FloatGen:
     def jump(self):
         self.b("bra.uni LOOP;")
 
-    def table(self, n_codes, table, slow_levels=()):
+    def table(self, n_codes, table, slow_levels=(), slow_levels_i=()):
         """The dispatch table TBL: the codes, then the sentinel (n_codes,
         DONE).  With slow_levels, a second table TBLD for the DIV blocks' own
         dispatch adds one entry per stack level, the folded division's slow
-        body (n_codes + 1 + l).  A separate dispatch site keeps the division
-        operands live only from a DIV block to its slow body: through the
-        common site they would be live across every body of the loop."""
+        body (n_codes + 1 + l), and with slow_levels_i one more per level for
+        the division by a constant with its reciprocal (n_codes + 1 + R + l).
+        A separate dispatch site keeps the division operands live only from a
+        DIV block to its slow body: through the common site they would be
+        live across every body of the loop."""
         self.n_codes = n_codes
         labels = [table.get(c, "CBAD") for c in range(n_codes)] + ["DONE"]
         self.b("TBL: .branchtargets " + ", ".join(labels) + ";")
         if slow_levels:
             labels += [f"D{l}_SLOW" if l in slow_levels else "CBAD" for l in range(R)]
+            if slow_levels_i:
+                labels += [f"DI{l}_SLOW" if l in slow_levels_i else "CBAD" for l in range(R)]
             self.b("TBLD: .branchtargets " + ", ".join(labels) + ";")
 
     def div_jump(self):
         """Dispatch after a folded division (the table with slow bodies)."""
         self.b("brx.idx.uni code, TBLD;")
 
-    def fold_to_slow(self, l):
+    def fold_to_slow(self, l, recip=False):
         """fold() of a level-l division: when not every lane took the fast
-        path, dispatch to the level's slow body instead of the next code."""
+        path, dispatch to the level's slow body instead of the next code
+        (recip: the slow body of the division by a constant with its
+        reciprocal)."""
         def emit():
-            self.b(f"@!dall mov.u32 code, {self.n_codes + 1 + l};")
+            self.b(f"@!dall mov.u32 code, {self.n_codes + 1 + (R if recip else 0) + l};")
         return emit
 
-    def slow_bodies(self, ta, tb, units_of_level, levels):
+    def slow_bodies(self, ta, tb, units_of_level, levels, tag="D"):
         """The slow bodies reload the next code from the instruction just
         fetched (adr was advanced past it) and dispatch it."""
         for l in levels:
-            emit_pdiv_slow_body(self.b, self.K, ta, tb, units_of_level(l), f"D{l}_")
+            emit_pdiv_slow_body(self.b, self.K, ta, tb, units_of_level(l), f"{tag}{l}_")
             self.b("ld.shared.u32 code, [adr+-16];")
             self.jump()
 
@@ -554,10 +641,12 @@ class FloatGen:
                         continue
                     if name in ("MOVX", "MOVC") and (l != 0 or op != 0):
                         continue
+                    if name in SF_RECIP and op != 3:
+                        continue
                     code = sform_code(f, l, op)
                     table[code] = f"C{code}"
                     bodies.append((code, name, l, op))
-        self.table(n_codes, table, slow_levels=range(rl))
+        self.table(n_codes, table, slow_levels=range(rl), slow_levels_i=range(rl))
         self.prologue()
         self.setup_inputs()
         if rl < R:
@@ -577,6 +666,26 @@ class FloatGen:
                 self.fetch()
                 self.copy(L(0), src)
                 self.jump()
+                continue
+            if name in SF_RECIP:
+                ka = name[0]
+                a = opnd(l, sA) if ka == "S" else (self.load_x(xA, "pa") if ka == "X" else self.const("cA", "pa"))
+                cb = self.const("cN" if l < rl else "cB", "pb")
+                if l >= rl:  # a level in shared memory: the general division
+                    self.copy(ta, a)
+                    self.copy(tb, cb)
+                    self.fetch()
+                    b(f"bra.uni DIV{l};")
+                    continue
+                cy = self.const("cY", "pc")
+                if name == "CI":  # both constants in the fast range: no test
+                    self.fetch()
+                    emit_pdivi(b, K, a, cb[0], cy[0], L(l))
+                    self.jump()
+                    continue
+                self.copy(ta, a)
+                self.fetch()
+                b(f"bra.uni DIVI{l};")
                 continue
             if name == "SS":
                 a, c = opnd(l, sA), opnd(l + 1, sB)
@@ -608,7 +717,16 @@ class FloatGen:
             self.spill_store(l, ta)
             self.jump()
             emit_pdiv_slow(b, K, ta, tb, f"D{l}_")
+        for l in range(rl):  # level l <- ta / b by its reciprocal (cN = b, cY)
+            b(f"DIVI{l}:")
+            emit_pdivi(b, K, ta, "cN", "cY", L(l), fold=self.fold_to_slow(l, recip=True))
+            self.div_jump()
         self.slow_bodies(ta, tb, L, range(rl))
+        for l in range(rl):
+            emit_pdivi_slow_body(b, K, ta, "cN", L(l), f"DI{l}_")
+            b("ld.shared.u32 code, [adr+-16];")
+            self.jump()
+
         self.epilogue(L(0))
         return b
 
@@ -819,6 +937,104 @@ class FloatGenLoop(FloatGen):
 
 
 # ---------------------------------------------------------------------------
+# register linear GP with the register file in shared memory
+# ---------------------------------------------------------------------------
+class LinearRFGen:
+    """Register machine r[d] = r[a] op r[b] whose eight registers live in
+    shared memory, this lane's K values of register r at
+    base + r * RSTRIDE + q * 32 * CB (chunk q of CB bytes; the lanes of a warp
+    side by side, so a warp's access to one chunk is conflict-free).  One
+    dispatch per instruction, on the function only (code >> 6: four bodies and
+    the sentinel); the operand and destination registers are addresses
+    computed from the code and the first payload.  No body holds a register
+    of the machine across the dispatch, so the interpreter needs few
+    registers and the kernel many warps.
+    Operands: %0 bad (out, u32); %1 program address, %2 this lane's register
+    file address (shared, u32)."""
+
+    def __init__(self, K):
+        assert K in (1, 2, 4, 8)
+        self.K = K
+        self.H = 1 if K == 1 else K // 2
+        self.cb = min(16, 4 * K)           # bytes of one chunk
+        self.nchunk = 4 * K // self.cb
+        self.rstride = self.nchunk * 32 * self.cb
+        self.b = Block()
+
+    @property
+    def ty(self):
+        return "f32" if self.K == 1 else "b64"
+
+    def load(self, dst, adr):
+        b, K = self.b, self.K
+        for q in range(self.nchunk):
+            off = f"+{q * 32 * self.cb}" if q else ""
+            if K == 1:
+                b(f"ld.shared.f32 {dst[0]}, [{adr}{off}];")
+            elif K == 2:
+                b(f"ld.shared.b64 {dst[0]}, [{adr}{off}];")
+            else:
+                b(f"ld.shared.v2.b64 {{{dst[2 * q]}, {dst[2 * q + 1]}}}, [{adr}{off}];")
+
+    def store(self, adr, src):
+        b, K = self.b, self.K
+        for q in range(self.nchunk):
+            off = f"+{q * 32 * self.cb}" if q else ""
+            if K == 1:
+                b(f"st.shared.f32 [{adr}{off}], {src[0]};")
+            elif K == 2:
+                b(f"st.shared.b64 [{adr}{off}], {src[0]};")
+            else:
+                b(f"st.shared.v2.b64 [{adr}{off}], {{{src[2 * q]}, {src[2 * q + 1]}}};")
+
+    def gen(self):
+        K, H, b = self.K, self.H, self.b
+        A = [f"rA{i}" for i in range(H)]
+        B = [f"rB{i}" for i in range(H)]
+        b("{")
+        b(f".reg .{self.ty} rA<{H}>, rB<{H}>;")
+        b(".reg .b32 code, pa, pb, pc, adr, base, ra, rb, aa, ab, ad, fn;")
+        for ln in pdiv_regs(K, H).split("\n"):
+            b(ln)
+        if K > 1:
+            b("mov.b64 one2, 0x3F8000003F800000;")
+            b("mov.b64 mone2, 0xBF800000BF800000;")
+        b("TBL: .branchtargets OP0, OP1, OP2, OP3, DONE;")
+        b("mov.u32 adr, %1;")
+        b("mov.u32 base, %2;")
+        b("mov.u32 %0, 0;")
+        b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
+        b("add.u32 adr, adr, 16;")
+        b("LOOP:")
+        b("shr.u32 fn, code, 6;")
+        b("brx.idx.uni fn, TBL;")
+        for op in range(4):
+            b(f"OP{op}:")
+            b("bfe.u32 ra, code, 3, 3;")
+            b("and.b32 rb, code, 7;")
+            b(f"mad.lo.u32 aa, ra, {self.rstride}, base;")
+            b(f"mad.lo.u32 ab, rb, {self.rstride}, base;")
+            b(f"mad.lo.u32 ad, pa, {self.rstride}, base;")
+            self.load(A, "aa")
+            self.load(B, "ab")
+            b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
+            b("add.u32 adr, adr, 16;")
+            if op == 3:
+                emit_pdiv(b, K, A, B, A, "D")
+                self.store("ad", A)
+                b("bra.uni LOOP;")
+                emit_pdiv_slow(b, K, A, B, "D")
+            else:
+                for i in range(H):
+                    b(f"{F32[op] if K == 1 else F32X2[op]} {A[i]}, {A[i]}, {B[i]};")
+                self.store("ad", A)
+                b("bra.uni LOOP;")
+        b("DONE:")
+        b("}")
+        return b
+
+
+# ---------------------------------------------------------------------------
 # extended float S-form (the full function sets of Sec. 4.2)
 # ---------------------------------------------------------------------------
 SFX_BIN_BASE = len(SF_FORMS) * R * 4              # 384
@@ -979,13 +1195,16 @@ class FloatGenX(FloatGen):
         xC = [f"xC{i}" for i in range(H)]
         T = self.t()
         table, bodies = {}, []
-        # basic S-form codes (same numbers as the basic interpreter)
+        # basic S-form codes (same numbers as the basic interpreter; the
+        # divisions by a constant with its reciprocal take the general path)
         for f, name in enumerate(SF_FORMS):
             for l in range(R):
                 for op in range(4):
                     if name in ("SS", "SSR") and l + 1 >= R:
                         continue
                     if name in ("MOVX", "MOVC") and (l != 0 or op != 0):
+                        continue
+                    if name in SF_RECIP and op != 3:
                         continue
                     code = sform_code(f, l, op)
                     table[code] = f"C{code}"
@@ -1387,6 +1606,48 @@ def pdiv_macro(K, fold=True):
     return b
 
 
+def pdivi_macro(K, test=True):
+    """Standalone division by a constant with its reciprocal (exactly the
+    interpreters' SF_XI / SF_SI sequence, or with test=False the SF_CI one),
+    for the division checker: K == 1 operands %0 = q, %1 = a, %2 = b,
+    %3 = RN(1/b) (f32); K == 4 operands %0, %1 = q pairs, %2, %3 = a pairs
+    (b64), %4 = b, %5 = RN(1/b) (f32).  With the test the slow path is
+    decided once per warp, as in the interpreters."""
+    b = Block()
+    H = 1 if K == 1 else K // 2
+    b("{")
+    for ln in pdiv_regs(K, H).split("\n"):
+        b(ln)
+    ty = "f32" if K == 1 else "b64"
+    b(f".reg .{ty} qa<{H}>, qq<{H}>;")
+    if K > 1:
+        b("mov.b64 one2, 0x3F8000003F800000;")
+        b("mov.b64 mone2, 0xBF800000BF800000;")
+    for i in range(H):
+        b(f"mov.{ty} qa{i}, %{H + i};")
+    if K == 1:
+        b("mov.f32 cN, %2;")
+        b("mov.f32 cY, %3;")
+    else:
+        b(f"mov.b64 cN, {{%{2 * H}, %{2 * H}}};")
+        b(f"mov.b64 cY, {{%{2 * H + 1}, %{2 * H + 1}}};")
+    qa = [f"qa{i}" for i in range(H)]
+    qq = [f"qq{i}" for i in range(H)]
+    if test:
+        emit_pdivi(b, K, qa, "cN", "cY", qq, fold=lambda: b("@!dall bra.uni PSLOW;"))
+    else:
+        emit_pdivi(b, K, qa, "cN", "cY", qq)
+    b("PRET:")
+    for i in range(H):
+        b(f"mov.{ty} %{i}, qq{i};")
+    b("bra.uni PEND;")
+    emit_pdivi_slow_body(b, K, qa, "cN", qq, "P")
+    b("bra.uni PRET;")
+    b("PEND:")
+    b("}")
+    return b
+
+
 def generate() -> str:
     parts = ["// gen_interp.h -- generated by paper_1601_00221_gb300/gen_interp.py; do not edit.\n",
              "#pragma once\n"]
@@ -1395,6 +1656,13 @@ def generate() -> str:
     parts.append(pdiv_macro(1, False).macro("GP_PTX_PDIV_LANE_K1", "protected division, one value, lane branch"))
     parts.append(pdiv_macro(4, False).macro("GP_PTX_PDIV_LANE_K4",
                                             "protected division, two packed pairs, lane branch"))
+    parts.append(pdivi_macro(1).macro("GP_PTX_PDIVI_K1", "division by a constant with its reciprocal, one value"))
+    parts.append(pdivi_macro(4).macro("GP_PTX_PDIVI_K4",
+                                      "division by a constant with its reciprocal, two packed pairs"))
+    parts.append(pdivi_macro(1, False).macro("GP_PTX_PDIVI_NT_K1",
+                                             "division of a constant by a constant with its reciprocal, one value"))
+    parts.append(pdivi_macro(4, False).macro("GP_PTX_PDIVI_NT_K4",
+                                             "division of a constant by a constant with its reciprocal, two pairs"))
     for K in (1, 2, 4, 8):
         for xm in ("reg", "smem"):
             X = xm.upper()
@@ -1426,6 +1694,8 @@ def generate() -> str:
                 f"GP_PTX_RPNX_K{K}_{X}", f"extended RPN interpreter, K={K}, inputs in {xm}"))
             outs, ins = g.operand_macros()
             parts.append(f"#define GP_SFX_OUT_K{K}_{X} {outs}\n#define GP_SFX_IN_K{K}_{X} {ins}\n")
+        parts.append(LinearRFGen(K).gen().macro(
+            f"GP_PTX_LINEAR_RF_K{K}", f"register linear-GP interpreter, registers in shared memory, K={K}"))
         parts.append(BoolGen(K).gen().macro(f"GP_PTX_BOOL_K{K}", f"Boolean interpreter, K={K} words"))
     return "".join(parts)
 

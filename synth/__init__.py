@@ -104,13 +104,39 @@ class _TreeGen:
         return n
 
 
+class _Uniforms:
+    """U[0, 1) draws taken from blocks of a numpy generator (a few hundred
+    nanoseconds per draw instead of a generator call per draw)."""
+
+    def __init__(self, rng, block: int = 1 << 16):
+        self.rng, self.block = rng, block
+        self.buf, self.i = rng.random(block), 0
+
+    def random(self) -> float:
+        if self.i == self.block:
+            self.buf, self.i = self.rng.random(self.block), 0
+        v = self.buf[self.i]
+        self.i += 1
+        return float(v)
+
+    def integers(self, lo: int, hi: int) -> int:
+        return lo + min(int(self.random() * (hi - lo)), hi - lo - 1)
+
+    def uniform(self, lo: float, hi: float) -> float:
+        return lo + (hi - lo) * self.random()
+
+
 def ramped_half_and_half(seed: int, n: int, depth_lo: int, depth_hi: int, max_nodes: int,
                          funcs: Sequence[int] = FLOAT_FUNCS, n_inputs: int = 1,
                          p_const: float = 0.5, const_lo: float = -1.0, const_hi: float = 1.0,
-                         full_fallback_to_grow: bool = False) -> List[np.ndarray]:
-    """n prefix trees; program i uses depth depth_lo + (i // 2) % span, full if i is even."""
+                         full_fallback_to_grow: bool = False, min_nodes: int = 1,
+                         block_draws: bool = False) -> List[np.ndarray]:
+    """n prefix trees; program i uses depth depth_lo + (i // 2) % span, full if i is even;
+    trees outside [min_nodes, max_nodes] nodes are drawn again.  block_draws:
+    the same distribution from blocks of uniform draws (much faster; other
+    trees than the default for the same seed)."""
     rng = np.random.default_rng(seed)
-    g = _TreeGen(rng, funcs, n_inputs, p_const, const_lo, const_hi)
+    g = _TreeGen(_Uniforms(rng) if block_draws else rng, funcs, n_inputs, p_const, const_lo, const_hi)
     span = depth_hi - depth_lo + 1
     progs = []
     for i in range(n):
@@ -120,7 +146,7 @@ def ramped_half_and_half(seed: int, n: int, depth_lo: int, depth_hi: int, max_no
             out: List[int] = []
             use_full = full and not (full_fallback_to_grow and attempt > 0)
             nodes = g.node(out, 1, d, use_full)
-            if nodes <= max_nodes:
+            if min_nodes <= nodes <= max_nodes:
                 break
         else:  # pragma: no cover - the caps used by the configs always fit
             raise RuntimeError("could not draw a tree under the node cap")
@@ -390,15 +416,41 @@ class ServingRun:
         return int(self.pop.nodes.sum()) * self.n_cases
 
 
-def serving_runs(seed: int = 5, n_runs: int = 64, pop_lo: int = 128, pop_hi: int = 2048,
-                 max_depth: int = 7, max_nodes: int = 255, log2_cases_lo: int = 10,
-                 log2_cases_hi: int = 20, p_bool: float = 0.25) -> List[ServingRun]:
+def _serving_run(spec) -> ServingRun:
+    """One serving run from its drawn parameters (a worker process may build it)."""
+    kind, n_progs, s, lg, k, n_inputs, max_depth, max_nodes, min_nodes = spec
+    if kind in ("mux", "parity"):
+        funcs = BOOL_FUNCS + ((IF,) if kind == "mux" else ())
+        progs = ramped_half_and_half(s, n_progs, 4, max_depth, max_nodes, funcs=funcs,
+                                     n_inputs=k, p_const=0.0, full_fallback_to_grow=True,
+                                     min_nodes=min_nodes, block_draws=True)
+        target = even_parity_target(k) if kind == "parity" else mux_target(k)
+        return ServingRun("bool", pack(progs), bool_case_bits(k), target, 1 << k)
+    n_cases = 1 << lg
+    progs = ramped_half_and_half(s, n_progs, 4, max_depth, max_nodes, n_inputs=n_inputs,
+                                 min_nodes=min_nodes, block_draws=True)
+    if n_inputs == 1:
+        x = uniform_cases(s + 1, 1, n_cases)
+        y = quartic_target(x[0])
+    else:
+        x = normal_cases(s + 1, 8, n_cases)
+        y = poly3_target(x, s + 2)
+    return ServingRun("float", pack(progs), x, y, n_cases)
+
+
+def serving_runs(seed: int = 5, n_runs: int = 64, pop_lo: int = 128, pop_hi: int = 8192,
+                 max_depth: int = 9, max_nodes: int = 512, log2_cases_lo: int = 10,
+                 log2_cases_hi: int = 20, p_bool: float = 0.25, min_nodes: int = 8,
+                 workers: int = 0) -> List[ServingRun]:
     """Independent runs of mixed kinds: float regression with 1 input (quartic
     target) or 8 inputs (random cubic target), and Boolean k-multiplexer or
-    even-k-parity; population sizes U{pop_lo..pop_hi}; case counts 2^U{lo..hi}
-    (Boolean: k inputs, 2^k cases with k in the same range)."""
+    even-k-parity; population sizes U{pop_lo..pop_hi}; trees ramped
+    half-and-half of depth 4..max_depth with min_nodes..max_nodes nodes; case
+    counts 2^U{lo..hi} (Boolean: k inputs, 2^k cases with k in the same
+    range).  workers > 1 builds the runs in that many spawned processes (the
+    same runs as one process builds)."""
     rng = np.random.default_rng(seed)
-    runs = []
+    specs = []
     for r in range(n_runs):
         n_progs = int(rng.integers(pop_lo, pop_hi + 1))
         s = int(rng.integers(0, 2**31 - 1))
@@ -408,23 +460,19 @@ def serving_runs(seed: int = 5, n_runs: int = 64, pop_lo: int = 128, pop_hi: int
             k = lg
             if kind == "mux":  # nearest multiplexer size a + 2^a within the range
                 k = min((a + (1 << a) for a in range(2, 5)), key=lambda v: abs(v - lg))
-            funcs = BOOL_FUNCS + ((IF,) if kind == "mux" else ())
-            progs = ramped_half_and_half(s, n_progs, 2, max_depth, max_nodes, funcs=funcs,
-                                         n_inputs=k, p_const=0.0, full_fallback_to_grow=True)
-            target = even_parity_target(k) if kind == "parity" else mux_target(k)
-            runs.append(ServingRun("bool", pack(progs), bool_case_bits(k), target, 1 << k))
+            specs.append((kind, n_progs, s, lg, k, k, max_depth, max_nodes, min_nodes))
         else:
             n_inputs = 1 if rng.random() < 0.5 else 8
-            n_cases = 1 << lg
-            progs = ramped_half_and_half(s, n_progs, 2, max_depth, max_nodes, n_inputs=n_inputs)
-            if n_inputs == 1:
-                x = uniform_cases(s + 1, 1, n_cases)
-                y = quartic_target(x[0])
-            else:
-                x = normal_cases(s + 1, 8, n_cases)
-                y = poly3_target(x, s + 2)
-            runs.append(ServingRun("float", pack(progs), x, y, n_cases))
-    return runs
+            specs.append(("float", n_progs, s, lg, 0, n_inputs, max_depth, max_nodes, min_nodes))
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        # largest first, so that the pool's last tasks are short
+        by_size = sorted(range(n_runs), key=lambda i: -specs[i][1])
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            built = dict(zip(by_size, ex.map(_serving_run, [specs[i] for i in by_size])))
+        return [built[i] for i in range(n_runs)]
+    return [_serving_run(sp) for sp in specs]
 
 
 # --------------------------------------------------------------------------

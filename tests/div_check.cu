@@ -1,9 +1,11 @@
 // div_check.cu -- checks the library's protected division (the generated PTX
 // sequences GP_PTX_PDIV_K4 / GP_PTX_PDIV_K1 with the slow path decided per
 // warp, as the basic interpreters run it, and GP_PTX_PDIV_LANE_K4 /
-// GP_PTX_PDIV_LANE_K1 with a per-lane branch, as the extended ones do)
-// against CUDA's correctly rounded division: q == (b == 0 ? 1 : a / b) bit
-// for bit, any NaN equal to any NaN.  Every lane of a warp runs the same
+// GP_PTX_PDIV_LANE_K1 with a per-lane branch, as the extended ones do; and
+// the division by a constant with its reciprocal, GP_PTX_PDIVI_K4 / _K1
+// with the numerator test and GP_PTX_PDIVI_NT_K4 / _K1 without it, wherever
+// the encoder would choose them) against CUDA's correctly rounded division:
+// q == (b == 0 ? 1 : a / b) bit for bit, any NaN equal to any NaN.  Every lane of a warp runs the same
 // sequence of calls, as the warp decision requires.  Test tool, built by
 // tests/test_division.py.
 //
@@ -71,7 +73,64 @@ __device__ __forceinline__ float pdiv1(float a, float b) {
   return q;
 }
 
+// the division by a constant with its reciprocal (SF_XI / SF_SI: the
+// numerators tested, one decision per warp; NT: SF_CI, no test): every lane
+// of the warp calls these, with its own b; the results count only where the
+// encoder would choose these forms (b, and for NT also a, in the fast range)
+__device__ __forceinline__ void pdivi4(const float (&a)[4], float b, float (&q)[4], bool test) {
+  unsigned long long a0, a1, q0, q1;
+  float2 t;
+  const float y = __frcp_rn(b);
+  t = make_float2(a[0], a[1]); a0 = *reinterpret_cast<unsigned long long*>(&t);
+  t = make_float2(a[2], a[3]); a1 = *reinterpret_cast<unsigned long long*>(&t);
+  if (test)
+    asm volatile(GP_PTX_PDIVI_K4 : "=l"(q0), "=l"(q1) : "l"(a0), "l"(a1), "f"(b), "f"(y));
+  else
+    asm volatile(GP_PTX_PDIVI_NT_K4 : "=l"(q0), "=l"(q1) : "l"(a0), "l"(a1), "f"(b), "f"(y));
+  t = *reinterpret_cast<float2*>(&q0); q[0] = t.x; q[1] = t.y;
+  t = *reinterpret_cast<float2*>(&q1); q[2] = t.x; q[3] = t.y;
+}
+
+__device__ __forceinline__ float pdivi1(float a, float b, bool test) {
+  float q;
+  const float y = __frcp_rn(b);
+  if (test)
+    asm volatile(GP_PTX_PDIVI_K1 : "=f"(q) : "f"(a), "f"(b), "f"(y));
+  else
+    asm volatile(GP_PTX_PDIVI_NT_K1 : "=f"(q) : "f"(a), "f"(b), "f"(y));
+  return q;
+}
+
+__device__ __forceinline__ bool fast_operand(float v) {
+  const uint32_t m = __float_as_uint(v) & 0x7fffffffu;
+  return m >= 0x26800000u && m <= 0x58800000u;
+}
+
+// a[j] / b[0] for j = 0..3 through the pair forms, a[j] / b[j] through the
+// scalar ones
+__device__ __forceinline__ void check4i(const float (&a)[4], const float (&b)[4]) {
+  float q[4], n[4];
+  pdivi4(a, b[0], q, true);
+  pdivi4(a, b[0], n, false);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float s = pdivi1(a[j], b[j], true);
+    const float u = pdivi1(a[j], b[j], false);
+    if (fast_operand(b[0])) {
+      const float r = ref_pdiv(a[j], b[0]);
+      if (!same(q[j], r)) report(a[j], b[0], q[j]);
+      if (fast_operand(a[j]) && !same(n[j], r)) report(a[j], b[0], n[j]);
+    }
+    if (fast_operand(b[j])) {
+      const float r = ref_pdiv(a[j], b[j]);
+      if (!same(s, r)) report(a[j], b[j], s);
+      if (fast_operand(a[j]) && !same(u, r)) report(a[j], b[j], u);
+    }
+  }
+}
+
 __device__ __forceinline__ void check4(const float (&a)[4], const float (&b)[4]) {
+  check4i(a, b);
   float q[4], p[4];
   pdiv4<false>(a, b, q);
   pdiv4<true>(a, b, p);

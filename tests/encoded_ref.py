@@ -9,7 +9,10 @@ import numpy as np
 
 R = 8
 F_NAMES = "+-*/"
-SF_FORMS = ["XX", "XC", "CX", "CC", "SX", "XS", "SC", "CS", "SS", "SSR", "MOVX", "MOVC"]
+SF_FORMS = ["XX", "XC", "CX", "CC", "SX", "XS", "SC", "CS", "SS", "SSR", "MOVX", "MOVC", "XI", "SI", "CI"]
+# division by a constant b (payload b) with RN(1/b) in payload c; numerator X, S or C
+SF_RECIP = ("XI", "SI", "CI")
+DIV_LO, DIV_HI = 0x26800000, 0x58800000  # 2^-50, 2^50 as binary32 bit patterns
 RF_FORMS = ["PUSHX", "PUSHC", "OP", "OPR"]
 BF_FORMS = ["XX", "XS", "SX", "SS", "SSR"]
 BOOL_IF_BASE = 5 * R * 4
@@ -172,7 +175,14 @@ def run_float(words, x):
                 S[0] = x[pa].copy(); continue
             if name == "MOVC":
                 S[0] = C(pa); continue
-            src = {"X": None, "C": None}
+            if name in SF_RECIP:
+                # the layout's promise: a divisor in [2^-50, 2^50] and its
+                # reciprocal rounded to nearest (numpy's IEEE binary32 division)
+                assert op == 3 and DIV_LO <= (pb & 0x7FFFFFFF) <= DIV_HI, (code, pb)
+                assert pc == int(np.array(np.float32(1) / _f(pb), np.float32).view(np.uint32)), (pb, pc)
+                a = S[lvl] if name[0] == "S" else (X(pa) if name[0] == "X" else C(pa))
+                S[lvl] = _apply(3, a, C(pb))
+                continue
             if name in ("SS", "SSR"):
                 a, b = (S[lvl], S[lvl + 1]) if name == "SS" else (S[lvl + 1], S[lvl])
             else:
@@ -226,6 +236,6 @@ def render_sform(words):
     for code, _, _, _ in instrs(words):
         op, form = code & 3, (code >> 2) // R
         name = SF_FORMS[form]
-        ops = {"SSR": "SS"}.get(name, name)
+        ops = {"SSR": "SS", "XI": "XC", "SI": "SC", "CI": "CC"}.get(name, name)
         out.append(f"{F_NAMES[op]}({ops})")
     return " ".join(out)

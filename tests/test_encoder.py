@@ -10,6 +10,7 @@ import synth
 import paper_1601_00221_gb300 as gp
 from synth import ADD, SUB, MUL, DIV, VAR, CONST, tok, const_tokens
 import encoded_ref as ref
+from div_trees import constant_divisor_trees, edge_cases, bitsf32
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sec5_worked_example.txt")
 
@@ -327,3 +328,35 @@ def test_if_forms_cover_every_operand_mix():
             seen.add(int(words[4 + 4 * (info["n_instr"] - 1)]))
             assert same_bits(ref.run_float(words, x), oracle.fset_outputs(p, x)), (combo, order)
     assert len(seen) >= 20
+
+
+
+def _f32bits(v):
+    return int(np.array(v, np.float32).view(np.uint32))
+
+
+@pytest.mark.parametrize("order", [gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH])
+def test_constant_divisors_take_the_reciprocal_forms_inside_the_fast_range(order):
+    """A division by a constant in [2^-50, 2^50] (and, for a constant
+    numerator, a numerator in that range too) is encoded with the divisor's
+    reciprocal, rounded to nearest, in payload c; any other constant divisor
+    keeps the plain forms.  Every program still evaluates as the oracle's."""
+    x = edge_cases(96, 67)
+    recip_seen = plain_seen = 0
+    for p in constant_divisor_trees():
+        words, info = gp.encode_tree(p, gp.KIND_SFORM, order)
+        (code, pa, pb, pc), = ref.instrs(words)[-1:]
+        name = ref.SF_FORMS[(code >> 2) // ref.R]
+        b = int(pb)
+        in_range = ref.DIV_LO <= (b & 0x7FFFFFFF) <= ref.DIV_HI
+        numer_const = name[0] == "C"
+        want = in_range and (not numer_const or ref.DIV_LO <= (int(pa) & 0x7FFFFFFF) <= ref.DIV_HI)
+        assert (name in ref.SF_RECIP) == want, (name, hex(b), hex(int(pa)))
+        if want:
+            recip_seen += 1
+            assert pc == _f32bits(np.float32(1) / np.float32(bitsf32(b)))
+        else:
+            plain_seen += 1
+            assert pc == 0
+        assert same_bits(ref.run_float(words, x), oracle.tree_outputs(p, x))
+    assert recip_seen >= 20 and plain_seen >= 20

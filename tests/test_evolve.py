@@ -49,6 +49,22 @@ def test_device_encoder_matches_host(order, funcs, n_inputs):
 
 
 @pytest.mark.parametrize("order", [gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH])
+def test_device_encoder_constant_divisors(order):
+    """Divisions by constants at and beyond the edges of the fast range: the
+    device encoder chooses the reciprocal forms exactly where the host one
+    does and writes the same reciprocal words."""
+    from div_trees import constant_divisor_trees
+    pop = synth.pack(constant_divisor_trees(1) + constant_divisor_trees(3))
+    host = gp.encode_population(pop.words, pop.offsets, pop.lengths, gp.KIND_SFORM, order)
+    out, off, ln = device_encode(pop, order)
+    assert np.array_equal(ln, host.lengths)
+    for p in range(pop.n):
+        a = host.words[host.offsets[p]: host.offsets[p] + host.lengths[p]]
+        b = out[off[p]: off[p] + ln[p]]
+        assert np.array_equal(a, b), p
+
+
+@pytest.mark.parametrize("order", [gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH])
 def test_device_encoder_at_the_node_limit(order):
     """Trees of exactly GP_DEVICE_ENCODE_MAX_NODES = 256 nodes: a chain of 255
     unary functions (255 instructions) and 85 nested IFs whose nested operand

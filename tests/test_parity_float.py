@@ -257,6 +257,41 @@ def test_register_linear_gp(k):
     assert_fitness(f, fit, "linear fitness")
 
 
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("n_inputs,n_cases", [(8, 4099), (3, 1000), (11, 2052), (8, 7)])
+def test_register_file_in_shared_memory(k, n_inputs, n_cases):
+    """The register-file variant (registers in shared memory, one jump per
+    instruction): per-case outputs bit for bit and fitness against the
+    oracle, with fewer inputs than registers (the rest start at 0), more
+    (only the first eight are registers), ragged and unaligned case counts
+    (the scalar staging path) and several chunks per program."""
+    pop = synth.linear_programs(80 + n_inputs, 96, 1, 128)
+    x = synth.normal_cases(81, n_inputs, n_cases)
+    x[:, :2] = 0.0
+    y = synth.normal_cases(82, 1, n_cases)[0]
+    enc = gp.encode_linear_population(pop.instr, pop.offsets, pop.lengths)
+    P, O, L = upload(enc)
+    exp = np.stack([oracle.linear_outputs(pop.program(p), x) for p in range(pop.n)])
+    fit = oracle.linear_population_fitness(pop.instr, pop.offsets, pop.lengths, x, y)
+    for block, chunk in ((64, 0), (256, 0), (128, 128 * k)):
+        cfg = gp.Config(gp.VARIANT_REGISTER_FILE, k, block, chunk)
+        out = gp.eval_outputs(P, O, L, dev(x), config=cfg).cpu().numpy()
+        assert_bits(out, exp, f"register file k={k} block={block}")
+        f = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy()
+        assert_fitness(f, fit, f"register file k={k} block={block} chunk={chunk}")
+    assert gp.last_error() == 0
+
+
+def test_register_file_rejects_tree_programs():
+    w = synth.regression_small(seed=83, n_progs=8, n_cases=100)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
+    P, O, L = upload(enc)
+    f = gp.eval_population(P, O, L, dev(w.cases), dev(w.targets),
+                           config=gp.Config(gp.VARIANT_REGISTER_FILE, 4, 64, 0)).cpu().numpy()
+    assert np.all(np.isnan(f))
+    assert gp.last_error() == 2
+
+
 def test_mixed_kinds_in_one_launch():
     w = synth.regression_small(seed=78, n_progs=30, n_cases=515)
     sf = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM)
@@ -358,3 +393,57 @@ def test_pass_loop_inside_the_interpreter_changes_nothing(fitness, chunk):
     per_pass = gp.eval_population(P, O, L, X, Y, outputs=outs, config=cfg).cpu().numpy()
     assert np.array_equal(loop.view(np.uint64), per_pass.view(np.uint64))
     assert np.isfinite(loop).sum() > w.pop.n // 2
+
+
+# ---------------------------------------------------------------------------
+# divisions by constants: the reciprocal forms (divisor in the fast range,
+# one remainder correction) and the plain forms beside them, with numerators
+# that send some warps to the slow path
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("n_inputs", [1, 2])
+@pytest.mark.parametrize("order", [gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH])
+def test_constant_divisors_bit_exact(k, n_inputs, order):
+    from div_trees import constant_divisor_trees, edge_cases
+    pop = synth.pack(constant_divisor_trees(n_inputs))
+    x = edge_cases(3001, 76, n_inputs)
+    y = synth.uniform_cases(77, 1, 3001)[0]
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths, gp.KIND_SFORM, order)
+    P, O, L = upload(enc)
+    ref = oracle_outputs(pop, x)
+    exp = oracle.population_fitness(pop.words, pop.offsets, pop.lengths, x, y)
+    for block in (32, 128):
+        cfg = gp.Config(gp.VARIANT_REGISTER, k, block, 0)
+        out = gp.eval_outputs(P, O, L, dev(x), config=cfg).cpu().numpy()
+        assert_bits(out, ref, f"k={k} inputs={n_inputs} block={block}")
+        f = gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy()
+        assert_fitness(f, exp, f"k={k} inputs={n_inputs} block={block}")
+    # the interpreters that take the plain division for these forms: the
+    # extended one and the one with levels 4..7 in shared memory
+    out = gp.eval_outputs(P, O, L, dev(x), config=gp.Config(gp.VARIANT_EXTENDED, k, 64, 0)).cpu().numpy()
+    assert_bits(out, ref, f"extended k={k}")
+    if k == 8:
+        out = gp.eval_outputs(P, O, L, dev(x), config=gp.Config(gp.VARIANT_REGISTER, 8, 64, 0, 0, 0, 4)).cpu().numpy()
+        assert_bits(out, ref, "levels 4..7 in shared memory")
+    assert gp.last_error() == 0
+
+
+def test_reciprocal_payload_is_checked_when_staged():
+    """An S-form division by a constant whose payload c is not the divisor's
+    reciprocal rounded to nearest is malformed (NaN fitness, status
+    GP_ERR_PROGRAM): the interpreter never runs with a wrong reciprocal."""
+    import torch
+    from div_trees import constant_divisor_trees
+    trees = constant_divisor_trees()[:2]  # x / 2^-50 and (x*x) / 2^-50: reciprocal forms
+    pop = synth.pack(trees)
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    words = enc.words.copy()
+    last = enc.offsets[1] + enc.lengths[1] - 1   # payload c of program 1's last instruction
+    assert words[last] != 0
+    words[last] ^= 1
+    P = torch.from_numpy(words.view(np.int32)).cuda()
+    O, L = dev(enc.offsets), dev(enc.lengths)
+    x = synth.uniform_cases(78, 1, 512)
+    f = gp.eval_population(P, O, L, dev(x), dev(np.zeros(512, np.float32))).cpu().numpy()
+    assert not np.isnan(f[0]) and np.isnan(f[1])
+    assert gp.last_error() == 2

@@ -179,3 +179,67 @@ def test_extended_functions_and_fitness_measures_are_served():
             exp = oracle.fset_population_fitness(w.pop.words, w.pop.offsets, w.pop.lengths, w.cases,
                                                  w.targets, oracle.FIT_CLASS)
             assert np.array_equal(out, exp)
+
+
+@pytest.fixture(scope="module")
+def blocker():
+    """A request that keeps the GPU busy for tens of milliseconds (4096 trees
+    x 2^20 cases), so that later submissions queue up behind it."""
+    return float_run(120, 4096, 1 << 20)
+
+
+def test_requests_of_different_runs_share_one_launch(runs, blocker):
+    """While one long request occupies the only in-flight slot, requests of
+    six other runs queue up; they are then admitted together -- the float
+    runs' requests (one and eight inputs, different case counts) in one
+    launch, the Boolean runs' in another -- and every result is bit-identical
+    to the same request served alone, and equal to the oracle's within the
+    tolerance (exact hits)."""
+    alone = []
+    with gp.Server(n_streams=1, max_inflight=1) as srv:
+        ids = [register(srv, r) for r in runs]
+        for i, r in zip(ids, runs):
+            alone.append(srv.wait(srv.submit(i, r["enc"], kind=r["kind"]))[0].copy())
+    with gp.Server(n_streams=1, max_inflight=1) as srv:
+        ids = [register(srv, r) for r in runs]
+        bid = register(srv, blocker)
+        qb = srv.submit(bid, blocker["enc"])
+        qs = [srv.submit(i, r["enc"], kind=r["kind"]) for i, r in zip(ids, runs)]
+        srv.wait(qb)
+        infos = []
+        for q, r, a in zip(qs, runs, alone):
+            out, info = srv.wait(q)
+            infos.append(info)
+            if r["kind"] == gp.RUN_FLOAT:
+                assert np.array_equal(out.view(np.uint64), a.view(np.uint64))
+                assert_fitness(out, oracle_result(r), "mixed launch")
+            else:
+                assert np.array_equal(out, a)
+                assert np.array_equal(out, oracle_result(r))
+        st = srv.stats()
+    # requests admitted together carry the same admission time
+    groups = {}
+    for j, info in enumerate(infos):
+        groups.setdefault(info.t_admit_us, []).append(j)
+    biggest = max(groups.values(), key=len)
+    assert len({runs[j]["kind"] for j in biggest}) == 1
+    assert len(biggest) >= 3, groups
+    assert st["launches"] <= 3 and st["completed"] == len(runs) + 1
+
+
+def test_a_large_head_is_passed_by_requests_that_fit(runs, blocker):
+    """Under a memory budget that the first queued request cannot get while
+    another launch holds memory, smaller requests behind it are admitted
+    first (a bounded number of times), and every result is still correct."""
+    small = runs[0]
+    with gp.Server(n_streams=2, max_inflight=2, memory_budget=5 << 20) as srv:  # one blocker: ~3 MB
+        rb, rs = register(srv, blocker), register(srv, small)
+        q0 = srv.submit(rb, blocker["enc"])   # admitted, holds most of the budget
+        q1 = srv.submit(rb, blocker["enc"])   # does not fit until q0 is done
+        q2 = srv.submit(rs, small["enc"])     # fits beside q0
+        out2, i2 = srv.wait(q2)
+        out1, i1 = srv.wait(q1)
+        out0, i0 = srv.wait(q0)
+    assert i2.t_admit_us < i1.t_admit_us
+    assert np.array_equal(out0.view(np.uint64), out1.view(np.uint64))
+    assert_fitness(out2, oracle_result(small), "passed head")

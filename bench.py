@@ -60,9 +60,14 @@ def parse():
     ap.add_argument("--serving-runs", type=int, default=64)
     ap.add_argument("--stack-table", action="store_true",
                     help="print the percentages of programs each stack limit evaluates (host only) and exit")
-    ap.add_argument("--once", choices=["sextic512", "mux20", "linear512"], default=None,
-                    help="evaluate one workload twice and exit (the small cases of the ncu "
-                         "captures): sextic512 = 512 sextic trees x 100000 cases, extended "
+    ap.add_argument("--once", choices=["c2", "c2_512", "sextic512", "shuttle512", "shuttle512_rpn", "mux20",
+                                       "linear512"], default=None,
+                    help="evaluate one workload twice and exit (the cases of the ncu "
+                         "captures): c2 = the timed workload at the timed shape (4096 trees x "
+                         "65536 cases, K = 8, block 256, 65536 cases per block); c2_512 = its "
+                         "first 512 trees, same shape; shuttle512 (_rpn) = 512 Shuttle-shaped trees x "
+                         "58000 cases, extended S-form (RPN) interpreter, K = 8, block 512; "
+                         "sextic512 = 512 sextic trees x 100000 cases, extended "
                          "interpreter; mux20 = 128 20-multiplexer trees x 2^20 cases, Boolean; "
                          "linear512 = 512 register programs x 262144 cases x 8 inputs, register "
                          "file in shared memory, K = 4, block 256 (all with the program buffer "
@@ -121,7 +126,27 @@ def run_once(args):
     import torch
     import paper_1601_00221_gb300 as gp
     import synth
-    if args.once == "sextic512":
+    if args.once in ("c2", "c2_512"):
+        w = synth.regression_large(seed=2, n_progs=4096 if args.once == "c2" else 512, n_cases=65536)
+        enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM,
+                                   gp.ORDER_MIN_DEPTH)
+        P, O, L = enc.to_device("cuda")
+        X, Y = torch.from_numpy(w.cases).cuda(), torch.from_numpy(w.targets).cuda()
+        cfg = gp.Config(gp.VARIANT_REGISTER, 8, 256, 65536)
+        for _ in range(2):
+            f = gp.eval_population(P, O, L, X, Y, config=cfg)
+        out = float(f[0])
+    elif args.once in ("shuttle512", "shuttle512_rpn"):
+        w = synth.shuttle_like_problem(n_progs=512)
+        kind = gp.KIND_RPN if args.once.endswith("rpn") else gp.KIND_SFORM
+        enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, kind)
+        P, O, L = enc.to_device("cuda")
+        X, Y = torch.from_numpy(w.cases).cuda(), torch.from_numpy(w.targets).cuda()
+        cfg = enc.config(fitness=w.fitness, k=8, block=512)
+        for _ in range(2):
+            f = gp.eval_population(P, O, L, X, Y, config=cfg)
+        out = float(f[0])
+    elif args.once == "sextic512":
         w = synth.sextic_problem(n_progs=512)
         enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths)
         P, O, L = enc.to_device("cuda")

@@ -253,6 +253,22 @@ int gp_eval_population_ex(const uint32_t* programs, const int64_t* offsets,
                           double* fitness_out, float* outputs, const gp_config* cfg,
                           gp_stream_t stream);
 
+/* Width split (many-input cases, Sec. 4.2's KDDcup shape): the staged-input
+ * tile of a block is sized for the widest program, which limits the blocks
+ * per multiprocessor for all.  Programs reading at most `split_inputs`
+ * distinct inputs are evaluated under `narrow` (its tile: split_inputs when
+ * narrow->tile_inputs is 0, at least split_inputs otherwise), every other
+ * program under `wide`, in two launches over the same cases after a small
+ * classification kernel on the device (asynchronous: the class sizes never
+ * reach the host).  Each program's fitness is what gp_eval_population_ex
+ * gives it under its class's configuration.  Tree variants only (register,
+ * extended, extended RPN); n_inputs <= 4096 and n_progs <= 160000. */
+int gp_eval_population_split(const uint32_t* programs, const int64_t* offsets,
+                             const int32_t* lengths, int32_t n_progs, const float* cases,
+                             int32_t n_inputs, int64_t n_cases, const float* targets,
+                             double* fitness_out, int32_t split_inputs, const gp_config* narrow,
+                             const gp_config* wide, gp_stream_t stream);
+
 /* Per-case outputs only (parity testing): outputs[p * n_cases + c]. */
 int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets, const int32_t* lengths,
                     int32_t n_progs, const float* cases, int32_t n_inputs, int64_t n_cases,

@@ -24,7 +24,7 @@ __all__ = [
     "encode_tree", "encode_population", "encode_linear_population",
     "eval_population", "eval_outputs", "eval_population_bool",
     "set_config", "reset_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
-    "eval_population_noalloc", "eval_segments", "MAX_SEGMENTS", "autotune_population", "autotune_population_ex",
+    "eval_population_noalloc", "eval_segments", "eval_population_split", "MAX_SEGMENTS", "autotune_population", "autotune_population_ex",
     "autotune_population_bool", "autotune_save", "autotune_load", "autotune_clear", "eval_launches",
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "KIND_RPN_EXT",
     "ORDER_PAPER",
@@ -134,6 +134,7 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_shutdown": [],
         "gp_eval_population_noalloc": [P, P, P, i32, P, i32, i64, P, P, P],
         "gp_eval_segments": [P, P, P, P, i32, i32, P, P],
+        "gp_eval_population_split": [P, P, P, i32, P, i32, i64, P, P, i32, P, P, P],
         "gp_server_create": [P, P],
         "gp_server_register_run": [P, i32, P, i32, i64, P, P],
         "gp_server_submit": [P, i32, P, P, P, i32, i64, P, P],
@@ -352,6 +353,21 @@ def eval_population(programs, offsets, lengths, cases, targets, fitness_out=None
                                        _tptr(cases), n_inputs, n_cases, _tptr(targets),
                                        _tptr(fitness_out), _tptr(outputs), _cfg(config),
                                        _stream(stream)))
+    return fitness_out
+
+
+def eval_population_split(programs, offsets, lengths, cases, targets, split_inputs, narrow, wide,
+                          fitness_out=None, stream=None):
+    """gp_eval_population_split: programs reading at most split_inputs
+    distinct inputs under `narrow`, the others under `wide` (Configs)."""
+    import torch
+    n = int(lengths.numel())
+    n_inputs, n_cases = (int(cases.shape[0]), int(cases.shape[1])) if cases.dim() == 2 else (1, int(cases.numel()))
+    if fitness_out is None:
+        fitness_out = torch.empty(n, dtype=torch.float64, device=cases.device)
+    _check(lib().gp_eval_population_split(_tptr(programs), _tptr(offsets), _tptr(lengths), n, _tptr(cases),
+                                          n_inputs, n_cases, _tptr(targets), _tptr(fitness_out), int(split_inputs),
+                                          _cfg(narrow), _cfg(wide), _stream(stream)))
     return fitness_out
 
 

@@ -330,7 +330,7 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   rc = get_workspace(s, n_chunks > 1 ? (size_t)n_chunks * n_progs : 0, n_chunks > 1 ? n_progs : 0, &w);
   if (rc) return rc;
 
-  FloatArgs a;
+  FloatArgs a{};
   a.programs = programs;
   a.offsets = offsets;
   a.lengths = lengths;
@@ -366,6 +366,90 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   const bool xreg = (n_inputs == 1);
   cudaError_t e = launch_float_config(a, c, xreg, grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return GP_OK;
+}
+
+extern "C" int gp_eval_population_split(const uint32_t* programs, const int64_t* offsets,
+                                        const int32_t* lengths, int32_t n_progs, const float* cases,
+                                        int32_t n_inputs, int64_t n_cases, const float* targets,
+                                        double* fitness_out, int32_t split_inputs, const gp_config* narrow,
+                                        const gp_config* wide, gp_stream_t stream) {
+  gp_clear_error();
+  if (n_progs < 0 || n_inputs < 0 || n_cases < 0 || split_inputs < 0)
+    return gp_fail(GP_ERR_INVALID_ARG, "negative size");
+  if (!fitness_out) return gp_fail(GP_ERR_INVALID_ARG, "null fitness_out");
+  if (n_progs == 0) return GP_OK;
+  if (!programs || !offsets || !lengths) return gp_fail(GP_ERR_INVALID_ARG, "null program arrays");
+  if (!aligned16(programs)) return gp_fail(GP_ERR_INVALID_ARG, "programs must be 16-byte aligned");
+  if (n_cases > 0 && n_inputs > 0 && !cases) return gp_fail(GP_ERR_INVALID_ARG, "null cases");
+  if (n_cases > 0 && !targets) return gp_fail(GP_ERR_INVALID_ARG, "null targets");
+  if (n_cases > kMaxCases) return gp_fail(GP_ERR_INVALID_ARG, "n_cases too large");
+  if (n_inputs > GP_COMPACT_MAX_INPUTS)
+    return gp_fail(GP_ERR_INVALID_ARG, "the width split takes at most %d inputs", GP_COMPACT_MAX_INPUTS);
+  if (n_progs > 160000) return gp_fail(GP_ERR_INVALID_ARG, "the width split takes at most 160000 programs");
+  gp_config cls[2];
+  const gp_config* user[2] = {narrow, wide};
+  size_t smem[2];
+  int64_t chunk[2], n_chunks[2];
+  for (int c = 0; c < 2; ++c) {
+    int rc = resolve_config(user[c], &cls[c]);
+    if (rc) return rc;
+    if (cls[c].variant == GP_VARIANT_REGISTER_FILE || cls[c].variant == GP_VARIANT_LOCAL)
+      return gp_fail(GP_ERR_INVALID_ARG, "the width split takes the tree interpreters' variants");
+    int32_t tile = (cls[c].tile_inputs > 0 && cls[c].tile_inputs < n_inputs) ? cls[c].tile_inputs : n_inputs;
+    if (c == 0 && (!user[0] || user[0]->tile_inputs == 0)) tile = std::min(split_inputs, n_inputs);
+    if (c == 0 && tile < std::min(split_inputs, n_inputs))
+      return gp_fail(GP_ERR_INVALID_ARG, "the narrow class's tile must hold split_inputs inputs");
+    cls[c].tile_inputs = tile;
+    rc = float_launch_smem(cls[c], tile, &smem[c]);
+    if (rc) return rc;
+    const int per_pass = cls[c].k * cls[c].block;
+    chunk[c] = choose_chunk(n_cases, n_progs, per_pass, cls[c].chunk_cases, kAutoBlocksPerSm);
+    n_chunks[c] = std::max<int64_t>(1, (n_cases + chunk[c] - 1) / chunk[c]);
+    if (n_chunks[c] * n_progs > 0x7fffffffLL) return gp_fail(GP_ERR_INVALID_ARG, "too many blocks");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t maxch = std::max(n_chunks[0], n_chunks[1]);
+  Workspace* w = nullptr;
+  int rc = get_workspace(s, maxch > 1 ? (size_t)(maxch * n_progs) : 0, maxch > 1 ? (size_t)n_progs : 0, &w);
+  if (rc) return rc;
+  int32_t* order = nullptr;
+  rc = get_order(w, 2 * (size_t)n_progs + 2, s, &order);  // two classes, then their sizes
+  if (rc) return rc;
+  int32_t* counts = order + 2 * (size_t)n_progs;
+  cudaError_t e = launch_split_by_inputs(programs, offsets, lengths, n_progs, n_inputs, split_inputs, order,
+                                         counts, s);
+  if (e != cudaSuccess) return cuda_fail(e, "width split launch");
+  for (int c = 0; c < 2; ++c) {
+    FloatArgs a{};
+    a.programs = programs;
+    a.offsets = offsets;
+    a.lengths = lengths;
+    a.n_progs = n_progs;
+    a.cases = cases;
+    a.n_inputs = n_inputs;
+    a.n_cases = n_cases;
+    a.targets = targets;
+    a.fitness_out = fitness_out;
+    a.outputs = nullptr;
+    a.partials = w->partials;
+    a.counters = w->counters;
+    a.status = w->status;
+    a.chunk_cases = chunk[c];
+    a.n_chunks = (int32_t)n_chunks[c];
+    a.x_aligned = aligned16(cases) && (n_inputs <= 1 || n_cases % 4 == 0);
+    a.y_aligned = aligned16(targets);
+    a.o_aligned = 0;
+    a.want_fitness = 1;
+    a.fitness_kind = cls[c].fitness;
+    a.tile_inputs = cls[c].tile_inputs;
+    a.prog_cap = cls[c].max_instructions;
+    a.order = order + (size_t)c * n_progs;
+    a.order_count = counts + c;
+    // a grid for every program; the blocks past the class's size return at once
+    e = launch_float_config(a, cls[c], n_inputs == 1, (int)(n_progs * n_chunks[c]), smem[c], s);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  }
   return GP_OK;
 }
 

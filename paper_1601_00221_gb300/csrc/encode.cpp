@@ -458,11 +458,25 @@ extern "C" int gp_encode_linear_population(const uint8_t* instr, const int64_t* 
       o[1] = (uint32_t)n;
       o[2] = (uint32_t)n;
       o[3] = 0;
-      for (int32_t i = 0; i < n; ++i) {
+      // Payload b carries flags for the interpreter with the registers in
+      // shared memory (the register variant ignores them): bit 0, operand a
+      // is the previous instruction's destination; bit 1, operand b is; bit
+      // 2, the result is overwritten before anything reads it from the
+      // register file (a read of the previous result through bit 0 or 1 does
+      // not count) and it is not register 0 at the end.  The liveness pass
+      // runs backwards from {register 0}.
+      uint32_t live = 1u;  // registers whose stored value a later read (or the output) needs
+      for (int32_t i = n - 1; i >= 0; --i) {
         uint8_t d = ins[4 * i], op = ins[4 * i + 1], a = ins[4 * i + 2], b = ins[4 * i + 3];
+        const uint8_t pd = i > 0 ? ins[4 * (i - 1)] : 0xff;
+        const uint32_t fa = (i > 0 && a == pd) ? 1u : 0u, fb = (i > 0 && b == pd) ? 1u : 0u;
+        const uint32_t dead = (live >> d) & 1u ? 0u : 1u;
+        live &= ~(1u << d);
+        if (!fa) live |= 1u << a;
+        if (!fb) live |= 1u << b;
         o[4 + 4 * i] = (uint32_t)lin_code(op - GP_OP_ADD, a, b);
         o[5 + 4 * i] = d;
-        o[6 + 4 * i] = 0;
+        o[6 + 4 * i] = fa | (fb << 1) | (dead << 2);
         o[7 + 4 * i] = 0;
       }
       out_offsets[p] = pos;

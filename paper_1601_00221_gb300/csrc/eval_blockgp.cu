@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(256) eval_blockgp_kernel(FloatArgs a) {
   __shared__ int meta_s;
   const int item = blockIdx.x;
   const int rank = item / a.n_chunks;
+  if (a.order_count && rank >= *a.order_count) return;  // (uniform over the block)
   const int p = a.order ? a.order[rank] : rank;
   const int chunk = item - rank * a.n_chunks;
   const int tid = threadIdx.x;

@@ -62,6 +62,8 @@ struct FloatArgs {
   const int32_t* order;  // the program of the i-th (program, chunks) group of blocks, longest
                          // first (launch_order_by_size), or null for 0, 1, 2, ...
   int32_t tile_inputs;   // inputs per case the staged tile holds (<= n_inputs)
+  const int32_t* order_count;  // with order: the number of its entries to evaluate (a device
+                               // count; blocks of later ranks return at once), or null for all
 };
 
 // Several populations in one launch (gp_eval_segments, the serving loop's
@@ -486,6 +488,7 @@ __device__ __forceinline__ void eval_float_block(const FloatArgs& a, const SegTa
   const int prog_base = SEG ? t->s[seg].prog_begin : 0;
   const int local = SEG ? item - t->s[seg].block_begin : item;
   const int rank = local / a_n_chunks;
+  if (!SEG && a.order_count && rank >= *a.order_count) return;  // (uniform over the block)
   const int p = a.order ? a.order[prog_base + rank] : prog_base + rank;
   const int chunk = local - rank * a_n_chunks;
   const int tid = threadIdx.x;

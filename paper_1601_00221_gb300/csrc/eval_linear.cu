@@ -43,8 +43,15 @@ __device__ __forceinline__ bool run_linear_rf(uint32_t prog, uint32_t base) {
   return bad == 0;
 }
 
+// blocks of 256 threads per multiprocessor the register budget is sized for:
+// the register files (4 K KB per warp) leave room for 24 warps at K = 8 and
+// 40 at K = 4 or 2; at these counts ptxas needs no spills (78, 48, 48, 40
+// registers, -Xptxas -v)
 template <int K>
-__global__ void __launch_bounds__(256, 3) eval_linear_rf_kernel(FloatArgs a) {
+constexpr int rf_min_blocks() { return K == 8 ? 3 : K == 1 ? 6 : 5; }
+
+template <int K>
+__global__ void __launch_bounds__(256, rf_min_blocks<K>()) eval_linear_rf_kernel(FloatArgs a) {
   using namespace gpisa;
   using L = RF<K>;
   extern __shared__ uint4 dyn_s[];
@@ -55,6 +62,7 @@ __global__ void __launch_bounds__(256, 3) eval_linear_rf_kernel(FloatArgs a) {
 
   const int item = blockIdx.x;
   const int rank = item / a.n_chunks;
+  if (a.order_count && rank >= *a.order_count) return;  // (uniform over the block)
   const int p = a.order ? a.order[rank] : rank;
   const int chunk = item - rank * a.n_chunks;
   const int tid = threadIdx.x;
@@ -82,8 +90,13 @@ __global__ void __launch_bounds__(256, 3) eval_linear_rf_kernel(FloatArgs a) {
       const uint4 in = g[i];
       prog_s[i] = in;
       ok &= valid_instr(K_LINEAR, in, a.n_inputs) ? 1 : 0;
+      // the flags (payload b): at most bits 0..2, and a forwarded operand
+      // must be the previous instruction's destination
+      const uint32_t pd = i > 0 ? g[i - 1].y : 0xffffffffu;
+      const uint32_t ra = (in.x >> 3) & 7u, rb = in.x & 7u;
+      ok &= (in.z < 8u && (!(in.z & 1u) || ra == pd) && (!(in.z & 2u) || rb == pd)) ? 1 : 0;
     }
-    if (tid == 0) prog_s[n_instr] = make_uint4(LIN_NCODES, 0u, 0u, 0u);  // the sentinel: function 4
+    if (tid == 0) prog_s[n_instr] = make_uint4(LIN_NCODES, 0u, 8u, 0u);  // the sentinel: dispatch index 32
     bad = !__syncthreads_and(ok);
   }
 
@@ -130,10 +143,19 @@ __global__ void __launch_bounds__(256, 3) eval_linear_rf_kernel(FloatArgs a) {
             reinterpret_cast<float*>(mine + v * L::RSTRIDE + q * 32 * L::CB)[w] = 0.0f;
       if (full && a.x_aligned) __pipeline_wait_prior(0);
       if (!run_linear_rf<K>(prog_addr, base)) flags |= FLAG_BAD;
-      float o[K];
+      float o[K];  // register 0, one vector load per chunk
+      if constexpr (K >= 4) {
 #pragma unroll
-      for (int j = 0; j < K; ++j)
-        o[j] = *reinterpret_cast<const float*>(mine + (j / (L::CB / 4)) * 32 * L::CB + (j % (L::CB / 4)) * 4);
+        for (int q = 0; q < L::NCHUNK; ++q) {
+          const float4 v = *reinterpret_cast<const float4*>(mine + q * 32 * L::CB);
+          o[4 * q] = v.x; o[4 * q + 1] = v.y; o[4 * q + 2] = v.z; o[4 * q + 3] = v.w;
+        }
+      } else if constexpr (K == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(mine);
+        o[0] = v.x; o[1] = v.y;
+      } else {
+        o[0] = *reinterpret_cast<const float*>(mine);
+      }
       if (out_row) {
         Vec<K> ov;
 #pragma unroll

@@ -68,6 +68,13 @@ cudaError_t launch_float_seg_k8(const FloatArgs& a, const SegTable& t, bool xreg
 // linear_rf_bytes(k, block); blocks of at most 256 threads.
 size_t linear_rf_bytes(int k, int block);
 cudaError_t launch_linear_rf(const FloatArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s);
+// The width split's classes (programs reading at most `split` distinct
+// inputs: class 0; the rest: class 1), each longest first in order[c * n ..],
+// their sizes in counts[0..1]; one block, n bytes of dynamic shared memory
+// (n <= 160000), n_inputs <= GP_COMPACT_MAX_INPUTS.
+cudaError_t launch_split_by_inputs(const uint32_t* programs, const int64_t* offsets, const int32_t* lengths,
+                                   int32_t n, int32_t n_inputs, int32_t split, int32_t* order, int32_t* counts,
+                                   cudaStream_t s);
 // one block per segment: zero Boolean hit counts, and with `order` write each
 // segment's programs longest first into order[prog_begin ..]
 cudaError_t launch_segment_prep(const SegTable& t, const int32_t* lengths, int32_t* order, bool zero_hits,

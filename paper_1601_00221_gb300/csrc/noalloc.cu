@@ -131,7 +131,7 @@ extern "C" int gp_eval_population_noalloc(const uint32_t* programs, const int64_
   if (e == cudaSuccess) e = cudaMemsetAsync(&scratch->status, 0, sizeof(int), s);
   if (e != cudaSuccess) return gp_fail(GP_ERR_CUDA, "clearing the scratch: %s", cudaGetErrorString(e));
 
-  FloatArgs a;
+  FloatArgs a{};
   a.programs = programs;
   a.offsets = offsets;
   a.lengths = lengths;

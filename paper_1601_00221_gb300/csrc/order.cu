@@ -78,7 +78,99 @@ __global__ void __launch_bounds__(1024) segment_prep_kernel(const __grid_constan
   if (order) order_range(lengths, d.prog_begin, d.n_progs, order, start);
 }
 
+// The two classes of a width split (one block of 1024 threads): a program
+// reading at most `split` distinct inputs goes to class 0, every other (and
+// any program whose header is not a float tree's) to class 1; each class is
+// written longest first into order[c * n ..], and its size into counts[c].
+// Warp w scans programs w, w + 32, ...: its lanes mark the inputs the
+// instructions read in the warp's bitmap (n_inputs <= GP_COMPACT_MAX_INPUTS)
+// and count them.
+__global__ void __launch_bounds__(1024) split_by_inputs_kernel(const uint32_t* __restrict__ programs,
+                                                               const int64_t* __restrict__ offsets,
+                                                               const int32_t* __restrict__ lengths, int32_t n,
+                                                               int32_t n_inputs, int32_t split,
+                                                               int32_t* __restrict__ order,
+                                                               int32_t* __restrict__ counts) {
+  using namespace gpisa;
+  constexpr int kWords = GP_COMPACT_MAX_INPUTS / 32;
+  __shared__ uint32_t used_s[32][kWords];
+  __shared__ int start[2][kPerLane * 32];
+  __shared__ int n_class[2];
+  extern __shared__ uint8_t cls_s[];  // the class of each program (dynamic: n bytes)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nw = (n_inputs + 31) >> 5;
+  for (int p = warp; p < n; p += 32) {
+    for (int i = lane; i < nw; i += 32) used_s[warp][i] = 0u;
+    __syncwarp();
+    int wide = 1;
+    const int64_t off = offsets[p];
+    const int32_t len = lengths[p];
+    if ((off & 3) == 0 && len >= 4) {
+      const uint4 h = *reinterpret_cast<const uint4*>(programs + off);
+      const uint32_t kind = h.x & 0xffu;
+      const int64_t ni = (int64_t)h.y;
+      if ((kind == K_SFORM || kind == K_RPN || kind == K_SFORMX || kind == K_RPNX) && 4 + 4 * ni <= len) {
+        const uint4* ins = reinterpret_cast<const uint4*>(programs + off) + 1;
+        for (int64_t i = lane; i < ni; i += 32) {
+          const uint4 in = ins[i];
+          const uint32_t f = input_fields(kind, in.x);
+          if ((f & 1u) && in.y < (uint32_t)n_inputs) atomicOr(&used_s[warp][in.y >> 5], 1u << (in.y & 31));
+          if ((f & 2u) && in.z < (uint32_t)n_inputs) atomicOr(&used_s[warp][in.z >> 5], 1u << (in.z & 31));
+          if ((f & 4u) && in.w < (uint32_t)n_inputs) atomicOr(&used_s[warp][in.w >> 5], 1u << (in.w & 31));
+        }
+        __syncwarp();
+        int c = 0;
+        for (int i = lane; i < nw; i += 32) c += __popc(used_s[warp][i]);
+        c = __reduce_add_sync(0xffffffffu, c);
+        wide = c > split ? 1 : 0;
+      }
+    }
+    if (lane == 0) cls_s[p] = (uint8_t)wide;
+    __syncwarp();
+  }
+  for (int i = tid; i < 2 * kPerLane * 32; i += blockDim.x) (&start[0][0])[i] = 0;
+  if (tid < 2) n_class[tid] = 0;
+  __syncthreads();
+  for (int p = tid; p < n; p += blockDim.x) {
+    atomicAdd(&start[cls_s[p]][kBuckets - 1 - size_bucket(lengths[p])], 1);
+    atomicAdd(&n_class[cls_s[p]], 1);
+  }
+  __syncthreads();
+  if (tid < 64) {  // exclusive prefix sums over each class's (reversed) buckets: warp c, class c
+    const int c = tid >> 5, l = tid & 31;
+    int sum = 0;
+    for (int j = 0; j < kPerLane; ++j) sum += start[c][l * kPerLane + j];
+    int before = sum;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, before, d);
+      if (l >= d) before += v;
+    }
+    before -= sum;
+    for (int j = 0; j < kPerLane; ++j) {
+      const int v = start[c][l * kPerLane + j];
+      start[c][l * kPerLane + j] = before;
+      before += v;
+    }
+  }
+  __syncthreads();
+  for (int p = tid; p < n; p += blockDim.x) {
+    const int c = cls_s[p];
+    order[(int64_t)c * n + atomicAdd(&start[c][kBuckets - 1 - size_bucket(lengths[p])], 1)] = p;
+  }
+  if (tid < 2) counts[tid] = n_class[tid];
+}
+
 }  // namespace
+
+cudaError_t launch_split_by_inputs(const uint32_t* programs, const int64_t* offsets, const int32_t* lengths,
+                                   int32_t n, int32_t n_inputs, int32_t split, int32_t* order, int32_t* counts,
+                                   cudaStream_t s) {
+  static std::atomic<size_t> configured{0};
+  const size_t smem = (size_t)n;
+  ensure_dynamic_smem(split_by_inputs_kernel, smem, configured);
+  split_by_inputs_kernel<<<1, 1024, smem, s>>>(programs, offsets, lengths, n, n_inputs, split, order, counts);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_order_by_size(const int32_t* lengths, int32_t n, int32_t* order, cudaStream_t s) {
   order_by_size_kernel<<<1, 1024, 0, s>>>(lengths, n, order);

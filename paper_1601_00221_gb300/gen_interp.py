@@ -944,11 +944,16 @@ class LinearRFGen:
     shared memory, this lane's K values of register r at
     base + r * RSTRIDE + q * 32 * CB (chunk q of CB bytes; the lanes of a warp
     side by side, so a warp's access to one chunk is conflict-free).  One
-    dispatch per instruction, on the function only (code >> 6: four bodies and
-    the sentinel); the operand and destination registers are addresses
-    computed from the code and the first payload.  No body holds a register
-    of the machine across the dispatch, so the interpreter needs few
-    registers and the kernel many warps.
+    dispatch per instruction, on (flags, function): index = pb * 4 + (code >> 6)
+    & 3, where the second payload pb holds the encoder's flags -- bit 0: a is
+    the previous instruction's destination, bit 1: b is, bit 2: the result is
+    overwritten before it is read again (and is not register 0 at the end) --
+    and the sentinel after the program has pb = 8 (index 32, DONE).  A
+    forwarded operand is the previous result, still in the body's registers,
+    so it is not loaded; a dead result is not stored.  The operand and
+    destination registers are shared-memory addresses computed from the code
+    and the first payload.  Few registers: the kernel's warps are bounded by
+    shared memory alone.
     Operands: %0 bad (out, u32); %1 program address, %2 this lane's register
     file address (shared, u32)."""
 
@@ -999,35 +1004,52 @@ class LinearRFGen:
         if K > 1:
             b("mov.b64 one2, 0x3F8000003F800000;")
             b("mov.b64 mone2, 0xBF800000BF800000;")
-        b("TBL: .branchtargets OP0, OP1, OP2, OP3, DONE;")
+        b("TBL: .branchtargets " + ", ".join(f"OP{i}" for i in range(32)) + ", DONE;")
         b("mov.u32 adr, %1;")
         b("mov.u32 base, %2;")
         b("mov.u32 %0, 0;")
+        zero = "0f00000000" if K == 1 else "0"
+        for u in A:  # (defined before the first jump; a program never forwards into its first instruction)
+            b(f"mov.{self.ty} {u}, {zero};")
         b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
         b("add.u32 adr, adr, 16;")
         b("LOOP:")
-        b("shr.u32 fn, code, 6;")
+        b("bfe.u32 fn, code, 6, 2;")
+        b("shl.b32 ra, pb, 2;")
+        b("add.u32 fn, fn, ra;")
         b("brx.idx.uni fn, TBL;")
-        for op in range(4):
-            b(f"OP{op}:")
-            b("bfe.u32 ra, code, 3, 3;")
-            b("and.b32 rb, code, 7;")
-            b(f"mad.lo.u32 aa, ra, {self.rstride}, base;")
-            b(f"mad.lo.u32 ab, rb, {self.rstride}, base;")
-            b(f"mad.lo.u32 ad, pa, {self.rstride}, base;")
-            self.load(A, "aa")
-            self.load(B, "ab")
+        for idx in range(32):
+            op, flags = idx & 3, idx >> 2
+            fa, fb, dead = flags & 1, (flags >> 1) & 1, (flags >> 2) & 1
+            b(f"OP{idx}:")
+            if not fa:
+                b("bfe.u32 ra, code, 3, 3;")
+                b(f"mad.lo.u32 aa, ra, {self.rstride}, base;")
+            if not fb:
+                b("and.b32 rb, code, 7;")
+                b(f"mad.lo.u32 ab, rb, {self.rstride}, base;")
+            if not dead:
+                b(f"mad.lo.u32 ad, pa, {self.rstride}, base;")
+            if fb:  # b is the previous result, in A
+                for i in range(H):
+                    b(f"mov.{self.ty} {B[i]}, {A[i]};")
+            else:
+                self.load(B, "ab")
+            if not fa:
+                self.load(A, "aa")
             b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
             b("add.u32 adr, adr, 16;")
             if op == 3:
-                emit_pdiv(b, K, A, B, A, "D")
-                self.store("ad", A)
+                emit_pdiv(b, K, A, B, A, f"D{idx}_")
+                if not dead:
+                    self.store("ad", A)
                 b("bra.uni LOOP;")
-                emit_pdiv_slow(b, K, A, B, "D")
+                emit_pdiv_slow(b, K, A, B, f"D{idx}_")
             else:
                 for i in range(H):
                     b(f"{F32[op] if K == 1 else F32X2[op]} {A[i]}, {A[i]}, {B[i]};")
-                self.store("ad", A)
+                if not dead:
+                    self.store("ad", A)
                 b("bra.uni LOOP;")
         b("DONE:")
         b("}")

@@ -112,18 +112,32 @@ def _apply(op, a, b):
         return np.where(b == 0, np.float32(1), a / safe).astype(np.float32)
 
 
-def run_float(words, x):
+def run_float(words, x, register_file=False):
     """Per-case outputs of an encoded float program (S-form, extended S-form,
-    RPN or register)."""
+    RPN or register).  register_file: run a register program the way the
+    shared-memory register-file interpreter does -- an operand flagged as the
+    previous result (payload b, bits 0 and 1) is taken from the previous
+    instruction instead of the register file, and a result flagged dead (bit
+    2) is not written to the register file -- so that wrong flags show as
+    wrong outputs."""
     x = np.asarray(x, np.float32)
     n_cases = x.shape[1]
     h = header(words)
     full = lambda v: np.full(n_cases, v, np.float32)
     if h["kind"] == 3:
         r = [x[i].copy() if i < x.shape[0] else full(0.0) for i in range(8)]
-        for code, d, _, _ in instrs(words):
+        prev = full(np.nan)
+        for code, d, flags, _ in instrs(words):
             op, a, b = code // 64, (code // 8) % 8, code % 8
-            r[d] = _apply(op, r[a], r[b])
+            if not register_file:
+                r[d] = _apply(op, r[a], r[b])
+                continue
+            assert flags < 8
+            va = prev if flags & 1 else r[a]
+            vb = prev if flags & 2 else r[b]
+            prev = _apply(op, va, vb)
+            if not flags & 4:
+                r[d] = prev
         return r[0]
     S = [None] * R
     for code, pa, pb, pc in instrs(words):

@@ -381,3 +381,33 @@ def test_blockgp_runs_the_extended_functions(exact_set, trans_set):
     P, O, L = upload(enc)
     assert_inside(gp.eval_outputs(P, O, L, dev(xt), config=cfg).cpu().numpy(), lo, hi, nan, "full set")
     assert gp.last_error() == 0
+
+
+# ---------------------------------------------------------------------------
+# width split: narrow programs under one configuration, wide ones under another
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("split", [2, 6, 40])
+def test_width_split_matches_each_class_alone(wide, split):
+    """Each program's fitness under gp_eval_population_split equals its
+    fitness under its class's configuration evaluated alone (bit for bit),
+    and the oracle's."""
+    import torch
+    pop, x, ref = wide
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    used = enc.info["inputs_used"]
+    y = np.rint(np.random.default_rng(131).uniform(-1, 3, x.shape[1])).astype(np.float32)
+    P, O, L = upload(enc)
+    X, Y = dev(x), dev(y)
+    narrow = ext_cfg(8, 128, 0, gp.FITNESS_CLASS)
+    narrow.tile_inputs = split
+    narrow.max_instructions = enc.max_instructions
+    widecfg = enc.config(fitness=gp.FITNESS_CLASS, k=2, block=256)
+    got = gp.eval_population_split(P, O, L, X, Y, split, narrow, widecfg).cpu().numpy()
+    a = gp.eval_population(P, O, L, X, Y, config=narrow).cpu().numpy()
+    b = gp.eval_population(P, O, L, X, Y, config=widecfg).cpu().numpy()
+    gp.last_error()  # (the narrow tile cannot hold the wide programs alone)
+    exp_cls = np.where(used <= split, a, b)
+    assert np.array_equal(got.view(np.uint64), exp_cls.view(np.uint64))
+    exp = oracle.fset_population_fitness(pop.words, pop.offsets, pop.lengths, x, y, oracle.FIT_CLASS)
+    assert np.array_equal(got, exp)
+    assert gp.last_error() == 0

@@ -374,6 +374,14 @@ __device__ __forceinline__ bool run_tree_ext(uint32_t prog, const float (&x)[K],
   return st == 0;
 }
 
+// payload c of a division by a constant is the divisor's reciprocal rounded
+// to nearest.  Out of line: inlined into every kernel's staging code, the
+// rounding sequence cost the extended K = 2 interpreter 10% (measured), and
+// it runs only for these instructions, once per block.
+static __device__ __noinline__ bool reciprocal_payload_ok(uint32_t b, uint32_t y) {
+  return y == __float_as_uint(__frcp_rn(__uint_as_float(b)));
+}
+
 // ---------------------------------------------------------------------------
 // Instruction validation (once per block, before the first pass): every code
 // known, every input index below n_inputs, every level pair in range.
@@ -391,7 +399,7 @@ __device__ __forceinline__ bool valid_instr(uint32_t kind, const uint4& in, int 
       // constant numerator) in the fast range, payload c its reciprocal
       // rounded to nearest even
       if (op != F_DIV || !div_fast_operand(in.z) || (form == SF_CI && !div_fast_operand(in.y)) ||
-          in.w != __float_as_uint(__frcp_rn(__uint_as_float(in.z))))
+          !reciprocal_payload_ok(in.z, in.w))
         return false;
     }
     const bool xa = form == SF_XX || form == SF_XC || form == SF_XS || form == SF_MOVX || form == SF_XI;

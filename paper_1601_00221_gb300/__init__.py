@@ -216,10 +216,13 @@ class EncodedPopulation:
 
     @property
     def max_instructions(self) -> int:
-        """Instructions of the longest program (0 when unknown: the API maximum)."""
-        if self.info is None or self.n == 0 or "n_instr" not in self.info.dtype.names:
+        """Instructions of the longest program (0 for an empty population: the
+        API maximum); an encoded program of n instructions takes 4 + 4 n words."""
+        if self.n == 0:
             return 0
-        return max(int(self.info["n_instr"].max()), 1)
+        if self.info is not None and "n_instr" in self.info.dtype.names:
+            return max(int(self.info["n_instr"].max()), 1)
+        return max((int(self.lengths.max()) - 4) // 4, 1)
 
     def config(self, fitness: int = FITNESS_SUM_ABS, k: int = 0, block: int = 0,
                chunk_cases: int = 0) -> "Config":

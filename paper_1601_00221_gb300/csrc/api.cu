@@ -873,9 +873,9 @@ void add_chunks(std::vector<gp_config>& out, gp_config c, int64_t n_units) {
   const int64_t per_pass = (int64_t)c.k * c.block;
   for (int ch0 : chunks) {
     int64_t ch = ch0;
-    if (ch0 < 0) {
+    if (ch0 < 0) {  // the whole set in one block per program
       ch = ((n_units + per_pass - 1) / per_pass) * per_pass;
-      if (ch > 0x7fffffff || ch <= 131072) continue;  // (a 32-bit field; sizes above cover the rest)
+      if (ch > 0x7fffffff) continue;  // (a 32-bit field)
     } else if (ch && (ch % per_pass || ch >= n_units)) {
       continue;
     }

@@ -1116,9 +1116,12 @@ class FloatGenX(FloatGen):
 
     def __init__(self, K, xmode):
         super().__init__(K, xmode)
-        # the per-lane branch: measured 2-3% faster here than the folded
-        # form, which costs these larger interpreters registers
-        self.fold_div = False
+        # division's slow path: decided once per warp (the basic
+        # interpreters' folded form) except at K = 8 with the input in
+        # registers, where the folded form costs spills and the per-lane
+        # branch stays (measured: the KDDcup-shaped set at K = 2 +16%,
+        # the sextic set at K = 8 -3% folded)
+        self.fold_div = not (K == 8 and xmode == "reg")
         self.RH = R * self.H
         self.o_adr = self.RH + self.H
         self.o_st = self.RH + self.H + 1
@@ -1254,7 +1257,7 @@ class FloatGenX(FloatGen):
                 table[code] = f"C{code}"
                 bodies.append((code, "if", d, l, None))
         assert max(table) < SFX_NCODES
-        self.table(SFX_NCODES, table)
+        self.table(SFX_NCODES, table, slow_levels=range(R) if self.fold_div else ())
         b("RSTBL: .branchtargets " + ", ".join(f"RS{l}" for l in range(R)) + ";")
         b(f"mov.u32 adr, %{self.o_adr};")
         self.setup_inputs()
@@ -1390,7 +1393,7 @@ class FloatGenX(FloatGen):
                 code = RPX_IF_BASE + perm * R + l
                 table[code] = f"C{code}"
                 bodies.append((code, "if", perm, l, None))
-        self.table(RPX_NCODES, table)
+        self.table(RPX_NCODES, table, slow_levels=range(R) if self.fold_div else ())
         b("RSTBL: .branchtargets " + ", ".join(f"RS{l}" for l in range(R)) + ";")
         b(f"mov.u32 adr, %{self.o_adr};")
         self.setup_inputs()

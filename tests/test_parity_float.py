@@ -320,11 +320,11 @@ def test_fitness_bit_identical_across_runs_and_streams():
     assert np.array_equal(f0, f1.cpu().numpy())
 
 
-@pytest.mark.parametrize("k,block,chunk", [(1, 128, 0), (8, 256, 16384), (8, 512, 0)])
+@pytest.mark.parametrize("k,block,chunk", [(1, 128, 0), (8, 256, 65536), (8, 256, 16384), (8, 512, 0)])
 def test_full_size_regression_sampled(k, block, chunk):
     """4096 trees (depth 2-8, <= 256 nodes) x 65536 cases, the benchmark's
     workload, in the launch shape the benchmark times (K = 8, block 256,
-    16384 cases per block) and others; the oracle checks a sample of 48
+    all 65536 cases per block) and others; the oracle checks a sample of 48
     programs entirely."""
     w = synth.regression_large()
     enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM,
@@ -346,6 +346,35 @@ def test_full_size_regression_sampled(k, block, chunk):
         out = gp.eval_outputs(Pp, Op, Lp, X, config=cfg).cpu().numpy()[0]
         assert_bits(out, oracle.tree_outputs(w.pop.program(int(p)), w.cases), f"program {p}")
     assert np.all(np.isfinite(f) | np.isinf(f))
+
+
+@pytest.mark.parametrize("variant,k,block,chunk", [(gp.VARIANT_REGISTER_FILE, 4, 256, 131072),
+                                                   (gp.VARIANT_REGISTER_FILE, 8, 128, 0),
+                                                   (gp.VARIANT_REGISTER, 8, 256, 0)])
+def test_full_size_register_gp_sampled(variant, k, block, chunk):
+    """The register-GP workload at its full size, 8192 programs of 16-128
+    instructions x 262144 cases x 8 inputs, in the launch shape the
+    benchmark's tuner picks (the register file in shared memory, K = 4,
+    block 256, 131072 cases per block) and others; the oracle checks the
+    fitness of 24 sampled programs over every case and the per-case outputs
+    of 3 of them."""
+    w = synth.linear_workload(n_progs=8192)
+    enc = gp.encode_linear_population(w.pop.instr, w.pop.offsets, w.pop.lengths)
+    P, O, L = upload(enc)
+    X, Y = dev(w.cases), dev(w.targets)
+    cfg = gp.Config(variant, k, block, chunk, 0, 0, 0, enc.max_instructions)
+    f = gp.eval_population(P, O, L, X, Y, config=cfg).cpu().numpy()
+    sample = np.sort(np.random.default_rng(6).choice(w.pop.n, 24, replace=False))
+    exp = np.array([oracle.linear_population_fitness(w.pop.instr, w.pop.offsets, w.pop.lengths, w.cases,
+                                                     w.targets, p_range=(int(p), int(p) + 1))[int(p)]
+                    for p in sample])
+    assert_fitness(f[sample], exp, "register GP full-size sample")
+    for p in sample[:3]:
+        sub = gp.EncodedPopulation(enc.words, enc.offsets[p:p + 1], enc.lengths[p:p + 1], 0, enc.kind, enc.order)
+        Pp, Op, Lp = upload(sub)
+        out = gp.eval_outputs(Pp, Op, Lp, X, config=cfg).cpu().numpy()[0]
+        assert_bits(out, oracle.linear_outputs(w.pop.program(int(p)), w.cases), f"program {p}")
+    assert gp.last_error() == 0
 
 
 @pytest.mark.parametrize("n_inputs", [1, 3])

@@ -44,11 +44,13 @@ __device__ __forceinline__ bool run_linear_rf(uint32_t prog, uint32_t base) {
 }
 
 // blocks of 256 threads per multiprocessor the register budget is sized for:
-// the register files (4 K KB per warp) leave room for 24 warps at K = 8 and
-// 40 at K = 4 or 2; at these counts ptxas needs no spills (78, 48, 48, 40
-// registers, -Xptxas -v)
+// the register files (4 K KB per warp) and a program buffer sized to the
+// population leave room for 24 warps at K = 8 and 48 at K = 4 or less (78
+// registers at K = 8, 40 below; at K = 4 and 2 ptxas spills 16 and 12 bytes,
+// and the 48 warps still beat 40 without spills: C4 3106 -> 3176 GPop/s at
+// K = 4, measured)
 template <int K>
-constexpr int rf_min_blocks() { return K == 8 ? 3 : K == 1 ? 6 : 5; }
+constexpr int rf_min_blocks() { return K == 8 ? 3 : 6; }
 
 template <int K>
 __global__ void __launch_bounds__(256, rf_min_blocks<K>()) eval_linear_rf_kernel(FloatArgs a) {

@@ -384,3 +384,34 @@ def test_constant_divisors_take_the_reciprocal_forms_inside_the_fast_range(order
             assert pc == 0
         assert same_bits(ref.run_float(words, x), oracle.tree_outputs(p, x))
     assert recip_seen >= 20 and plain_seen >= 20
+
+
+def test_stack_levels_sform_below_rpn_and_min_depth_below_paper_order():
+    """The stack-limit table's claims, tree by tree: the S-form never needs
+    more stack levels than the RPN form of the same tree, and the
+    Sethi-Ullman child order never more than the paper's left-to-right order
+    (for both forms); on a population with deep trees the orders differ."""
+    import ctypes
+    L = gp.lib()
+    progs = synth.ramped_half_and_half(71, 300, 2, 9, 511, funcs=synth.SHUTTLE_FUNCS, n_inputs=3,
+                                       full_fallback_to_grow=True)
+
+    def depth(p, kind, order):
+        cap = 4 + 4 * p.size
+        buf = np.zeros(cap, np.uint32)
+        info = gp._ProgInfo()
+        L.gp_encode_tree(p.ctypes.data_as(ctypes.c_void_p), p.size, kind, order,
+                         buf.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(info))
+        return info.max_depth
+
+    strict = 0
+    for p in progs:
+        p = np.ascontiguousarray(p, np.uint32)
+        d = {(k, o): depth(p, k, o) for k in (gp.KIND_SFORM, gp.KIND_RPN)
+             for o in (gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH)}
+        for o in (gp.ORDER_PAPER, gp.ORDER_MIN_DEPTH):
+            assert d[(gp.KIND_SFORM, o)] <= d[(gp.KIND_RPN, o)]
+        for k in (gp.KIND_SFORM, gp.KIND_RPN):
+            assert d[(k, gp.ORDER_MIN_DEPTH)] <= d[(k, gp.ORDER_PAPER)]
+        strict += d[(gp.KIND_RPN, gp.ORDER_MIN_DEPTH)] < d[(gp.KIND_RPN, gp.ORDER_PAPER)]
+    assert strict > 20

@@ -328,17 +328,13 @@ __device__ __forceinline__ void sfx_apply(uint32_t fn, typename SfxUnit<K>::type
   asm volatile(GP_PTX_RPNX_K##K_##_##X_ : GP_SFX_OUT_K##K_##_##X_ : GP_SFX_IN_K##K_##_##X_ : "memory")
 
 // RPN: the (extended) RPN interpreter, else the (extended) S-form one
+// The stack s and the operand t are the caller's, defined once and kept
+// across passes like the basic interpreters' stack (every program writes a
+// level before reading it; t is written before each exit).
 template <int K, bool XREG, bool RPN>
 __device__ __forceinline__ bool run_tree_ext(uint32_t prog, const float (&x)[K], uint32_t tile,
-                                             float (&o)[K]) {
-  using U = typename SfxUnit<K>::type;
-  constexpr int H = K == 1 ? 1 : K / 2;
-  U s[R * H];
-  U t[H];
-#pragma unroll
-  for (int i = 0; i < R * H; ++i) s[i] = U(0);
-#pragma unroll
-  for (int i = 0; i < H; ++i) t[i] = U(0);
+                                             typename SfxUnit<K>::type (&s)[stack_units<K>()],
+                                             typename SfxUnit<K>::type (&t)[K == 1 ? 1 : K / 2], float (&o)[K]) {
   uint32_t adr = prog, st = 0;
 #pragma unroll 1
   for (;;) {
@@ -646,6 +642,10 @@ __device__ __forceinline__ void eval_float_block(const FloatArgs& a, const SegTa
   typename SfxUnit<K>::type stk[stack_units<K>()];
 #pragma unroll
   for (int i = 0; i < stack_units<K>(); ++i) stk[i] = 0;
+  // the extended interpreters' unary-function operand (unused otherwise)
+  typename SfxUnit<K>::type tfn[K == 1 ? 1 : K / 2];
+#pragma unroll
+  for (int i = 0; i < (K == 1 ? 1 : K / 2); ++i) tfn[i] = 0;
 
   if (!bad) {
     int64_t wb_first = c_begin + (int64_t)warp * 32 * K;
@@ -715,7 +715,7 @@ __device__ __forceinline__ void eval_float_block(const FloatArgs& a, const SegTa
       }
       bool ok;
       if constexpr (EXT) {
-        ok = run_tree_ext<K, XREG, EXT == 2>(prog_addr, x, tile_addr, o);
+        ok = run_tree_ext<K, XREG, EXT == 2>(prog_addr, x, tile_addr, stk, tfn, o);
       } else if constexpr (RL < R) {
         static_assert(K == 8 && RL == 4, "shared-memory levels are generated for K = 8, RL = 4");
         ok = run_tree_rl4<XREG>(prog_addr, (uint32_t)n_instr, x, tile_addr, sbase, o);

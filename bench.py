@@ -589,7 +589,8 @@ def bench_boolean(gp, synth, torch, device):
     the 6-input problems (64 cases), 4096 for 11 inputs, 1024 for the
     20-multiplexer; GPop counts cases as bits (32 per word), as the paper's
     20-multiplexer figure does.  The library's Boolean tuner picks the kernel
-    (one program per lane, or a warp per program with K words per thread),
+    (one program per lane; a warp per program, several programs per block
+    over one staged case set; or blocks per program with K words per thread),
     K, block and chunk on each population."""
     import numpy as np
     out = {}
@@ -608,7 +609,10 @@ def bench_boolean(gp, synth, torch, device):
         ms = _time_events(torch, lambda: gp.eval_population_bool(P, O, L, cb, w.n_cases, tb,
                                                                  hits_out=hits, config=cfg))
         lanes = int(best.variant) == gp.VARIANT_LANES
-        out[f"{kind}{k}"] = {"programs": w.pop.n, "cases": w.n_cases,
+        kernel = ("program per lane" if lanes else
+                  "warp per program, block/32 programs per block" if int(best.variant) == gp.VARIANT_WARPS
+                  else "blocks per program")
+        out[f"{kind}{k}"] = {"programs": w.pop.n, "cases": w.n_cases, "kernel": kernel,
                              "k": "lane per program" if lanes else int(best.k),
                              "block": 0 if lanes else int(best.block),
                              "chunk_words": int(best.chunk_cases), "tuned_by": "gp_autotune_population_bool",

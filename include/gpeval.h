@@ -178,9 +178,14 @@ typedef enum gp_variant {
                                (runs GP_KIND_SFORM and GP_KIND_SFORM_EXT programs) */
   GP_VARIANT_EXTENDED_RPN = 5, /* the RPN interpreter with the extended float functions
                                (runs GP_KIND_RPN and GP_KIND_RPN_EXT programs) */
-  GP_VARIANT_REGISTER_FILE = 6 /* GP_KIND_LINEAR programs only, their eight registers in shared
+  GP_VARIANT_REGISTER_FILE = 6, /* GP_KIND_LINEAR programs only, their eight registers in shared
                                memory: one jump per instruction and a kernel of few
                                registers (blocks of at most 256 threads) */
+  GP_VARIANT_WARPS = 7      /* Boolean only: one warp per program, block / 32 programs per
+                               block sharing one staged copy of the case set (at most 256
+                               threads; the case set and the block's programs must fit in
+                               200 KB of shared memory); GP_VARIANT_AUTO picks it for 5 to
+                               256 words (129 to 8192 cases) */
 } gp_variant;
 
 /* Fitness measure of a float program (Sec. 4.2 parameter table: mean squared
@@ -319,6 +324,10 @@ int gp_eval_population_noalloc(const uint32_t* programs, const int64_t* offsets,
  * case_bits[v * n_words + (c >> 5)].  target_bits uint32 [n_words].
  * hits_out uint64 [n_progs]: cases c < n_cases whose output bit equals the
  * target bit (bits beyond n_cases in the last word are ignored).  Exact.
+ * By default case sets of at most 4 words run one program per lane
+ * (GP_VARIANT_LANES), 5 to 256 words one warp per program
+ * (GP_VARIANT_WARPS), larger ones the register variant's blocks, unless the
+ * autotuner's record for the shape says otherwise.
  * ---------------------------------------------------------------------- */
 int gp_eval_population_bool(const uint32_t* programs, const int64_t* offsets,
                             const int32_t* lengths, int32_t n_progs, const uint32_t* case_bits,
@@ -487,9 +496,11 @@ int gp_server_destroy(gp_server* srv);
  * stack levels too.  gp_autotune_population is the _ex call with base NULL.
  *
  * gp_autotune_population_bool does the same for a Boolean population:
- * k in {1, 2, 4, 8} x block in {32, 64, 128, 256} x cases per block, and one
- * program per lane when the cases fit 4 words; the record applies to Boolean
- * evaluations that leave k and block at 0.
+ * k in {1, 2, 4, 8} x block in {32, 64, 128, 256} x cases per block, one
+ * program per lane when the cases fit 4 words, and one warp per program
+ * (k x block in {64, 128, 256}) when the case set fits the per-warp
+ * variant's shared memory; the record applies to Boolean evaluations that
+ * leave k and block at 0.
  *
  * The tuners synchronise `stream` and allocate a temporary output buffer.
  * gp_autotune_save writes every record to a text file (one line per record:
@@ -517,8 +528,8 @@ int gp_autotune_load(const char* path);
 int gp_autotune_clear(void);
 
 /* Kernels one evaluation (gp_eval_population*, gp_eval_outputs,
- * gp_eval_population_noalloc, gp_eval_population_bool with a warp per
- * program) of n_progs programs over n_cases cases launches on the current
+ * gp_eval_population_noalloc, gp_eval_population_bool with the register or
+ * per-warp variant) of n_progs programs over n_cases cases launches on the current
  * device: the interpreter, plus the ordering kernel that takes the programs
  * longest first once n_progs fills two blocks per multiprocessor and n_cases
  * is at least 16384.  (The Boolean variant with one program per lane launches

@@ -29,7 +29,7 @@ __all__ = [
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "KIND_RPN_EXT",
     "ORDER_PAPER",
     "ORDER_MIN_DEPTH", "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL", "VARIANT_LANES",
-    "VARIANT_EXTENDED", "VARIANT_EXTENDED_RPN", "VARIANT_REGISTER_FILE", "FITNESS_SUM_ABS", "FITNESS_MSE", "FITNESS_CLASS",
+    "VARIANT_EXTENDED", "VARIANT_EXTENDED_RPN", "VARIANT_REGISTER_FILE", "VARIANT_WARPS", "FITNESS_SUM_ABS", "FITNESS_MSE", "FITNESS_CLASS",
     "encode_population_device", "EvolveParams", "Evolver",
 ]
 
@@ -38,6 +38,7 @@ ORDER_PAPER, ORDER_MIN_DEPTH = 0, 1
 VARIANT_AUTO, VARIANT_REGISTER, VARIANT_LOCAL, VARIANT_LANES, VARIANT_EXTENDED = 0, 1, 2, 3, 4
 VARIANT_EXTENDED_RPN = 5
 VARIANT_REGISTER_FILE = 6
+VARIANT_WARPS = 7
 FITNESS_SUM_ABS, FITNESS_MSE, FITNESS_CLASS = 0, 1, 2
 STACK_LEVELS = 8
 MAX_INSTR = 1024

@@ -169,7 +169,7 @@ int resolve_config(const gp_config* user, gp_config* c) {
   if (c->variant != GP_VARIANT_REGISTER && c->variant != GP_VARIANT_LOCAL &&
       c->variant != GP_VARIANT_AUTO && c->variant != GP_VARIANT_LANES &&
       c->variant != GP_VARIANT_EXTENDED && c->variant != GP_VARIANT_EXTENDED_RPN &&
-      c->variant != GP_VARIANT_REGISTER_FILE)
+      c->variant != GP_VARIANT_REGISTER_FILE && c->variant != GP_VARIANT_WARPS)
     return gp_fail(GP_ERR_INVALID_ARG, "unknown variant %d", c->variant);
   if (c->fitness != GP_FITNESS_SUM_ABS && c->fitness != GP_FITNESS_MSE && c->fitness != GP_FITNESS_CLASS)
     return gp_fail(GP_ERR_INVALID_ARG, "unknown fitness measure %d", c->fitness);
@@ -477,6 +477,69 @@ extern "C" int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets,
                                nullptr, nullptr, outputs, cfg, stream);
 }
 
+namespace {
+// case sets the per-warp variant takes by default (8192 cases)
+constexpr int64_t kWarpsAutoWords = 256;
+
+// The per-warp Boolean launch: k words per lane per pass (the caller's, the
+// tuner's, else the fewest passes up to k = 8), block / 32 programs per block
+// (the caller's, the tuner's, else 128 threads).
+int eval_bool_warps(const uint32_t* programs, const int64_t* offsets, const int32_t* lengths, int32_t n_progs,
+                    const uint32_t* case_bits, int32_t n_inputs, int64_t n_cases, const uint32_t* target_bits,
+                    uint64_t* hits_out, uint32_t* out_words, const gp_config* cfg, const gp_config* tuned,
+                    gp_config c, cudaStream_t s) {
+  const int64_t n_words = (n_cases + 31) / 32;
+  if (n_words == 0) {  // no cases: every program scores 0 hits
+    if (hits_out) {
+      cudaError_t e = cudaMemsetAsync(hits_out, 0, sizeof(uint64_t) * (size_t)n_progs, s);
+      if (e != cudaSuccess) return cuda_fail(e, "clearing hits");
+    }
+    return GP_OK;
+  }
+  if (!cfg || !cfg->k) c.k = tuned ? tuned->k : (n_words <= 32 ? 1 : n_words <= 64 ? 2 : n_words <= 128 ? 4 : 8);
+  if (!cfg || !cfg->block) c.block = tuned ? tuned->block : 128;
+  if (c.block > 256) return gp_fail(GP_ERR_INVALID_ARG, "the per-warp variant takes at most 256 threads per block");
+  const size_t smem = bool_warps_smem(c.k, c.block, n_inputs, n_words, c.max_instructions);
+  if (smem > kMaxTileBytes)
+    return gp_fail(GP_ERR_INVALID_ARG, "%d inputs x %lld words need %zu bytes of shared memory per block (max %zu)",
+                   n_inputs, (long long)n_words, smem, kMaxTileBytes);
+  Workspace* w = nullptr;
+  int rc = get_workspace(s, 0, 0, &w);
+  if (rc) return rc;
+  BoolArgs a;
+  a.programs = programs;
+  a.offsets = offsets;
+  a.lengths = lengths;
+  a.n_progs = n_progs;
+  a.case_bits = case_bits;
+  a.n_inputs = n_inputs;
+  a.n_cases = n_cases;
+  a.n_words = n_words;
+  a.target_bits = hits_out ? target_bits : nullptr;
+  a.hits_out = reinterpret_cast<unsigned long long*>(hits_out);
+  a.out_words = out_words;
+  a.status = w->status;
+  a.chunk_words = n_words;
+  a.n_chunks = 1;
+  a.aligned = aligned16(case_bits);
+  a.prog_cap = c.max_instructions;
+  a.order = nullptr;
+  cudaError_t e;
+  if (order_blocks(n_progs, n_cases, sm_count())) {
+    int32_t* order = nullptr;
+    rc = get_order(w, (size_t)n_progs, s, &order);
+    if (rc) return rc;
+    e = launch_order_by_size(lengths, n_progs, order, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering launch");
+    a.order = order;
+  }
+  const int per_block = c.block / 32;
+  e = launch_bool_warps(a, c.k, c.block, (n_progs + per_block - 1) / per_block, smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return GP_OK;
+}
+}  // namespace
+
 extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_t* offsets,
                                           const int32_t* lengths, int32_t n_progs,
                                           const uint32_t* case_bits, int32_t n_inputs,
@@ -544,9 +607,19 @@ extern "C" int gp_eval_population_bool_ex(const uint32_t* programs, const int64_
   gp_config c;
   int rc = resolve_config(cfg, &c);
   if (rc) return rc;
+  // a warp per program for case sets of a few hundred words, unless a
+  // variant is forced
+  const bool warps = (cfg && cfg->variant == GP_VARIANT_WARPS) ||
+                     ((!cfg || cfg->variant == GP_VARIANT_AUTO) &&
+                      (have_tuned ? tuned.variant == GP_VARIANT_WARPS
+                                  : (n_words > 4 && n_words <= kWarpsAutoWords)));
+  if (warps)
+    return eval_bool_warps(programs, offsets, lengths, n_progs, case_bits, n_inputs, n_cases, target_bits,
+                           hits_out, out_words, cfg, have_tuned ? &tuned : nullptr, c, (cudaStream_t)stream);
   if (c.variant == GP_VARIANT_EXTENDED || c.variant == GP_VARIANT_EXTENDED_RPN)
     c.variant = GP_VARIANT_REGISTER;  // a float-only choice
-  if (c.variant != GP_VARIANT_REGISTER) return gp_fail(GP_ERR_INVALID_ARG, "Boolean programs use the register or per-lane variant");
+  if (c.variant != GP_VARIANT_REGISTER)
+    return gp_fail(GP_ERR_INVALID_ARG, "Boolean programs use the register, per-lane or per-warp variant");
   if (c.block > 256) c.block = 256;  // the Boolean kernel's block limit
   // Defaults for many inputs: the staged tile (inputs x 32 lanes x K words
   // per warp) limits the blocks per SM.  K = 4 and 64-thread blocks, measured
@@ -983,6 +1056,17 @@ extern "C" int gp_autotune_population_bool(const uint32_t* programs, const int64
       c.block = blk;
       c.stack_registers = 0;
       add_chunks(cands, c, n_words);
+    }
+  for (int k : {1, 2, 4, 8})  // a warp per program, where the case set fits its shared memory
+    for (int blk : {64, 128, 256}) {
+      if (bool_warps_smem(k, blk, n_inputs, n_words, b.max_instructions) > kMaxTileBytes) continue;
+      gp_config c = b;
+      c.variant = GP_VARIANT_WARPS;
+      c.k = k;
+      c.block = blk;
+      c.chunk_cases = 0;
+      c.stack_registers = 0;
+      cands.push_back(c);
     }
   auto eval = [&](const gp_config& c) {
     return gp_eval_population_bool_ex(programs, offsets, lengths, n_progs, case_bits, n_inputs, n_cases,

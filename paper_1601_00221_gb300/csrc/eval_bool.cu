@@ -37,6 +37,23 @@ cudaError_t launch_bool_seg(const BoolArgs& a, const SegTable& t, int k, int blo
   return cudaGetLastError();
 }
 
+template <int K>
+static void launch_warps_k(const BoolArgs& a, int block, int grid, size_t smem, cudaStream_t s) {
+  static std::atomic<size_t> configured{0};
+  ensure_dynamic_smem(eval_bool_warps_kernel<K>, smem, configured);
+  eval_bool_warps_kernel<K><<<grid, block, smem, s>>>(a);
+}
+
+cudaError_t launch_bool_warps(const BoolArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s) {
+  switch (k) {
+    case 1: launch_warps_k<1>(a, block, grid, smem, s); break;
+    case 2: launch_warps_k<2>(a, block, grid, smem, s); break;
+    case 4: launch_warps_k<4>(a, block, grid, smem, s); break;
+    default: launch_warps_k<8>(a, block, grid, smem, s); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bool_lanes(const BoolArgs& a, int w, int grid, size_t smem, cudaStream_t s) {
   switch (w) {
     case 1: eval_bool_lanes_kernel<1><<<grid, 32, smem, s>>>(a); break;

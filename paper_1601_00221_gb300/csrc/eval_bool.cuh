@@ -90,7 +90,7 @@ __device__ __forceinline__ bool valid_bool_instr(const uint4& in, int n_inputs) 
   }
   if (in.x < (uint32_t)BOOL_MOVX) {
     const int f = (in.x - BOOL_IF_BASE) / R, level = (in.x - BOOL_IF_BASE) % R;
-    const int desc = if_form_desc(f);
+    const int desc = if_form_desc_fast(f);
     const int dc = desc / 16, da = (desc / 4) % 4, db = desc % 4;
     const int m = (dc > 0) + (da > 0) + (db > 0);
     if (level + (m > 0 ? m - 1 : 0) >= R) return false;
@@ -403,6 +403,149 @@ __global__ void __launch_bounds__(32) eval_bool_lanes_kernel(BoolArgs a) {
 
 inline size_t bool_lanes_smem(int w, int block, int n_inputs) {
   return sizeof(uint32_t) * ((size_t)n_inputs * w + (size_t)(block / 32) * gpisa::R * 32 * w);
+}
+
+// ---------------------------------------------------------------------------
+// Warp per program, several programs per block, for case sets of a few
+// hundred words (the 11-input problems: 64 words).  The block kernel above
+// gives every program blocks of its own, each staging the inputs again and
+// reducing across its warps; with 64 words a program is one pass of one warp,
+// so those fixed costs dominate.  Here the block stages the whole case set
+// once, as pass tiles [pass][input][32 lanes][K words] (the generated
+// interpreter's tile layout, so every pass of every warp reads its inputs
+// from the same place), and each warp stages its own program, interprets it
+// over every pass and writes its hit count: no barrier after the staging, no
+// cross-warp reduction.  The block's warps take consecutive ranks of the
+// order (longest first), so they finish together.
+// dynamic shared memory: the pass tiles (n_pass * n_inputs * 32 * K words),
+// then one program buffer (prog_cap + 1 instructions) per warp.
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(256) eval_bool_warps_kernel(BoolArgs a) {
+  using namespace gpisa;
+  extern __shared__ uint4 dyn_s[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+  constexpr int kPassWords = 32 * K;
+  const int64_t n_words = a.n_words;
+  const int n_pass = (int)((n_words + kPassWords - 1) / kPassWords);
+  const int nin = a.n_inputs;
+  const size_t tile_words = (size_t)n_pass * nin * kPassWords;  // a multiple of 32
+  uint32_t* tile_s = reinterpret_cast<uint32_t*>(dyn_s);
+  uint4* prog_s = dyn_s + tile_words / 4 + (size_t)warp * (a.prog_cap + 1);
+
+  // the case set, four words at a time (a group never straddles a pass tile:
+  // tiles hold a multiple of 32 words); words past the end are 0
+  const int64_t row = (int64_t)n_pass * kPassWords;  // padded words per input
+  const bool vec = a.aligned && (n_words & 3) == 0;
+  for (int64_t q = tid; q < (int64_t)nin * row / 4; q += blockDim.x) {
+    const int64_t e = q * 4;
+    const int v = (int)(e / row);
+    const int64_t w = e - (int64_t)v * row;
+    const int pass = (int)(w / kPassWords);
+    const int r = (int)(w - (int64_t)pass * kPassWords);
+    const uint32_t* src = a.case_bits + (int64_t)v * n_words + w;
+    uint4 val;
+    if (vec && w + 4 <= n_words) {
+      val = __ldg(reinterpret_cast<const uint4*>(src));
+    } else {
+      val.x = w < n_words ? __ldg(src) : 0u;
+      val.y = w + 1 < n_words ? __ldg(src + 1) : 0u;
+      val.z = w + 2 < n_words ? __ldg(src + 2) : 0u;
+      val.w = w + 3 < n_words ? __ldg(src + 3) : 0u;
+    }
+    *reinterpret_cast<uint4*>(tile_s + ((size_t)pass * nin + v) * kPassWords + r) = val;
+  }
+
+  // this warp's program (ranks past the population stage nothing)
+  const int rank = blockIdx.x * nwarps + warp;
+  const bool active = rank < a.n_progs;
+  const int p = !active ? 0 : (a.order ? a.order[rank] : rank);
+  int n_instr = -1;
+  if (active) {
+    if (lane == 0) {
+      const int64_t off = a.offsets[p];
+      const int32_t len = a.lengths[p];
+      if ((off & 3) == 0 && len >= 4) {
+        const uint4 h = *reinterpret_cast<const uint4*>(a.programs + off);
+        const int n = (int)h.y;
+        if ((h.x & 0xffu) == K_BOOL && (h.x >> 16) == VERSION && n >= 1 && n <= a.prog_cap &&
+            4 + 4 * (int64_t)n <= len)
+          n_instr = n;
+      }
+    }
+    n_instr = __shfl_sync(0xffffffffu, n_instr, 0);
+    if (n_instr >= 0) {
+      const uint4* g = reinterpret_cast<const uint4*>(a.programs + a.offsets[p]) + 1;
+      bool ok = true;
+      for (int i = lane; i < n_instr; i += 32) {
+        const uint4 in = g[i];
+        prog_s[i] = in;
+        ok &= valid_bool_instr(in, nin);
+      }
+      if (lane == 0) prog_s[n_instr] = make_uint4(BOOL_NCODES, 0u, 0u, 0u);  // end sentinel
+      if (!__all_sync(0xffffffffu, ok)) n_instr = -1;
+    }
+  }
+  __syncthreads();  // the case set is staged (each warp's program: its own lanes, ordered by the barrier)
+  if (!active) return;
+  unsigned long long* hits_row = a.hits_out ? a.hits_out + p : nullptr;
+  if (n_instr < 0) {
+    if (lane == 0) {
+      atomicOr(a.status, 2 /* GP_ERR_PROGRAM */);
+      if (hits_row) *hits_row = ~0ull;
+    }
+    return;
+  }
+
+  const uint32_t tail = (uint32_t)(a.n_cases & 31);
+  const uint32_t last_mask = tail ? ((1u << tail) - 1u) : 0xffffffffu;
+  uint32_t* out_row = a.out_words ? a.out_words + (int64_t)p * n_words : nullptr;
+  const uint32_t prog_addr = (uint32_t)__cvta_generic_to_shared(prog_s);
+  const uint32_t tile_addr0 = (uint32_t)__cvta_generic_to_shared(tile_s) + (uint32_t)(lane * K * 4);
+  unsigned hits = 0;  // at most n_words * 32 / 32 lanes per lane, below 2^32
+  bool bad = false;
+#pragma unroll 1
+  for (int pass = 0; pass < n_pass; ++pass) {
+    const int64_t w0 = (int64_t)pass * kPassWords + lane * K;
+    uint32_t o[K];
+    if (!run_bool<K>(prog_addr, (uint32_t)n_instr,
+                     tile_addr0 + (uint32_t)((size_t)pass * nin * kPassWords * 4), o))
+      bad = true;
+    if (out_row) {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (w0 + j < n_words) out_row[w0 + j] = o[j];
+    }
+    if (a.target_bits) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const int64_t w = w0 + j;
+        if (w < n_words) {
+          const uint32_t m = w < n_words - 1 ? 0xffffffffu : last_mask;
+          hits += __popc(~(o[j] ^ __ldg(a.target_bits + w)) & m);
+        }
+      }
+    }
+  }
+  // (an unknown code stops every lane of the warp: the program is warp-uniform)
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) {
+      atomicOr(a.status, 2 /* GP_ERR_PROGRAM */);
+      if (hits_row) *hits_row = ~0ull;
+    }
+    return;
+  }
+  if (!hits_row || !a.target_bits) return;
+  hits = __reduce_add_sync(0xffffffffu, hits);  // integer sums: any order gives the same count
+  if (lane == 0) *hits_row = hits;
+}
+
+// dynamic shared memory of eval_bool_warps_kernel
+inline size_t bool_warps_smem(int k, int block, int n_inputs, int64_t n_words, int prog_cap) {
+  const int64_t pass_words = 32 * (int64_t)k;
+  const int64_t n_pass = (n_words + pass_words - 1) / pass_words;
+  return sizeof(uint32_t) * (size_t)(n_pass * n_inputs * pass_words) +
+         (size_t)(block / 32) * (size_t)(prog_cap + 1) * sizeof(uint4);
 }
 
 }  // namespace gpdev

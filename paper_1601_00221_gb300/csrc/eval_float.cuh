@@ -127,7 +127,7 @@ __device__ __forceinline__ uint32_t input_fields(uint32_t kind, uint32_t code) {
   if (code < (uint32_t)SF_NCODES) return bin((int)((code >> 2) / R));
   if (code < (uint32_t)SFX_UN_BASE) return bin(((int)code - SFX_BIN_BASE) / XB_NOPS / R);
   if (code < (uint32_t)SFX_IF_BASE) return ((int)code - SFX_UN_BASE) / XU_NOPS / R == UF_X ? 1u : 0u;
-  const int desc = xif_form_desc(((int)code - SFX_IF_BASE) / R);
+  const int desc = xif_form_desc_fast(((int)code - SFX_IF_BASE) / R);
   return (desc / 25 == 0 ? 1u : 0u) | ((desc / 5) % 5 == 0 ? 2u : 0u) | (desc % 5 == 0 ? 4u : 0u);
 }
 
@@ -442,7 +442,7 @@ __device__ __forceinline__ bool valid_instr_ext(uint32_t kind, const uint4& in, 
     return !(uform == UF_X && in.y >= nin);
   }
   const int c = (int)in.x - SFX_IF_BASE;
-  const int level = c % R, desc = xif_form_desc(c / R);
+  const int level = c % R, desc = xif_form_desc_fast(c / R);
   const int d[3] = {desc / 25, (desc / 5) % 5, desc % 5};
   const uint32_t pay[3] = {in.y, in.z, in.w};
   int m = 0;

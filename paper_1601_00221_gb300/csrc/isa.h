@@ -103,6 +103,26 @@ GPISA_HD constexpr int xif_form_desc(int idx) {  // inverse: dc*25 + da*5 + db
   return -1;
 }
 constexpr int SFX_IF_FORMS = 38;
+// xif_form_desc without the scan, for the kernels' per-instruction decoding:
+// the 38 descriptors (7 bits each) packed nine to a 64-bit constant
+GPISA_HD constexpr uint64_t xif_desc_pack(int first) {
+  uint64_t w = 0;
+  for (int j = 0; j < 9 && first + j < SFX_IF_FORMS; ++j) w |= (uint64_t)xif_form_desc(first + j) << (7 * j);
+  return w;
+}
+GPISA_HD constexpr int xif_form_desc_fast(int idx) {  // idx in [0, SFX_IF_FORMS)
+  constexpr uint64_t w0 = xif_desc_pack(0), w1 = xif_desc_pack(9), w2 = xif_desc_pack(18);
+  constexpr uint64_t w3 = xif_desc_pack(27), w4 = xif_desc_pack(36);
+  const int q = idx / 9;
+  const uint64_t w = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : q == 3 ? w3 : w4;
+  return (int)((w >> (7 * (idx - 9 * q))) & 127u);
+}
+GPISA_HD constexpr bool xif_fast_matches() {
+  for (int i = 0; i < SFX_IF_FORMS; ++i)
+    if (xif_form_desc_fast(i) != xif_form_desc(i)) return false;
+  return true;
+}
+static_assert(xif_fast_matches(), "packed IF descriptors differ from the scan");
 GPISA_HD constexpr int sfx_if_code(int iform, int level) { return SFX_IF_BASE + iform * R + level; }
 constexpr int SFX_NCODES = SFX_IF_BASE + SFX_IF_FORMS * R;  // 1280
 
@@ -166,6 +186,23 @@ GPISA_HD constexpr int if_form_desc(int idx) {  // inverse: returns dc*16+da*4+d
   return -1;
 }
 constexpr int BOOL_IF_FORMS = 16;
+// if_form_desc without the scan: the 16 descriptors (6 bits each) packed
+// eight to a 64-bit constant
+GPISA_HD constexpr uint64_t if_desc_pack(int first) {
+  uint64_t w = 0;
+  for (int j = 0; j < 8; ++j) w |= (uint64_t)if_form_desc(first + j) << (6 * j);
+  return w;
+}
+GPISA_HD constexpr int if_form_desc_fast(int idx) {  // idx in [0, BOOL_IF_FORMS)
+  constexpr uint64_t lo = if_desc_pack(0), hi = if_desc_pack(8);
+  return (int)(((idx < 8 ? lo : hi) >> (6 * (idx & 7))) & 63u);
+}
+GPISA_HD constexpr bool if_fast_matches() {
+  for (int i = 0; i < BOOL_IF_FORMS; ++i)
+    if (if_form_desc_fast(i) != if_form_desc(i)) return false;
+  return true;
+}
+static_assert(if_fast_matches(), "packed IF descriptors differ from the scan");
 GPISA_HD constexpr int bool_if_code(int iform, int level) { return BOOL_IF_BASE + iform * R + level; }
 constexpr int BOOL_MOVX = BOOL_IF_BASE + BOOL_IF_FORMS * R;  // 288
 constexpr int BOOL_NCODES = BOOL_MOVX + 1;

@@ -102,4 +102,7 @@ cudaError_t launch_bool_seg(const BoolArgs& a, const SegTable& t, int k, int blo
                             cudaStream_t s);
 // Boolean, one program per lane over w <= 4 words (one warp per block).
 cudaError_t launch_bool_lanes(const BoolArgs& a, int w, int grid, size_t smem, cudaStream_t s);
+// Boolean, a warp per program (block / 32 programs per block over one staged
+// case set); smem = bool_warps_smem
+cudaError_t launch_bool_warps(const BoolArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s);
 }  // namespace gpdev

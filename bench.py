@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--stack-table", action="store_true",
                     help="print the percentages of programs each stack limit evaluates (host only) and exit")
     ap.add_argument("--once", choices=["c2", "c2_512", "sextic512", "shuttle512", "shuttle512_rpn", "mux20",
-                                       "linear512"], default=None,
+                                       "mux11", "linear512"], default=None,
                     help="evaluate one workload twice and exit (the cases of the ncu "
                          "captures): c2 = the timed workload at the timed shape (4096 trees x "
                          "65536 cases, K = 8, block 256, 65536 cases per block); c2_512 = its "
@@ -69,6 +69,8 @@ def parse():
                          "58000 cases, extended S-form (RPN) interpreter, K = 8, block 512; "
                          "sextic512 = 512 sextic trees x 100000 cases, extended "
                          "interpreter; mux20 = 128 20-multiplexer trees x 2^20 cases, Boolean; "
+                         "mux11 = 4096 11-multiplexer trees x 2048 cases, a warp per program, "
+                         "K = 2, block 256; "
                          "linear512 = 512 register programs x 262144 cases x 8 inputs, register "
                          "file in shared memory, K = 4, block 256 (all with the program buffer "
                          "sized to the population)")
@@ -164,6 +166,16 @@ def run_once(args):
         for _ in range(2):
             f = gp.eval_population(P, O, L, X, Y, config=cfg)
         out = float(f[0])
+    elif args.once == "mux11":
+        b = synth.boolean_problem("mux", 11, n_progs=4096)
+        enc = gp.encode_population(b.pop.words, b.pop.offsets, b.pop.lengths, gp.KIND_BOOL)
+        P, O, L = enc.to_device("cuda")
+        cb = torch.from_numpy(b.case_bits.view(np.int32)).cuda()
+        tb = torch.from_numpy(b.target_bits.view(np.int32)).cuda()
+        cfg = gp.Config(gp.VARIANT_WARPS, 2, 256, 0, 0, 0, 0, enc.max_instructions)
+        for _ in range(2):
+            h = gp.eval_population_bool(P, O, L, cb, b.n_cases, tb, config=cfg)
+        out = int(h[0])
     else:
         b = synth.boolean_problem("mux", 20, n_progs=128)
         enc = gp.encode_population(b.pop.words, b.pop.offsets, b.pop.lengths, gp.KIND_BOOL)

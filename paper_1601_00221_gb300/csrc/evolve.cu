@@ -256,6 +256,13 @@ struct EncArgs {
   unsigned long long* node_total;  // may be null: adds the nodes of every tree encoded
 };
 
+// gpisa::xif_form_index by the valid-descriptor masks (no scan)
+__device__ __forceinline__ int xif_index(int dc, int da, int db) {
+  constexpr uint64_t lo = xif_valid_mask(0), hi = xif_valid_mask(64);
+  const int t = dc * 25 + da * 5 + db;
+  return t < 64 ? __popcll(lo & ((1ull << t) - 1)) : __popcll(lo) + __popcll(hi & ((1ull << (t - 64)) - 1));
+}
+
 __device__ int xbin(uint32_t op) {
   return op == GP_OP_GT ? XB_GT : op == GP_OP_LT ? XB_LT : op == GP_OP_EQ ? XB_EQ
                                 : op == GP_OP_AND ? XB_AND : XB_OR;
@@ -337,7 +344,7 @@ __device__ __forceinline__ uint4 enc_instruction(const EncScratch& s, int v, int
     const int uf = k0 == 0 ? UF_X : k0 == 1 ? UF_C : UF_S;
     code = (uint32_t)sfx_un_code(uf, l, (int)(op - GP_OP_SIN));
   } else if (ar == 3) {
-    code = (uint32_t)sfx_if_code(xif_form_index(k0, k1, k2), l);
+    code = (uint32_t)sfx_if_code(xif_index(k0, k1, k2), l);
   } else {
     // forms by (a, b): X X, X C, C X, C C, S0 X, X S0, S0 C, C S0, S0 S1, S1 S0
     int form;

@@ -123,6 +123,32 @@ GPISA_HD constexpr bool xif_fast_matches() {
   return true;
 }
 static_assert(xif_fast_matches(), "packed IF descriptors differ from the scan");
+// xif_form_index without the scan: bit t of the 128-bit mask (lo, hi) is set
+// for each valid descriptor t; the index is the number of set bits below t
+GPISA_HD constexpr uint64_t xif_valid_mask(int first) {
+  uint64_t m = 0;
+  for (int j = 0; j < 64 && first + j < 125; ++j) {
+    const int t = first + j;
+    if (xif_desc_valid(t / 25, (t / 5) % 5, t % 5)) m |= (uint64_t)1 << j;
+  }
+  return m;
+}
+GPISA_HD constexpr int popcount64_c(uint64_t x) {  // (constant evaluation only)
+  int c = 0;
+  for (; x; x &= x - 1) ++c;
+  return c;
+}
+GPISA_HD constexpr bool xif_masks_match() {
+  for (int t = 0; t < 125; ++t) {
+    const uint64_t lo = xif_valid_mask(0), hi = xif_valid_mask(64);
+    const int idx = t < 64 ? popcount64_c(lo & (((uint64_t)1 << t) - 1))
+                           : popcount64_c(lo) + popcount64_c(hi & (((uint64_t)1 << (t - 64)) - 1));
+    if (xif_desc_valid(t / 25, (t / 5) % 5, t % 5) && idx != xif_form_index(t / 25, (t / 5) % 5, t % 5))
+      return false;
+  }
+  return true;
+}
+static_assert(xif_masks_match(), "the valid-descriptor masks do not give the scan's index");
 GPISA_HD constexpr int sfx_if_code(int iform, int level) { return SFX_IF_BASE + iform * R + level; }
 constexpr int SFX_NCODES = SFX_IF_BASE + SFX_IF_FORMS * R;  // 1280
 

@@ -35,10 +35,12 @@ DEVICE_ENCODE_MAX_NODES = 256  # GP_DEVICE_ENCODE_MAX_NODES
 class GenerationGraph:
     def __init__(self, n_progs: int, max_tokens: int, cases, targets, config: Optional[Config] = None,
                  kind: int = KIND_SFORM, order: int = ORDER_MIN_DEPTH, device="cuda",
-                 device_encode: bool = False):
+                 device_encode: bool = False, shared_cases: Optional["GenerationGraph"] = None):
         """n_progs: population size; max_tokens: the largest total number of
         user-format words of any population to be evaluated; cases/targets:
-        host arrays, binary32 [n_inputs, n_cases] and [n_cases]."""
+        host arrays, binary32 [n_inputs, n_cases] and [n_cases] (ignored when
+        shared_cases, another graph on the same device, lends its resident
+        copy)."""
         import torch
         self.torch = torch
         self.n = int(n_progs)
@@ -48,11 +50,15 @@ class GenerationGraph:
             raise ValueError("the device-side encoder writes the S-form only")
         self.max_tokens = int(max_tokens)
         self.device = torch.device(device)
-        x = np.ascontiguousarray(cases, np.float32)
-        x = x[None, :] if x.ndim == 1 else x
-        self.n_inputs, self.n_cases = int(x.shape[0]), int(x.shape[1])
-        self.X = torch.from_numpy(x).to(self.device)
-        self.Y = torch.from_numpy(np.ascontiguousarray(targets, np.float32)).to(self.device)
+        if shared_cases is not None:
+            self.X, self.Y = shared_cases.X, shared_cases.Y
+            self.n_inputs, self.n_cases = shared_cases.n_inputs, shared_cases.n_cases
+        else:
+            x = np.ascontiguousarray(cases, np.float32)
+            x = x[None, :] if x.ndim == 1 else x
+            self.n_inputs, self.n_cases = int(x.shape[0]), int(x.shape[1])
+            self.X = torch.from_numpy(x).to(self.device)
+            self.Y = torch.from_numpy(np.ascontiguousarray(targets, np.float32)).to(self.device)
         self.cap = 4 * self.n + 4 * int(max_tokens)
         pin = lambda n, dt: torch.empty(n, dtype=dt).pin_memory()
         self.h_words = pin(self.cap, torch.int32)
@@ -65,6 +71,8 @@ class GenerationGraph:
         self.d_fit = torch.empty(self.n, dtype=torch.float64, device=self.device)
         self.cfg = config or Config(VARIANT_REGISTER, 8, 256, 0)
         self.stream = torch.cuda.Stream(device=self.device)
+        self.done = torch.cuda.Event()
+        self.pending = False  # a replay whose fitness has not been collected
         self.graph = None
         self.nodes = 0
         if self.device_encode:
@@ -154,14 +162,85 @@ class GenerationGraph:
             self._device_work()
         return self
 
-    def run(self, words, offsets, lengths) -> np.ndarray:
-        """Fitness (host float64 [n_progs]) of one generation's population."""
+    def launch(self, words, offsets, lengths) -> None:
+        """Stages one population into the pinned buffers and replays the graph
+        on this graph's stream without waiting for it; `collect` returns its
+        fitness.  A launch first waits for the previous replay of this graph
+        (its pinned buffers are about to be overwritten); that replay's
+        fitness must have been collected."""
+        if self.pending:
+            raise RuntimeError("collect the previous launch's fitness first")
         if self.graph is None:
             self.capture(words, offsets, lengths)
-        if len(lengths) != self.n:
+        elif len(lengths) != self.n:
             raise ValueError("population size differs from the graph's")
-        self._encode(words, offsets, lengths)
-        self.graph.replay()
-        self.torch.cuda.current_stream().synchronize()
-        self.stream.synchronize()
+        else:
+            self._encode(words, offsets, lengths)
+        with self.torch.cuda.stream(self.stream):
+            self.graph.replay()
+            self.done.record(self.stream)
+        self.pending = True
+
+    def collect(self) -> np.ndarray:
+        """Fitness (host float64 [n_progs]) of the last launch."""
+        if not self.pending:
+            raise RuntimeError("nothing launched")
+        self.done.synchronize()
+        self.pending = False
         return self.h_fit.numpy().copy()
+
+    def run(self, words, offsets, lengths) -> np.ndarray:
+        """Fitness (host float64 [n_progs]) of one generation's population."""
+        self.launch(words, offsets, lengths)
+        return self.collect()
+
+
+class EvaluationPipeline:
+    """Independent populations of one size (the generations of several GP
+    runs, a queue of evaluation requests) through `depth` generation graphs
+    in turn, each on its own stream: while one population evaluates, the
+    host stages the next into another graph's pinned buffers and that
+    graph's copy and device encoding run beside the evaluation, so a stream
+    of populations approaches the evaluation's own rate.  Every population
+    still crosses the host-device boundary both ways (trees in, fitness
+    out).  The graphs share one resident copy of the cases.
+
+        pipe = EvaluationPipeline(n, max_tokens, cases, targets, device_encode=True)
+        for pop in populations:
+            for ticket, fit in pipe.submit(pop.words, pop.offsets, pop.lengths):
+                ...   # results that finished, in submission order
+        for ticket, fit in pipe.drain():
+            ...
+    """
+
+    def __init__(self, n_progs: int, max_tokens: int, cases, targets, depth: int = 2, **kwargs):
+        if depth < 1:
+            raise ValueError("depth must be at least 1")
+        first = GenerationGraph(n_progs, max_tokens, cases, targets, **kwargs)
+        self.graphs = [first] + [GenerationGraph(n_progs, max_tokens, None, None, shared_cases=first, **kwargs)
+                                 for _ in range(depth - 1)]
+        self.next_ticket = 0
+        self.inflight = []  # (ticket, graph) in submission order
+
+    def submit(self, words, offsets, lengths):
+        """Launches one population; returns the (ticket, fitness) pairs of the
+        populations that had to be collected to free a graph (at most one),
+        oldest first.  Tickets count submissions from 0."""
+        out = []
+        g = self.graphs[self.next_ticket % len(self.graphs)]
+        if g.pending:  # the oldest launch holds this graph
+            t, og = self.inflight.pop(0)
+            assert og is g
+            out.append((t, g.collect()))
+        g.launch(words, offsets, lengths)
+        self.inflight.append((self.next_ticket, g))
+        self.next_ticket += 1
+        return out
+
+    def drain(self):
+        """(ticket, fitness) of every population still in flight, oldest first."""
+        out = []
+        while self.inflight:
+            t, g = self.inflight.pop(0)
+            out.append((t, g.collect()))
+        return out

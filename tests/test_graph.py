@@ -85,3 +85,49 @@ def test_device_encoding_graph_matches_host_encoding(funcs, n_inputs, fitness):
         a = gh.run(words, offsets, pop.lengths)
         b = gd.run(words, offsets, pop.lengths)
         assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+@pytest.mark.parametrize("depth,device_encode", [(2, True), (3, False), (1, True)])
+def test_pipeline_results_match_each_population(depth, device_encode):
+    """Different populations submitted back to back through the pipeline's
+    graphs: every ticket's fitness is that population's own (a result from
+    another slot, or a slot overwritten before its copy finished, would
+    differ), bit-identical to the direct evaluation, in submission order."""
+    from paper_1601_00221_gb300.graph import EvaluationPipeline
+    n, n_cases = 400, 7000
+    x = synth.uniform_cases(205, 1, n_cases)
+    y = synth.quartic_target(x[0])
+    pops = [synth.pack(synth.ramped_half_and_half(340 + g, n, 2, 8, 255)) for g in range(7)]
+    max_tokens = max(int(p.lengths.sum()) for p in pops)
+    cfg = gp.Config(gp.VARIANT_REGISTER, 8, 256, 0)
+    refs = []
+    for pop in pops:
+        enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+        P, O, L = upload(enc)
+        refs.append(gp.eval_population(P, O, L, dev(x), dev(y), config=cfg).cpu().numpy())
+    pipe = EvaluationPipeline(n, max_tokens, x, y, depth=depth, config=cfg, device_encode=device_encode)
+    got = []
+    for pop in pops:
+        got += pipe.submit(pop.words, pop.offsets, pop.lengths)
+        assert len(pipe.inflight) <= depth
+    got += pipe.drain()
+    assert [t for t, _ in got] == list(range(len(pops)))
+    for t, fit in got:
+        assert np.array_equal(fit.view(np.uint64), refs[t].view(np.uint64)), t
+    assert pipe.drain() == []
+
+
+def test_graph_launch_needs_collect():
+    """A graph launched twice without collecting in between refuses: its
+    pinned buffers still hold the launch in flight."""
+    x = synth.uniform_cases(206, 1, 2000)
+    y = synth.quartic_target(x[0])
+    pop = synth.pack(synth.ramped_half_and_half(350, 64, 2, 6, 63))
+    gg = GenerationGraph(64, int(pop.lengths.sum()), x, y)
+    gg.launch(pop.words, pop.offsets, pop.lengths)
+    with pytest.raises(RuntimeError):
+        gg.launch(pop.words, pop.offsets, pop.lengths)
+    first = gg.collect()
+    with pytest.raises(RuntimeError):
+        gg.collect()
+    assert np.array_equal(first.view(np.uint64), gg.run(pop.words, pop.offsets, pop.lengths).view(np.uint64))

@@ -3,11 +3,18 @@
 #include "launch.h"
 
 namespace gpdev {
+template <int K, bool COMPACT>
+static void launch_kc(const BoolArgs& a, int block, int grid, size_t smem, cudaStream_t s) {
+  static std::atomic<size_t> configured{0};
+  ensure_dynamic_smem(eval_bool_kernel<K, COMPACT>, smem, configured);
+  eval_bool_kernel<K, COMPACT><<<grid, block, smem, s>>>(a);
+}
+// the listing kernel when a block runs at least four passes (its own check
+// decides per block; segments always take it)
 template <int K>
 static void launch_k(const BoolArgs& a, int block, int grid, size_t smem, cudaStream_t s) {
-  static std::atomic<size_t> configured{0};
-  ensure_dynamic_smem(eval_bool_kernel<K>, smem, configured);
-  eval_bool_kernel<K><<<grid, block, smem, s>>>(a);
+  if (a.chunk_words >= 4 * (int64_t)block * K) launch_kc<K, true>(a, block, grid, smem, s);
+  else launch_kc<K, false>(a, block, grid, smem, s);
 }
 
 cudaError_t launch_bool(const BoolArgs& a, int k, int block, int grid, size_t smem, cudaStream_t s) {

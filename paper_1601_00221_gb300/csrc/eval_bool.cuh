@@ -101,9 +101,26 @@ __device__ __forceinline__ bool valid_bool_instr(const uint4& in, int n_inputs) 
   return false;
 }
 
+// which payload words of a (validated) Boolean instruction are input
+// indices: bit 0 = y, bit 1 = z, bit 2 = w
+__device__ __forceinline__ uint32_t bool_input_fields(uint32_t code) {
+  using namespace gpisa;
+  if (code < (uint32_t)BOOL_IF_BASE) {
+    const int form = (int)(code >> 2) / R;
+    return (form == BF_XX ? 3u : 0u) | (form == BF_XS ? 1u : 0u) | (form == BF_SX ? 2u : 0u);
+  }
+  if (code < (uint32_t)BOOL_MOVX) {
+    const int desc = if_form_desc_fast((int)(code - BOOL_IF_BASE) / R);
+    return (desc / 16 == 0 ? 1u : 0u) | ((desc / 4) % 4 == 0 ? 2u : 0u) | (desc % 4 == 0 ? 4u : 0u);
+  }
+  return 1u;  // MOVX
+}
+
 // SEG: the block's population, cases and hit counts come from segment table
 // t (eval_float.cuh's SegTable: Boolean segments hold words); otherwise from a.
-template <int K, bool SEG>
+// COMPACT: a block of at least four passes stages only the inputs its
+// program reads (the listing's shared arrays exist in these kernels only).
+template <int K, bool SEG, bool COMPACT>
 __device__ __forceinline__ void eval_bool_block(const BoolArgs& a, const SegTable* t) {
   using namespace gpisa;
   // dynamic: the program (prog_cap instructions + the end sentinel), then the
@@ -170,6 +187,73 @@ __device__ __forceinline__ void eval_bool_block(const BoolArgs& a, const SegTabl
     return;
   }
 
+  // Inputs to stage: only those the program reads, in increasing order (slot
+  // s holds input list_s[s]), its input payloads rewritten to slots -- as the
+  // float kernels do.  Every pass stages its words of each listed input only.
+  // Blocks of fewer than four passes stage every input: the listing's
+  // barriers and atomics cost them more than the copies they save (measured:
+  // one pass per block, 11- and 13-input sets 11-15% slower listed; sixteen,
+  // the 20-multiplexer 8% faster), and launches whose chunks are that short
+  // take the kernel without the listing (its shared arrays and code cost
+  // those sets 6% even unused, measured).
+  int n_stage = a_n_inputs;
+  bool listed = false;
+  const uint32_t* list_p = nullptr;  // input of each staged slot when listed
+  if constexpr (COMPACT) {
+    __shared__ uint32_t used_s[GP_COMPACT_MAX_INPUTS / 32];    // bitmap of the inputs the program reads
+    __shared__ uint32_t before_s[GP_COMPACT_MAX_INPUTS / 32];  // set bits in earlier words
+    __shared__ uint32_t list_s[GP_COMPACT_MAX_LIST];
+    __shared__ int n_stage_s;
+    list_p = list_s;
+    if (a_n_inputs <= GP_COMPACT_MAX_INPUTS && a_chunk_words >= 4 * (int64_t)blockDim.x * K) {
+      const int nw = (a_n_inputs + 31) >> 5;
+      for (int i = tid; i < nw; i += blockDim.x) used_s[i] = 0u;
+      __syncthreads();
+      for (int i = tid; i < n_instr; i += blockDim.x) {
+        const uint4 in = prog_s[i];
+        const uint32_t f = bool_input_fields(in.x);
+        if (f & 1u) atomicOr(&used_s[in.y >> 5], 1u << (in.y & 31));
+        if (f & 2u) atomicOr(&used_s[in.z >> 5], 1u << (in.z & 31));
+        if (f & 4u) atomicOr(&used_s[in.w >> 5], 1u << (in.w & 31));
+      }
+      __syncthreads();
+      if (tid == 0) {
+        uint32_t c = 0;
+        for (int i = 0; i < nw; ++i) {
+          before_s[i] = c;
+          c += (uint32_t)__popc(used_s[i]);
+        }
+        n_stage_s = (int)c;
+      }
+      __syncthreads();
+      if (n_stage_s <= GP_COMPACT_MAX_LIST) {  // (block-uniform)
+        n_stage = n_stage_s;
+        listed = true;
+        auto slot = [&](uint32_t v) {
+          return before_s[v >> 5] + (uint32_t)__popc(used_s[v >> 5] & ((1u << (v & 31)) - 1u));
+        };
+        for (int i = tid; i < n_instr; i += blockDim.x) {
+          uint4 in = prog_s[i];
+          const uint32_t f = bool_input_fields(in.x);
+          if (f & 1u) in.y = slot(in.y);
+          if (f & 2u) in.z = slot(in.z);
+          if (f & 4u) in.w = slot(in.w);
+          prog_s[i] = in;
+        }
+        for (int i = tid; i < nw; i += blockDim.x) {
+          uint32_t m = used_s[i];
+          uint32_t s0 = before_s[i];
+          while (m) {
+            const int b = __ffs(m) - 1;
+            list_s[s0++] = (uint32_t)(i * 32 + b);
+            m &= m - 1u;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+
   const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
   const int64_t w_begin = (int64_t)chunk * a_chunk_words;
   int64_t w_end = w_begin + a_chunk_words;
@@ -193,8 +277,8 @@ __device__ __forceinline__ void eval_bool_block(const BoolArgs& a, const SegTabl
       // (16-, 8- or 4-byte aligned: rows aligned, w0 a multiple of K): all
       // inputs in one global round trip, no registers held.  A lane reads
       // back only its own words, so its own wait suffices.
-      for (; v < a_n_inputs; ++v) {
-        const uint32_t* src = a_case_bits + (int64_t)v * a_n_words + w0;
+      for (; v < n_stage; ++v) {
+        const uint32_t* src = a_case_bits + (int64_t)(listed ? list_p[v] : (uint32_t)v) * a_n_words + w0;
         uint32_t* dst = tile + v * 32 * K;
         if constexpr (K == 8) {
           __pipeline_memcpy_async(dst, src, 16);
@@ -206,9 +290,10 @@ __device__ __forceinline__ void eval_bool_block(const BoolArgs& a, const SegTabl
       __pipeline_commit();
       __pipeline_wait_prior(0);
     }
-    for (; v < a_n_inputs; ++v) {
+    for (; v < n_stage; ++v) {
       UVec<K> tv;
-      uload<K>(tv, a_case_bits + (int64_t)v * a_n_words, w0, a_n_words, full && a_aligned);
+      uload<K>(tv, a_case_bits + (int64_t)(listed ? list_p[v] : (uint32_t)v) * a_n_words, w0, a_n_words,
+               full && a_aligned);
 #pragma unroll
       for (int j = 0; j < K; ++j) tile[v * 32 * K + j] = tv.w[j];
     }
@@ -252,15 +337,15 @@ __device__ __forceinline__ void eval_bool_block(const BoolArgs& a, const SegTabl
 #undef GP_SEG
 }
 
-template <int K>
+template <int K, bool COMPACT>
 __global__ void __launch_bounds__(256) eval_bool_kernel(BoolArgs a) {
-  eval_bool_block<K, false>(a, nullptr);
+  eval_bool_block<K, false, COMPACT>(a, nullptr);
 }
 
 // several populations in one launch; each segment's hits are zero before it
 template <int K>
 __global__ void __launch_bounds__(256) eval_bool_seg_kernel(BoolArgs a, const __grid_constant__ SegTable t) {
-  eval_bool_block<K, true>(a, &t);
+  eval_bool_block<K, true, true>(a, &t);
 }
 
 }  // namespace gpdev

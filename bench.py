@@ -68,7 +68,8 @@ def parse():
                          "first 512 trees, same shape; shuttle512 (_rpn) = 512 Shuttle-shaped trees x "
                          "58000 cases, extended S-form (RPN) interpreter, K = 8, block 512; "
                          "sextic512 = 512 sextic trees x 100000 cases, extended "
-                         "interpreter; mux20 = 128 20-multiplexer trees x 2^20 cases, Boolean; "
+                         "interpreter; mux20 = 128 20-multiplexer trees x 2^20 cases, Boolean, K = 4, "
+                         "block 128, 8192 words per block; "
                          "mux11 = 4096 11-multiplexer trees x 2048 cases, a warp per program, "
                          "K = 2, block 256; "
                          "linear512 = 512 register programs x 262144 cases x 8 inputs, register "
@@ -182,7 +183,7 @@ def run_once(args):
         P, O, L = enc.to_device("cuda")
         cb = torch.from_numpy(b.case_bits.view(np.int32)).cuda()
         tb = torch.from_numpy(b.target_bits.view(np.int32)).cuda()
-        cfg = gp.Config(gp.VARIANT_REGISTER, 0, 0, 0, 0, 0, 0, enc.max_instructions)  # default K, block
+        cfg = gp.Config(gp.VARIANT_REGISTER, 4, 128, 8192, 0, 0, 0, enc.max_instructions)  # the tuner's shape
         for _ in range(2):
             h = gp.eval_population_bool(P, O, L, cb, b.n_cases, tb, config=cfg)
         out = int(h[0])

@@ -459,25 +459,49 @@ extern "C" int gp_encode_linear_population(const uint8_t* instr, const int64_t* 
       o[2] = (uint32_t)n;
       o[3] = 0;
       // Payload b carries flags for the interpreter with the registers in
-      // shared memory (the register variant ignores them): bit 0, operand a
-      // is the previous instruction's destination; bit 1, operand b is; bit
-      // 2, the result is overwritten before anything reads it from the
-      // register file (a read of the previous result through bit 0 or 1 does
-      // not count) and it is not register 0 at the end.  The liveness pass
-      // runs backwards from {register 0}.
-      uint32_t live = 1u;  // registers whose stored value a later read (or the output) needs
-      for (int32_t i = n - 1; i >= 0; --i) {
-        uint8_t d = ins[4 * i], op = ins[4 * i + 1], a = ins[4 * i + 2], b = ins[4 * i + 3];
-        const uint8_t pd = i > 0 ? ins[4 * (i - 1)] : 0xff;
-        const uint32_t fa = (i > 0 && a == pd) ? 1u : 0u, fb = (i > 0 && b == pd) ? 1u : 0u;
-        const uint32_t dead = (live >> d) & 1u ? 0u : 1u;
-        live &= ~(1u << d);
-        if (!fa) live |= 1u << a;
-        if (!fb) live |= 1u << b;
+      // shared memory (the register variant ignores them).  That
+      // interpreter keeps two values in machine registers: A, the previous
+      // instruction's result, and B, a value it loaded from the register
+      // file earlier.  Bits 0-1: where operand a comes from (0 the file, 1
+      // A, 2 B); bits 2-3: operand b likewise (at most one operand from A
+      // or B); bit 4: the result is
+      // overwritten before anything reads it from the file (a read from A
+      // or B does not count) and it is not register 0 at the end.
+      // Forward pass: A holds register d of the previous instruction; B
+      // holds the register whose value the body's fixed rules last loaded
+      // into B (operand a from the file is loaded into A, or into B when b
+      // is A; operand b from the file into B, or into A when a is B), valid
+      // until that register is written.
+      int a_reg = -1, b_reg = -1;
+      for (int32_t i = 0; i < n; ++i) {
+        const uint8_t d = ins[4 * i], op = ins[4 * i + 1], a = ins[4 * i + 2], b = ins[4 * i + 3];
+        auto src = [&](int r) -> uint32_t { return r == a_reg ? 1u : (r == b_reg ? 2u : 0u); };
+        // (both operands from A or B -- 6% of the instructions of random
+        // programs -- take b from the file: the interpreter has no bodies for
+        // them, which keeps its code small)
+        const uint32_t sa = src(a), sb = sa ? 0u : src(b);
+        int nb = b_reg;
+        if (sa == 0 && sb == 0) nb = b;
+        else if (sa == 0 && sb == 1) nb = a;
+        else if (sa == 1 && sb == 0) nb = b;
+        a_reg = d;
+        b_reg = nb == d ? -1 : nb;
         o[4 + 4 * i] = (uint32_t)lin_code(op - GP_OP_ADD, a, b);
         o[5 + 4 * i] = d;
-        o[6 + 4 * i] = fa | (fb << 1) | (dead << 2);
+        o[6 + 4 * i] = sa | (sb << 2);
         o[7 + 4 * i] = 0;
+      }
+      // Backward pass from {register 0}: registers whose value in the file
+      // a later read from the file (or the output) needs.
+      uint32_t live = 1u;
+      for (int32_t i = n - 1; i >= 0; --i) {
+        const uint8_t d = ins[4 * i], a = ins[4 * i + 2], b = ins[4 * i + 3];
+        const uint32_t f = o[6 + 4 * i];
+        const uint32_t dead = (live >> d) & 1u ? 0u : 1u;
+        live &= ~(1u << d);
+        if ((f & 3u) == 0) live |= 1u << a;
+        if (((f >> 2) & 3u) == 0) live |= 1u << b;
+        o[6 + 4 * i] = f | (dead << 4);
       }
       out_offsets[p] = pos;
       out_lengths[p] = (int32_t)words;

@@ -8,11 +8,14 @@
 // file lives in shared memory, [register][chunk][lane][chunk bytes] per warp
 // (a warp's access to one chunk of one register is conflict-free), and an
 // instruction is one jump on its function: its operand and destination
-// registers are shared-memory addresses computed from the code.  Each pass
-// stages the lane's K cases of the first min(n_inputs, 8) inputs straight
-// into registers 0.. by asynchronous copies (the initial register values of
-// the register machine: r[i] = input i, the rest 0), runs the program and
-// reads register 0.  The kernel needs few registers, so shared memory alone
+// registers are shared-memory addresses computed from the code.  Two values
+// stay in machine registers, A (the previous result) and B (a value loaded
+// earlier), and the encoder's flags take an operand from either instead of
+// the file and skip the store of a result no later instruction reads from
+// the file.  Each pass stages the lane's K cases of the first
+// min(n_inputs, 8) inputs straight into registers 0.. by asynchronous copies
+// (the initial register values of the register machine: r[i] = input i, the
+// rest 0), runs the program and reads register 0.  The kernel needs few registers, so shared memory alone
 // bounds its warps per multiprocessor.  Fitness is formed and reduced as in
 // the other float kernels (per-case error in binary32, compensated per-thread
 // sums, warp, block, binary64 across blocks).
@@ -92,14 +95,35 @@ __global__ void __launch_bounds__(256, rf_min_blocks<K>()) eval_linear_rf_kernel
       const uint4 in = g[i];
       prog_s[i] = in;
       ok &= valid_instr(K_LINEAR, in, a.n_inputs) ? 1 : 0;
-      // the flags (payload b): at most bits 0..2, and a forwarded operand
-      // must be the previous instruction's destination
-      const uint32_t pd = i > 0 ? g[i - 1].y : 0xffffffffu;
-      const uint32_t ra = (in.x >> 3) & 7u, rb = in.x & 7u;
-      ok &= (in.z < 8u && (!(in.z & 1u) || ra == pd) && (!(in.z & 2u) || rb == pd)) ? 1 : 0;
+      ok &= in.z < 32u ? 1 : 0;  // the flags (payload b): bits 0..4
     }
-    if (tid == 0) prog_s[n_instr] = make_uint4(LIN_NCODES, 0u, 8u, 0u);  // the sentinel: dispatch index 32
+    if (tid == 0) prog_s[n_instr] = make_uint4(LIN_NCODES, 0u, 32u, 0u);  // the sentinel: dispatch index 128
     bad = !__syncthreads_and(ok);
+    if (!bad) {
+      // an operand taken from A or B must be the register that A or B holds:
+      // one thread replays the encoder's forward pass on the flags as given
+      // (the body's load rules decide what B holds next)
+      if (tid == 0) {
+        int a_reg = -1, b_reg = -1, good = 1;
+        for (int i = 0; i < n_instr; ++i) {
+          const uint4 in = prog_s[i];
+          const int ra = (int)((in.x >> 3) & 7u), rb = (int)(in.x & 7u), d = (int)in.y;
+          const uint32_t sa = in.z & 3u, sb = (in.z >> 2) & 3u;
+          good &= (sa == 0u || (sa == 1u && ra == a_reg) || (sa == 2u && ra == b_reg)) ? 1 : 0;
+          good &= (sb == 0u || (sb == 1u && rb == a_reg) || (sb == 2u && rb == b_reg)) ? 1 : 0;
+          good &= (sa == 0u || sb == 0u) ? 1 : 0;  // (at most one operand held)
+          int nb = b_reg;
+          if (sa == 0u && sb == 0u) nb = rb;
+          else if (sa == 0u && sb == 1u) nb = ra;
+          else if (sa == 1u && sb == 0u) nb = rb;
+          a_reg = d;
+          b_reg = nb == d ? -1 : nb;
+        }
+        meta_s = good;
+      }
+      __syncthreads();
+      bad = meta_s == 0;
+    }
   }
 
   CSum acc = {0.0f, 0.0f};

@@ -945,15 +945,19 @@ class LinearRFGen:
     base + r * RSTRIDE + q * 32 * CB (chunk q of CB bytes; the lanes of a warp
     side by side, so a warp's access to one chunk is conflict-free).  One
     dispatch per instruction, on (flags, function): index = pb * 4 + (code >> 6)
-    & 3, where the second payload pb holds the encoder's flags -- bit 0: a is
-    the previous instruction's destination, bit 1: b is, bit 2: the result is
-    overwritten before it is read again (and is not register 0 at the end) --
-    and the sentinel after the program has pb = 8 (index 32, DONE).  A
-    forwarded operand is the previous result, still in the body's registers,
-    so it is not loaded; a dead result is not stored.  The operand and
-    destination registers are shared-memory addresses computed from the code
-    and the first payload.  Few registers: the kernel's warps are bounded by
-    shared memory alone.
+    & 3, where the second payload pb holds the encoder's flags -- bits 0-1:
+    where operand a is (0 the register file, 1 A, 2 B), bits 2-3: operand b
+    likewise (at most one of the two held), bit 4: the result is overwritten before anything reads it from
+    the file (and is not register 0 at the end) -- and the sentinel after the
+    program has pb = 32 (index 128, DONE).  Two values stay in machine
+    registers: A, the previous result, and B, which holds what the body's
+    rules last loaded into it (operand a from the file is loaded into A, or
+    into B when b is A; operand b from the file into B, or into A when a is
+    B); the encoder tracks what each holds, so an operand found there is not
+    loaded, and a dead result is not stored.  The operand and destination
+    registers are shared-memory addresses computed from the code and the
+    first payload.  Few registers: the kernel's warps are bounded by shared
+    memory alone.
     Operands: %0 bad (out, u32); %1 program address, %2 this lane's register
     file address (shared, u32)."""
 
@@ -1004,12 +1008,21 @@ class LinearRFGen:
         if K > 1:
             b("mov.b64 one2, 0x3F8000003F800000;")
             b("mov.b64 mone2, 0xBF800000BF800000;")
-        b("TBL: .branchtargets " + ", ".join(f"OP{i}" for i in range(32)) + ", DONE;")
+        # dispatch index = flags * 4 + function, flags = (source of a) |
+        # (source of b) << 2 | dead << 4, a source 0 the file, 1 A, 2 B, at
+        # most one of them held (the rest CBAD); the sentinel's flags are 32
+        # (index 128, DONE)
+        held = lambda sa, sb: sa == 3 or sb == 3 or (sa and sb)
+        labels = []
+        for idx in range(128):
+            sa, sb = (idx >> 2) & 3, (idx >> 4) & 3
+            labels.append("CBAD" if held(sa, sb) else f"OP{idx}")
+        b("TBL: .branchtargets " + ", ".join(labels) + ", DONE;")
         b("mov.u32 adr, %1;")
         b("mov.u32 base, %2;")
         b("mov.u32 %0, 0;")
         zero = "0f00000000" if K == 1 else "0"
-        for u in A:  # (defined before the first jump; a program never forwards into its first instruction)
+        for u in A + B:  # (defined before the first jump; the flags never read them unset)
             b(f"mov.{self.ty} {u}, {zero};")
         b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
         b("add.u32 adr, adr, 16;")
@@ -1018,39 +1031,57 @@ class LinearRFGen:
         b("shl.b32 ra, pb, 2;")
         b("add.u32 fn, fn, ra;")
         b("brx.idx.uni fn, TBL;")
-        for idx in range(32):
-            op, flags = idx & 3, idx >> 2
-            fa, fb, dead = flags & 1, (flags >> 1) & 1, (flags >> 2) & 1
+        for idx in range(128):
+            op, sa, sb, dead = idx & 3, (idx >> 2) & 3, (idx >> 4) & 3, (idx >> 6) & 1
+            if held(sa, sb):
+                continue
             b(f"OP{idx}:")
-            if not fa:
+            # where each operand is: a loaded operand a goes to A (to B when b
+            # is A), a loaded b to B (to A when a is B) -- the encoder's rules
+            la = A if sa == 0 and sb != 1 else (B if sa == 0 else None)
+            lb = B if sb == 0 and sa != 2 else (A if sb == 0 else None)
+            xa = la if sa == 0 else (A if sa == 1 else B)
+            xb = lb if sb == 0 else (A if sb == 1 else B)
+            if sa == 0:
                 b("bfe.u32 ra, code, 3, 3;")
                 b(f"mad.lo.u32 aa, ra, {self.rstride}, base;")
-            if not fb:
+            if sb == 0:
                 b("and.b32 rb, code, 7;")
                 b(f"mad.lo.u32 ab, rb, {self.rstride}, base;")
             if not dead:
                 b(f"mad.lo.u32 ad, pa, {self.rstride}, base;")
-            if fb:  # b is the previous result, in A
-                for i in range(H):
-                    b(f"mov.{self.ty} {B[i]}, {A[i]};")
-            else:
-                self.load(B, "ab")
-            if not fa:
-                self.load(A, "aa")
+            if sb == 0:
+                self.load(lb, "ab")
+            if sa == 0:
+                self.load(la, "aa")
             b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
             b("add.u32 adr, adr, 16;")
-            if op == 3:
-                emit_pdiv(b, K, A, B, A, f"D{idx}_")
-                if not dead:
-                    self.store("ad", A)
-                b("bra.uni LOOP;")
-                emit_pdiv_slow(b, K, A, B, f"D{idx}_")
+            if op == 3:  # the division blocks below, one per operand placement
+                b(f"bra.uni DIV_{'A' if xa is A else 'B'}{'A' if xb is A else 'B'}{dead};")
             else:
                 for i in range(H):
-                    b(f"{F32[op] if K == 1 else F32X2[op]} {A[i]}, {A[i]}, {B[i]};")
+                    b(f"{F32[op] if K == 1 else F32X2[op]} {A[i]}, {xa[i]}, {xb[i]};")
                 if not dead:
                     self.store("ad", A)
                 b("bra.uni LOOP;")
+        # A <- a / b (protected) with a, b in A or B (not both held, so
+        # never the same register), then the store unless dead: shared blocks
+        # instead of the division in each division body (their code in every
+        # body cost the instruction cache)
+        for na, xa in (("A", A), ("B", B)):
+            for nb, xb in (("A", A), ("B", B)):
+                if na == nb:
+                    continue
+                for dead in (0, 1):
+                    tag = f"DIV_{na}{nb}{dead}"
+                    b(f"{tag}:")
+                    emit_pdiv(b, K, xa, xb, A, f"{tag}_")
+                    if not dead:
+                        self.store("ad", A)
+                    b("bra.uni LOOP;")
+                    emit_pdiv_slow(b, K, xa, xb, f"{tag}_")
+        b("CBAD:")
+        b("mov.u32 %0, 1;")
         b("DONE:")
         b("}")
         return b

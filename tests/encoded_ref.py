@@ -115,29 +115,39 @@ def _apply(op, a, b):
 def run_float(words, x, register_file=False):
     """Per-case outputs of an encoded float program (S-form, extended S-form,
     RPN or register).  register_file: run a register program the way the
-    shared-memory register-file interpreter does -- an operand flagged as the
-    previous result (payload b, bits 0 and 1) is taken from the previous
-    instruction instead of the register file, and a result flagged dead (bit
-    2) is not written to the register file -- so that wrong flags show as
-    wrong outputs."""
+    shared-memory register-file interpreter does -- two values held beside
+    the register file, A (the previous result) and B (what the load rules
+    last put there); payload b says where each operand is (bits 0-1 for a,
+    2-3 for b: 0 the file, 1 A, 2 B), an operand from the file is loaded into
+    A or B by the rules (a into A, or into B when b is A; b into B, or into A
+    when a is B), and a result flagged dead (bit 4) is not written to the
+    register file -- so that wrong flags show as wrong outputs."""
     x = np.asarray(x, np.float32)
     n_cases = x.shape[1]
     h = header(words)
     full = lambda v: np.full(n_cases, v, np.float32)
     if h["kind"] == 3:
         r = [x[i].copy() if i < x.shape[0] else full(0.0) for i in range(8)]
-        prev = full(np.nan)
+        A, B = full(np.nan), full(np.nan)
         for code, d, flags, _ in instrs(words):
             op, a, b = code // 64, (code // 8) % 8, code % 8
             if not register_file:
                 r[d] = _apply(op, r[a], r[b])
                 continue
-            assert flags < 8
-            va = prev if flags & 1 else r[a]
-            vb = prev if flags & 2 else r[b]
-            prev = _apply(op, va, vb)
-            if not flags & 4:
-                r[d] = prev
+            assert flags < 32
+            sa, sb = flags & 3, (flags >> 2) & 3
+            assert sa < 3 and sb < 3
+            va = r[a] if sa == 0 else (A if sa == 1 else B)
+            vb = r[b] if sb == 0 else (A if sb == 1 else B)
+            if sa == 0 and sb == 0:
+                B = vb
+            elif sa == 0 and sb == 1:
+                B = va
+            elif sa == 1 and sb == 0:
+                B = vb
+            A = _apply(op, va, vb)
+            if not flags & 16:
+                r[d] = A
         return r[0]
     S = [None] * R
     for code, pa, pb, pc in instrs(words):

@@ -197,13 +197,14 @@ def test_encoded_linear_matches_oracle():
 
 
 def test_register_file_flags_are_sound():
-    """The encoder's forwarding and dead-result flags: a program run with
-    forwarded operands taken from the previous result and dead results never
-    written gives the oracle's outputs, on programs full of repeated
-    registers (2 and 8 registers in use), with 3 to 11 inputs; and the flags
-    do fire (some operands forwarded, some results dead)."""
+    """The encoder's operand-source and dead-result flags: a program run with
+    operands taken from A (the previous result) or B (the value the load
+    rules last put there) and dead results never written gives the oracle's
+    outputs, on programs full of repeated registers (2 and 8 registers in
+    use), with 3 to 11 inputs; and the flags do fire (operands from A and
+    from B, dead results)."""
     x = synth.normal_cases(67, 11, 29)
-    fwd = dead = 0
+    fwd = from_b = dead = 0
     for seed, n_regs in ((68, 2), (69, 8), (70, 3)):
         pop = synth.linear_programs(seed, 60, 1, 90, n_regs=n_regs)
         enc = gp.encode_linear_population(pop.instr, pop.offsets, pop.lengths)
@@ -215,9 +216,11 @@ def test_register_file_flags_are_sound():
                                  oracle.linear_outputs(pop.program(p), xi)), (seed, n_in, p)
         flags = np.array([f for _, _, f, _ in (ins for p in range(pop.n) for ins in
                           ref.instrs(enc.words[enc.offsets[p]: enc.offsets[p] + enc.lengths[p]]))])
-        fwd += int(np.sum(flags & 3 != 0))
-        dead += int(np.sum(flags & 4 != 0))
-    assert fwd > 100 and dead > 100
+        fwd += int(np.sum(flags & 3 == 1) + np.sum((flags >> 2) & 3 == 1))
+        from_b += int(np.sum(flags & 3 == 2) + np.sum((flags >> 2) & 3 == 2))
+        dead += int(np.sum(flags & 16 != 0))
+        assert not np.any((flags & 3 != 0) & ((flags >> 2) & 3 != 0))  # at most one operand held
+    assert fwd > 100 and from_b > 100 and dead > 100
 
 
 @pytest.mark.parametrize("bad", [

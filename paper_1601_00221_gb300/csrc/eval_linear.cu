@@ -7,8 +7,9 @@
 // the file at K = 8 hold the kernel at 16 warps per multiprocessor.  Here the
 // file lives in shared memory, [register][chunk][lane][chunk bytes] per warp
 // (a warp's access to one chunk of one register is conflict-free), and an
-// instruction is one jump on its function: its operand and destination
-// registers are shared-memory addresses computed from the code.  Two values
+// instruction is one jump on its function and flags: its operand and
+// destination registers are byte offsets in the warp's file, which the block
+// writes into its staged copy of the program.  Two values
 // stay in machine registers, A (the previous result) and B (a value loaded
 // earlier), and the encoder's flags take an operand from either instead of
 // the file and skip the store of a result no later instruction reads from
@@ -123,6 +124,19 @@ __global__ void __launch_bounds__(256, rf_min_blocks<K>()) eval_linear_rf_kernel
       }
       __syncthreads();
       bad = meta_s == 0;
+    }
+    if (!bad) {
+      // the staged program in the interpreter's form: (dispatch index = flags
+      // * 4 + function, and the byte offsets in this warp's register file of
+      // the destination, operand a and operand b), so that a dispatch needs
+      // no decoding; the sentinel's index is 128
+      for (int i = tid; i < n_instr; i += blockDim.x) {
+        const uint4 in = prog_s[i];
+        prog_s[i] = make_uint4((in.z << 2) | ((in.x >> 6) & 3u), in.y * (uint32_t)L::RSTRIDE,
+                               ((in.x >> 3) & 7u) * (uint32_t)L::RSTRIDE, (in.x & 7u) * (uint32_t)L::RSTRIDE);
+      }
+      if (tid == 0) prog_s[n_instr] = make_uint4(128u, 0u, 0u, 0u);
+      __syncthreads();
     }
   }
 

@@ -944,20 +944,21 @@ class LinearRFGen:
     shared memory, this lane's K values of register r at
     base + r * RSTRIDE + q * 32 * CB (chunk q of CB bytes; the lanes of a warp
     side by side, so a warp's access to one chunk is conflict-free).  One
-    dispatch per instruction, on (flags, function): index = pb * 4 + (code >> 6)
-    & 3, where the second payload pb holds the encoder's flags -- bits 0-1:
+    dispatch per instruction, on (flags, function): index = flags * 4 +
+    function, where the encoder's flags (second payload) are -- bits 0-1:
     where operand a is (0 the register file, 1 A, 2 B), bits 2-3: operand b
     likewise (at most one of the two held), bit 4: the result is overwritten before anything reads it from
     the file (and is not register 0 at the end) -- and the sentinel after the
-    program has pb = 32 (index 128, DONE).  Two values stay in machine
+    program has index 128 (DONE).  Two values stay in machine
     registers: A, the previous result, and B, which holds what the body's
     rules last loaded into it (operand a from the file is loaded into A, or
     into B when b is A; operand b from the file into B, or into A when a is
     B); the encoder tracks what each holds, so an operand found there is not
-    loaded, and a dead result is not stored.  The operand and destination
-    registers are shared-memory addresses computed from the code and the
-    first payload.  Few registers: the kernel's warps are bounded by shared
-    memory alone.
+    loaded, and a dead result is not stored.  The kernel rewrites its staged
+    copy of each instruction as (index, byte offsets of the destination,
+    operand a and operand b in the warp's register file), so a body adds
+    the lane's file address to offsets and the loop jumps on the index.  Few
+    registers: the kernel's warps are bounded by shared memory alone.
     Operands: %0 bad (out, u32); %1 program address, %2 this lane's register
     file address (shared, u32)."""
 
@@ -1002,7 +1003,7 @@ class LinearRFGen:
         B = [f"rB{i}" for i in range(H)]
         b("{")
         b(f".reg .{self.ty} rA<{H}>, rB<{H}>;")
-        b(".reg .b32 code, pa, pb, pc, adr, base, ra, rb, aa, ab, ad, fn;")
+        b(".reg .b32 code, pa, pb, pc, adr, base, aa, ab, ad;")
         for ln in pdiv_regs(K, H).split("\n"):
             b(ln)
         if K > 1:
@@ -1027,10 +1028,7 @@ class LinearRFGen:
         b("ld.shared.v4.u32 {code, pa, pb, pc}, [adr];")
         b("add.u32 adr, adr, 16;")
         b("LOOP:")
-        b("bfe.u32 fn, code, 6, 2;")
-        b("shl.b32 ra, pb, 2;")
-        b("add.u32 fn, fn, ra;")
-        b("brx.idx.uni fn, TBL;")
+        b("brx.idx.uni code, TBL;")
         for idx in range(128):
             op, sa, sb, dead = idx & 3, (idx >> 2) & 3, (idx >> 4) & 3, (idx >> 6) & 1
             if held(sa, sb):
@@ -1043,13 +1041,11 @@ class LinearRFGen:
             xa = la if sa == 0 else (A if sa == 1 else B)
             xb = lb if sb == 0 else (A if sb == 1 else B)
             if sa == 0:
-                b("bfe.u32 ra, code, 3, 3;")
-                b(f"mad.lo.u32 aa, ra, {self.rstride}, base;")
+                b("add.u32 aa, pb, base;")
             if sb == 0:
-                b("and.b32 rb, code, 7;")
-                b(f"mad.lo.u32 ab, rb, {self.rstride}, base;")
+                b("add.u32 ab, pc, base;")
             if not dead:
-                b(f"mad.lo.u32 ad, pa, {self.rstride}, base;")
+                b("add.u32 ad, pa, base;")
             if sb == 0:
                 self.load(lb, "ab")
             if sa == 0:

@@ -260,13 +260,17 @@ def kernel_source_digest() -> str:
     for f in sorted(os.listdir(d)):
         if f.startswith(("eval_float", "common", "isa")):
             h.update(open(os.path.join(d, f), "rb").read())
-    # the generated interpreters as compiled (the generator's output, not its text)
+    # the generated interpreters this kernel compiles (the generator's output,
+    # not its text): the K = 8 S-form, RPN and register interpreters with the
+    # input in registers and the S-form pass loop
     import importlib.util
     spec = importlib.util.spec_from_file_location(
         "gen_interp", os.path.join(ROOT, "paper_1601_00221_gb300", "gen_interp.py"))
     gen = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(gen)
-    h.update(gen.generate().encode())
+    for block in (gen.FloatGen(8, "reg").sform(), gen.FloatGen(8, "reg").rpn(),
+                  gen.FloatGen(8, "smem").linear(), gen.FloatGenLoop().sform()):
+        h.update("\n".join(block.lines).encode())
     return h.hexdigest()[:16]
 
 

@@ -174,3 +174,33 @@ def test_program_buffer_sized_to_the_population(k):
     assert over.sum() >= 1 and np.all(short[over] == np.uint64(0xFFFFFFFFFFFFFFFF))
     assert np.array_equal(short[~over], exp[~over])
     assert gp.last_error() == 2
+
+
+@pytest.mark.parametrize("k,block", [(4, 128), (2, 64), (8, 32)])
+def test_input_listing_matches_the_oracle(k, block):
+    """Blocks of at least four passes stage only the inputs their tree reads
+    (payloads rewritten to slots); blocks of fewer stage every input.  Trees
+    over 16 inputs that each read a few of them, at a chunk of eight passes
+    (listed) and of one pass (every input): both give the oracle's hits and
+    output words."""
+    import torch
+    progs = synth.ramped_half_and_half(190 + k, 200, 2, 6, 63, funcs=synth.BOOL_FUNCS + (IF,),
+                                       n_inputs=16, p_const=0.0, full_fallback_to_grow=True)
+    pop = synth.pack(progs)
+    n_cases = 1 << 16
+    w = synth.BooleanWorkload("l", pop, synth.bool_case_bits(16), synth.even_parity_target(16), n_cases)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL)
+    P, O, L = upload(enc)
+    cb, tb = dev(w.case_bits.view(np.int32)), dev(w.target_bits.view(np.int32))
+    exp = oracle.bool_population_hits(w.pop.words, w.pop.offsets, w.pop.lengths, w.case_bits,
+                                      w.n_cases, w.target_bits)
+    nw = n_cases // 32
+    for passes in (8, 1):
+        cfg = gp.Config(gp.VARIANT_REGISTER, k, block, passes * k * block, 0, 0, 0, enc.max_instructions)
+        hits = gp.eval_population_bool(P, O, L, cb, n_cases, tb, config=cfg).cpu().numpy()
+        assert np.array_equal(hits.astype(np.uint64), exp), passes
+        out = torch.zeros((w.pop.n, nw), dtype=torch.int32, device="cuda")
+        gp.eval_population_bool(P, O, L, cb, n_cases, tb, hits_out=None, out_words=out, config=cfg)
+        out = out.cpu().numpy().view(np.uint32)
+        for p in range(0, w.pop.n, 29):
+            assert np.array_equal(out[p], oracle.bool_outputs(w.pop.program(p), w.case_bits)), (passes, p)

@@ -155,7 +155,15 @@ int gp_encode_population(const uint32_t* words, const int64_t* offsets, const in
 
 /* Register linear GP programs: instr[(offsets[p] + i)*4 + {0,1,2,3}] =
  * {dst, op, a, b} (registers 0..7, op GP_OP_ADD..GP_OP_DIV).  Same output
- * conventions as gp_encode_population; nodes = instructions. */
+ * conventions as gp_encode_population; nodes = instructions.  An encoded
+ * instruction is {code (function and operands), dst, flags, 0}; the flags
+ * serve GP_VARIANT_REGISTER_FILE, which holds two values beside the register
+ * file (the previous result, and the value its load rules last loaded):
+ * bits 0-1 say where operand a is (0 the file, 1 the previous result, 2 the
+ * loaded value), bits 2-3 the same for b (at most one of the two held),
+ * bit 4 that the result is never read from the file and is not stored.  The
+ * kernel checks the flags against the program and reports GP_ERR_PROGRAM for
+ * flags that do not match; the register variant ignores them. */
 int gp_encode_linear_population(const uint8_t* instr, const int64_t* offsets,
                                 const int32_t* lengths, int32_t n_progs, uint32_t* out,
                                 int64_t cap_words, int64_t* out_offsets, int32_t* out_lengths,

@@ -223,7 +223,12 @@ int issue(gp_server* s, Launch* L) {
   const int64_t* dofs = reinterpret_cast<const int64_t*>(din + w_bytes);
   const int32_t* dlen = reinterpret_cast<const int32_t*>(din + w_bytes + o_bytes);
   int rc;
-  if (L->segments) {
+  // a Boolean request alone in its launch takes the library's own choice of
+  // kernel for its case set (one program per lane, a warp per program, or
+  // blocks per program); hit counts are exact whichever kernel runs, so its
+  // result is the one it would have in a merged launch
+  const bool bool_alone = run.kind == GP_RUN_BOOL && L->reqs.size() == 1;
+  if (L->segments && !bool_alone) {
     // one segment per request, each on its own run's cases and chunk
     std::vector<gp_segment> segs;
     int32_t pbeg = 0;
@@ -247,12 +252,17 @@ int issue(gp_server* s, Launch* L) {
     rc = gp_eval_population_ex(dw, dofs, dlen, (int32_t)L->n_progs, static_cast<const float*>(run.d_cases),
                                run.n_inputs, run.n_cases, static_cast<const float*>(run.d_targets),
                                static_cast<double*>(L->d_out), nullptr, &run.cfg, (gp_stream_t)st);
-  else
+  else {
+    gp_config bc = run.cfg;
+    bc.variant = GP_VARIANT_AUTO;
+    bc.k = 0;
+    bc.block = 0;
+    bc.chunk_cases = 0;
     rc = gp_eval_population_bool_ex(dw, dofs, dlen, (int32_t)L->n_progs,
                                     static_cast<const uint32_t*>(run.d_cases), run.n_inputs,
                                     run.n_cases, static_cast<const uint32_t*>(run.d_targets),
-                                    static_cast<uint64_t*>(L->d_out), nullptr, &run.cfg,
-                                    (gp_stream_t)st);
+                                    static_cast<uint64_t*>(L->d_out), nullptr, &bc, (gp_stream_t)st);
+  }
   if (rc != GP_OK) return rc;
   e = cudaMemcpyAsync(L->h_out.p, L->d_out, 8 * (size_t)L->n_progs, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return GP_ERR_CUDA;
@@ -441,7 +451,8 @@ extern "C" int gp_server_create(const gp_server_opts* opts, gp_server** out) {
   // Float requests of different runs share a launch when the configuration
   // is the register variant (the several-populations kernels); Boolean ones
   // always do, with K = 4 and 64-thread blocks (the staged input tile of
-  // many inputs bounds the blocks per multiprocessor)
+  // many inputs bounds the blocks per multiprocessor), and a Boolean request
+  // alone in its launch takes the library's automatic choice
   s->launch_cfg[0] = o.config;
   s->launch_cfg[1] = o.config;
   s->launch_cfg[1].variant = GP_VARIANT_REGISTER;

@@ -476,3 +476,36 @@ def test_reciprocal_payload_is_checked_when_staged():
     f = gp.eval_population(P, O, L, dev(x), dev(np.zeros(512, np.float32))).cpu().numpy()
     assert not np.isnan(f[0]) and np.isnan(f[1])
     assert gp.last_error() == 2
+
+
+def test_register_file_rejects_flags_that_do_not_match():
+    """The register-file kernel replays the encoder's rules for what A and B
+    hold: a program whose flags claim an operand from B that B does not
+    hold, or both operands held, or a source that does not exist, is
+    malformed (NaN fitness, program-error status); the programs beside it are
+    exact."""
+    pop = synth.linear_programs(84, 12, 8, 40)
+    x = synth.normal_cases(85, 8, 700)
+    y = synth.normal_cases(86, 1, 700)[0]
+    enc = gp.encode_linear_population(pop.instr, pop.offsets, pop.lengths)
+    fit = oracle.linear_population_fitness(pop.instr, pop.offsets, pop.lengths, x, y)
+    cfg = gp.Config(gp.VARIANT_REGISTER_FILE, 4, 64, 0)
+    for p, change in ((3, "from_b"), (5, "both"), (7, "three")):
+        words = enc.words.copy()
+        base = int(enc.offsets[p]) + 4
+        n = int(pop.lengths[p])
+        # the first instruction: nothing is held yet
+        f = int(words[base + 2])
+        if change == "from_b":
+            words[base + 2] = (f & ~3) | 2
+        elif change == "both":
+            words[base + 2] = (f & ~15) | 1 | (2 << 2)
+        else:
+            words[base + 2] = (f & ~3) | 3
+        assert n >= 1
+        gp.last_error()
+        got = gp.eval_population(dev(words.view(np.int32)), dev(enc.offsets), dev(enc.lengths), dev(x), dev(y),
+                                 config=cfg).cpu().numpy()
+        assert np.isnan(got[p]) and gp.last_error() == 2, change
+        others = np.arange(pop.n) != p
+        assert_fitness(got[others], fit[others], change)

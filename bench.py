@@ -825,23 +825,24 @@ def bench_function_sets(gp, synth, torch, device):
             except gp.GPError:
                 continue
             rpn = tr if rpn is None else min(rpn, tr)
-        # many inputs: the width split (trees reading at most 16 inputs with a
-        # 16-input tile, the others with the population's tile), each class at
-        # the best of a few shapes
+        # many inputs: the width split (trees reading at most `th` inputs with
+        # a th-input tile, the others with the population's tile), each class
+        # at the best of a few shapes
         split = None
         if w.cases.shape[0] > 16:
-            for (kn, bn), (kw, bw) in (((4, 256), (2, 256)), ((4, 128), (2, 256)), ((4, 256), (4, 128))):
-                narrow = enc.config(fitness=w.fitness, k=kn, block=bn)
-                narrow.tile_inputs, narrow.chunk_cases = 16, 65536
-                widec = enc.config(fitness=w.fitness, k=kw, block=bw)
-                widec.chunk_cases = 65536
-                try:
-                    ts = _time_events(torch, lambda: gp.eval_population_split(P, O, L, X, Y, 16, narrow, widec,
-                                                                              fitness_out=fit), steps=3, warmup=1)
-                except gp.GPError:
-                    continue
-                if split is None or ts < split[0]:
-                    split = (ts, f"narrow k={kn} block={bn}, wide k={kw} block={bw}")
+            for th in (6, 8, 12, 16):
+                for (kn, bn), (kw, bw) in (((8, 256), (2, 256)), ((4, 256), (2, 256))):
+                    narrow = enc.config(fitness=w.fitness, k=kn, block=bn)
+                    narrow.tile_inputs, narrow.chunk_cases = th, 65536
+                    widec = enc.config(fitness=w.fitness, k=kw, block=bw)
+                    widec.chunk_cases = 65536
+                    try:
+                        ts = _time_events(torch, lambda: gp.eval_population_split(
+                            P, O, L, X, Y, th, narrow, widec, fitness_out=fit), steps=3, warmup=1)
+                    except gp.GPError:
+                        continue
+                    if split is None or ts < split[0]:
+                        split = (ts, f"at most {th} inputs: k={kn} block={bn}; the rest k={kw} block={bw}")
         # the BlockGP-style interpreter (the paper's baseline) on the RPN form,
         # at its best block size
         blockgp = None
@@ -869,8 +870,8 @@ def bench_function_sets(gp, synth, torch, device):
                        "speedup_2d_over_blockgp": round(blockgp / ms, 3),
                        "paper_best_GPop_per_s_context": PAPER_BEST[w.name]}
         if split:
-            out[w.name]["width_split_16_GPop_per_s"] = round(w.gpop / split[0] / 1e6, 1)
-            out[w.name]["width_split_16_config"] = split[1]
+            out[w.name]["width_split_GPop_per_s"] = round(w.gpop / split[0] / 1e6, 1)
+            out[w.name]["width_split_config"] = split[1]
         data[w.name] = (w, sample, fit.cpu().numpy(), outs.cpu().numpy())
     return out, data
 

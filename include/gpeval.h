@@ -181,7 +181,7 @@ typedef enum gp_variant {
   GP_VARIANT_LOCAL = 2,     /* BlockGP-style one-case-per-thread stack in local memory
                                (Sec. 3 prior art), GP_KIND_RPN and GP_KIND_RPN_EXT programs */
   GP_VARIANT_LANES = 3,     /* Boolean only: one program per lane over at most 4 words
-                               (128 cases); GP_VARIANT_AUTO picks it for such case sets */
+                               (128 cases); taken when forced or when the tuner picks it */
   GP_VARIANT_EXTENDED = 4,  /* the S-form interpreter with the extended float functions
                                (runs GP_KIND_SFORM and GP_KIND_SFORM_EXT programs) */
   GP_VARIANT_EXTENDED_RPN = 5, /* the RPN interpreter with the extended float functions
@@ -192,8 +192,8 @@ typedef enum gp_variant {
   GP_VARIANT_WARPS = 7      /* Boolean only: one warp per program, block / 32 programs per
                                block sharing one staged copy of the case set (at most 256
                                threads; the case set and the block's programs must fit in
-                               200 KB of shared memory); GP_VARIANT_AUTO picks it for 5 to
-                               256 words (129 to 8192 cases) */
+                               200 KB of shared memory); GP_VARIANT_AUTO picks it for 1 to
+                               256 words (up to 8192 cases) */
 } gp_variant;
 
 /* Fitness measure of a float program (Sec. 4.2 parameter table: mean squared
@@ -332,10 +332,10 @@ int gp_eval_population_noalloc(const uint32_t* programs, const int64_t* offsets,
  * case_bits[v * n_words + (c >> 5)].  target_bits uint32 [n_words].
  * hits_out uint64 [n_progs]: cases c < n_cases whose output bit equals the
  * target bit (bits beyond n_cases in the last word are ignored).  Exact.
- * By default case sets of at most 4 words run one program per lane
- * (GP_VARIANT_LANES), 5 to 256 words one warp per program
+ * By default case sets of up to 256 words run one warp per program
  * (GP_VARIANT_WARPS), larger ones the register variant's blocks, unless the
- * autotuner's record for the shape says otherwise.
+ * autotuner's record for the shape says otherwise (it also considers one
+ * program per lane, GP_VARIANT_LANES, for up to 4 words).
  * ---------------------------------------------------------------------- */
 int gp_eval_population_bool(const uint32_t* programs, const int64_t* offsets,
                             const int32_t* lengths, int32_t n_progs, const uint32_t* case_bits,

@@ -80,10 +80,10 @@ def test_warps_ragged_case_counts(n_cases, k):
 
 
 def test_warps_chosen_automatically():
-    """5 to 256 words go to the per-warp kernel by default; the result is the
+    """Up to 256 words go to the per-warp kernel by default; the result is the
     oracle's either way, and equals the forced variant's and the register
     variant's."""
-    for k_inputs in (8, 11, 13):
+    for k_inputs in (5, 6, 8, 11, 13):  # 1 to 256 words
         w = _workload("parity", k_inputs, 150, seed=150 + k_inputs)
         auto, _ = _eval(w, None)
         forced, _ = _eval(w, gp.Config(gp.VARIANT_WARPS, 0, 0, 0))

@@ -170,3 +170,25 @@ def test_warps_known_correct_programs():
         for k in (1, 2):
             hits, _ = _eval(w, gp.Config(gp.VARIANT_WARPS, k, 64, 0))
             assert np.all(hits == np.uint64(1 << 11))
+
+
+@pytest.mark.parametrize("variant,k,block", [(gp.VARIANT_WARPS, 2, 128), (gp.VARIANT_WARPS, 1, 64),
+                                             (gp.VARIANT_REGISTER, 4, 64)])
+def test_case_bits_not_16_byte_aligned(variant, k, block):
+    """Case bits and targets that start one word past a 16-byte boundary (the
+    staging then loads word by word): hits exact for the per-warp and the
+    block kernels."""
+    import torch
+    w = _workload("mux", 11, 120, seed=200)
+    enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_BOOL)
+    P, O, L = upload(enc)
+    nin, nw = w.case_bits.shape
+    buf = torch.zeros(nin * nw + 1, dtype=torch.int32, device="cuda")
+    buf[1:] = torch.from_numpy(w.case_bits.reshape(-1).view(np.int32)).cuda()
+    cb = buf[1:].view(nin, nw)
+    tbuf = torch.zeros(nw + 1, dtype=torch.int32, device="cuda")
+    tbuf[1:] = torch.from_numpy(w.target_bits.view(np.int32)).cuda()
+    tb = tbuf[1:]
+    assert cb.data_ptr() % 16 != 0 and tb.data_ptr() % 16 != 0
+    hits = gp.eval_population_bool(P, O, L, cb, w.n_cases, tb, config=gp.Config(variant, k, block, 0))
+    assert np.array_equal(hits.cpu().numpy().view(np.uint64), _expected(w))

@@ -798,8 +798,15 @@ def bench_function_sets(gp, synth, torch, device):
         tuned = gp.autotune_population_ex(P, O, L, X, Y, base=base, repeats=2)
         cfg = enc.config(fitness=w.fitness, k=int(tuned.k), block=int(tuned.block))
         cfg.chunk_cases = int(tuned.chunk_cases)
-        ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg),
+        # the library's choice after tuning: k and block left at 0 take the
+        # record, a width split when the tuner found one faster
+        auto = enc.config(fitness=w.fitness)
+        ms = _time_events(torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=auto),
                           steps=3, warmup=1)
+        split_th, split_n, split_w = gp.autotune_split_record(int(base.variant), int(w.cases.shape[0]),
+                                                              int(w.cases.shape[1]), w.pop.n)
+        ms_single = ms if not split_th else _time_events(
+            torch, lambda: gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg), steps=3, warmup=1)
         # the one-dimensional stack (one case per thread per pass) on the same trees
         one = None
         for block in (128, 256):
@@ -853,7 +860,7 @@ def bench_function_sets(gp, synth, torch, device):
                                                                     config=cb), steps=1, warmup=1)
                 blockgp = tb if blockgp is None else min(blockgp, tb)
         del Pr, Or, Lr
-        gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=cfg)
+        gp.eval_population(P, O, L, X, Y, fitness_out=fit, config=auto)  # (the library's choice, checked below)
         sample = np.arange(0, w.pop.n, w.pop.n // 4)[:4]
         outs = gp.eval_outputs(P, O, L, X, config=cfg)[torch.from_numpy(sample).to(device)]
         out[w.name] = {"programs": w.pop.n, "cases": int(w.cases.shape[1]),
@@ -862,6 +869,10 @@ def bench_function_sets(gp, synth, torch, device):
                        "k": int(cfg.k), "block": int(cfg.block), "chunk_cases": int(cfg.chunk_cases),
                        "tile_inputs": int(cfg.tile_inputs), "tuned_by": "gp_autotune_population_ex",
                        "ms": round(ms, 3), "GPop_per_s": round(w.gpop / ms / 1e6, 1),
+                       "tuned_choice": (f"width split: at most {split_th} inputs k={int(split_n.k)} "
+                                        f"block={int(split_n.block)}, the rest k={int(split_w.k)} "
+                                        f"block={int(split_w.block)}") if split_th else "one launch",
+                       "single_launch_GPop_per_s": round(w.gpop / ms_single / 1e6, 1),
                        "stack1d_GPop_per_s": round(w.gpop / one / 1e6, 1) if one else None,
                        "speedup_2d_over_1d": round(one / ms, 3) if one else None,
                        "rpn_GPop_per_s": round(w.gpop / rpn / 1e6, 1) if rpn else None,

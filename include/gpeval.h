@@ -307,6 +307,10 @@ int gp_eval_outputs(const uint32_t* programs, const int64_t* offsets, const int3
  *     a recorded tuning of small chunks over many cases), the cases are split
  *     into fewer blocks and the fitness then agrees with gp_eval_population
  *     within the fitness tolerance (1e-5 relative) instead of bit for bit.
+ *   - A width split the autotuner recorded for the shape (more than 16
+ *     inputs) is not run: this entry point runs the recorded single-launch
+ *     configuration, whose fitness agrees with the split's within the
+ *     fitness tolerance (bit for bit under the classification measure).
  *   - The first call on a device, with that device current, looks up the
  *     array's device address (cudaGetSymbolAddress) and keeps it; make that
  *     first call before any stream capture.  gp_shutdown forgets the
@@ -503,6 +507,17 @@ int gp_server_destroy(gp_server* srv);
  * GP_VARIANT_AUTO or it passes no configuration, the record's variant and
  * stack levels too.  gp_autotune_population is the _ex call with base NULL.
  *
+ * For a population of more than 16 inputs the float tuner also times the
+ * width split (gp_eval_population_split): programs reading at most 6, 8, 12
+ * or 16 inputs with a tile of that many inputs at k = 8 or 4 and block 256,
+ * the others under the configuration it found.  When a split is more than
+ * 2% faster it is recorded under the same key, and a later
+ * gp_eval_population(_ex) of fitness (not outputs) whose configuration
+ * leaves k and block at 0 runs it (with the caller's fitness measure,
+ * program buffer and tile for the wide class); gp_autotune_split_record
+ * reports it (split_inputs 0: none), and gp_eval_population_noalloc never
+ * runs it.
+ *
  * gp_autotune_population_bool does the same for a Boolean population:
  * k in {1, 2, 4, 8} x block in {32, 64, 128, 256} x cases per block, one
  * program per lane when the cases fit 4 words, and one warp per program
@@ -513,7 +528,9 @@ int gp_server_destroy(gp_server* srv);
  * The tuners synchronise `stream` and allocate a temporary output buffer.
  * gp_autotune_save writes every record to a text file (one line per record:
  * family, several, log2 n_cases, log2 n_progs, variant, k, block, chunk_cases,
- * stack_registers); gp_autotune_load adds the records of such a file
+ * stack_registers; a split record: "split", the key's four numbers,
+ * split_inputs, then variant, k, block and chunk_cases of the narrow and of
+ * the wide class); gp_autotune_load adds the records of such a file
  * (GP_ERR_INVALID_ARG for an unreadable file or a malformed line, which
  * loads nothing).  gp_autotune_clear forgets every record.
  * ---------------------------------------------------------------------- */
@@ -531,6 +548,8 @@ int gp_autotune_population_bool(const uint32_t* programs, const int64_t* offsets
                                 int32_t n_inputs, int64_t n_cases, const uint32_t* target_bits,
                                 const gp_config* base, int32_t repeats, gp_config* best,
                                 gp_stream_t stream);
+int gp_autotune_split_record(int32_t family, int32_t n_inputs, int64_t n_cases, int32_t n_progs,
+                             int32_t* split_inputs, gp_config* narrow, gp_config* wide);
 int gp_autotune_save(const char* path);
 int gp_autotune_load(const char* path);
 int gp_autotune_clear(void);

@@ -26,6 +26,7 @@ __all__ = [
     "set_config", "reset_config", "get_config", "last_error", "shutdown", "version", "Server", "RUN_FLOAT", "RUN_BOOL",
     "eval_population_noalloc", "eval_segments", "eval_population_split", "MAX_SEGMENTS", "autotune_population", "autotune_population_ex",
     "autotune_population_bool", "autotune_save", "autotune_load", "autotune_clear", "eval_launches",
+    "autotune_split_record",
     "KIND_SFORM", "KIND_RPN", "KIND_LINEAR", "KIND_BOOL", "KIND_SFORM_EXT", "KIND_RPN_EXT",
     "ORDER_PAPER",
     "ORDER_MIN_DEPTH", "VARIANT_AUTO", "VARIANT_REGISTER", "VARIANT_LOCAL", "VARIANT_LANES",
@@ -150,6 +151,7 @@ def lib(rebuild: bool = False) -> ctypes.CDLL:
         "gp_autotune_population_bool": [P, P, P, i32, P, i32, i64, P, P, i32, P, P],
         "gp_autotune_save": [ctypes.c_char_p],
         "gp_autotune_load": [ctypes.c_char_p],
+        "gp_autotune_split_record": [i32, i32, i64, i32, P, P, P],
         "gp_eval_launches": [i32, i64, P],
         "gp_encode_population_device": [P, P, P, i32, i32, P, P, P, P],
         "gp_encode_slots_device": [P, i32, P, P],
@@ -561,6 +563,17 @@ def autotune_population_bool(programs, offsets, lengths, case_bits, n_cases, tar
                                              _tptr(case_bits), n_inputs, int(n_cases), _tptr(target_bits),
                                              _cfg(base), repeats, ctypes.byref(best), _stream(stream)))
     return best
+
+
+def autotune_split_record(family, n_inputs, n_cases, n_progs):
+    """gp_autotune_split_record: the width split the float tuner recorded for
+    this shape, as (split_inputs, narrow Config, wide Config); split_inputs 0
+    when none was recorded."""
+    th = ctypes.c_int32(0)
+    narrow, wide = Config(), Config()
+    _check(lib().gp_autotune_split_record(int(family), int(n_inputs), int(n_cases), int(n_progs),
+                                          ctypes.byref(th), ctypes.byref(narrow), ctypes.byref(wide)))
+    return int(th.value), narrow, wide
 
 
 def autotune_save(path: str):

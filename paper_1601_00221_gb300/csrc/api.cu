@@ -50,6 +50,14 @@ std::vector<Workspace*> g_ws;
 using TuneKey = std::tuple<int, int, int, int>;
 std::map<TuneKey, gp_config> g_tuned;
 constexpr int kTuneBool = 100;
+// width splits the float tuner found faster than one launch, by the same key:
+// programs reading at most split_inputs inputs under `narrow`, the rest
+// under `wide` (gp_eval_population_split)
+struct SplitRec {
+  int32_t split_inputs;
+  gp_config narrow, wide;
+};
+std::map<TuneKey, SplitRec> g_split;
 
 int ilog2(int64_t v) {
   int r = 0;
@@ -311,6 +319,31 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
   gp_config c;
   int rc = resolve_config(cfg, &c);
   if (rc) return rc;
+  // a width split the tuner recorded for this shape, when the caller leaves
+  // K and block to the library (fitness only; the caller's measure, program
+  // buffer and wide tile)
+  if (fitness_out && !outputs && (!cfg || (!cfg->k && !cfg->block))) {
+    SplitRec rec;
+    bool have = false;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      auto it = g_split.find(tune_key((cfg && cfg->variant) ? cfg->variant : c.variant, n_inputs, n_cases, n_progs));
+      if (it != g_split.end()) {
+        rec = it->second;
+        have = true;
+      }
+    }
+    if (have && n_inputs > rec.split_inputs) {
+      for (gp_config* x : {&rec.narrow, &rec.wide}) {
+        x->fitness = c.fitness;
+        x->max_instructions = c.max_instructions;
+      }
+      rec.narrow.tile_inputs = rec.split_inputs;
+      rec.wide.tile_inputs = c.tile_inputs;
+      return gp_eval_population_split(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases, targets,
+                                      fitness_out, rec.split_inputs, &rec.narrow, &rec.wide, stream);
+    }
+  }
   apply_tuned(cfg, &c, n_inputs, n_cases, n_progs);
   if (c.chunk_cases % ((int64_t)c.k * c.block) != 0)
     return gp_fail(GP_ERR_INVALID_ARG, "chunk_cases must be a multiple of k*block");
@@ -1009,13 +1042,69 @@ extern "C" int gp_autotune_population_ex(const uint32_t* programs, const int64_t
   gp_config best_c = b;
   float best_ms = 0;
   rc = tune_over(cands, repeats, s, eval, &best_c, &best_ms);
+  if (rc) {
+    cudaFreeAsync(fit, s);
+    return rc;
+  }
+  // Many inputs: also the width split -- programs reading at most `th`
+  // inputs with a th-input tile and their own K and block, the rest under
+  // the configuration just found (a split candidate is a gp_config whose
+  // tile_inputs holds th and whose k and block are the narrow class's)
+  SplitRec split{0, best_c, best_c};
+  const bool tree_family = best_c.variant == GP_VARIANT_REGISTER || best_c.variant == GP_VARIANT_EXTENDED ||
+                           best_c.variant == GP_VARIANT_EXTENDED_RPN;
+  if (tree_family && n_inputs > 16 && n_inputs <= GP_COMPACT_MAX_INPUTS && n_progs <= 160000 &&
+      best_c.stack_registers == 0) {
+    std::vector<gp_config> scands;
+    for (int th : {6, 8, 12, 16})
+      for (int k : {8, 4})
+        for (int64_t ch : {(int64_t)best_c.chunk_cases, (int64_t)0}) {  // the single launch's chunk, automatic
+          if (ch % ((int64_t)k * 256) != 0 || (ch == 0 && best_c.chunk_cases == 0 && !scands.empty() &&
+                                               scands.back().tile_inputs == th && scands.back().k == k))
+            continue;
+          gp_config c = best_c;
+          c.k = k;
+          c.block = 256;
+          c.chunk_cases = (int32_t)ch;
+          c.tile_inputs = th;
+          scands.push_back(c);
+        }
+    auto eval_split = [&](const gp_config& c) {
+      return gp_eval_population_split(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases, targets,
+                                      fit, c.tile_inputs, &c, &best_c, stream);
+    };
+    gp_config sb = best_c;
+    float sms = 0;
+    // (a shape that cannot run is skipped; none running leaves the single launch)
+    if (tune_over(scands, repeats, s, eval_split, &sb, &sms) == GP_OK && sms < 0.98f * best_ms) {
+      split.split_inputs = sb.tile_inputs;
+      split.narrow = sb;
+    }
+    gp_clear_error();
+  }
   cudaFreeAsync(fit, s);
-  if (rc) return rc;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    g_tuned[tune_key(family, n_inputs, n_cases, n_progs)] = best_c;
+    const TuneKey key = tune_key(family, n_inputs, n_cases, n_progs);
+    g_tuned[key] = best_c;
+    if (split.split_inputs > 0) g_split[key] = split;
+    else g_split.erase(key);
   }
   if (best) *best = best_c;
+  return GP_OK;
+}
+
+extern "C" int gp_autotune_split_record(int32_t family, int32_t n_inputs, int64_t n_cases, int32_t n_progs,
+                                        int32_t* split_inputs, gp_config* narrow, gp_config* wide) {
+  gp_clear_error();
+  if (!split_inputs) return gp_fail(GP_ERR_INVALID_ARG, "null split_inputs");
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_split.find(tune_key(family, n_inputs, n_cases, n_progs));
+  *split_inputs = it == g_split.end() ? 0 : it->second.split_inputs;
+  if (it != g_split.end()) {
+    if (narrow) *narrow = it->second.narrow;
+    if (wide) *wide = it->second.wide;
+  }
   return GP_OK;
 }
 
@@ -1094,11 +1183,19 @@ extern "C" int gp_autotune_save(const char* path) {
   std::lock_guard<std::mutex> lk(g_mu);
   fprintf(f, "# gpeval autotune v1: family several log2_cases log2_progs variant k block chunk_cases "
              "stack_registers\n");
+  fprintf(f, "# split family several log2_cases log2_progs split_inputs  narrow: variant k block chunk_cases  "
+             "wide: variant k block chunk_cases\n");
   for (const auto& kv : g_tuned) {
     const gp_config& c = kv.second;
     fprintf(f, "%d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
             std::get<2>(kv.first), std::get<3>(kv.first), c.variant, c.k, c.block, c.chunk_cases,
             c.stack_registers);
+  }
+  for (const auto& kv : g_split) {
+    const SplitRec& r = kv.second;
+    fprintf(f, "split %d %d %d %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+            std::get<2>(kv.first), std::get<3>(kv.first), r.split_inputs, r.narrow.variant, r.narrow.k,
+            r.narrow.block, r.narrow.chunk_cases, r.wide.variant, r.wide.k, r.wide.block, r.wide.chunk_cases);
   }
   const bool ok = fclose(f) == 0;
   return ok ? GP_OK : gp_fail(GP_ERR_INVALID_ARG, "cannot write %s", path);
@@ -1110,11 +1207,36 @@ extern "C" int gp_autotune_load(const char* path) {
   FILE* f = fopen(path, "r");
   if (!f) return gp_fail(GP_ERR_INVALID_ARG, "cannot read %s", path);
   std::vector<std::pair<TuneKey, gp_config>> recs;
+  std::vector<std::pair<TuneKey, SplitRec>> splits;
   char line[512];
   int rc = GP_OK, ln = 0;
   while (fgets(line, sizeof line, f)) {
     ++ln;
     if (line[0] == '#' || line[0] == '\n') continue;
+    if (strncmp(line, "split", 5) == 0) {
+      int fam, sev, lc, lp, th, nv, nk, nb, nch, wv, wk, wb, wch;
+      if (sscanf(line + 5, "%d %d %d %d %d %d %d %d %d %d %d %d %d", &fam, &sev, &lc, &lp, &th, &nv, &nk, &nb,
+                 &nch, &wv, &wk, &wb, &wch) != 13 || th <= 0) {
+        rc = gp_fail(GP_ERR_INVALID_ARG, "%s line %d: expected 'split' and 13 integers", path, ln);
+        break;
+      }
+      SplitRec r{th, kLibraryDefault, kLibraryDefault};
+      r.narrow.variant = nv;
+      r.narrow.k = nk;
+      r.narrow.block = nb;
+      r.narrow.chunk_cases = nch;
+      r.wide.variant = wv;
+      r.wide.k = wk;
+      r.wide.block = wb;
+      r.wide.chunk_cases = wch;
+      gp_config chk;
+      if (resolve_config(&r.narrow, &chk) != GP_OK || resolve_config(&r.wide, &chk) != GP_OK) {
+        rc = gp_fail(GP_ERR_INVALID_ARG, "%s line %d: not a valid configuration", path, ln);
+        break;
+      }
+      splits.emplace_back(TuneKey(fam, sev, lc, lp), r);
+      continue;
+    }
     int fam, sev, lc, lp, var, k, blk, ch, sr;
     if (sscanf(line, "%d %d %d %d %d %d %d %d %d", &fam, &sev, &lc, &lp, &var, &k, &blk, &ch, &sr) != 9) {
       rc = gp_fail(GP_ERR_INVALID_ARG, "%s line %d: expected 9 integers", path, ln);
@@ -1137,6 +1259,7 @@ extern "C" int gp_autotune_load(const char* path) {
   if (rc) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
   for (auto& r : recs) g_tuned[r.first] = r.second;
+  for (auto& r : splits) g_split[r.first] = r.second;
   return GP_OK;
 }
 
@@ -1151,5 +1274,6 @@ extern "C" int gp_autotune_clear(void) {
   gp_clear_error();
   std::lock_guard<std::mutex> lk(g_mu);
   g_tuned.clear();
+  g_split.clear();
   return GP_OK;
 }

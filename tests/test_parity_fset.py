@@ -411,3 +411,63 @@ def test_width_split_matches_each_class_alone(wide, split):
     exp = oracle.fset_population_fitness(pop.words, pop.offsets, pop.lengths, x, y, oracle.FIT_CLASS)
     assert np.array_equal(got, exp)
     assert gp.last_error() == 0
+
+
+@pytest.mark.parametrize("fit", [gp.FITNESS_CLASS, gp.FITNESS_SUM_ABS])
+def test_recorded_width_split_runs_for_automatic_configurations(wide, tmp_path, fit):
+    """A width split recorded for the population's shape (as the float tuner
+    records one) runs when the configuration leaves k and block at 0: the
+    fitness equals that of gp_eval_population_split with the record's
+    classes, bit for bit, and the oracle's (exactly for classification,
+    within the tolerance for absolute errors); a request for outputs ignores
+    the record."""
+    pop, x, ref = wide
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    y = np.rint(np.random.default_rng(132).uniform(-1, 3, x.shape[1])).astype(np.float32)
+    P, O, L = upload(enc)
+    X, Y = dev(x), dev(y)
+    n_cases = x.shape[1]
+    key = (gp.VARIANT_EXTENDED, 1, int(np.log2(n_cases)), int(np.log2(pop.n)))
+    gp.autotune_clear()
+    rec = tmp_path / "split.txt"
+    rec.write_text("split %d %d %d %d 6 %d 8 256 0 %d 2 128 0\n" % (key + (gp.VARIANT_EXTENDED, gp.VARIANT_EXTENDED)))
+    gp.autotune_load(str(rec))
+    assert gp.autotune_split_record(gp.VARIANT_EXTENDED, 41, n_cases, pop.n)[0] == 6
+    auto = enc.config(fitness=fit)  # k = block = 0: the library's choice
+    assert auto.k == 0 and auto.block == 0
+    got = gp.eval_population(P, O, L, X, Y, config=auto).cpu().numpy()
+    narrow = enc.config(fitness=fit, k=8, block=256)
+    narrow.tile_inputs = 6
+    widecfg = enc.config(fitness=fit, k=2, block=128)
+    split = gp.eval_population_split(P, O, L, X, Y, 6, narrow, widecfg).cpu().numpy()
+    assert np.array_equal(got.view(np.uint64), split.view(np.uint64))
+    ofit = oracle.FIT_CLASS if fit == gp.FITNESS_CLASS else oracle.FIT_ABS
+    exp = oracle.fset_population_fitness(pop.words, pop.offsets, pop.lengths, x, y, ofit)
+    if fit == gp.FITNESS_CLASS:
+        assert np.array_equal(got, exp)
+    else:
+        assert_fitness(got, exp, "recorded split, absolute errors")
+    outs = gp.eval_outputs(P, O, L, X, config=auto).cpu().numpy()  # outputs: one launch
+    assert_bits(outs, ref, "outputs under a recorded split")
+    gp.autotune_clear()
+    assert gp.last_error() == 0
+
+
+def test_tuner_records_a_width_split_only_when_faster(wide):
+    """The float tuner on a 41-input population: whatever it records (a split
+    or none), the automatic evaluation afterwards gives the oracle's
+    classification fitness; a recorded split names one of the thresholds it
+    tries."""
+    pop, x, ref = wide
+    enc = gp.encode_population(pop.words, pop.offsets, pop.lengths)
+    y = np.rint(np.random.default_rng(133).uniform(-1, 3, x.shape[1])).astype(np.float32)
+    P, O, L = upload(enc)
+    X, Y = dev(x), dev(y)
+    gp.autotune_clear()
+    gp.autotune_population_ex(P, O, L, X, Y, base=enc.config(fitness=gp.FITNESS_CLASS), repeats=1)
+    th = gp.autotune_split_record(gp.VARIANT_EXTENDED, 41, x.shape[1], pop.n)[0]
+    assert th in (0, 6, 8, 12, 16)
+    got = gp.eval_population(P, O, L, X, Y, config=enc.config(fitness=gp.FITNESS_CLASS)).cpu().numpy()
+    exp = oracle.fset_population_fitness(pop.words, pop.offsets, pop.lengths, x, y, oracle.FIT_CLASS)
+    assert np.array_equal(got, exp)
+    gp.autotune_clear()

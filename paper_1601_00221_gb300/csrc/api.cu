@@ -1047,9 +1047,10 @@ extern "C" int gp_autotune_population_ex(const uint32_t* programs, const int64_t
     return rc;
   }
   // Many inputs: also the width split -- programs reading at most `th`
-  // inputs with a th-input tile and their own K and block, the rest under
-  // the configuration just found (a split candidate is a gp_config whose
-  // tile_inputs holds th and whose k and block are the narrow class's)
+  // inputs with a th-input tile and their own K, block and chunk, the rest
+  // under the configuration just found (a split candidate is a gp_config
+  // whose tile_inputs holds th and whose k, block and chunk are the narrow
+  // class's)
   SplitRec split{0, best_c, best_c};
   const bool tree_family = best_c.variant == GP_VARIANT_REGISTER || best_c.variant == GP_VARIANT_EXTENDED ||
                            best_c.variant == GP_VARIANT_EXTENDED_RPN;
@@ -1058,10 +1059,8 @@ extern "C" int gp_autotune_population_ex(const uint32_t* programs, const int64_t
     std::vector<gp_config> scands;
     for (int th : {6, 8, 12, 16})
       for (int k : {8, 4})
-        for (int64_t ch : {(int64_t)best_c.chunk_cases, (int64_t)0}) {  // the single launch's chunk, automatic
-          if (ch % ((int64_t)k * 256) != 0 || (ch == 0 && best_c.chunk_cases == 0 && !scands.empty() &&
-                                               scands.back().tile_inputs == th && scands.back().k == k))
-            continue;
+        for (int64_t ch : {(int64_t)0, (int64_t)16384, (int64_t)65536, (int64_t)131072}) {
+          if (ch >= n_cases && ch > 0) continue;  // (the automatic chunk covers it)
           gp_config c = best_c;
           c.k = k;
           c.block = 256;

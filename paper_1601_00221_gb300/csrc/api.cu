@@ -1059,7 +1059,7 @@ extern "C" int gp_autotune_population_ex(const uint32_t* programs, const int64_t
     std::vector<gp_config> scands;
     for (int th : {6, 8, 12, 16})
       for (int k : {8, 4})
-        for (int64_t ch : {(int64_t)0, (int64_t)16384, (int64_t)65536, (int64_t)131072}) {
+        for (int64_t ch : {(int64_t)0, (int64_t)65536, (int64_t)131072}) {
           if (ch >= n_cases && ch > 0) continue;  // (the automatic chunk covers it)
           gp_config c = best_c;
           c.k = k;
@@ -1068,17 +1068,31 @@ extern "C" int gp_autotune_population_ex(const uint32_t* programs, const int64_t
           c.tile_inputs = th;
           scands.push_back(c);
         }
-    auto eval_split = [&](const gp_config& c) {
-      return gp_eval_population_split(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases, targets,
-                                      fit, c.tile_inputs, &c, &best_c, stream);
-    };
-    gp_config sb = best_c;
-    float sms = 0;
-    // (a shape that cannot run is skipped; none running leaves the single launch)
-    if (tune_over(scands, repeats, s, eval_split, &sb, &sms) == GP_OK && sms < 0.98f * best_ms) {
-      split.split_inputs = sb.tile_inputs;
-      split.narrow = sb;
+    // the wide class holds few programs, so it may want shorter chunks than
+    // the single launch (more blocks to fill the GPU): its chunk is tried too
+    float split_ms = 1e30f;
+    std::vector<int64_t> wchunks{best_c.chunk_cases};
+    for (int64_t wch : {(int64_t)65536, (int64_t)32768})
+      if (wch != best_c.chunk_cases && wch % ((int64_t)best_c.k * best_c.block) == 0 && wch < n_cases)
+        wchunks.push_back(wch);
+    for (int64_t wch : wchunks) {
+      gp_config wide = best_c;
+      wide.chunk_cases = (int32_t)wch;
+      auto eval_split = [&](const gp_config& c) {
+        return gp_eval_population_split(programs, offsets, lengths, n_progs, cases, n_inputs, n_cases, targets,
+                                        fit, c.tile_inputs, &c, &wide, stream);
+      };
+      gp_config sb = best_c;
+      float sms = 0;
+      // (a shape that cannot run is skipped; none running leaves the single launch)
+      if (tune_over(scands, repeats, s, eval_split, &sb, &sms) == GP_OK && sms < split_ms) {
+        split_ms = sms;
+        split.split_inputs = sb.tile_inputs;
+        split.narrow = sb;
+        split.wide = wide;
+      }
     }
+    if (!(split_ms < 0.98f * best_ms)) split.split_inputs = 0;
     gp_clear_error();
   }
   cudaFreeAsync(fit, s);

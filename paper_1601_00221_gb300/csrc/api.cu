@@ -58,6 +58,8 @@ struct SplitRec {
   gp_config narrow, wide;
 };
 std::map<TuneKey, SplitRec> g_split;
+// programs the width split takes (its order buffer holds two classes)
+constexpr int32_t kSplitMaxProgs = 160000;
 
 int ilog2(int64_t v) {
   int r = 0;
@@ -333,7 +335,8 @@ extern "C" int gp_eval_population_ex(const uint32_t* programs, const int64_t* of
         have = true;
       }
     }
-    if (have && n_inputs > rec.split_inputs) {
+    // (a population of the same key beyond the split's limits runs one launch)
+    if (have && n_inputs > rec.split_inputs && n_inputs <= GP_COMPACT_MAX_INPUTS && n_progs <= kSplitMaxProgs) {
       for (gp_config* x : {&rec.narrow, &rec.wide}) {
         x->fitness = c.fitness;
         x->max_instructions = c.max_instructions;
@@ -419,7 +422,8 @@ extern "C" int gp_eval_population_split(const uint32_t* programs, const int64_t*
   if (n_cases > kMaxCases) return gp_fail(GP_ERR_INVALID_ARG, "n_cases too large");
   if (n_inputs > GP_COMPACT_MAX_INPUTS)
     return gp_fail(GP_ERR_INVALID_ARG, "the width split takes at most %d inputs", GP_COMPACT_MAX_INPUTS);
-  if (n_progs > 160000) return gp_fail(GP_ERR_INVALID_ARG, "the width split takes at most 160000 programs");
+  if (n_progs > kSplitMaxProgs)
+    return gp_fail(GP_ERR_INVALID_ARG, "the width split takes at most %d programs", kSplitMaxProgs);
   gp_config cls[2];
   const gp_config* user[2] = {narrow, wide};
   size_t smem[2];
@@ -1054,7 +1058,7 @@ extern "C" int gp_autotune_population_ex(const uint32_t* programs, const int64_t
   SplitRec split{0, best_c, best_c};
   const bool tree_family = best_c.variant == GP_VARIANT_REGISTER || best_c.variant == GP_VARIANT_EXTENDED ||
                            best_c.variant == GP_VARIANT_EXTENDED_RPN;
-  if (tree_family && n_inputs > 16 && n_inputs <= GP_COMPACT_MAX_INPUTS && n_progs <= 160000 &&
+  if (tree_family && n_inputs > 16 && n_inputs <= GP_COMPACT_MAX_INPUTS && n_progs <= kSplitMaxProgs &&
       best_c.stack_registers == 0) {
     std::vector<gp_config> scands;
     for (int th : {6, 8, 12, 16})

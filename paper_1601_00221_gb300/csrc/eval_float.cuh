@@ -797,15 +797,37 @@ __device__ __forceinline__ void eval_float_block(const FloatArgs& a, const SegTa
 #undef GP_SEG
 }
 
+// Registers per thread of an interpreter kernel.  Each dispatch waits on an
+// indirect jump and its body's dependent arithmetic, so more resident warps
+// hide more of that latency: the basic interpreters at K = 4 fit 80 registers
+// (24 warps per SM in blocks of 256) and at K = 1, 2 fit 64 (32 warps) with
+// no spills, where the compiler's own choice under a 512-thread bound was 121
+// to 124 registers (16 warps).  K = 8 needs all 128 (its stack alone is 64)
+// and so do the shared-memory stack levels; the extended interpreters keep the
+// compiler's choice (their many-input tiles limit residency by shared memory).
+// (The 128-register kernels keep the bound of one 512-thread block per SM,
+// under which the compiler lays them out as before; a capped kernel takes no
+// block minimum, which is what lets K = 4 fit 80 registers without spills.)
+template <int K, int EXT, int RL>
+__host__ __device__ constexpr int float_reg_cap() {
+  return (K == 8 || EXT != 0 || RL < gpisa::R) ? 128 : K == 4 ? 80 : 64;
+}
+template <int K, int EXT, int RL>
+__host__ __device__ constexpr int float_min_blocks() {
+  return float_reg_cap<K, EXT, RL>() == 128 ? 1 : 0;
+}
+
 template <int K, bool XREG, int EXT = 0, int RL = gpisa::R>
-__global__ void __launch_bounds__(512, 1) eval_float_kernel(FloatArgs a) {
+__global__ void __launch_bounds__(512, (float_min_blocks<K, EXT, RL>())) __maxnreg__((float_reg_cap<K, EXT, RL>()))
+    eval_float_kernel(FloatArgs a) {
   eval_float_block<K, XREG, EXT, RL, false>(a, nullptr);
 }
 
 // several populations in one launch (basic interpreters, all stack levels in
 // registers); a.partials / a.counters span every segment
 template <int K, bool XREG>
-__global__ void __launch_bounds__(512, 1) eval_float_seg_kernel(FloatArgs a, const __grid_constant__ SegTable t) {
+__global__ void __launch_bounds__(512, (float_min_blocks<K, 0, gpisa::R>())) __maxnreg__((float_reg_cap<K, 0, gpisa::R>()))
+    eval_float_seg_kernel(FloatArgs a, const __grid_constant__ SegTable t) {
   eval_float_block<K, XREG, 0, gpisa::R, true>(a, &t);
 }
 

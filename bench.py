@@ -135,7 +135,7 @@ def run_once(args):
                                    gp.ORDER_MIN_DEPTH)
         P, O, L = enc.to_device("cuda")
         X, Y = torch.from_numpy(w.cases).cuda(), torch.from_numpy(w.targets).cuda()
-        cfg = gp.Config(gp.VARIANT_REGISTER, 8, 256, 65536)
+        cfg = gp.Config(gp.VARIANT_REGISTER, args.k, args.block, args.chunk)  # default K = 8, 256, 65536
         for _ in range(2):
             f = gp.eval_population(P, O, L, X, Y, config=cfg)
         out = float(f[0])

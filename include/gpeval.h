@@ -250,6 +250,12 @@ typedef struct gp_config {
  *                n_cases; GP_FITNESS_CLASS counts the cases whose output,
  *                rounded to the nearest integer (ties to even), differs from
  *                the target label (NaN never matches; never +inf).
+ *                Accuracy: within 1e-5 relative of the same measure summed in
+ *                binary64 over the binary32 per-case errors, and equal to it
+ *                where that sum is 0 or +inf; classification counts exact.
+ *                One case differs: when every per-case error is finite but a
+ *                thread's binary32 sum passes the largest binary32 value, the
+ *                fitness is +inf although the binary64 sum is finite.
  * The result depends only on (program, cases, config), never on what else
  * runs on the GPU.  n_cases may be 0 (fitness 0).  Sec. 4.1, Listing 1/2.
  * ---------------------------------------------------------------------- */

@@ -320,12 +320,14 @@ def test_fitness_bit_identical_across_runs_and_streams():
     assert np.array_equal(f0, f1.cpu().numpy())
 
 
-@pytest.mark.parametrize("k,block,chunk", [(1, 128, 0), (8, 256, 65536), (8, 256, 16384), (8, 512, 0)])
+@pytest.mark.parametrize("k,block,chunk", [(1, 128, 0), (8, 256, 65536), (8, 256, 16384), (8, 512, 0),
+                                           (4, 512, 0), (4, 256, 65536), (2, 512, 0), (1, 512, 0)])
 def test_full_size_regression_sampled(k, block, chunk):
     """4096 trees (depth 2-8, <= 256 nodes) x 65536 cases, the benchmark's
     workload, in the launch shape the benchmark times (K = 8, block 256,
-    all 65536 cases per block) and others; the oracle checks a sample of 48
-    programs entirely."""
+    all 65536 cases per block) and others, among them the register-capped
+    K = 1, 2, 4 kernels at their largest blocks; the oracle checks a sample
+    of 48 programs entirely."""
     w = synth.regression_large()
     enc = gp.encode_population(w.pop.words, w.pop.offsets, w.pop.lengths, gp.KIND_SFORM,
                                gp.ORDER_MIN_DEPTH)
